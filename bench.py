@@ -1,0 +1,339 @@
+#!/usr/bin/env python3
+"""Throughput benchmark of the semi-Lagrangian foot -> locate -> P1 path.
+
+One benchmark step is one run of the whole hot path over the workload: the
+S-step time loop of Algorithm 2 (foot, clip, walk from the previous foot
+triangle, P1) replayed as one CUDA graph, starting from the initial start
+triangles (so the first step's long strategy-(a) walk is included).
+
+Default workload: the 4096 x 4096 graded, jittered mesh (16 785 409 nodes,
+33 554 432 triangles), solid rotation, Gaussian data, dt = 0.02, 50 steps,
+FP64, Hilbert-renumbered.  Metric: node-updates/s = N * S / time.
+
+Prints ONE JSON line (rank 0).  `--impl reference` times the CPU oracle on
+the host cores instead, on bounded samples of the same workload.
+Launch on N GPUs with torchrun: every rank runs its own copy of the workload
+(independent problems, no collective on the data path), timing is the max
+over ranks, value counts every rank's node-updates.
+"""
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import sl_inputs as si  # noqa: E402
+
+BYTES_PER_NODE = {"fp64": 64, "fp32": 48}   # algorithmic bytes per node-update
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--config", default="C3", choices=["C1", "C2", "C3", "C4"])
+    ap.add_argument("--cells", type=int, default=None, help="override cells per side (smaller test runs)")
+    ap.add_argument("--kernel", type=int, default=0, help="SL_OPT_KERNEL (0 auto, 1 plain FP64, 2 tiled)")
+    ap.add_argument("--curve", default="hilbert", choices=["none", "hilbert", "morton"])
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    return ap.parse_args()
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms."""
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in self.lines:
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, val in zip(names, parts[5:9]):
+                if val.lower().startswith("active"):
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def build_workload(args):
+    prob = si.config(args.config, M=args.cells)
+    return prob
+
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f), "measured"
+    except Exception:
+        return {"hbm_gbs": 6800.0}, "fallback"
+
+
+def cpu_sample(prob, seconds, steps=2):
+    """Time the oracle (as it stands) on a bounded sample of the workload:
+    `steps` steps of a node range sized to about `seconds` of CPU work."""
+    import oracle
+    threads = oracle.default_threads()
+    om = oracle.OracleMesh(prob.mesh.xy, prob.mesh.tri)
+    kind, par = prob.field.kind, prob.field.packed()
+    # calibrate on a small range
+    n_cal = min(prob.mesh.n_nodes, 200_000)
+    t0 = time.perf_counter()
+    om.step(kind, par, prob.dt, 0, prob.v0, lo=0, hi=n_cal, nthreads=threads, want_feet=False)
+    rate = n_cal / max(time.perf_counter() - t0, 1e-6)
+    n_s = int(min(prob.mesh.n_nodes, max(10_000, rate * seconds / steps)))
+    lo = (prob.mesh.n_nodes - n_s) // 2
+    t0 = time.perf_counter()
+    v = prob.v0
+    for s in range(steps):
+        out, _, _, _ = om.step(kind, par, prob.dt, s, v, lo=lo, hi=lo + n_s, nthreads=threads, want_feet=False)
+    dt = time.perf_counter() - t0
+    om.close()
+    return {"value": n_s * steps / dt, "unit": "node-updates/s", "cores": threads, "kind": "oracle",
+            "sample": f"{steps} steps (n=0..{steps - 1}) of nodes [{lo}, {lo + n_s}) of {prob.mesh.n_nodes}; "
+                      f"bin grid build excluded; {threads} threads"}
+
+
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return
+    prob = build_workload(args)
+    per_step = max(1.0, 120.0 / max(1, args.steps + args.warmup))
+    import oracle
+    threads = oracle.default_threads()
+    om = oracle.OracleMesh(prob.mesh.xy, prob.mesh.tri)
+    kind, par = prob.field.kind, prob.field.packed()
+    n_cal = min(prob.mesh.n_nodes, 100_000)
+    t0 = time.perf_counter()
+    om.step(kind, par, prob.dt, 0, prob.v0, lo=0, hi=n_cal, nthreads=threads, want_feet=False)
+    rate = n_cal / max(time.perf_counter() - t0, 1e-6)
+    n_s = int(min(prob.mesh.n_nodes, max(10_000, rate * per_step)))
+    times = []
+    v = prob.v0
+    for k in range(args.warmup + args.steps):
+        t0 = time.perf_counter()
+        om.step(kind, par, prob.dt, k % prob.n_steps, v, lo=0, hi=n_s, nthreads=threads, want_feet=False)
+        if k >= args.warmup:
+            times.append(time.perf_counter() - t0)
+    total = sum(times)
+    value = n_s * len(times) / total
+    line = {
+        "impl": "reference", "metric": "node-updates/s (foot+locate+P1)", "value": value,
+        "unit": "node-updates/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": 1e3 * total / len(times), "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": workload_config(args, prob),
+        "cpu_baseline": {"value": value, "unit": "node-updates/s", "cores": threads, "kind": "oracle",
+                         "sample": f"each step: one SL step of nodes [0, {n_s}) of {prob.mesh.n_nodes}"},
+        "e2e": {"value": value, "unit": "node-updates/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def workload_config(args, prob):
+    m = prob.mesh
+    return {"workload": f"{prob.name}: {m.M}x{m.M} {'graded ' if m.graded else ''}jittered mesh "
+                        f"({m.n_nodes} nodes, {m.n_tri} triangles), field kind {prob.field.kind}, "
+                        f"dt={prob.dt}, {prob.n_steps} steps, {prob.precision}, curve={args.curve}",
+            "nodes": m.n_nodes, "triangles": m.n_tri, "steps_per_run": prob.n_steps,
+            "precision": prob.precision, "l2": "inputs larger than L2 (mesh + values ~1.5 GB)"}
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+    import torch
+    import paper_2104_09189_gb300 as sl
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    prob = build_workload(args)
+    mesh = prob.mesh
+    S = prob.n_steps
+    N = mesh.n_nodes
+    prec = sl.SL_FP64 if prob.precision == "fp64" else sl.SL_FP32
+    t_setup = time.perf_counter()
+    no, to, xy, tri = sl.pack_meshes([(mesh.xy, mesh.tri)])
+    h = sl.sl_mesh_create(no, to, xy, tri, precision=prec, seed=prob.seed)
+    curve = {"none": sl.SL_CURVE_NONE, "hilbert": sl.SL_CURVE_HILBERT, "morton": sl.SL_CURVE_MORTON}[args.curve]
+    perm, _ = sl.sl_mesh_reorder(h, curve)
+    if args.kernel:
+        sl.sl_mesh_set_option(h, sl.SL_OPT_KERNEL, args.kernel)
+    probs = sl.problems([(prob.field.kind, prob.dt, prob.field.packed())])
+    vt = torch.float64 if prec == sl.SL_FP64 else torch.float32
+    v0 = torch.tensor(prob.v0[perm], dtype=vt, device="cuda")
+    v = v0.clone()
+    w = torch.empty_like(v)
+    stream = torch.cuda.current_stream()
+    setup_s = time.perf_counter() - t_setup
+
+    def one_run():
+        sl.sl_mesh_reset_t0(h)
+        sl.sl_run(h, probs, 0, S, v, w, use_graph=True)
+
+    # first run records the graph; collect walk statistics on a separate run
+    sl.sl_mesh_set_option(h, sl.SL_OPT_STATS, 1)
+    sl.sl_mesh_stats(h, reset=True)
+    one_run()
+    stats = sl.sl_mesh_stats(h, reset=True)
+    sl.sl_mesh_set_option(h, sl.SL_OPT_STATS, 0)
+    for _ in range(args.warmup):
+        one_run()
+    torch.cuda.synchronize()
+
+    sampler = ClockSampler(local)
+    sampler.start()
+    time.sleep(0.3)
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    for _ in range(args.steps):
+        sl.sl_mesh_reset_t0(h)
+        sl.sl_run(h, probs, 0, S, v, w, use_graph=True)
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    elapsed = ev0.elapsed_time(ev1) / 1e3
+    clocks = sampler.stop()
+    if dist:
+        tt = torch.tensor([elapsed], dtype=torch.float64, device="cuda")
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        elapsed = float(tt.item())
+
+    units = N * S * args.steps * world
+    value = units / elapsed
+    launch_s = elapsed / (args.steps * S)
+    bpn = BYTES_PER_NODE[prob.precision]
+    peaks, peak_src = measured_peaks()
+    achieved_gbs = bpn * N / launch_s / 1e9
+
+    # end to end through the C ABI with host buffers (pinned)
+    e2e = None
+    if not args.no_e2e:
+        host = torch.tensor(prob.v0[perm], dtype=vt).pin_memory()
+        hv = host.numpy()
+        sl.sl_mesh_reset_t0(h)
+        sl.sl_run_host(h, probs, 0, S, hv, use_graph=True)
+        torch.cuda.synchronize()
+        k_e2e = max(1, min(args.steps, 5))
+        t0 = time.perf_counter()
+        for _ in range(k_e2e):
+            sl.sl_mesh_reset_t0(h)
+            sl.sl_run_host(h, probs, 0, S, hv, use_graph=True)
+        e2e_s = time.perf_counter() - t0
+        esize = 8 if prec == sl.SL_FP64 else 4
+        e2e = {"value": N * S * k_e2e * world / e2e_s, "unit": "node-updates/s",
+               "h2d_bytes_per_step": N * esize, "d2h_bytes_per_step": N * esize,
+               "api": "sl_run_host (pinned host V in/out, graph replay, status read)"}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu:
+        cpu = cpu_sample(prob, args.cpu_seconds)
+
+    sl.sl_mesh_destroy(h)
+    if rank != 0:
+        if dist:
+            dist.destroy_process_group()
+        return
+    line = {
+        "metric": "node-updates/s (foot+locate+P1)",
+        "value": value,
+        "unit": "node-updates/s",
+        "n_gpus": world,
+        "steps": args.steps,
+        "warmup": args.warmup,
+        "ms_per_step": 1e3 * elapsed / args.steps,
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "f64" if prec == sl.SL_FP64 else "f32",
+        "data": "synthetic",
+        "config": workload_config(args, prob),
+        "roofline": {"bound": "hbm", "achieved": achieved_gbs, "peak": peaks.get("hbm_gbs", 6800.0),
+                     "unit": "GB/s", "frac": achieved_gbs / peaks.get("hbm_gbs", 6800.0), "traffic": None,
+                     "peak_source": peak_src,
+                     "algorithmic_bytes_per_node": bpn,
+                     "kernel": "sl step kernel (one launch = one SL step over all nodes)",
+                     "launch_ms": launch_s * 1e3},
+        "cpu_baseline": cpu,
+        "e2e": e2e,
+        "gpu_launches": args.steps * S,
+        "clocks": clocks,
+        "walk": {"first_run_mean_hops_per_node_update": stats["walk_moves"] / max(1, stats["node_updates"]),
+                 "max_hops": stats["max_moves"], "exact_tests": stats["exact_tests"],
+                 "clipped": stats["clipped"], "fallbacks": stats["fallbacks"]},
+        "setup_s": setup_s,
+    }
+    print(json.dumps(line), flush=True)
+    if dist:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,254 @@
+/*
+ * sl.h -- C ABI of the GB300 semi-Lagrangian foot / locate / P1 library.
+ *
+ * One semi-Lagrangian step (Cacace & Ferretti, Sec. 1 and Algorithm 2) maps
+ * the node values V^n of a triangulation of the unit square to V^{n+1}:
+ *
+ *     v_i^{n+1} = I[V^n]( X^Delta(x_i, t_{n+1}; t_n) )                (Eq. 3)
+ *
+ * with the Euler foot X = x_i - dt f(x_i, t_{n+1}) (Eq. 4), clipped to the
+ * square where it leaves it, located by a barycentric walk over the triangle
+ * adjacency (Sec. 2.2, Algorithm 1) that starts from the triangle found for
+ * the same node at the previous step (walk strategy (b), Sec. 3), and
+ * evaluated by P1 interpolation with the barycentric coordinates of Eq. 6
+ * (Remark 1 of Sec. 2.2).
+ *
+ * Conventions shared by every entry point:
+ *   - Every function returns an sl_status; nothing throws across the ABI.
+ *     sl_last_error() returns a thread-local message for the last failure.
+ *   - "host" pointers are ordinary CPU memory; "device" pointers are CUDA
+ *     device memory of the current device.  The caller keeps ownership of
+ *     everything it passes; host inputs are copied before the call returns.
+ *   - Indices are 0-based and local to their problem (the paper's lists are
+ *     1-based, Sec. 3).
+ *   - `stream` is a cudaStream_t passed as void* (NULL = legacy default
+ *     stream).  Work is enqueued asynchronously on it; errors found while
+ *     launching are returned at once, conditions found by the kernels (a walk
+ *     that gave up) are reported by sl_mesh_status() or sl_run().
+ *   - A mesh handle may be used by one stream at a time.
+ */
+#ifndef SL_H
+#define SL_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    SL_OK = 0,
+    SL_E_ARG = 1,          /* invalid argument (null pointer, bad size, NaN/Inf parameter) */
+    SL_E_MESH = 2,         /* malformed mesh (see sl_mesh_create) */
+    SL_E_NOMEM = 3,        /* host or device allocation failed */
+    SL_E_CUDA = 4,         /* a CUDA runtime call failed */
+    SL_E_WALK_LIMIT = 5,   /* some walk exceeded its hop cap and its fallback */
+    SL_E_STATE = 6         /* call not valid in the handle's current state */
+} sl_status;
+
+typedef enum { SL_FP64 = 0, SL_FP32 = 1 } sl_precision;
+
+typedef enum { SL_CURVE_NONE = 0, SL_CURVE_HILBERT = 1, SL_CURVE_MORTON = 2 } sl_curve;
+
+/* Advecting fields f(x, t); p = sl_problem.p.
+ *   ZERO      f = 0
+ *   AFFINE    f_x = p0 + p1 x + p2 y + p3 t,  f_y = p4 + p5 x + p6 y + p7 t
+ *   ROTATION  f = p0 (p2 - y, x - p1)
+ *   SWIRL     f = cos(pi t / p0) (sin^2(pi x) sin(2 pi y), -sin^2(pi y) sin(2 pi x))
+ *   FOURIER8  psi = sum_{m<8} a_m cos(2 pi t + phi_m) sin(k_m pi x) sin(l_m pi y),
+ *             f = (d psi/dy, -d psi/dx); (k_m, l_m, a_m, phi_m) = p[4m .. 4m+3]
+ *   PAPER     f = (cos(p0 r + p1 t), sin(p0 r + p1 t)), r = |x - (p2, p3)|:
+ *             the test field of the paper's Sec. 4 (C0 = p0, C1 = p1). */
+typedef enum {
+    SL_FIELD_ZERO = 0,
+    SL_FIELD_AFFINE = 1,
+    SL_FIELD_ROTATION = 2,
+    SL_FIELD_SWIRL = 3,
+    SL_FIELD_FOURIER8 = 4,
+    SL_FIELD_PAPER = 5
+} sl_field_kind;
+
+#define SL_NPARAMS 48
+
+/* One problem's field and time step.  Host memory. */
+typedef struct {
+    int32_t kind;          /* sl_field_kind */
+    int32_t reserved;      /* must be 0 */
+    double dt;             /* time step (> 0, finite) */
+    double p[SL_NPARAMS];  /* field parameters (finite) */
+} sl_problem;
+
+/* Per-node flag bits written to sl_debug.flags */
+enum {
+    SL_NODE_CLIPPED = 1,      /* the Euler foot left the square and was clipped */
+    SL_NODE_DEGENERATE = 2,   /* the foot lies on an edge line of its triangle */
+    SL_NODE_EXACT = 4,        /* an orientation sign needed the exact stage */
+    SL_NODE_FALLBACK = 8,     /* the walk hit its hop cap and used the fallback walk */
+    SL_NODE_WALK_LIMIT = 16,  /* the fallback failed too: the value is not valid */
+    SL_NODE_RANGE = 32        /* a coordinate outside the exact predicate's range */
+};
+
+typedef struct sl_mesh sl_mesh;   /* opaque; owns device mesh arrays and T^0 */
+
+/* Optional per-node outputs of sl_step (device pointers, each may be NULL).
+ * Arrays are indexed by node in the mesh's current numbering (all problems
+ * concatenated). */
+typedef struct {
+    double *feet;     /* 2N doubles: the clipped foot (x, y) of every node */
+    int32_t *tri;     /* N: located triangle, global index in current numbering */
+    int32_t *moves;   /* N: walk hops (0 if the start triangle contains the foot) */
+    uint8_t *flags;   /* N: SL_NODE_* bits */
+} sl_debug;
+
+/* Counters accumulated on the device by sl_step / sl_run when enabled with
+ * sl_mesh_set_option(SL_OPT_STATS, 1).  Read with sl_mesh_stats(). */
+typedef struct {
+    uint64_t node_updates;   /* nodes stepped */
+    uint64_t walk_moves;     /* total hops */
+    uint64_t max_moves;      /* longest walk */
+    uint64_t exact_tests;    /* orientation signs that needed the exact stage */
+    uint64_t filter2_tests;  /* signs decided by the second (FP64) filter stage */
+    uint64_t clipped;        /* feet clipped to the boundary */
+    uint64_t fallbacks;      /* walks that switched to the fallback rule */
+    uint64_t walk_limit;     /* walks that failed */
+} sl_stats;
+
+/* Tunable options (sl_mesh_set_option) */
+typedef enum {
+    SL_OPT_STATS = 0,        /* 0/1: accumulate sl_stats counters (default 0) */
+    SL_OPT_WALK_CAP = 1,     /* hops before the fallback rule (default max(64, 4 (M+1))) */
+    SL_OPT_KERNEL = 2,       /* 0 = auto, 1 = plain FP64 reference kernel, 2 = tiled kernel */
+    SL_OPT_BLOCK = 3,        /* threads per block (0 = auto) */
+    SL_OPT_TILES_PER_SM = 4  /* resident tiles (CTAs) per SM for the persistent kernel (0 = auto) */
+} sl_option;
+
+/*
+ * sl_mesh_create -- validate a batch of triangulations and upload it.
+ *
+ * Builds the data of the paper's Sec. 3 (node list V, triangle list T,
+ * neighbour list N with j_k the triangle across the edge opposite vertex
+ * i_k, and the start-triangle list T^0, initialised to a random triangle
+ * incident to each node) for `n_problems` independent meshes.
+ *
+ *   n_problems   >= 1
+ *   node_off     host, n_problems+1 int64: problem p owns nodes
+ *                [node_off[p], node_off[p+1]) of xy; node_off[0] = 0
+ *   tri_off      host, n_problems+1 int64: the same for triangles
+ *   xy           host, 2*N doubles (x, y) in [0,1]^2
+ *   tri          host, 3*Nt int32 vertex indices local to the problem,
+ *                counter-clockwise
+ *   nbr          host, 3*Nt int32 or NULL: neighbour triangles local to the
+ *                problem, nbr[3j+k] across the edge opposite tri[3j+k],
+ *                -1 on the boundary; NULL = built here
+ *   precision    SL_FP64 or SL_FP32 (FP32 stores coordinates rounded to
+ *                nearest float; the caller's V buffers are then float)
+ *   seed         selects the initial incident triangle of every node:
+ *                T^0_i = the (h mod deg_i)-th incident triangle in ascending
+ *                index, h = SplitMix64 value number i of `seed`
+ *   out          receives the handle
+ *
+ * Returns SL_E_MESH for: an index out of range, a triangle that is not
+ * strictly counter-clockwise (exact test), an edge shared by more than two
+ * triangles or by two triangles with the same orientation, an inconsistent
+ * supplied nbr, a boundary edge not lying on one side of the square, a node
+ * outside the square or in no triangle, or a total area that is not 1.
+ */
+sl_status sl_mesh_create(int32_t n_problems, const int64_t *node_off, const int64_t *tri_off,
+                         const double *xy, const int32_t *tri, const int32_t *nbr,
+                         int32_t precision, uint64_t seed, sl_mesh **out);
+
+/*
+ * sl_mesh_validate -- the host half of sl_mesh_create on its own: the same
+ * arguments and checks, and the neighbour list and initial start triangles
+ * it builds, without touching any GPU.
+ *   nbr_out  host, 3*Nt int32 or NULL: neighbours, local to the problem, -1
+ *            on the boundary (Sec. 3: j_k across the edge opposite i_k)
+ *   t0_out   host, N int32 or NULL: initial T^0, local to the problem
+ * Returns what sl_mesh_create would return for the mesh (SL_E_MESH, ...).
+ */
+sl_status sl_mesh_validate(int32_t n_problems, const int64_t *node_off, const int64_t *tri_off,
+                           const double *xy, const int32_t *tri, const int32_t *nbr, uint64_t seed,
+                           int32_t *nbr_out, int32_t *t0_out);
+
+/*
+ * sl_mesh_reorder -- renumber nodes and triangles along a space-filling
+ * curve (per problem; problems keep their ranges).  Nodes are ordered by the
+ * curve index of their position, triangles by that of their centroid; T, N
+ * and T^0 are remapped so results are unchanged up to the permutation.
+ * node_perm (host, N, may be NULL) receives new -> old node indices (local to
+ * the problem), tri_perm (host, Nt, may be NULL) the same for triangles.
+ * Must be called before the caller fills V buffers in the new numbering.
+ */
+sl_status sl_mesh_reorder(sl_mesh *m, int32_t curve, int32_t *node_perm, int32_t *tri_perm);
+
+/*
+ * sl_step -- one semi-Lagrangian step n -> n+1 for every node of every
+ * problem (Eq. 3 with the Euler foot of Eq. 4 at t_{n+1} = (n+1) dt).
+ *
+ *   probs   host, n_problems entries
+ *   v_in    device, N values V^n (double for SL_FP64, float for SL_FP32)
+ *   v_out   device, N values V^{n+1}; must not alias v_in
+ *   dbg     host struct of device pointers, or NULL
+ * T^0 is updated in place to the located triangles (strategy (b)).
+ */
+sl_status sl_step(sl_mesh *m, const sl_problem *probs, int64_t n, const void *v_in, void *v_out,
+                  const sl_debug *dbg, void *stream);
+
+/*
+ * sl_run -- n_steps steps from n0 (Algorithm 2's time loop).  `v` (device,
+ * N values) holds V^{n0} on entry and V^{n0+n_steps} on return; `v_scratch`
+ * (device, N values) is used for the ping-pong.  With use_graph != 0 the
+ * steps are recorded once into a CUDA graph and replayed (the graph is kept
+ * in the handle and reused while n0, n_steps, the buffers and the problems
+ * are unchanged).  Synchronises the stream and returns the deferred device
+ * status (SL_E_WALK_LIMIT if a walk failed).  stats may be NULL.
+ */
+sl_status sl_run(sl_mesh *m, const sl_problem *probs, int64_t n0, int32_t n_steps, void *v,
+                 void *v_scratch, int32_t use_graph, sl_stats *stats, void *stream);
+
+/*
+ * sl_run_host -- sl_run on HOST value buffers: copies V^{n0} (host, N values)
+ * to device buffers owned by the handle, runs, copies V^{n0+n_steps} back
+ * into the same host array, and synchronises.  Page-locked host memory makes
+ * the copies asynchronous DMA; pageable memory works but is slower.
+ */
+sl_status sl_run_host(sl_mesh *m, const sl_problem *probs, int64_t n0, int32_t n_steps, void *v_host,
+                      int32_t use_graph, sl_stats *stats, void *stream);
+
+/* T^0 export / import (device, N int32 global triangle indices in current
+ * numbering); with V^n this is the whole state of a run (resume). */
+sl_status sl_mesh_get_t0(const sl_mesh *m, int32_t *t0_dev, void *stream);
+sl_status sl_mesh_set_t0(sl_mesh *m, const int32_t *t0_dev, void *stream);
+
+/* Put T^0 back to the initial start triangles chosen by sl_mesh_create (in
+ * the current numbering), on the device, asynchronously on `stream`: the
+ * next step then starts every walk from a triangle incident to its node, as
+ * the first step of a run does (Sec. 3: strategies (a) and (b) coincide on
+ * the first step). */
+sl_status sl_mesh_reset_t0(sl_mesh *m, void *stream);
+
+/* Synchronise `stream` and return (and clear) the deferred device status. */
+sl_status sl_mesh_status(sl_mesh *m, void *stream);
+
+/* Read (and with reset != 0, clear) the device counters; synchronises. */
+sl_status sl_mesh_stats(sl_mesh *m, sl_stats *out, int32_t reset, void *stream);
+
+sl_status sl_mesh_set_option(sl_mesh *m, int32_t option, int64_t value);
+
+/* Sizes of the handle: n_nodes, n_tri, n_problems, precision. */
+sl_status sl_mesh_info(const sl_mesh *m, int64_t *n_nodes, int64_t *n_tri, int32_t *n_problems,
+                       int32_t *precision);
+
+/* Export the mesh in its current numbering (host arrays: 2N doubles,
+ * 3Nt int32 local vertex indices, 3Nt int32 local neighbours). */
+sl_status sl_mesh_export(const sl_mesh *m, double *xy, int32_t *tri, int32_t *nbr);
+
+void sl_mesh_destroy(sl_mesh *m);
+
+const char *sl_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

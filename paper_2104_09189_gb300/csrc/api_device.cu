@@ -1,0 +1,416 @@
+// api_device.cu -- entry points of sl.h that touch the device: upload,
+// sl_step, sl_run (CUDA graph of the time loop), sl_run_host, T^0 import /
+// export, deferred status, counters, renumbering and destruction.
+#include <cmath>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "sl_internal.h"
+#include "step_kernels.cuh"
+
+namespace sl {
+
+#define SL_CUDA(call)                                                                        \
+    do {                                                                                     \
+        cudaError_t e_ = (call);                                                             \
+        if (e_ != cudaSuccess)                                                               \
+            return fail(e_ == cudaErrorMemoryAllocation ? SL_E_NOMEM : SL_E_CUDA,            \
+                        std::string(#call) + ": " + cudaGetErrorString(e_));                 \
+    } while (0)
+
+int32_t default_walk_cap(const sl_mesh *m)
+{
+    int32_t M = 1;
+    for (int32_t c : m->cells) M = c > M ? c : M;
+    int32_t cap = 4 * (M + 1);
+    return cap < 64 ? 64 : cap;
+}
+
+void free_device(sl_mesh *m)
+{
+    DeviceMesh &d = m->d;
+    void *ptrs[] = {d.xy, d.tv[0], d.tv[1], d.tv[2], d.tn[0], d.tn[1], d.tn[2], d.t0, d.t0_init, d.node_off,
+                    d.status, d.stats, d.probs, m->host_v, m->host_v2};
+    for (void *p : ptrs)
+        if (p) cudaFree(p);
+    d = DeviceMesh();
+    m->host_v = m->host_v2 = nullptr;
+    if (m->graph.exec) cudaGraphExecDestroy((cudaGraphExec_t)m->graph.exec);
+    m->graph = GraphCache();
+    if (m->capture_stream) cudaStreamDestroy((cudaStream_t)m->capture_stream);
+    m->capture_stream = nullptr;
+}
+
+// Copy the host arrays (current numbering) to the device, converting local
+// indices to global ones.
+static sl_status upload_arrays(sl_mesh *m)
+{
+    DeviceMesh &d = m->d;
+    const int64_t N = m->N, Nt = m->Nt;
+    if (m->precision == SL_FP64) {
+        SL_CUDA(cudaMemcpy(d.xy, m->xy.data(), sizeof(double) * 2 * N, cudaMemcpyHostToDevice));
+    } else {
+        std::vector<float> f(2 * N);
+        for (int64_t q = 0; q < 2 * N; ++q) f[q] = (float)m->xy[q];
+        SL_CUDA(cudaMemcpy(d.xy, f.data(), sizeof(float) * 2 * N, cudaMemcpyHostToDevice));
+    }
+    std::vector<int32_t> col(Nt);
+    for (int k = 0; k < 3; ++k) {
+        for (int32_t p = 0; p < m->n_problems; ++p)
+            for (int64_t j = m->tri_off[p]; j < m->tri_off[p + 1]; ++j)
+                col[j] = m->tri[3 * j + k] + (int32_t)m->node_off[p];
+        SL_CUDA(cudaMemcpy(d.tv[k], col.data(), sizeof(int32_t) * Nt, cudaMemcpyHostToDevice));
+        for (int32_t p = 0; p < m->n_problems; ++p)
+            for (int64_t j = m->tri_off[p]; j < m->tri_off[p + 1]; ++j) {
+                int32_t nb = m->nbr[3 * j + k];
+                col[j] = nb < 0 ? -1 : nb + (int32_t)m->tri_off[p];
+            }
+        SL_CUDA(cudaMemcpy(d.tn[k], col.data(), sizeof(int32_t) * Nt, cudaMemcpyHostToDevice));
+    }
+    SL_CUDA(cudaMemcpy(d.t0, m->t0.data(), sizeof(int32_t) * N, cudaMemcpyHostToDevice));
+    SL_CUDA(cudaMemcpy(d.t0_init, m->t0_init.data(), sizeof(int32_t) * N, cudaMemcpyHostToDevice));
+    SL_CUDA(cudaMemcpy(d.node_off, m->node_off.data(), sizeof(int64_t) * (m->n_problems + 1), cudaMemcpyHostToDevice));
+    return SL_OK;
+}
+
+sl_status upload(sl_mesh *m)
+{
+    SL_CUDA(cudaGetDevice(&m->device));
+    DeviceMesh &d = m->d;
+    const int64_t N = m->N, Nt = m->Nt;
+    const size_t cs = m->precision == SL_FP64 ? 2 * sizeof(double) : 2 * sizeof(float);
+    SL_CUDA(cudaMalloc(&d.xy, cs * N));
+    for (int k = 0; k < 3; ++k) {
+        SL_CUDA(cudaMalloc(&d.tv[k], sizeof(int32_t) * Nt));
+        SL_CUDA(cudaMalloc(&d.tn[k], sizeof(int32_t) * Nt));
+    }
+    SL_CUDA(cudaMalloc(&d.t0, sizeof(int32_t) * N));
+    SL_CUDA(cudaMalloc(&d.t0_init, sizeof(int32_t) * N));
+    SL_CUDA(cudaMalloc(&d.node_off, sizeof(int64_t) * (m->n_problems + 1)));
+    SL_CUDA(cudaMalloc(&d.status, sizeof(uint32_t) * kStatusWords));
+    SL_CUDA(cudaMalloc(&d.stats, sizeof(unsigned long long) * kStatCounters));
+    SL_CUDA(cudaMemset(d.status, 0, sizeof(uint32_t) * kStatusWords));
+    SL_CUDA(cudaMemset(d.stats, 0, sizeof(unsigned long long) * kStatCounters));
+    return upload_arrays(m);
+}
+
+// Host-side evaluation of the time factors of each field at t_{n+1}.
+static sl_status fill_step(const sl_mesh *m, const sl_problem *probs, int64_t n, ProbStep *out)
+{
+    const double pi = 3.14159265358979323846;
+    for (int32_t p = 0; p < m->n_problems; ++p) {
+        const sl_problem &q = probs[p];
+        if (q.kind < SL_FIELD_ZERO || q.kind > SL_FIELD_PAPER)
+            return fail(SL_E_ARG, "problem " + std::to_string(p) + ": unknown field kind");
+        if (!(std::isfinite(q.dt) && q.dt > 0.0))
+            return fail(SL_E_ARG, "problem " + std::to_string(p) + ": dt must be finite and > 0");
+        for (int k = 0; k < SL_NPARAMS; ++k)
+            if (!std::isfinite(q.p[k])) return fail(SL_E_ARG, "problem " + std::to_string(p) + ": non-finite field parameter");
+        if (q.kind == SL_FIELD_SWIRL && q.p[0] == 0.0) return fail(SL_E_ARG, "swirl period p0 must be nonzero");
+        ProbStep &s = out[p];
+        std::memset(&s, 0, sizeof(s));
+        s.kind = q.kind;
+        s.dt = q.dt;
+        s.t = (double)(n + 1) * q.dt;
+        std::memcpy(s.p, q.p, sizeof(s.p));
+        if (q.kind == SL_FIELD_SWIRL) s.c[0] = std::cos(pi * s.t / q.p[0]);
+        if (q.kind == SL_FIELD_FOURIER8)
+            for (int mm = 0; mm < 8; ++mm) s.c[mm] = q.p[4 * mm + 2] * std::cos(2.0 * pi * s.t + q.p[4 * mm + 3]);
+        if (q.kind == SL_FIELD_PAPER) s.c[0] = q.p[1] * s.t;
+    }
+    return SL_OK;
+}
+
+static sl_status ensure_probs(sl_mesh *m, size_t bytes)
+{
+    if (m->d.probs_bytes >= bytes) return SL_OK;
+    cudaFree(m->d.probs);
+    m->d.probs = nullptr;
+    m->d.probs_bytes = 0;
+    SL_CUDA(cudaMalloc(&m->d.probs, bytes));
+    m->d.probs_bytes = bytes;
+    return SL_OK;
+}
+
+static StepArgs make_args(const sl_mesh *m, const ProbStep *probs_dev, const void *vin, void *vout,
+                          const sl_debug *dbg)
+{
+    StepArgs a;
+    std::memset(&a, 0, sizeof(a));
+    a.xy = m->d.xy;
+    for (int k = 0; k < 3; ++k) {
+        a.tv[k] = m->d.tv[k];
+        a.tn[k] = m->d.tn[k];
+    }
+    a.t0 = m->d.t0;
+    a.vin = vin;
+    a.vout = vout;
+    a.probs = probs_dev;
+    a.node_off = m->d.node_off;
+    a.nprob = m->n_problems;
+    a.walk_cap = m->opt_walk_cap > 0 ? m->opt_walk_cap : default_walk_cap(m);
+    a.N = m->N;
+    a.status = m->d.status;
+    a.stats = m->d.stats;
+    if (dbg) a.dbg = *dbg;
+    return a;
+}
+
+static sl_status launch_step(const sl_mesh *m, const StepArgs &a, bool debug, cudaStream_t s)
+{
+    if (m->precision != SL_FP64) return fail(SL_E_STATE, "no FP32 kernel is built into this library yet");
+    launch_plain_f64(a, m->opt_stats != 0, debug, m->opt_block, s);
+    SL_CUDA(cudaGetLastError());
+    return SL_OK;
+}
+
+static sl_status check_device(const sl_mesh *m)
+{
+    int dev = -1;
+    SL_CUDA(cudaGetDevice(&dev));
+    if (dev != m->device) return fail(SL_E_STATE, "the current device is not the device the mesh was created on");
+    return SL_OK;
+}
+
+static sl_status read_status(sl_mesh *m, cudaStream_t s)
+{
+    uint32_t st[kStatusWords];
+    SL_CUDA(cudaMemcpyAsync(st, m->d.status, sizeof(st), cudaMemcpyDeviceToHost, s));
+    SL_CUDA(cudaStreamSynchronize(s));
+    SL_CUDA(cudaMemsetAsync(m->d.status, 0, sizeof(st), s));
+    SL_CUDA(cudaStreamSynchronize(s));
+    if (st[0] & (1u << SL_E_WALK_LIMIT)) return fail(SL_E_WALK_LIMIT, "a barycentric walk exceeded its hop cap and its fallback");
+    if (st[0] & (1u << SL_E_ARG))
+        return fail(SL_E_ARG, "a coordinate fell outside the exact orientation predicate's range");
+    return SL_OK;
+}
+
+static sl_status run_steps(sl_mesh *m, const sl_problem *probs, int64_t n0, int32_t n_steps, void *v, void *v2,
+                           int32_t use_graph, cudaStream_t s)
+{
+    const size_t per = sizeof(ProbStep) * m->n_problems;
+    std::vector<ProbStep> host(per / sizeof(ProbStep) * (size_t)n_steps);
+    for (int32_t k = 0; k < n_steps; ++k) {
+        sl_status st = fill_step(m, probs, n0 + k, host.data() + (size_t)k * m->n_problems);
+        if (st != SL_OK) return st;
+    }
+    const size_t elem = m->precision == SL_FP64 ? sizeof(double) : sizeof(float);
+    GraphCache &g = m->graph;
+    std::vector<uint8_t> key((const uint8_t *)probs, (const uint8_t *)(probs + m->n_problems));
+    const bool reuse = use_graph && g.valid && g.exec && g.n0 == n0 && g.n_steps == n_steps && g.v == v &&
+                       g.v_scratch == v2 && g.probs == key && g.kernel == m->opt_kernel;
+    if (!reuse) {
+        sl_status st = ensure_probs(m, per * n_steps);
+        if (st != SL_OK) return st;
+        // synchronous copy: a graph recorded below may replay it later
+        SL_CUDA(cudaStreamSynchronize(s));
+        SL_CUDA(cudaMemcpy(m->d.probs, host.data(), per * n_steps, cudaMemcpyHostToDevice));
+    }
+    auto enqueue = [&](cudaStream_t q) -> sl_status {
+        void *a = v, *b = v2;
+        for (int32_t k = 0; k < n_steps; ++k) {
+            StepArgs args = make_args(m, (const ProbStep *)((char *)m->d.probs + per * k), a, b, nullptr);
+            sl_status st = launch_step(m, args, false, q);
+            if (st != SL_OK) return st;
+            void *t = a;
+            a = b;
+            b = t;
+        }
+        if (a != v) SL_CUDA(cudaMemcpyAsync(v, a, elem * m->N, cudaMemcpyDeviceToDevice, q));
+        return SL_OK;
+    };
+    if (!use_graph) return enqueue(s);
+    if (!reuse) {
+        if (g.exec) cudaGraphExecDestroy((cudaGraphExec_t)g.exec);
+        g = GraphCache();
+        // Record on a private stream: the caller's stream may be the legacy
+        // default stream, which cannot be captured.  Recording executes
+        // nothing; the graph is then launched on the caller's stream.
+        if (!m->capture_stream) SL_CUDA(cudaStreamCreateWithFlags((cudaStream_t *)&m->capture_stream, cudaStreamNonBlocking));
+        cudaStream_t cs = (cudaStream_t)m->capture_stream;
+        cudaGraph_t graph;
+        SL_CUDA(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
+        sl_status st = enqueue(cs);
+        cudaError_t ce = cudaStreamEndCapture(cs, &graph);
+        if (st != SL_OK) {
+            if (ce == cudaSuccess) cudaGraphDestroy(graph);
+            return st;
+        }
+        if (ce != cudaSuccess) return fail(SL_E_CUDA, std::string("cudaStreamEndCapture: ") + cudaGetErrorString(ce));
+        cudaGraphExec_t exec;
+        ce = cudaGraphInstantiate(&exec, graph, 0);
+        cudaGraphDestroy(graph);
+        if (ce != cudaSuccess) return fail(SL_E_CUDA, std::string("cudaGraphInstantiate: ") + cudaGetErrorString(ce));
+        g.exec = exec;
+        g.valid = true;
+        g.n0 = n0;
+        g.n_steps = n_steps;
+        g.v = v;
+        g.v_scratch = v2;
+        g.probs = key;
+        g.kernel = m->opt_kernel;
+    }
+    SL_CUDA(cudaGraphLaunch((cudaGraphExec_t)g.exec, s));
+    return SL_OK;
+}
+
+}  // namespace sl
+
+using namespace sl;
+
+extern "C" sl_status sl_step(sl_mesh *m, const sl_problem *probs, int64_t n, const void *v_in, void *v_out,
+                             const sl_debug *dbg, void *stream)
+{
+    if (!m || !probs || !v_in || !v_out) return fail(SL_E_ARG, "sl_step: NULL argument");
+    if (v_in == v_out) return fail(SL_E_ARG, "sl_step: v_in and v_out must not alias");
+    if (n < 0) return fail(SL_E_ARG, "sl_step: n must be >= 0");
+    sl_status st = check_device(m);
+    if (st != SL_OK) return st;
+    cudaStream_t s = (cudaStream_t)stream;
+    std::vector<ProbStep> host(m->n_problems);
+    st = fill_step(m, probs, n, host.data());
+    if (st != SL_OK) return st;
+    st = ensure_probs(m, sizeof(ProbStep) * m->n_problems);
+    if (st != SL_OK) return st;
+    m->graph.valid = false;   // the problem buffer is overwritten
+    SL_CUDA(cudaMemcpyAsync(m->d.probs, host.data(), sizeof(ProbStep) * m->n_problems, cudaMemcpyHostToDevice, s));
+    SL_CUDA(cudaStreamSynchronize(s));   // the host staging vector goes out of scope
+    StepArgs a = make_args(m, (const ProbStep *)m->d.probs, v_in, v_out, dbg);
+    bool debug = dbg && (dbg->feet || dbg->tri || dbg->moves || dbg->flags);
+    st = launch_step(m, a, debug, s);
+    m->stepped = true;
+    return st;
+}
+
+extern "C" sl_status sl_run(sl_mesh *m, const sl_problem *probs, int64_t n0, int32_t n_steps, void *v,
+                            void *v_scratch, int32_t use_graph, sl_stats *stats, void *stream)
+{
+    if (!m || !probs || !v || !v_scratch) return fail(SL_E_ARG, "sl_run: NULL argument");
+    if (v == v_scratch) return fail(SL_E_ARG, "sl_run: v and v_scratch must not alias");
+    if (n0 < 0 || n_steps < 0) return fail(SL_E_ARG, "sl_run: n0 and n_steps must be >= 0");
+    sl_status st = check_device(m);
+    if (st != SL_OK) return st;
+    cudaStream_t s = (cudaStream_t)stream;
+    if (n_steps > 0) {
+        st = run_steps(m, probs, n0, n_steps, v, v_scratch, use_graph, s);
+        if (st != SL_OK) return st;
+        m->stepped = true;
+    }
+    st = read_status(m, s);
+    if (stats) {
+        sl_status s2 = sl_mesh_stats(m, stats, 0, stream);
+        if (st == SL_OK) st = s2;
+    }
+    return st;
+}
+
+extern "C" sl_status sl_run_host(sl_mesh *m, const sl_problem *probs, int64_t n0, int32_t n_steps, void *v_host,
+                                 int32_t use_graph, sl_stats *stats, void *stream)
+{
+    if (!m || !probs || !v_host) return fail(SL_E_ARG, "sl_run_host: NULL argument");
+    sl_status st = check_device(m);
+    if (st != SL_OK) return st;
+    cudaStream_t s = (cudaStream_t)stream;
+    const size_t bytes = (m->precision == SL_FP64 ? sizeof(double) : sizeof(float)) * m->N;
+    if (!m->host_v) {
+        SL_CUDA(cudaMalloc(&m->host_v, bytes));
+        SL_CUDA(cudaMalloc(&m->host_v2, bytes));
+    }
+    SL_CUDA(cudaMemcpyAsync(m->host_v, v_host, bytes, cudaMemcpyHostToDevice, s));
+    if (n_steps > 0) {
+        st = run_steps(m, probs, n0, n_steps, m->host_v, m->host_v2, use_graph, s);
+        if (st != SL_OK) return st;
+        m->stepped = true;
+    }
+    SL_CUDA(cudaMemcpyAsync(v_host, m->host_v, bytes, cudaMemcpyDeviceToHost, s));
+    st = read_status(m, s);
+    if (stats) {
+        sl_status s2 = sl_mesh_stats(m, stats, 0, stream);
+        if (st == SL_OK) st = s2;
+    }
+    return st;
+}
+
+extern "C" sl_status sl_mesh_get_t0(const sl_mesh *m, int32_t *t0_dev, void *stream)
+{
+    if (!m || !t0_dev) return fail(SL_E_ARG, "sl_mesh_get_t0: NULL argument");
+    SL_CUDA(cudaMemcpyAsync(t0_dev, m->d.t0, sizeof(int32_t) * m->N, cudaMemcpyDeviceToDevice, (cudaStream_t)stream));
+    return SL_OK;
+}
+
+extern "C" sl_status sl_mesh_set_t0(sl_mesh *m, const int32_t *t0_dev, void *stream)
+{
+    if (!m || !t0_dev) return fail(SL_E_ARG, "sl_mesh_set_t0: NULL argument");
+    std::vector<int32_t> h(m->N);
+    SL_CUDA(cudaMemcpyAsync(h.data(), t0_dev, sizeof(int32_t) * m->N, cudaMemcpyDeviceToHost, (cudaStream_t)stream));
+    SL_CUDA(cudaStreamSynchronize((cudaStream_t)stream));
+    for (int32_t p = 0; p < m->n_problems; ++p)
+        for (int64_t i = m->node_off[p]; i < m->node_off[p + 1]; ++i)
+            if (h[i] < m->tri_off[p] || h[i] >= m->tri_off[p + 1])
+                return fail(SL_E_ARG, "sl_mesh_set_t0: entry " + std::to_string(i) + " is not a triangle of its problem");
+    SL_CUDA(cudaMemcpyAsync(m->d.t0, t0_dev, sizeof(int32_t) * m->N, cudaMemcpyDeviceToDevice, (cudaStream_t)stream));
+    return SL_OK;
+}
+
+extern "C" sl_status sl_mesh_reset_t0(sl_mesh *m, void *stream)
+{
+    if (!m) return fail(SL_E_ARG, "sl_mesh_reset_t0: mesh is NULL");
+    SL_CUDA(cudaMemcpyAsync(m->d.t0, m->d.t0_init, sizeof(int32_t) * m->N, cudaMemcpyDeviceToDevice,
+                            (cudaStream_t)stream));
+    return SL_OK;
+}
+
+extern "C" sl_status sl_mesh_status(sl_mesh *m, void *stream)
+{
+    if (!m) return fail(SL_E_ARG, "sl_mesh_status: mesh is NULL");
+    return read_status(m, (cudaStream_t)stream);
+}
+
+extern "C" sl_status sl_mesh_stats(sl_mesh *m, sl_stats *out, int32_t reset, void *stream)
+{
+    if (!m) return fail(SL_E_ARG, "sl_mesh_stats: mesh is NULL");
+    cudaStream_t s = (cudaStream_t)stream;
+    unsigned long long c[kStatCounters];
+    SL_CUDA(cudaMemcpyAsync(c, m->d.stats, sizeof(c), cudaMemcpyDeviceToHost, s));
+    SL_CUDA(cudaStreamSynchronize(s));
+    if (reset) {
+        SL_CUDA(cudaMemsetAsync(m->d.stats, 0, sizeof(c), s));
+        SL_CUDA(cudaStreamSynchronize(s));
+    }
+    if (out) {
+        out->node_updates = c[0];
+        out->walk_moves = c[1];
+        out->max_moves = c[2];
+        out->exact_tests = c[3];
+        out->filter2_tests = c[4];
+        out->clipped = c[5];
+        out->fallbacks = c[6];
+        out->walk_limit = c[7];
+    }
+    return SL_OK;
+}
+
+extern "C" sl_status sl_mesh_reorder(sl_mesh *m, int32_t curve, int32_t *node_perm, int32_t *tri_perm)
+{
+    if (!m) return fail(SL_E_ARG, "sl_mesh_reorder: mesh is NULL");
+    if (curve < SL_CURVE_NONE || curve > SL_CURVE_MORTON) return fail(SL_E_ARG, "sl_mesh_reorder: unknown curve");
+    sl_status st = check_device(m);
+    if (st != SL_OK) return st;
+    if (m->stepped) {   // keep the walk state: bring the current T^0 back first
+        SL_CUDA(cudaDeviceSynchronize());
+        SL_CUDA(cudaMemcpy(m->t0.data(), m->d.t0, sizeof(int32_t) * m->N, cudaMemcpyDeviceToHost));
+    }
+    st = reorder_host(m, curve, node_perm, tri_perm);
+    if (st != SL_OK) return st;
+    if (m->graph.exec) cudaGraphExecDestroy((cudaGraphExec_t)m->graph.exec);
+    m->graph = GraphCache();
+    return upload_arrays(m);
+}
+
+extern "C" void sl_mesh_destroy(sl_mesh *m)
+{
+    if (!m) return;
+    free_device(m);
+    delete m;
+}

@@ -1,0 +1,89 @@
+// sl_internal.h -- the mesh handle and helpers shared by the library's
+// translation units (host code + CUDA code of the product library only).
+#pragma once
+
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "../../include/sl.h"
+
+namespace sl {
+
+// Set the thread-local error message and return the status.
+sl_status fail(sl_status st, const std::string &msg);
+
+// SplitMix64 (Steele, Lea & Flood 2014): the output mix applied to a counter.
+inline uint64_t mix64(uint64_t z)
+{
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ULL;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBULL;
+    return z ^ (z >> 31);
+}
+inline uint64_t splitmix_at(uint64_t seed, uint64_t i)
+{
+    const uint64_t g = 0x9E3779B97F4A7C15ULL;
+    return mix64(mix64(seed * g) + (i + 1) * g);
+}
+
+struct DeviceMesh {
+    void *xy = nullptr;               // double2[N] (FP64) or float2[N] (FP32)
+    int32_t *tv[3] = {nullptr, nullptr, nullptr};   // vertex k of triangle j (global node index)
+    int32_t *tn[3] = {nullptr, nullptr, nullptr};   // neighbour across edge opposite vertex k (global, -1)
+    int32_t *t0 = nullptr;            // start / last foot triangle of node i (global)
+    int32_t *t0_init = nullptr;       // the initial start triangles (global)
+    int64_t *node_off = nullptr;      // n_problems + 1
+    uint32_t *status = nullptr;       // [0] = OR of (1 << sl_status); others reserved
+    unsigned long long *stats = nullptr;   // 8 counters (sl_stats order)
+    void *probs = nullptr;            // per-problem step data (device)
+    size_t probs_bytes = 0;
+};
+
+struct GraphCache {
+    bool valid = false;
+    void *exec = nullptr;             // cudaGraphExec_t
+    int64_t n0 = 0;
+    int32_t n_steps = 0;
+    const void *v = nullptr, *v_scratch = nullptr;
+    std::vector<uint8_t> probs;       // problems the graph was recorded with
+    int32_t kernel = 0;
+};
+
+}  // namespace sl
+
+struct sl_mesh {
+    int32_t n_problems = 0;
+    int64_t N = 0, Nt = 0;
+    int32_t precision = SL_FP64;
+    int device = 0;
+    uint64_t seed = 1;
+    std::vector<int64_t> node_off, tri_off;
+    // host copies in the current numbering (local indices per problem)
+    std::vector<double> xy;
+    std::vector<int32_t> tri, nbr;
+    std::vector<int32_t> t0;          // T^0, global triangle indices (host copy)
+    std::vector<int32_t> t0_init;     // the initial T^0 chosen at creation
+    std::vector<int32_t> cells;       // per problem: sqrt(Nt/2), the M of a grid mesh
+    // options
+    int32_t opt_stats = 0;
+    int32_t opt_walk_cap = 0;         // 0 = default
+    int32_t opt_kernel = 0;
+    int32_t opt_block = 0;
+    int32_t opt_tiles_per_sm = 0;
+    bool stepped = false;
+    sl::DeviceMesh d;
+    sl::GraphCache graph;
+    // device value buffers for sl_run_host
+    void *host_v = nullptr, *host_v2 = nullptr;
+    void *capture_stream = nullptr;   // cudaStream_t used only to record graphs
+};
+
+namespace sl {
+// host side (mesh_host.cpp)
+sl_status build_and_validate(sl_mesh *m, const int32_t *nbr_in);
+sl_status reorder_host(sl_mesh *m, int32_t curve, int32_t *node_perm, int32_t *tri_perm);
+// device side (step.cu)
+sl_status upload(sl_mesh *m);
+void free_device(sl_mesh *m);
+int32_t default_walk_cap(const sl_mesh *m);
+}  // namespace sl

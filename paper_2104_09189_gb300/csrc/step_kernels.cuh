@@ -1,0 +1,64 @@
+// step_kernels.cuh -- arguments and helpers of the step kernels.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cstdint>
+
+#include "predicates.cuh"
+#include "step_common.cuh"
+
+namespace sl {
+
+struct StepArgs {
+    const void *xy;               // double2[N] or float2[N]
+    const int32_t *tv[3];         // triangle vertices (global node indices), SoA
+    const int32_t *tn[3];         // neighbours (global triangle indices, -1 = boundary), SoA
+    int32_t *t0;                  // start / located triangle per node (in place)
+    const void *vin;              // V^n
+    void *vout;                   // V^{n+1}
+    const ProbStep *probs;        // per-problem data of this step (device)
+    const int64_t *node_off;      // problem node offsets (device)
+    int32_t nprob;
+    int32_t walk_cap;
+    int64_t N;
+    uint32_t *status;             // deferred status bits
+    unsigned long long *stats;    // counters in sl_stats order
+    sl_debug dbg;                 // optional per-node outputs (device pointers)
+};
+
+__device__ __forceinline__ uint64_t mix64_dev(uint64_t z)
+{
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ULL;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBULL;
+    return z ^ (z >> 31);
+}
+
+// Warp-aggregated counters: one atomic per warp and counter.
+__device__ __forceinline__ void warp_stats(unsigned long long *stats, bool active, uint32_t hops,
+                                           uint32_t exact_tests, uint32_t clipped, uint32_t fallback,
+                                           uint32_t limit, uint32_t filter2 = 0)
+{
+    const unsigned full = 0xffffffffu;
+    unsigned n = __reduce_add_sync(full, active ? 1u : 0u);
+    unsigned h = __reduce_add_sync(full, hops);
+    unsigned hm = __reduce_max_sync(full, hops);
+    unsigned e = __reduce_add_sync(full, exact_tests);
+    unsigned f2 = __reduce_add_sync(full, filter2);
+    unsigned c = __reduce_add_sync(full, clipped);
+    unsigned fb = __reduce_add_sync(full, fallback);
+    unsigned l = __reduce_add_sync(full, limit);
+    if ((threadIdx.x & 31) == 0) {
+        if (n) atomicAdd(&stats[0], (unsigned long long)n);
+        if (h) atomicAdd(&stats[1], (unsigned long long)h);
+        if (hm) atomicMax(&stats[2], (unsigned long long)hm);
+        if (e) atomicAdd(&stats[3], (unsigned long long)e);
+        if (f2) atomicAdd(&stats[4], (unsigned long long)f2);
+        if (c) atomicAdd(&stats[5], (unsigned long long)c);
+        if (fb) atomicAdd(&stats[6], (unsigned long long)fb);
+        if (l) atomicAdd(&stats[7], (unsigned long long)l);
+    }
+}
+
+void launch_plain_f64(const StepArgs &a, bool stats, bool debug, int block, cudaStream_t s);
+
+}  // namespace sl

@@ -1,0 +1,209 @@
+"""GPU path vs the CPU oracle, through the C ABI (sl_step / sl_run).
+
+Values: normwise relative error <= 1e-12 at every step (FP64).
+Triangles: bit-exact for feet that are not within 1e-12 of an edge line of
+their triangle; the others are counted and must be contained exactly.
+"""
+import numpy as np
+import pytest
+
+import oracle
+import paper_2104_09189_gb300 as sl
+import sl_inputs as si
+from gpu_helpers import GpuRun, compare_step
+
+pytestmark = pytest.mark.gpu
+
+
+def _parity_run(prob, steps, curve=sl.SL_CURVE_NONE, kernel=0, seed=1, check_every=1):
+    mesh = prob.mesh
+    om = oracle.OracleMesh(mesh.xy, mesh.tri)
+    g = GpuRun(mesh, prob.field, prob.dt, curve=curve, kernel=kernel, seed=seed)
+    v_dev = g.to_dev(prob.v0)
+    v_orc = prob.v0.copy()
+    worst, near_total = 0.0, 0
+    for n in range(steps):
+        v_dev, res = g.step(n, v_dev)
+        ov, otri, oflags, ofeet = om.step(prob.field.kind, prob.field.packed(), prob.dt, n, v_orc)
+        v_orc = ov
+        if n % check_every == 0 or n == steps - 1:
+            err, near = compare_step(om, res, ov, otri, ofeet)
+            worst = max(worst, err)
+            near_total += near
+    g.close()
+    return worst, near_total, res
+
+
+def test_c1_swirl_full_parity():
+    prob = si.config("C1")
+    worst, near, res = _parity_run(prob, prob.n_steps)
+    assert worst <= 1e-12
+    # boundary nodes of the swirl have f = 0 (or ~1e-16): their feet are
+    # vertices and must be flagged degenerate
+    assert near >= 4 * 64
+
+
+@pytest.mark.parametrize("curve", [sl.SL_CURVE_NONE, sl.SL_CURVE_HILBERT, sl.SL_CURVE_MORTON])
+def test_c2_construction_swirl_parity(curve):
+    prob = si.config("C2", M=256)
+    _parity_run(prob, 6, curve=curve)
+
+
+def test_c2_full_size_parity_hilbert():
+    prob = si.config("C2")
+    _parity_run(prob, 3, curve=sl.SL_CURVE_HILBERT)
+
+
+def test_c3_construction_rotation_parity_and_zero_hops():
+    """Graded mesh, solid rotation: feet are computed with the same rounded
+    operations on both sides, so they agree bit for bit; a time-constant
+    field needs no walk move after the first step (Sec. 3, strategy (b))."""
+    prob = si.config("C3", M=256)
+    mesh = prob.mesh
+    om = oracle.OracleMesh(mesh.xy, mesh.tri)
+    g = GpuRun(mesh, prob.field, prob.dt, curve=sl.SL_CURVE_HILBERT)
+    v_dev = g.to_dev(prob.v0)
+    v_orc = prob.v0.copy()
+    for n in range(4):
+        v_dev, res = g.step(n, v_dev)
+        ov, otri, oflags, ofeet = om.step(prob.field.kind, prob.field.packed(), prob.dt, n, v_orc)
+        v_orc = ov
+        assert np.array_equal(res["feet"], ofeet)
+        compare_step(om, res, ov, otri, ofeet, delta=0.0)
+        if n == 0:
+            assert res["moves"].mean() > 5      # strategy (a) on the first step: ~ Courant number
+        else:
+            assert res["moves"].max() == 0
+    g.close()
+
+
+def test_other_fields_parity():
+    mesh = si.grid_mesh(96, 0.25, 12)
+    v0 = si.gaussian(mesh.xy, 0.45, 0.55, 0.1)
+    for fld, dt in [(si.fourier8_field(77), 0.03), (si.paper_field(), 0.02), (si.swirl_field(), 0.1)]:
+        prob = si.Problem("x", mesh, fld, dt, 4, v0, "fp64", 12)
+        _parity_run(prob, 4)
+
+
+def test_linear_data_closed_form_on_gpu():
+    """Contracting affine field with linear data: V^n = u0(c + (1-k dt)^n (x - c))."""
+    mesh = si.grid_mesh(128, 0.25, 4)
+    k, cx, cy, dt, steps = 3.0, 0.4, 0.6, 0.05, 10
+    p = np.zeros(48)
+    p[:8] = (-k * cx, k, 0.0, 0.0, -k * cy, 0.0, k, 0.0)
+    fld = si.Field(si.FIELD_AFFINE, p, 1.0)
+    g = GpuRun(mesh, fld, dt, curve=sl.SL_CURVE_HILBERT)
+    lin = lambda q: 0.25 + q[:, 0] - 0.5 * q[:, 1]
+    v = g.to_dev(lin(mesh.xy))
+    w = g.torch.empty_like(v)
+    sl.sl_run(g.h, g.probs, 0, steps, v, w, use_graph=True)
+    r = (1 - k * dt) ** steps
+    want = lin(np.stack([cx + r * (mesh.xy[:, 0] - cx), cy + r * (mesh.xy[:, 1] - cy)], 1))
+    assert np.abs(g.from_dev(v) - want).max() < 1e-13
+    g.close()
+
+
+def test_zero_field_leaves_values_bitwise():
+    mesh = si.grid_mesh(64, 0.25, 2)
+    v0 = si.cosine_bump(mesh.xy)
+    g = GpuRun(mesh, si.zero_field(), 0.1)
+    v_dev = g.to_dev(v0)
+    for n in range(3):
+        v_dev, res = g.step(n, v_dev)
+        assert np.array_equal(res["v"], v0)
+        assert np.all(res["flags"] & sl.SL_NODE_DEGENERATE)
+    g.close()
+
+
+def test_graph_eager_reorder_and_resume_are_bitwise_identical():
+    prob = si.config("C2", M=192)
+    mesh = prob.mesh
+    outs = []
+    for curve, graph in [(sl.SL_CURVE_NONE, False), (sl.SL_CURVE_NONE, True), (sl.SL_CURVE_HILBERT, True),
+                         (sl.SL_CURVE_MORTON, False)]:
+        g = GpuRun(mesh, prob.field, prob.dt, curve=curve)
+        v = g.to_dev(prob.v0)
+        w = g.torch.empty_like(v)
+        sl.sl_run(g.h, g.probs, 0, 7, v, w, use_graph=graph)
+        outs.append(g.from_dev(v))
+        g.close()
+    for o in outs[1:]:
+        assert np.array_equal(o, outs[0])
+    # resume: 3 steps, export T^0 and V, new handle, import, 4 more steps
+    g = GpuRun(mesh, prob.field, prob.dt)
+    v = g.to_dev(prob.v0)
+    w = g.torch.empty_like(v)
+    sl.sl_run(g.h, g.probs, 0, 3, v, w)
+    t0 = g.torch.empty(mesh.n_nodes, dtype=g.torch.int32, device=g.dev)
+    sl.sl_mesh_get_t0(g.h, t0)
+    g2 = GpuRun(mesh, prob.field, prob.dt)
+    sl.sl_mesh_set_t0(g2.h, t0)
+    sl.sl_run(g2.h, g2.probs, 3, 4, v, w)
+    assert np.array_equal(g2.from_dev(v), outs[0])
+    g.close()
+    g2.close()
+
+
+def test_run_host_matches_device_run():
+    prob = si.config("C1")
+    g = GpuRun(prob.mesh, prob.field, prob.dt)
+    v = g.to_dev(prob.v0)
+    w = g.torch.empty_like(v)
+    sl.sl_run(g.h, g.probs, 0, 5, v, w)
+    dev_result = g.from_dev(v)
+    g.close()
+    g = GpuRun(prob.mesh, prob.field, prob.dt)
+    host = prob.v0.copy()
+    sl.sl_run_host(g.h, g.probs, 0, 5, host)
+    assert np.array_equal(host, dev_result)
+    g.close()
+
+
+def test_walk_cap_reports_status_without_hanging():
+    """A tiny hop cap (debug knob) must end in SL_E_WALK_LIMIT, not a hang."""
+    prob = si.config("C2", M=128)
+    g = GpuRun(prob.mesh, prob.field, prob.dt)
+    sl.sl_mesh_set_option(g.h, sl.SL_OPT_WALK_CAP, 1)
+    v = g.to_dev(prob.v0)
+    w = g.torch.empty_like(v)
+    with pytest.raises(sl.SLError) as e:
+        sl.sl_run(g.h, g.probs, 0, 1, v, w, use_graph=False)
+    assert e.value.status == sl.SL_E_WALK_LIMIT
+    # the handle stays usable
+    sl.sl_mesh_set_option(g.h, sl.SL_OPT_WALK_CAP, 0)
+    sl.sl_run(g.h, g.probs, 1, 1, v, w, use_graph=False)
+    g.close()
+
+
+def test_batched_problems_match_single_runs():
+    probs = si.batch_config(6, nmin=2e3, nmax=2e4, steps=3)
+    meshes = [(p.mesh.xy, p.mesh.tri) for p in probs]
+    no, to, xy, tri = sl.pack_meshes(meshes)
+    import torch
+    h = sl.sl_mesh_create(no, to, xy, tri)
+    pr = sl.problems([(p.field.kind, p.dt, p.field.packed()) for p in probs])
+    v = torch.tensor(np.concatenate([p.v0 for p in probs]), dtype=torch.float64, device="cuda:0")
+    w = torch.empty_like(v)
+    sl.sl_run(h, pr, 0, 3, v, w)
+    got = v.cpu().numpy()
+    sl.sl_mesh_destroy(h)
+    for k, p in enumerate(probs):
+        om = oracle.OracleMesh(p.mesh.xy, p.mesh.tri)
+        want = om.run(p.field.kind, p.field.packed(), p.dt, 0, 3, p.v0)
+        seg = got[no[k]:no[k + 1]]
+        assert np.abs(seg - want).max() <= 1e-12 * np.abs(want).max()
+
+
+def test_bad_step_arguments():
+    prob = si.config("C1", M=8)
+    g = GpuRun(prob.mesh, prob.field, prob.dt)
+    v = g.to_dev(prob.v0)
+    with pytest.raises(sl.SLError) as e:
+        sl.sl_step(g.h, g.probs, 0, v, v)
+    assert e.value.status == sl.SL_E_ARG
+    bad = sl.problems([(prob.field.kind, float("nan"), prob.field.packed())])
+    w = g.torch.empty_like(v)
+    with pytest.raises(sl.SLError) as e:
+        sl.sl_step(g.h, bad, 0, v, w)
+    assert e.value.status == sl.SL_E_ARG
+    g.close()
