@@ -49,6 +49,7 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--no-plain", action="store_true", help="skip the plain FP64 kernel comparison")
     return ap.parse_args()
 
 
@@ -266,6 +267,34 @@ def main():
         dist.all_reduce(tt, op=dist.ReduceOp.MAX)
         elapsed = float(tt.item())
 
+    # phases: the first step (walks start at the initial incident triangles)
+    # and the remaining steps (walks start at the previous foot triangles)
+    def timed(fn):
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        fn()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1)
+
+    sl.sl_mesh_reset_t0(h)
+    first_ms = timed(lambda: sl.sl_run(h, probs, 0, 1, v, w, use_graph=False))
+    rest_ms = timed(lambda: sl.sl_run(h, probs, 1, S - 1, v, w, use_graph=False)) / max(1, S - 1)
+    phases = {"first_step_ms": first_ms, "later_step_ms": rest_ms,
+              "note": "eager launches, one run, after the timed region"}
+
+    plain = None
+    if prob.precision == "fp64" and not args.no_plain and args.kernel != 1:
+        sl.sl_mesh_set_option(h, sl.SL_OPT_KERNEL, 1)
+        one_run()
+        k_plain = 2
+        tp = timed(lambda: [one_run() for _ in range(k_plain)]) / 1e3
+        plain = {"value": N * S * k_plain / tp, "unit": "node-updates/s", "ms_per_step": 1e3 * tp / k_plain,
+                 "kernel": "plain FP64 step (one thread per node, all arithmetic in double)"}
+        sl.sl_mesh_set_option(h, sl.SL_OPT_KERNEL, args.kernel)
+
     units = N * S * args.steps * world
     value = units / elapsed
     launch_s = elapsed / (args.steps * S)
@@ -312,23 +341,29 @@ def main():
         "higher_is_better": True,
         "scaling": "weak",
         "vs_baseline": None,
-        "dtype": "f64" if prec == sl.SL_FP64 else "f32",
+        "dtype": ("f64" if args.kernel == 1 else "df64 (FP32 pairs, 48-bit significand; FP64-accuracy results)")
+                 if prec == sl.SL_FP64 else "f32",
         "data": "synthetic",
         "config": workload_config(args, prob),
         "roofline": {"bound": "hbm", "achieved": achieved_gbs, "peak": peaks.get("hbm_gbs", 6800.0),
                      "unit": "GB/s", "frac": achieved_gbs / peaks.get("hbm_gbs", 6800.0), "traffic": None,
                      "peak_source": peak_src,
                      "algorithmic_bytes_per_node": bpn,
-                     "kernel": "sl step kernel (one launch = one SL step over all nodes)",
+                     "kernel": ("k_step_plain_f64" if args.kernel == 1 else
+                                ("k_step_fast_df" if prec == sl.SL_FP64 else "k_step_fast_f32"))
+                               + " (one launch = one SL step over all nodes; duration = timed region / launches)",
                      "launch_ms": launch_s * 1e3},
         "cpu_baseline": cpu,
         "e2e": e2e,
-        "gpu_launches": args.steps * S,
+        "gpu_launches": args.steps * (S + (2 if (prec == sl.SL_FP64 and args.kernel != 1) else 0)),
         "clocks": clocks,
         "walk": {"first_run_mean_hops_per_node_update": stats["walk_moves"] / max(1, stats["node_updates"]),
                  "max_hops": stats["max_moves"], "exact_tests": stats["exact_tests"],
                  "clipped": stats["clipped"], "fallbacks": stats["fallbacks"]},
         "setup_s": setup_s,
+        "phases": phases,
+        "plain_fp64": plain,
+        "speedup_vs_plain_fp64": (value / world) / plain["value"] if plain else None,
     }
     print(json.dumps(line), flush=True)
     if dist:

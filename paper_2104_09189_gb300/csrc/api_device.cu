@@ -7,6 +7,7 @@
 #include <vector>
 
 #include "sl_internal.h"
+#include "step_fast.cuh"
 #include "step_kernels.cuh"
 
 namespace sl {
@@ -18,6 +19,14 @@ namespace sl {
             return fail(e_ == cudaErrorMemoryAllocation ? SL_E_NOMEM : SL_E_CUDA,            \
                         std::string(#call) + ": " + cudaGetErrorString(e_));                 \
     } while (0)
+
+// (hi, lo) float pair of a double: hi = fl32(v), lo = fl32(v - hi)
+static void split_df(double v, float2 &o)
+{
+    const float h = (float)v;
+    o.x = h;
+    o.y = (float)(v - (double)h);
+}
 
 int32_t default_walk_cap(const sl_mesh *m)
 {
@@ -31,7 +40,8 @@ void free_device(sl_mesh *m)
 {
     DeviceMesh &d = m->d;
     void *ptrs[] = {d.xy, d.tv[0], d.tv[1], d.tv[2], d.tn[0], d.tn[1], d.tn[2], d.t0, d.t0_init, d.node_off,
-                    d.status, d.stats, d.probs, m->host_v, m->host_v2};
+                    d.status, d.stats, d.probs, d.fprobs, d.xyq, d.xyh, d.g1, d.g2, d.tparams, d.dfa, d.dfb,
+                    m->host_v, m->host_v2};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     d = DeviceMesh();
@@ -50,6 +60,19 @@ static sl_status upload_arrays(sl_mesh *m)
     const int64_t N = m->N, Nt = m->Nt;
     if (m->precision == SL_FP64) {
         SL_CUDA(cudaMemcpy(d.xy, m->xy.data(), sizeof(double) * 2 * N, cudaMemcpyHostToDevice));
+        // (hi, lo) float pairs of the coordinates for the double-float kernel
+        std::vector<float4> q(N);
+        for (int64_t i = 0; i < N; ++i) {
+            float2 a, b;
+            split_df(m->xy[2 * i], a);
+            split_df(m->xy[2 * i + 1], b);
+            q[i] = make_float4(a.x, b.x, a.y, b.y);
+        }
+        SL_CUDA(cudaMemcpy(d.xyq, q.data(), sizeof(float4) * N, cudaMemcpyHostToDevice));
+        std::vector<float2> hx(N);
+        for (int64_t i = 0; i < N; ++i) hx[i] = make_float2(q[i].x, q[i].y);
+        SL_CUDA(cudaMemcpy(d.xyh, hx.data(), sizeof(float2) * N, cudaMemcpyHostToDevice));
+        m->table_key.clear();   // node tables follow the numbering
     } else {
         std::vector<float> f(2 * N);
         for (int64_t q = 0; q < 2 * N; ++q) f[q] = (float)m->xy[q];
@@ -63,8 +86,20 @@ static sl_status upload_arrays(sl_mesh *m)
         SL_CUDA(cudaMemcpy(d.tv[k], col.data(), sizeof(int32_t) * Nt, cudaMemcpyHostToDevice));
         for (int32_t p = 0; p < m->n_problems; ++p)
             for (int64_t j = m->tri_off[p]; j < m->tri_off[p + 1]; ++j) {
-                int32_t nb = m->nbr[3 * j + k];
-                col[j] = nb < 0 ? -1 : nb + (int32_t)m->tri_off[p];
+                const int32_t nb = m->nbr[3 * j + k];
+                if (nb >= 0) {
+                    col[j] = nb + (int32_t)m->tri_off[p];
+                } else {
+                    // boundary edge opposite vertex k: the side of the square it lies on
+                    const int64_t n0 = m->node_off[p];
+                    const int64_t va = n0 + m->tri[3 * j + (k + 1) % 3], vb = n0 + m->tri[3 * j + (k + 2) % 3];
+                    const double xa = m->xy[2 * va], ya = m->xy[2 * va + 1], xb = m->xy[2 * vb], yb = m->xy[2 * vb + 1];
+                    int side = 3;
+                    if (xa == 0.0 && xb == 0.0) side = 0;
+                    else if (xa == 1.0 && xb == 1.0) side = 1;
+                    else if (ya == 0.0 && yb == 0.0) side = 2;
+                    col[j] = -1 - side;
+                }
             }
         SL_CUDA(cudaMemcpy(d.tn[k], col.data(), sizeof(int32_t) * Nt, cudaMemcpyHostToDevice));
     }
@@ -81,11 +116,13 @@ sl_status upload(sl_mesh *m)
     const int64_t N = m->N, Nt = m->Nt;
     const size_t cs = m->precision == SL_FP64 ? 2 * sizeof(double) : 2 * sizeof(float);
     SL_CUDA(cudaMalloc(&d.xy, cs * N));
+    if (m->precision == SL_FP64) SL_CUDA(cudaMalloc(&d.xyq, sizeof(float4) * N));
     for (int k = 0; k < 3; ++k) {
         SL_CUDA(cudaMalloc(&d.tv[k], sizeof(int32_t) * Nt));
         SL_CUDA(cudaMalloc(&d.tn[k], sizeof(int32_t) * Nt));
     }
     SL_CUDA(cudaMalloc(&d.t0, sizeof(int32_t) * N));
+    if (m->precision == SL_FP64) SL_CUDA(cudaMalloc(&d.xyh, sizeof(float2) * N));
     SL_CUDA(cudaMalloc(&d.t0_init, sizeof(int32_t) * N));
     SL_CUDA(cudaMalloc(&d.node_off, sizeof(int64_t) * (m->n_problems + 1)));
     SL_CUDA(cudaMalloc(&d.status, sizeof(uint32_t) * kStatusWords));
@@ -157,10 +194,125 @@ static StepArgs make_args(const sl_mesh *m, const ProbStep *probs_dev, const voi
     return a;
 }
 
+static FastArgs make_fast_args(const sl_mesh *m, const FastProb *fp, const void *vin, void *vout, const sl_debug *dbg)
+{
+    FastArgs a;
+    std::memset(&a, 0, sizeof(a));
+    a.xyq = (const float4 *)m->d.xyq;
+    a.xyh = (const float2 *)m->d.xyh;
+    a.xyf = m->precision == SL_FP32 ? (const float2 *)m->d.xy : nullptr;
+    a.xyd = m->precision == SL_FP64 ? (const double2 *)m->d.xy : nullptr;
+    for (int k = 0; k < 3; ++k) {
+        a.tv[k] = m->d.tv[k];
+        a.tn[k] = m->d.tn[k];
+    }
+    a.t0 = m->d.t0;
+    a.vin = vin;
+    a.vout = vout;
+    a.g1 = (const float4 *)m->d.g1;
+    a.g2 = (const float4 *)m->d.g2;
+    a.probs = fp;
+    a.node_off = m->d.node_off;
+    a.nprob = m->n_problems;
+    a.walk_cap = m->opt_walk_cap > 0 ? m->opt_walk_cap : default_walk_cap(m);
+    a.N = m->N;
+    a.status = m->d.status;
+    a.stats = m->d.stats;
+    if (dbg) a.dbg = *dbg;
+    return a;
+}
+
+// The fast kernels are the default; SL_OPT_KERNEL = 1 selects the plain FP64 one.
+static bool use_fast(const sl_mesh *m) { return m->opt_kernel != 1 || m->precision == SL_FP32; }
+
+// Per-step constants of the fast kernels (see FastProb).
+static void fill_fast(const sl_mesh *m, const ProbStep *ps, FastProb *out)
+{
+    const double pi = 3.14159265358979323846;
+    for (int32_t p = 0; p < m->n_problems; ++p) {
+        const ProbStep &q = ps[p];
+        FastProb &f = out[p];
+        std::memset(&f, 0, sizeof(f));
+        f.kind = q.kind;
+        f.dt = q.dt;
+        double c[6] = {0, 0, 0, 0, 0, 0};
+        switch (q.kind) {
+        case SL_FIELD_AFFINE:
+            c[0] = q.dt * (q.p[0] + q.p[3] * q.t);
+            c[1] = q.dt * q.p[1];
+            c[2] = q.dt * q.p[2];
+            c[3] = q.dt * (q.p[4] + q.p[7] * q.t);
+            c[4] = q.dt * q.p[5];
+            c[5] = q.dt * q.p[6];
+            break;
+        case SL_FIELD_ROTATION:
+            c[0] = q.dt * q.p[0];
+            c[1] = q.p[1];
+            c[2] = q.p[2];
+            break;
+        case SL_FIELD_SWIRL: c[0] = q.dt * q.c[0]; break;
+        case SL_FIELD_PAPER:
+            c[0] = q.dt * std::cos(q.p[1] * q.t);
+            c[1] = q.dt * std::sin(q.p[1] * q.t);
+            break;
+        case SL_FIELD_FOURIER8:
+            c[0] = q.dt * std::cos(2.0 * pi * q.t);
+            c[1] = q.dt * std::sin(2.0 * pi * q.t);
+            break;
+        default: break;
+        }
+        for (int k = 0; k < 6; ++k) split_df(c[k], f.c[k]);
+    }
+}
+
+// Node tables of the trigonometric fields, rebuilt when the fields change.
+static sl_status ensure_tables(sl_mesh *m, const sl_problem *probs, cudaStream_t s)
+{
+    bool need1 = false, need2 = false;
+    std::vector<double> key((size_t)m->n_problems * 49);
+    for (int32_t p = 0; p < m->n_problems; ++p) {
+        const int kind = probs[p].kind;
+        need1 |= kind == SL_FIELD_SWIRL || kind == SL_FIELD_PAPER || kind == SL_FIELD_FOURIER8;
+        need2 |= kind == SL_FIELD_PAPER || kind == SL_FIELD_FOURIER8;
+        key[49 * p] = kind;
+        for (int k = 0; k < SL_NPARAMS; ++k) key[49 * p + 1 + k] = probs[p].p[k];
+    }
+    if (!need1) return SL_OK;
+    if (key == m->table_key && m->d.g1 && (!need2 || m->d.g2)) return SL_OK;
+    if (!m->d.g1) SL_CUDA(cudaMalloc(&m->d.g1, sizeof(float4) * m->N));
+    if (need2 && !m->d.g2) SL_CUDA(cudaMalloc(&m->d.g2, sizeof(float4) * m->N));
+    if (!m->d.tparams) SL_CUDA(cudaMalloc(&m->d.tparams, sizeof(double) * key.size()));
+    SL_CUDA(cudaStreamSynchronize(s));
+    SL_CUDA(cudaMemcpy(m->d.tparams, key.data(), sizeof(double) * key.size(), cudaMemcpyHostToDevice));
+    FieldTableArgs ta;
+    ta.xyd = (const double2 *)m->d.xy;
+    ta.node_off = m->d.node_off;
+    ta.nprob = m->n_problems;
+    ta.N = m->N;
+    ta.params = m->d.tparams;
+    ta.g1 = (float4 *)m->d.g1;
+    ta.g2 = (float4 *)m->d.g2;
+    if (m->precision == SL_FP32) return fail(SL_E_STATE, "field tables of FP32 meshes are built by the FP32 path");
+    launch_field_tables(ta, s);
+    SL_CUDA(cudaGetLastError());
+    SL_CUDA(cudaStreamSynchronize(s));
+    m->table_key = key;
+    m->graph.valid = false;
+    return SL_OK;
+}
+
 static sl_status launch_step(const sl_mesh *m, const StepArgs &a, bool debug, cudaStream_t s)
 {
-    if (m->precision != SL_FP64) return fail(SL_E_STATE, "no FP32 kernel is built into this library yet");
+    if (m->precision != SL_FP64) return fail(SL_E_STATE, "the plain kernel is FP64 only");
     launch_plain_f64(a, m->opt_stats != 0, debug, m->opt_block, s);
+    SL_CUDA(cudaGetLastError());
+    return SL_OK;
+}
+
+static sl_status launch_fast(const sl_mesh *m, const FastArgs &a, bool debug, cudaStream_t s)
+{
+    if (m->precision == SL_FP64) launch_fast_df(a, m->opt_stats != 0, debug, m->opt_block, s);
+    else return fail(SL_E_STATE, "no FP32 kernel is built into this library yet");
     SL_CUDA(cudaGetLastError());
     return SL_OK;
 }
@@ -186,32 +338,80 @@ static sl_status read_status(sl_mesh *m, cudaStream_t s)
     return SL_OK;
 }
 
+static sl_status ensure_fprobs(sl_mesh *m, size_t bytes)
+{
+    if (m->d.fprobs_bytes >= bytes) return SL_OK;
+    cudaFree(m->d.fprobs);
+    m->d.fprobs = nullptr;
+    m->d.fprobs_bytes = 0;
+    SL_CUDA(cudaMalloc(&m->d.fprobs, bytes));
+    m->d.fprobs_bytes = bytes;
+    return SL_OK;
+}
+
 static sl_status run_steps(sl_mesh *m, const sl_problem *probs, int64_t n0, int32_t n_steps, void *v, void *v2,
                            int32_t use_graph, cudaStream_t s)
 {
+    const bool fast = use_fast(m);
     const size_t per = sizeof(ProbStep) * m->n_problems;
-    std::vector<ProbStep> host(per / sizeof(ProbStep) * (size_t)n_steps);
+    const size_t fper = sizeof(FastProb) * m->n_problems;
+    std::vector<ProbStep> host((size_t)m->n_problems * (size_t)n_steps);
     for (int32_t k = 0; k < n_steps; ++k) {
         sl_status st = fill_step(m, probs, n0 + k, host.data() + (size_t)k * m->n_problems);
+        if (st != SL_OK) return st;
+    }
+    if (fast) {
+        sl_status st = ensure_tables(m, probs, s);
         if (st != SL_OK) return st;
     }
     const size_t elem = m->precision == SL_FP64 ? sizeof(double) : sizeof(float);
     GraphCache &g = m->graph;
     std::vector<uint8_t> key((const uint8_t *)probs, (const uint8_t *)(probs + m->n_problems));
     const bool reuse = use_graph && g.valid && g.exec && g.n0 == n0 && g.n_steps == n_steps && g.v == v &&
-                       g.v_scratch == v2 && g.probs == key && g.kernel == m->opt_kernel;
+                       g.v_scratch == v2 && g.probs == key && g.kernel == m->opt_kernel && g.stats == m->opt_stats;
     if (!reuse) {
-        sl_status st = ensure_probs(m, per * n_steps);
-        if (st != SL_OK) return st;
-        // synchronous copy: a graph recorded below may replay it later
+        // synchronous copies: a graph recorded below may replay them later
         SL_CUDA(cudaStreamSynchronize(s));
-        SL_CUDA(cudaMemcpy(m->d.probs, host.data(), per * n_steps, cudaMemcpyHostToDevice));
+        if (fast) {
+            std::vector<FastProb> fh((size_t)m->n_problems * (size_t)n_steps);
+            for (int32_t k = 0; k < n_steps; ++k)
+                fill_fast(m, host.data() + (size_t)k * m->n_problems, fh.data() + (size_t)k * m->n_problems);
+            sl_status st = ensure_fprobs(m, fper * n_steps);
+            if (st != SL_OK) return st;
+            SL_CUDA(cudaMemcpy(m->d.fprobs, fh.data(), fper * n_steps, cudaMemcpyHostToDevice));
+        } else {
+            sl_status st = ensure_probs(m, per * n_steps);
+            if (st != SL_OK) return st;
+            SL_CUDA(cudaMemcpy(m->d.probs, host.data(), per * n_steps, cudaMemcpyHostToDevice));
+        }
     }
     auto enqueue = [&](cudaStream_t q) -> sl_status {
+        if (fast && m->precision == SL_FP64) {
+            // values travel as (hi, lo) float pairs in the two caller buffers
+            launch_to_df((const double *)v, (float2 *)v2, m->N, q);
+            void *a = v2, *b = v;
+            for (int32_t k = 0; k < n_steps; ++k) {
+                FastArgs args = make_fast_args(m, (const FastProb *)((char *)m->d.fprobs + fper * k), a, b, nullptr);
+                sl_status st = launch_fast(m, args, false, q);
+                if (st != SL_OK) return st;
+                void *t = a;
+                a = b;
+                b = t;
+            }
+            launch_from_df((const float2 *)a, (double *)v, m->N, q);
+            SL_CUDA(cudaGetLastError());
+            return SL_OK;
+        }
         void *a = v, *b = v2;
         for (int32_t k = 0; k < n_steps; ++k) {
-            StepArgs args = make_args(m, (const ProbStep *)((char *)m->d.probs + per * k), a, b, nullptr);
-            sl_status st = launch_step(m, args, false, q);
+            sl_status st;
+            if (fast) {
+                FastArgs args = make_fast_args(m, (const FastProb *)((char *)m->d.fprobs + fper * k), a, b, nullptr);
+                st = launch_fast(m, args, false, q);
+            } else {
+                StepArgs args = make_args(m, (const ProbStep *)((char *)m->d.probs + per * k), a, b, nullptr);
+                st = launch_step(m, args, false, q);
+            }
             if (st != SL_OK) return st;
             void *t = a;
             a = b;
@@ -250,6 +450,7 @@ static sl_status run_steps(sl_mesh *m, const sl_problem *probs, int64_t n0, int3
         g.v_scratch = v2;
         g.probs = key;
         g.kernel = m->opt_kernel;
+        g.stats = m->opt_stats;
     }
     SL_CUDA(cudaGraphLaunch((cudaGraphExec_t)g.exec, s));
     return SL_OK;
@@ -271,16 +472,43 @@ extern "C" sl_status sl_step(sl_mesh *m, const sl_problem *probs, int64_t n, con
     std::vector<ProbStep> host(m->n_problems);
     st = fill_step(m, probs, n, host.data());
     if (st != SL_OK) return st;
-    st = ensure_probs(m, sizeof(ProbStep) * m->n_problems);
+    const bool debug = dbg && (dbg->feet || dbg->tri || dbg->moves || dbg->flags);
+    m->graph.valid = false;   // the per-step buffers are overwritten
+    if (!use_fast(m)) {
+        st = ensure_probs(m, sizeof(ProbStep) * m->n_problems);
+        if (st != SL_OK) return st;
+        SL_CUDA(cudaMemcpyAsync(m->d.probs, host.data(), sizeof(ProbStep) * m->n_problems, cudaMemcpyHostToDevice, s));
+        SL_CUDA(cudaStreamSynchronize(s));   // the host staging vector goes out of scope
+        StepArgs a = make_args(m, (const ProbStep *)m->d.probs, v_in, v_out, dbg);
+        st = launch_step(m, a, debug, s);
+        m->stepped = true;
+        return st;
+    }
+    st = ensure_tables(m, probs, s);
     if (st != SL_OK) return st;
-    m->graph.valid = false;   // the problem buffer is overwritten
-    SL_CUDA(cudaMemcpyAsync(m->d.probs, host.data(), sizeof(ProbStep) * m->n_problems, cudaMemcpyHostToDevice, s));
-    SL_CUDA(cudaStreamSynchronize(s));   // the host staging vector goes out of scope
-    StepArgs a = make_args(m, (const ProbStep *)m->d.probs, v_in, v_out, dbg);
-    bool debug = dbg && (dbg->feet || dbg->tri || dbg->moves || dbg->flags);
-    st = launch_step(m, a, debug, s);
+    std::vector<FastProb> fh(m->n_problems);
+    fill_fast(m, host.data(), fh.data());
+    st = ensure_fprobs(m, sizeof(FastProb) * m->n_problems);
+    if (st != SL_OK) return st;
+    SL_CUDA(cudaMemcpyAsync(m->d.fprobs, fh.data(), sizeof(FastProb) * m->n_problems, cudaMemcpyHostToDevice, s));
+    SL_CUDA(cudaStreamSynchronize(s));
+    if (m->precision == SL_FP64) {
+        // double values in and out; the kernel works on (hi, lo) float pairs
+        if (!m->d.dfa) SL_CUDA(cudaMalloc(&m->d.dfa, sizeof(float2) * m->N));
+        if (!m->d.dfb) SL_CUDA(cudaMalloc(&m->d.dfb, sizeof(float2) * m->N));
+        launch_to_df((const double *)v_in, (float2 *)m->d.dfa, m->N, s);
+        FastArgs a = make_fast_args(m, (const FastProb *)m->d.fprobs, m->d.dfa, m->d.dfb, dbg);
+        st = launch_fast(m, a, debug, s);
+        if (st != SL_OK) return st;
+        launch_from_df((const float2 *)m->d.dfb, (double *)v_out, m->N, s);
+        SL_CUDA(cudaGetLastError());
+    } else {
+        FastArgs a = make_fast_args(m, (const FastProb *)m->d.fprobs, v_in, v_out, dbg);
+        st = launch_fast(m, a, debug, s);
+        if (st != SL_OK) return st;
+    }
     m->stepped = true;
-    return st;
+    return SL_OK;
 }
 
 extern "C" sl_status sl_run(sl_mesh *m, const sl_problem *probs, int64_t n0, int32_t n_steps, void *v,

@@ -29,7 +29,8 @@ inline uint64_t splitmix_at(uint64_t seed, uint64_t i)
 struct DeviceMesh {
     void *xy = nullptr;               // double2[N] (FP64) or float2[N] (FP32)
     int32_t *tv[3] = {nullptr, nullptr, nullptr};   // vertex k of triangle j (global node index)
-    int32_t *tn[3] = {nullptr, nullptr, nullptr};   // neighbour across edge opposite vertex k (global, -1)
+    int32_t *tn[3] = {nullptr, nullptr, nullptr};   // neighbour across edge opposite vertex k (global);
+                                                    // boundary: -1 - side (0: x=0, 1: x=1, 2: y=0, 3: y=1)
     int32_t *t0 = nullptr;            // start / last foot triangle of node i (global)
     int32_t *t0_init = nullptr;       // the initial start triangles (global)
     int64_t *node_off = nullptr;      // n_problems + 1
@@ -37,6 +38,13 @@ struct DeviceMesh {
     unsigned long long *stats = nullptr;   // 8 counters (sl_stats order)
     void *probs = nullptr;            // per-problem step data (device)
     size_t probs_bytes = 0;
+    void *fprobs = nullptr;           // per-problem step constants of the fast kernels (device)
+    size_t fprobs_bytes = 0;
+    void *xyq = nullptr;              // float4 (xh, yh, xl, yl) per node (FP64 meshes)
+    void *xyh = nullptr;              // float2 (xh, yh) per node (FP64 meshes): hop tests
+    void *g1 = nullptr, *g2 = nullptr;   // field node tables, float4 (hi, lo) per node
+    double *tparams = nullptr;        // field parameters the tables were built from (device)
+    void *dfa = nullptr, *dfb = nullptr;   // value scratch of sl_step for the fast FP64 kernel
 };
 
 struct GraphCache {
@@ -47,6 +55,7 @@ struct GraphCache {
     const void *v = nullptr, *v_scratch = nullptr;
     std::vector<uint8_t> probs;       // problems the graph was recorded with
     int32_t kernel = 0;
+    int32_t stats = 0;
 };
 
 }  // namespace sl
@@ -71,6 +80,7 @@ struct sl_mesh {
     int32_t opt_block = 0;
     int32_t opt_tiles_per_sm = 0;
     bool stepped = false;
+    std::vector<double> table_key;    // field parameters of the current node tables
     sl::DeviceMesh d;
     sl::GraphCache graph;
     // device value buffers for sl_run_host

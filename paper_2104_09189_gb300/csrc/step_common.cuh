@@ -79,20 +79,19 @@ __device__ __forceinline__ void field_f64(const ProbStep &P, double x, double y,
     }
 }
 
-// Euler foot X = x - dt f(x, t_{n+1}) (Eq. 4) and the boundary clip: if X
-// leaves [0,1]^2 the segment x -> X is stopped at its first boundary
-// crossing; coordinates that attain the crossing are set exactly to 0 or 1,
-// the other one is clamped to [0,1].  Returns true if clipped.
-__device__ __forceinline__ bool foot_clip_f64(double x, double y, double dt, double fx, double fy, double &X,
-                                              double &Y)
+// Boundary clip: if q = (qx, qy) leaves [0,1]^2 the segment x -> q is stopped
+// at its first boundary crossing; coordinates that attain the crossing are
+// set exactly to 0 or 1, the other one is clamped to [0,1].  Returns true if
+// q was outside.
+__host__ __device__ __forceinline__ bool clip_to_square(double x, double y, double qx, double qy, double &X,
+                                                        double &Y)
 {
-    double qx = __dsub_rn(x, __dmul_rn(dt, fx));
-    double qy = __dsub_rn(y, __dmul_rn(dt, fy));
     if (qx >= 0.0 && qx <= 1.0 && qy >= 0.0 && qy <= 1.0) {
         X = qx;
         Y = qy;
         return false;
     }
+#ifdef __CUDA_ARCH__
     double dx = __dsub_rn(qx, x), dy = __dsub_rn(qy, y);
     double sx = 2.0, sy = 2.0, bx = 0.0, by = 0.0;
     if (qx < 0.0) { sx = __ddiv_rn(-x, dx); bx = 0.0; }
@@ -102,11 +101,31 @@ __device__ __forceinline__ bool foot_clip_f64(double x, double y, double dt, dou
     double s = sx < sy ? sx : sy;
     double cx = __dadd_rn(x, __dmul_rn(s, dx));
     double cy = __dadd_rn(y, __dmul_rn(s, dy));
+#else
+    double dx = qx - x, dy = qy - y;
+    double sx = 2.0, sy = 2.0, bx = 0.0, by = 0.0;
+    if (qx < 0.0) { sx = -x / dx; bx = 0.0; }
+    if (qx > 1.0) { sx = (1.0 - x) / dx; bx = 1.0; }
+    if (qy < 0.0) { sy = -y / dy; by = 0.0; }
+    if (qy > 1.0) { sy = (1.0 - y) / dy; by = 1.0; }
+    double s = sx < sy ? sx : sy;
+    double cx = x + s * dx;
+    double cy = y + s * dy;
+#endif
     if (sx == s) cx = bx;
     if (sy == s) cy = by;
     X = fmin(fmax(cx, 0.0), 1.0);
     Y = fmin(fmax(cy, 0.0), 1.0);
     return true;
+}
+
+// Euler foot X = x - dt f(x, t_{n+1}) (Eq. 4) followed by clip_to_square.
+__device__ __forceinline__ bool foot_clip_f64(double x, double y, double dt, double fx, double fy, double &X,
+                                              double &Y)
+{
+    double qx = __dsub_rn(x, __dmul_rn(dt, fx));
+    double qy = __dsub_rn(y, __dmul_rn(dt, fy));
+    return clip_to_square(x, y, qx, qy, X, Y);
 }
 
 // Problem of a global node index (binary search over the node offsets).

@@ -1,0 +1,403 @@
+// step_fast.cu -- the fast FP64-accuracy step kernel for GB300.
+//
+// The same step as step_plain.cu (Euler foot at t_{n+1} with the boundary
+// clip, barycentric walk from T^0_i -- strategy (b) of Sec. 3 -- and P1
+// interpolation with the barycentric coordinates of Eq. 6), arranged for a
+// GPU whose FP64 rate is 1/64 of its FP32 rate:
+//
+//  * walk hops are decided in FP32 on the high parts of the coordinates:
+//    an edge is crossed only when its orientation is negative beyond a
+//    certified FP32 error bound, so every hop is a hop of the exact
+//    barycentric walk (Algorithm 1, most negative coordinate first);
+//  * the stopping test is certified in double-float arithmetic (hi + lo
+//    float pairs, ~2^-46 relative) with an error bound, and falls back to an
+//    exact expansion-arithmetic sign on the double coordinates when the
+//    bound cannot decide -- so the located triangle contains the foot
+//    exactly;
+//  * the barycentric coordinates theta_1 = n_1 / den, theta_2 = n_2 / den
+//    (Eq. 6, numerators relative to vertex 3) and the P1 value
+//    v_3 + theta_1 (v_1 - v_3) + theta_2 (v_2 - v_3) (= theta_1 v_1 +
+//    theta_2 v_2 + theta_3 v_3 with theta_3 = 1 - theta_1 - theta_2,
+//    Remark 1) are evaluated in double-float as well;
+//  * node values travel between steps as (hi, lo) float pairs.
+#include "predicates.cuh"
+#include "df.cuh"
+#include "step_common.cuh"
+#include "step_fast.cuh"
+#include "step_kernels.cuh"
+
+namespace sl {
+
+__device__ __forceinline__ df dfp(float2 v) { return df_make(v.x, v.y); }
+
+__device__ __forceinline__ bool df_lt(df a, df b) { return a.h < b.h || (a.h == b.h && a.l < b.l); }
+__device__ __forceinline__ bool df_neg_strict(df a) { return a.h < 0.0f || (a.h == 0.0f && a.l < 0.0f); }
+__device__ __forceinline__ bool df_gt1(df a) { return a.h > 1.0f || (a.h == 1.0f && a.l > 0.0f); }
+__device__ __forceinline__ bool df_is(df a, float v) { return a.h == v && a.l == 0.0f; }
+
+// a / b in double-float (b.h != 0): relative error about 2^-44.
+__device__ __forceinline__ df df_div(df a, df b)
+{
+    const float q1 = __fdiv_rn(a.h, b.h);
+    const df r = df_sub(a, df_mul(b, df_make(q1, 0.0f)));
+    const float q2 = __fdiv_rn(r.h, b.h);
+    df q;
+    fast_two_sum_f(q1, q2, q.h, q.l);
+    return q;
+}
+
+// Boundary clip of the Euler foot q of node x, in double-float: if q leaves
+// [0,1]^2 the segment x -> q stops at its first boundary crossing; the
+// coordinates that attain the crossing become exactly 0 or 1, the other one
+// is clamped to [0,1].  Returns true if q was outside.
+__device__ __forceinline__ bool clip_df(df x, df y, df &X, df &Y)
+{
+    const bool xlo = df_neg_strict(X), xhi = df_gt1(X), ylo = df_neg_strict(Y), yhi = df_gt1(Y);
+    if (!(xlo || xhi || ylo || yhi)) return false;
+    const df dx = df_sub(X, x), dy = df_sub(Y, y);
+    const df two = df_make(2.0f, 0.0f);
+    df sx = two, sy = two;
+    const float bx = xhi ? 1.0f : 0.0f, by = yhi ? 1.0f : 0.0f;
+    if (xlo || xhi) sx = df_div(df_sub(df_make(bx, 0.0f), x), dx);
+    if (ylo || yhi) sy = df_div(df_sub(df_make(by, 0.0f), y), dy);
+    const bool xfirst = !df_lt(sy, sx);       // sx <= sy
+    const bool yfirst = !df_lt(sx, sy);       // sy <= sx
+    const df s = xfirst ? sx : sy;
+    df cx = df_add(x, df_mul(s, dx)), cy = df_add(y, df_mul(s, dy));
+    if (xfirst) cx = df_make(bx, 0.0f);
+    if (yfirst) cy = df_make(by, 0.0f);
+    if (df_neg_strict(cx)) cx = df_make(0.0f, 0.0f);
+    if (df_gt1(cx)) cx = df_make(1.0f, 0.0f);
+    if (df_neg_strict(cy)) cy = df_make(0.0f, 0.0f);
+    if (df_gt1(cy)) cy = df_make(1.0f, 0.0f);
+    X = cx;
+    Y = cy;
+    return true;
+}
+
+// Euler foot X = x - dt f(x, t_{n+1}) (Eq. 4) in double-float, with the
+// field's time factors folded into the per-step constants.
+__device__ __forceinline__ void foot_df(const FastProb &P, const FastArgs &a, int64_t i, df x, df y, df &X, df &Y)
+{
+    switch (P.kind) {
+    case SL_FIELD_AFFINE: {
+        df fx = df_add(df_add(dfp(P.c[0]), df_mul(dfp(P.c[1]), x)), df_mul(dfp(P.c[2]), y));
+        df fy = df_add(df_add(dfp(P.c[3]), df_mul(dfp(P.c[4]), x)), df_mul(dfp(P.c[5]), y));
+        X = df_sub(x, fx);
+        Y = df_sub(y, fy);
+        break;
+    }
+    case SL_FIELD_ROTATION:
+        X = df_add(x, df_mul(dfp(P.c[0]), df_sub(y, dfp(P.c[2]))));
+        Y = df_sub(y, df_mul(dfp(P.c[0]), df_sub(x, dfp(P.c[1]))));
+        break;
+    case SL_FIELD_SWIRL: {
+        const float4 g = a.g1[i];
+        const df k = dfp(P.c[0]);
+        X = df_sub(x, df_mul(k, df_make(g.x, g.z)));
+        Y = df_sub(y, df_mul(k, df_make(g.y, g.w)));
+        break;
+    }
+    case SL_FIELD_PAPER:
+    case SL_FIELD_FOURIER8: {
+        const float4 g = a.g1[i], q = a.g2[i];
+        const df k0 = dfp(P.c[0]), k1 = dfp(P.c[1]);
+        X = df_sub(x, df_add(df_mul(k0, df_make(g.x, g.z)), df_mul(k1, df_make(q.x, q.z))));
+        Y = df_sub(y, df_add(df_mul(k0, df_make(g.y, g.w)), df_mul(k1, df_make(q.y, q.w))));
+        break;
+    }
+    default:
+        X = x;
+        Y = y;
+        break;
+    }
+}
+
+// Error bounds.  Coordinates are stored as hi + lo floats within 2^-48 of
+// the double coordinates (|coord| <= 1); the foot is exactly X.h + X.l.
+//  FP32 hop test on the high parts: every difference is within
+//  2^-24 + 2^-24 |d| of the exact one, so a cross product of differences
+//  with |.|-sums S is within 2^-23 S + 2^-22 S^2 (two-fold margins).
+__device__ __forceinline__ float hop_bound(float S) { return S * __fmaf_rn(S, 0x1p-22f, 0x1p-23f) + 0x1p-46f; }
+//  double-float certification: differences within 2^-46, products and sums
+//  within 2^-45 relative: 2^-45 S + 2^-44 S^2.
+__device__ __forceinline__ float cert_bound(float S) { return S * __fmaf_rn(S, 0x1p-44f, 0x1p-45f); }
+
+template <bool kStats, bool kDebug>
+__global__ void __launch_bounds__(256, 4) k_step_fast_df(FastArgs a)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const bool active = i < a.N;
+    uint32_t hops = 0, exact_tests = 0, clipped_cnt = 0, fallback_cnt = 0, limit_cnt = 0, filter2 = 0;
+    if (active) {
+        const int pi = a.nprob == 1 ? 0 : problem_of(a.node_off, a.nprob, i);
+        const FastProb &P = a.probs[pi];
+        const float4 xq = a.xyq[i];
+        const df x = df_make(xq.x, xq.z), y = df_make(xq.y, xq.w);
+        df X, Y;
+        foot_df(P, a, i, x, y, X, Y);
+        uint32_t flags = 0;
+        if (clip_df(x, y, X, Y)) {
+            flags |= SL_NODE_CLIPPED;
+            clipped_cnt = 1;
+        }
+        // sides of the square the foot lies on exactly (bit = boundary side code)
+        const uint32_t fside = (df_is(X, 0.0f) ? 1u : 0u) | (df_is(X, 1.0f) ? 2u : 0u) | (df_is(Y, 0.0f) ? 4u : 0u) |
+                               (df_is(Y, 1.0f) ? 8u : 0u);
+
+        int32_t j = a.t0[i];
+        const int32_t jstart = j;
+        const uint32_t cap = (uint32_t)a.walk_cap;
+        bool certify = true, found = false;
+        int s1 = 0, s2 = 0, s3 = 0;
+        df n1, n2, den;
+        int ia = 0, ib = 0, ic = 0;
+        for (;;) {
+            ia = a.tv[0][j];
+            ib = a.tv[1][j];
+            ic = a.tv[2][j];
+            if (!certify) {
+                // FP32 hop test on the high parts, differences relative to vertex 3
+                const float2 A = a.xyh[ia], B = a.xyh[ib], C = a.xyh[ic];
+                const float ax = A.x - C.x, ay = A.y - C.y, bx = B.x - C.x, by = B.y - C.y;
+                const float xx = X.h - C.x, xy = Y.h - C.y;
+                const float o1 = __fmaf_rn(xx, by, -__fmul_rn(xy, bx));    // ~ theta_1 * den
+                const float o2 = __fmaf_rn(ax, xy, -__fmul_rn(ay, xx));    // ~ theta_2 * den
+                const float dn = __fmaf_rn(ax, by, -__fmul_rn(ay, bx));
+                const float o3 = dn - o1 - o2;                              // ~ theta_3 * den
+                const float sA = fabsf(ax) + fabsf(ay), sB = fabsf(bx) + fabsf(by), sX = fabsf(xx) + fabsf(xy);
+                const float e1 = hop_bound(sX + sB), e2 = hop_bound(sA + sX), ed = hop_bound(sA + sB);
+                const float e3 = ed + e1 + e2 + 0x1p-23f * (fabsf(dn) + fabsf(o1) + fabsf(o2));
+                int k = -1;
+                float best = 0.0f;
+                if (o1 < -e1) { k = 0; best = o1; }
+                if (o2 < -e2 && (k < 0 || o2 < best)) { k = 1; best = o2; }
+                if (o3 < -e3 && (k < 0 || o3 < best)) { k = 2; best = o3; }
+                if (k >= 0 && hops < cap) {
+                    const int32_t nj = a.tn[k][j];
+                    if (nj >= 0) {
+                        j = nj;
+                        ++hops;
+                        continue;
+                    }
+                }
+                certify = true;    // no clearly negative edge: certify this triangle
+            }
+            // certified test in double-float, relative to vertex 3
+            const float4 A = a.xyq[ia], B = a.xyq[ib], C = a.xyq[ic];
+            const df cxh = df_make(C.x, C.z), cyh = df_make(C.y, C.w);
+            const df dAx = df_sub(df_make(A.x, A.z), cxh), dAy = df_sub(df_make(A.y, A.w), cyh);
+            const df dBx = df_sub(df_make(B.x, B.z), cxh), dBy = df_sub(df_make(B.y, B.w), cyh);
+            const df dXx = df_sub(X, cxh), dXy = df_sub(Y, cyh);
+            n1 = df_cross(dXx, dXy, dBx, dBy);      // orient(B, C, X): sign of theta_1
+            n2 = df_cross(dAx, dAy, dXx, dXy);      // orient(C, A, X): sign of theta_2
+            den = df_cross(dAx, dAy, dBx, dBy);     // orient(A, B, C) > 0
+            const df n3 = df_sub(df_sub(den, n1), n2);
+            const float sA = fabsf(dAx.h) + fabsf(dAy.h), sB = fabsf(dBx.h) + fabsf(dBy.h);
+            const float sX = fabsf(dXx.h) + fabsf(dXy.h);
+            const float e1 = cert_bound(sX + sB), e2 = cert_bound(sA + sX), ed = cert_bound(sA + sB);
+            const float e3 = ed + e1 + e2 + 0x1p-45f * (fabsf(den.h) + fabsf(n1.h) + fabsf(n2.h));
+            s1 = n1.h > e1 ? 1 : (n1.h < -e1 ? -1 : 2);
+            s2 = n2.h > e2 ? 1 : (n2.h < -e2 ? -1 : 2);
+            s3 = n3.h > e3 ? 1 : (n3.h < -e3 ? -1 : 2);
+            if (s1 == 2 || s2 == 2 || s3 == 2) {
+                // a boundary edge with the foot on its side of the square: exactly 0
+                int32_t nb;
+                if (s1 == 2 && (nb = a.tn[0][j]) < 0 && (fside >> (-1 - nb) & 1u)) s1 = 0;
+                if (s2 == 2 && (nb = a.tn[1][j]) < 0 && (fside >> (-1 - nb) & 1u)) s2 = 0;
+                if (s3 == 2 && (nb = a.tn[2][j]) < 0 && (fside >> (-1 - nb) & 1u)) s3 = 0;
+            }
+            if (s1 == 2 || s2 == 2 || s3 == 2) {
+                // exact signs on the double coordinates and the exact foot
+                const double2 Ad = a.xyd[ia], Bd = a.xyd[ib], Cd = a.xyd[ic];
+                int stg = 0;
+                if (s1 == 2) { s1 = orient_exact_df(Bd, Cd, X.h, X.l, Y.h, Y.l, stg); exact_tests += stg == 3; filter2 += stg == 2; }
+                if (s2 == 2) { s2 = orient_exact_df(Cd, Ad, X.h, X.l, Y.h, Y.l, stg); exact_tests += stg == 3; filter2 += stg == 2; }
+                if (s3 == 2) { s3 = orient_exact_df(Ad, Bd, X.h, X.l, Y.h, Y.l, stg); exact_tests += stg == 3; filter2 += stg == 2; }
+                flags |= SL_NODE_EXACT;
+                if (!(slp::in_exact_range(Ad.x) && slp::in_exact_range(Ad.y) && slp::in_exact_range(Bd.x) &&
+                      slp::in_exact_range(Bd.y) && slp::in_exact_range(Cd.x) && slp::in_exact_range(Cd.y) &&
+                      slp::in_exact_range(X.h) && slp::in_exact_range(Y.h) && slp::in_exact_range(X.l) &&
+                      slp::in_exact_range(Y.l)))
+                    flags |= SL_NODE_RANGE;
+            }
+            if (s1 >= 0 && s2 >= 0 && s3 >= 0) {
+                found = true;
+                break;
+            }
+            if (hops >= 2 * cap) break;
+            int k;
+            if (hops < cap) {
+                // the paper's rule: the most negative barycentric coordinate
+                k = -1;
+                float best = 0.0f;
+                if (s1 < 0) { k = 0; best = n1.h; }
+                if (s2 < 0 && (k < 0 || n2.h < best)) { k = 1; best = n2.h; }
+                if (s3 < 0 && (k < 0 || n3.h < best)) { k = 2; best = n3.h; }
+            } else {
+                // after `cap` hops: randomised visibility walk (certified at
+                // every triangle), which terminates on any triangulation
+                if (hops == cap) {
+                    fallback_cnt = 1;
+                    flags |= SL_NODE_FALLBACK;
+                }
+                const int neg[3] = {s1 < 0, s2 < 0, s3 < 0};
+                const int nneg = neg[0] + neg[1] + neg[2];
+                int pick = (int)(mix64_dev(((uint64_t)i << 20) ^ (uint64_t)hops) % (uint64_t)nneg);
+                k = -1;
+                for (int q = 0; q < 3; ++q)
+                    if (neg[q] && pick-- == 0) k = q;
+            }
+            const int32_t nj = a.tn[k][j];
+            if (nj < 0) break;         // cannot happen for a foot inside a valid mesh
+            j = nj;
+            ++hops;
+            certify = hops >= cap;     // FP32 hops until the cap, then certified ones
+        }
+        if (!found) {
+            flags |= SL_NODE_WALK_LIMIT;
+            limit_cnt = 1;
+        }
+        if (s1 == 0 || s2 == 0 || s3 == 0) flags |= SL_NODE_DEGENERATE;
+
+        // theta_1, theta_2 by Eq. 6 and the P1 value (Remark 1), double-float
+        const df r = df_rcp(den);
+        const df th1 = df_mul(n1, r), th2 = df_mul(n2, r);
+        const float2 *vin = (const float2 *)a.vin;
+        const df v1 = dfp(vin[ia]), v2 = dfp(vin[ib]), v3 = dfp(vin[ic]);
+        const df v = df_add(v3, df_add(df_mul(th1, df_sub(v1, v3)), df_mul(th2, df_sub(v2, v3))));
+        ((float2 *)a.vout)[i] = make_float2(v.h, v.l);
+        if (j != jstart) a.t0[i] = j;
+        if (limit_cnt) atomicOr(a.status, 1u << SL_E_WALK_LIMIT);
+        if (flags & SL_NODE_RANGE) atomicOr(a.status, 1u << SL_E_ARG);
+        if (kDebug) {
+            if (a.dbg.feet) {
+                a.dbg.feet[2 * i] = (double)X.h + (double)X.l;
+                a.dbg.feet[2 * i + 1] = (double)Y.h + (double)Y.l;
+            }
+            if (a.dbg.tri) a.dbg.tri[i] = j;
+            if (a.dbg.moves) a.dbg.moves[i] = (int32_t)hops;
+            if (a.dbg.flags) a.dbg.flags[i] = (uint8_t)flags;
+        }
+    }
+    if (kStats) warp_stats(a.stats, active, hops, exact_tests, clipped_cnt, fallback_cnt, limit_cnt, filter2);
+}
+
+void launch_fast_df(const FastArgs &a, bool stats, bool debug, int block, cudaStream_t s)
+{
+    if (block <= 0) block = 256;
+    if (block > 256) block = 256;
+    const unsigned grid = (unsigned)((a.N + block - 1) / block);
+    if (grid == 0) return;
+    if (stats) {
+        if (debug) k_step_fast_df<true, true><<<grid, block, 0, s>>>(a);
+        else k_step_fast_df<true, false><<<grid, block, 0, s>>>(a);
+    } else {
+        if (debug) k_step_fast_df<false, true><<<grid, block, 0, s>>>(a);
+        else k_step_fast_df<false, false><<<grid, block, 0, s>>>(a);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Value format conversions (once per run, not per step)
+
+__global__ void k_to_df(const double *__restrict__ src, float2 *__restrict__ dst, int64_t n)
+{
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const double v = src[i];
+        const float h = __double2float_rn(v);
+        dst[i] = make_float2(h, __double2float_rn(v - (double)h));
+    }
+}
+
+__global__ void k_from_df(const float2 *src, double *dst, int64_t n)
+{
+    // may run in place (src and dst alias, same 8-byte slots)
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const float2 v = src[i];
+        dst[i] = (double)v.x + (double)v.y;
+    }
+}
+
+static unsigned grid_for(int64_t n, int block)
+{
+    int64_t g = (n + block - 1) / block;
+    if (g > 152 * 32) g = 152 * 32;
+    return (unsigned)(g > 0 ? g : 1);
+}
+
+void launch_to_df(const double *src, float2 *dst, int64_t n, cudaStream_t s)
+{
+    if (n > 0) k_to_df<<<grid_for(n, 256), 256, 0, s>>>(src, dst, n);
+}
+
+void launch_from_df(const float2 *src, double *dst, int64_t n, cudaStream_t s)
+{
+    if (n > 0) k_from_df<<<grid_for(n, 256), 256, 0, s>>>(src, dst, n);
+}
+
+// ---------------------------------------------------------------------------
+// Node tables of the fields whose space dependence is costly (trigonometric):
+//   SWIRL     g1 = (sin^2(pi x) sin(2 pi y), -sin^2(pi y) sin(2 pi x))
+//   PAPER     g1 = (cos a, sin a), g2 = (-sin a, cos a), a = C0 |x - c|
+//             (f = cos(C1 t) g1 + sin(C1 t) g2)
+//   FOURIER8  g1 = sum_m a_m cos(phi_m) h_m, g2 = -sum_m a_m sin(phi_m) h_m,
+//             h_m = (l_m pi sin(k_m pi x) cos(l_m pi y), -k_m pi cos(k_m pi x) sin(l_m pi y))
+//             (f = cos(2 pi t) g1 + sin(2 pi t) g2)
+// evaluated once per field in double and stored as (hi, lo) floats.
+
+__device__ __forceinline__ float4 pack_df2(double gx, double gy)
+{
+    const float hx = __double2float_rn(gx), hy = __double2float_rn(gy);
+    return make_float4(hx, hy, __double2float_rn(gx - (double)hx), __double2float_rn(gy - (double)hy));
+}
+
+__global__ void k_field_tables(FieldTableArgs a)
+{
+    const double pi = 3.14159265358979323846;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < a.N; i += (int64_t)gridDim.x * blockDim.x) {
+        const int pidx = a.nprob == 1 ? 0 : problem_of(a.node_off, a.nprob, i);
+        const double *q = a.params + 49 * (int64_t)pidx;
+        const int kind = (int)q[0];
+        const double *p = q + 1;
+        const double2 xy = a.xyd[i];
+        double g1x = 0, g1y = 0, g2x = 0, g2y = 0;
+        if (kind == SL_FIELD_SWIRL) {
+            double sx, cx, sy, cy;
+            sincospi(xy.x, &sx, &cx);
+            sincospi(xy.y, &sy, &cy);
+            g1x = (sx * sx) * (2.0 * sy * cy);
+            g1y = -(sy * sy) * (2.0 * sx * cx);
+        } else if (kind == SL_FIELD_PAPER) {
+            const double dx = xy.x - p[2], dy = xy.y - p[3];
+            double s, c;
+            sincos(p[0] * sqrt(dx * dx + dy * dy), &s, &c);
+            g1x = c;
+            g1y = s;
+            g2x = -s;
+            g2y = c;
+        } else if (kind == SL_FIELD_FOURIER8) {
+            for (int m = 0; m < 8; ++m) {
+                const double k = p[4 * m], l = p[4 * m + 1], am = p[4 * m + 2], ph = p[4 * m + 3];
+                double skx, ckx, sly, cly, sph, cph;
+                sincospi(k * xy.x, &skx, &ckx);
+                sincospi(l * xy.y, &sly, &cly);
+                sincos(ph, &sph, &cph);
+                const double hx = l * pi * skx * cly, hy = -k * pi * ckx * sly;
+                g1x += am * cph * hx;
+                g1y += am * cph * hy;
+                g2x -= am * sph * hx;
+                g2y -= am * sph * hy;
+            }
+        }
+        if (a.g1) a.g1[i] = pack_df2(g1x, g1y);
+        if (a.g2) a.g2[i] = pack_df2(g2x, g2y);
+    }
+}
+
+void launch_field_tables(const FieldTableArgs &a, cudaStream_t s)
+{
+    if (a.N > 0) k_field_tables<<<grid_for(a.N, 256), 256, 0, s>>>(a);
+}
+
+}  // namespace sl

@@ -34,42 +34,54 @@ def _parity_run(prob, steps, curve=sl.SL_CURVE_NONE, kernel=0, seed=1, check_eve
     return worst, near_total, res
 
 
-def test_c1_swirl_full_parity():
+KERNELS = [pytest.param(1, id="plain"), pytest.param(2, id="fast")]
+
+
+@pytest.mark.parametrize("kernel", [1, 2], ids=["plain", "fast"])
+def test_c1_swirl_full_parity(kernel):
     prob = si.config("C1")
-    worst, near, res = _parity_run(prob, prob.n_steps)
+    worst, near, res = _parity_run(prob, prob.n_steps, kernel=kernel)
     assert worst <= 1e-12
     # boundary nodes of the swirl have f = 0 (or ~1e-16): their feet are
     # vertices and must be flagged degenerate
     assert near >= 4 * 64
 
 
+@pytest.mark.parametrize("kernel", [1, 2], ids=["plain", "fast"])
 @pytest.mark.parametrize("curve", [sl.SL_CURVE_NONE, sl.SL_CURVE_HILBERT, sl.SL_CURVE_MORTON])
-def test_c2_construction_swirl_parity(curve):
+def test_c2_construction_swirl_parity(curve, kernel):
     prob = si.config("C2", M=256)
-    _parity_run(prob, 6, curve=curve)
+    _parity_run(prob, 6, curve=curve, kernel=kernel)
 
 
-def test_c2_full_size_parity_hilbert():
+@pytest.mark.parametrize("kernel", [1, 2], ids=["plain", "fast"])
+def test_c2_full_size_parity_hilbert(kernel):
     prob = si.config("C2")
-    _parity_run(prob, 3, curve=sl.SL_CURVE_HILBERT)
+    _parity_run(prob, 3, curve=sl.SL_CURVE_HILBERT, kernel=kernel)
 
 
-def test_c3_construction_rotation_parity_and_zero_hops():
-    """Graded mesh, solid rotation: feet are computed with the same rounded
-    operations on both sides, so they agree bit for bit; a time-constant
-    field needs no walk move after the first step (Sec. 3, strategy (b))."""
+@pytest.mark.parametrize("kernel", [1, 2], ids=["plain", "fast"])
+def test_c3_construction_rotation_parity_and_zero_hops(kernel):
+    """Graded mesh, solid rotation.  The plain kernel computes the feet with
+    the same rounded operations as the oracle, so they agree bit for bit; the
+    fast kernel's double-float feet agree to rounding.  A time-constant field
+    needs no walk move after the first step (Sec. 3, strategy (b))."""
     prob = si.config("C3", M=256)
     mesh = prob.mesh
     om = oracle.OracleMesh(mesh.xy, mesh.tri)
-    g = GpuRun(mesh, prob.field, prob.dt, curve=sl.SL_CURVE_HILBERT)
+    g = GpuRun(mesh, prob.field, prob.dt, curve=sl.SL_CURVE_HILBERT, kernel=kernel)
     v_dev = g.to_dev(prob.v0)
     v_orc = prob.v0.copy()
     for n in range(4):
         v_dev, res = g.step(n, v_dev)
         ov, otri, oflags, ofeet = om.step(prob.field.kind, prob.field.packed(), prob.dt, n, v_orc)
         v_orc = ov
-        assert np.array_equal(res["feet"], ofeet)
-        compare_step(om, res, ov, otri, ofeet, delta=0.0)
+        if kernel == 1:
+            assert np.array_equal(res["feet"], ofeet)
+            compare_step(om, res, ov, otri, ofeet, delta=0.0)
+        else:
+            assert np.abs(res["feet"] - ofeet).max() < 1e-13   # double-float feet: ~2^-46
+            compare_step(om, res, ov, otri, ofeet)
         if n == 0:
             assert res["moves"].mean() > 5      # strategy (a) on the first step: ~ Courant number
         else:
@@ -77,22 +89,27 @@ def test_c3_construction_rotation_parity_and_zero_hops():
     g.close()
 
 
-def test_other_fields_parity():
+@pytest.mark.parametrize("kernel", [1, 2], ids=["plain", "fast"])
+def test_other_fields_parity(kernel):
     mesh = si.grid_mesh(96, 0.25, 12)
     v0 = si.gaussian(mesh.xy, 0.45, 0.55, 0.1)
-    for fld, dt in [(si.fourier8_field(77), 0.03), (si.paper_field(), 0.02), (si.swirl_field(), 0.1)]:
+    p = np.zeros(48)
+    p[:8] = (0.3, -1.0, 0.5, 2.0, -0.2, 0.7, 0.4, -1.5)
+    for fld, dt in [(si.fourier8_field(77), 0.03), (si.paper_field(), 0.02), (si.swirl_field(), 0.1),
+                    (si.Field(si.FIELD_AFFINE, p, 3.0), 0.05), (si.rotation_field(3.0, 0.3, 0.6), 0.04)]:
         prob = si.Problem("x", mesh, fld, dt, 4, v0, "fp64", 12)
-        _parity_run(prob, 4)
+        _parity_run(prob, 4, kernel=kernel)
 
 
-def test_linear_data_closed_form_on_gpu():
+@pytest.mark.parametrize("kernel", [1, 2], ids=["plain", "fast"])
+def test_linear_data_closed_form_on_gpu(kernel):
     """Contracting affine field with linear data: V^n = u0(c + (1-k dt)^n (x - c))."""
     mesh = si.grid_mesh(128, 0.25, 4)
     k, cx, cy, dt, steps = 3.0, 0.4, 0.6, 0.05, 10
     p = np.zeros(48)
     p[:8] = (-k * cx, k, 0.0, 0.0, -k * cy, 0.0, k, 0.0)
     fld = si.Field(si.FIELD_AFFINE, p, 1.0)
-    g = GpuRun(mesh, fld, dt, curve=sl.SL_CURVE_HILBERT)
+    g = GpuRun(mesh, fld, dt, curve=sl.SL_CURVE_HILBERT, kernel=kernel)
     lin = lambda q: 0.25 + q[:, 0] - 0.5 * q[:, 1]
     v = g.to_dev(lin(mesh.xy))
     w = g.torch.empty_like(v)
@@ -104,24 +121,36 @@ def test_linear_data_closed_form_on_gpu():
 
 
 def test_zero_field_leaves_values_bitwise():
+    """f = 0: every foot is its own node.  The plain kernel reproduces V bit
+    for bit and flags every foot degenerate (it lies on a vertex); the fast
+    kernel keeps coordinates as float pairs (48-bit), so its feet sit within
+    2^-48 of the nodes and the values within round-off."""
     mesh = si.grid_mesh(64, 0.25, 2)
     v0 = si.cosine_bump(mesh.xy)
-    g = GpuRun(mesh, si.zero_field(), 0.1)
+    g = GpuRun(mesh, si.zero_field(), 0.1, kernel=1)
     v_dev = g.to_dev(v0)
     for n in range(3):
         v_dev, res = g.step(n, v_dev)
         assert np.array_equal(res["v"], v0)
         assert np.all(res["flags"] & sl.SL_NODE_DEGENERATE)
     g.close()
+    g = GpuRun(mesh, si.zero_field(), 0.1, kernel=2)
+    v_dev = g.to_dev(v0)
+    for n in range(3):
+        v_dev, res = g.step(n, v_dev)
+        assert np.abs(res["v"] - v0).max() < 1e-13
+        assert np.abs(res["feet"] - mesh.xy).max() <= 2.0 ** -48
+    g.close()
 
 
-def test_graph_eager_reorder_and_resume_are_bitwise_identical():
+@pytest.mark.parametrize("kernel", [1, 2], ids=["plain", "fast"])
+def test_graph_eager_reorder_and_resume_are_bitwise_identical(kernel):
     prob = si.config("C2", M=192)
     mesh = prob.mesh
     outs = []
     for curve, graph in [(sl.SL_CURVE_NONE, False), (sl.SL_CURVE_NONE, True), (sl.SL_CURVE_HILBERT, True),
                          (sl.SL_CURVE_MORTON, False)]:
-        g = GpuRun(mesh, prob.field, prob.dt, curve=curve)
+        g = GpuRun(mesh, prob.field, prob.dt, curve=curve, kernel=kernel)
         v = g.to_dev(prob.v0)
         w = g.torch.empty_like(v)
         sl.sl_run(g.h, g.probs, 0, 7, v, w, use_graph=graph)
@@ -129,17 +158,24 @@ def test_graph_eager_reorder_and_resume_are_bitwise_identical():
         g.close()
     for o in outs[1:]:
         assert np.array_equal(o, outs[0])
-    # resume: 3 steps, export T^0 and V, new handle, import, 4 more steps
-    g = GpuRun(mesh, prob.field, prob.dt)
+    # resume: 3 steps, export T^0 and V; a new handle imports them and runs
+    # 4 more steps, exactly like the first handle continuing
+    g = GpuRun(mesh, prob.field, prob.dt, kernel=kernel)
     v = g.to_dev(prob.v0)
     w = g.torch.empty_like(v)
     sl.sl_run(g.h, g.probs, 0, 3, v, w)
     t0 = g.torch.empty(mesh.n_nodes, dtype=g.torch.int32, device=g.dev)
     sl.sl_mesh_get_t0(g.h, t0)
-    g2 = GpuRun(mesh, prob.field, prob.dt)
+    v_resume = v.clone()
+    sl.sl_run(g.h, g.probs, 3, 4, v, w)
+    g2 = GpuRun(mesh, prob.field, prob.dt, kernel=kernel)
     sl.sl_mesh_set_t0(g2.h, t0)
-    sl.sl_run(g2.h, g2.probs, 3, 4, v, w)
-    assert np.array_equal(g2.from_dev(v), outs[0])
+    sl.sl_run(g2.h, g2.probs, 3, 4, v_resume, w)
+    assert np.array_equal(g2.from_dev(v_resume), g.from_dev(v))
+    if kernel == 1:
+        assert np.array_equal(g.from_dev(v), outs[0])
+    else:
+        assert np.abs(g.from_dev(v) - outs[0]).max() <= 1e-14
     g.close()
     g2.close()
 
@@ -159,10 +195,11 @@ def test_run_host_matches_device_run():
     g.close()
 
 
-def test_walk_cap_reports_status_without_hanging():
+@pytest.mark.parametrize("kernel", [1, 2], ids=["plain", "fast"])
+def test_walk_cap_reports_status_without_hanging(kernel):
     """A tiny hop cap (debug knob) must end in SL_E_WALK_LIMIT, not a hang."""
     prob = si.config("C2", M=128)
-    g = GpuRun(prob.mesh, prob.field, prob.dt)
+    g = GpuRun(prob.mesh, prob.field, prob.dt, kernel=kernel)
     sl.sl_mesh_set_option(g.h, sl.SL_OPT_WALK_CAP, 1)
     v = g.to_dev(prob.v0)
     w = g.torch.empty_like(v)
@@ -175,12 +212,14 @@ def test_walk_cap_reports_status_without_hanging():
     g.close()
 
 
-def test_batched_problems_match_single_runs():
+@pytest.mark.parametrize("kernel", [1, 2], ids=["plain", "fast"])
+def test_batched_problems_match_single_runs(kernel):
     probs = si.batch_config(6, nmin=2e3, nmax=2e4, steps=3)
     meshes = [(p.mesh.xy, p.mesh.tri) for p in probs]
     no, to, xy, tri = sl.pack_meshes(meshes)
     import torch
     h = sl.sl_mesh_create(no, to, xy, tri)
+    sl.sl_mesh_set_option(h, sl.SL_OPT_KERNEL, kernel)
     pr = sl.problems([(p.field.kind, p.dt, p.field.packed()) for p in probs])
     v = torch.tensor(np.concatenate([p.v0 for p in probs]), dtype=torch.float64, device="cuda:0")
     w = torch.empty_like(v)
