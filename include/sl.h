@@ -216,6 +216,40 @@ sl_status sl_run(sl_mesh *m, const sl_problem *probs, int64_t n0, int32_t n_step
 sl_status sl_run_host(sl_mesh *m, const sl_problem *probs, int64_t n0, int32_t n_steps, void *v_host,
                       int32_t use_graph, sl_stats *stats, void *stream);
 
+/* Limits of sl_step_noalloc's static scratch (see below). */
+#define SL_NOALLOC_MAX_NODES (1 << 20)
+#define SL_NOALLOC_MAX_PROBLEMS 256
+
+/*
+ * sl_step_noalloc -- the same step as sl_step for FP64 meshes (double values
+ * in and out), performing no device allocation.  The paper has no
+ * counterpart: this exists for callers that cannot allocate device memory
+ * while they step -- code running inside a host application whose caching
+ * allocator owns the device memory, callbacks that must not synchronise the
+ * device (cudaMalloc and cudaFree do), or programs with a fixed memory
+ * budget reserved at start-up.
+ *
+ *   probs   host, n_problems entries (at most SL_NOALLOC_MAX_PROBLEMS)
+ *   v_in    device, N doubles V^n
+ *   v_out   device, N doubles V^{n+1}; must not alias v_in
+ * The mesh must have at most SL_NOALLOC_MAX_NODES nodes (over all problems)
+ * and must be an FP64 mesh; otherwise SL_E_ARG with a message naming the
+ * limit.  Fields with node tables (SWIRL, PAPER, FOURIER8) need the tables
+ * already built for these exact problems by an earlier sl_step / sl_run call
+ * on the mesh (that call allocates them); otherwise SL_E_STATE.
+ *
+ * All scratch lives in one library-owned static device array per GPU
+ * (8 MiB of value pairs + 16 KiB of per-problem constants), held by every
+ * GPU that loads the library until the process exits.  The first call on a
+ * device looks up the array's device address (cudaGetSymbolAddress); make
+ * that first call before any stream capture.  Every call on a device shares
+ * the array and overwrites what it uses, so calls that overlap on the GPU
+ * (other streams, other meshes) race on it: serialise them.  T^0 is updated
+ * in place as in sl_step; device conditions are reported by sl_mesh_status.
+ */
+sl_status sl_step_noalloc(sl_mesh *m, const sl_problem *probs, int64_t n, const double *v_in, double *v_out,
+                          void *stream);
+
 /* T^0 export / import (device, N int32 global triangle indices in current
  * numbering); with V^n this is the whole state of a run (resume). */
 sl_status sl_mesh_get_t0(const sl_mesh *m, int32_t *t0_dev, void *stream);

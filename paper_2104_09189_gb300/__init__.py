@@ -22,7 +22,8 @@ __all__ = [
     "SL_NODE_RANGE", "SLError", "sl_problem", "problems", "pack_meshes",
     "sl_mesh_create", "sl_mesh_validate", "sl_mesh_reorder", "sl_step", "sl_run", "sl_run_host", "sl_mesh_get_t0",
     "sl_mesh_set_t0", "sl_mesh_reset_t0", "sl_mesh_status", "sl_mesh_stats", "sl_mesh_set_option", "sl_mesh_info",
-    "sl_mesh_export", "sl_mesh_destroy", "sl_last_error", "library", "EXPORTED",
+    "sl_mesh_export", "sl_mesh_destroy", "sl_last_error", "library", "EXPORTED", "sl_step_noalloc",
+    "SL_NOALLOC_MAX_NODES", "SL_NOALLOC_MAX_PROBLEMS",
 ]
 
 SL_OK, SL_E_ARG, SL_E_MESH, SL_E_NOMEM, SL_E_CUDA, SL_E_WALK_LIMIT, SL_E_STATE = range(7)
@@ -32,6 +33,8 @@ SL_OPT_STATS, SL_OPT_WALK_CAP, SL_OPT_KERNEL, SL_OPT_BLOCK, SL_OPT_TILES_PER_SM 
 SL_NODE_CLIPPED, SL_NODE_DEGENERATE, SL_NODE_EXACT, SL_NODE_FALLBACK, SL_NODE_WALK_LIMIT, SL_NODE_RANGE = (
     1, 2, 4, 8, 16, 32)
 SL_NPARAMS = 48
+SL_NOALLOC_MAX_NODES = 1 << 20
+SL_NOALLOC_MAX_PROBLEMS = 256
 
 _STATUS_NAMES = {0: "SL_OK", 1: "SL_E_ARG", 2: "SL_E_MESH", 3: "SL_E_NOMEM", 4: "SL_E_CUDA",
                  5: "SL_E_WALK_LIMIT", 6: "SL_E_STATE"}
@@ -39,7 +42,7 @@ _STATUS_NAMES = {0: "SL_OK", 1: "SL_E_ARG", 2: "SL_E_MESH", 3: "SL_E_NOMEM", 4: 
 # every entry point declared in include/sl.h
 EXPORTED = ("sl_mesh_create", "sl_mesh_validate", "sl_mesh_reorder", "sl_step", "sl_run", "sl_run_host", "sl_mesh_get_t0",
             "sl_mesh_set_t0", "sl_mesh_reset_t0", "sl_mesh_status", "sl_mesh_stats", "sl_mesh_set_option", "sl_mesh_info",
-            "sl_mesh_export", "sl_mesh_destroy", "sl_last_error")
+            "sl_mesh_export", "sl_mesh_destroy", "sl_last_error", "sl_step_noalloc")
 
 
 class SLError(RuntimeError):
@@ -94,6 +97,7 @@ def library():
         "sl_mesh_set_option": [P, I32, I64],
         "sl_mesh_info": [P, P, P, P, P],
         "sl_mesh_export": [P, P, P, P],
+        "sl_step_noalloc": [P, P, I64, P, P, P],
     }
     for name, args in sig.items():
         f = getattr(L, name)
@@ -280,3 +284,11 @@ def sl_mesh_set_option(h, option, value):
 def sl_mesh_destroy(h):
     if h:
         library().sl_mesh_destroy(h)
+
+
+def sl_step_noalloc(h, probs, n, v_in, v_out, stream=None):
+    """sl_step without any device allocation (FP64 meshes, double tensors);
+    its scratch is a fixed static device array of the library (meshes of at
+    most SL_NOALLOC_MAX_NODES nodes).  For callers that cannot allocate device
+    memory while stepping."""
+    _check(library().sl_step_noalloc(h, probs, int(n), _ptr(v_in), _ptr(v_out), _stream(stream)))
