@@ -118,9 +118,11 @@ typedef struct {
 typedef enum {
     SL_OPT_STATS = 0,        /* 0/1: accumulate sl_stats counters (default 0) */
     SL_OPT_WALK_CAP = 1,     /* hops before the fallback rule (default max(64, 4 (M+1))) */
-    SL_OPT_KERNEL = 2,       /* 0 = auto, 1 = plain FP64 reference kernel, 2 = tiled kernel */
+    SL_OPT_KERNEL = 2,       /* 0 = auto (fast), 1 = plain FP64 kernel, 2 = fast kernel */
     SL_OPT_BLOCK = 3,        /* threads per block (0 = auto) */
-    SL_OPT_TILES_PER_SM = 4  /* resident tiles (CTAs) per SM for the persistent kernel (0 = auto) */
+    SL_OPT_TILES_PER_SM = 4, /* reserved */
+    SL_OPT_CONFIG = 5        /* launch configuration of the fast kernels, 0..3:
+                                threads per block x blocks per SM = 256x4, 256x3, 128x8, 128x6 */
 } sl_option;
 
 /*

@@ -311,7 +311,7 @@ static sl_status launch_step(const sl_mesh *m, const StepArgs &a, bool debug, cu
 
 static sl_status launch_fast(const sl_mesh *m, const FastArgs &a, bool debug, cudaStream_t s)
 {
-    if (m->precision == SL_FP64) launch_fast_df(a, m->opt_stats != 0, debug, m->opt_block, s);
+    if (m->precision == SL_FP64) launch_fast_df(a, m->opt_stats != 0, debug, m->opt_config, s);
     else return fail(SL_E_STATE, "no FP32 kernel is built into this library yet");
     SL_CUDA(cudaGetLastError());
     return SL_OK;

@@ -79,6 +79,7 @@ struct sl_mesh {
     int32_t opt_kernel = 0;
     int32_t opt_block = 0;
     int32_t opt_tiles_per_sm = 0;
+    int32_t opt_config = 0;           // launch configuration of the fast kernels
     bool stepped = false;
     std::vector<double> table_key;    // field parameters of the current node tables
     sl::DeviceMesh d;

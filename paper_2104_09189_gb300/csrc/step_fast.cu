@@ -117,14 +117,16 @@ __device__ __forceinline__ void foot_df(const FastProb &P, const FastArgs &a, in
 // the double coordinates (|coord| <= 1); the foot is exactly X.h + X.l.
 //  FP32 hop test on the high parts: every difference is within
 //  2^-24 + 2^-24 |d| of the exact one, so a cross product of differences
-//  with |.|-sums S is within 2^-23 S + 2^-22 S^2 (two-fold margins).
+//  whose |.|-sum is at most S is within 2^-23 S + 2^-22 S^2 (two-fold
+//  margins); theta_3's numerator (den - n1 - n2) adds the three errors and
+//  two roundings.
 __device__ __forceinline__ float hop_bound(float S) { return S * __fmaf_rn(S, 0x1p-22f, 0x1p-23f) + 0x1p-46f; }
 //  double-float certification: differences within 2^-46, products and sums
 //  within 2^-45 relative: 2^-45 S + 2^-44 S^2.
 __device__ __forceinline__ float cert_bound(float S) { return S * __fmaf_rn(S, 0x1p-44f, 0x1p-45f); }
 
-template <bool kStats, bool kDebug>
-__global__ void __launch_bounds__(256, 4) k_step_fast_df(FastArgs a)
+template <bool kStats, bool kDebug, int kBlock, int kMinBlocks>
+__global__ void __launch_bounds__(kBlock, kMinBlocks) k_step_fast_df(FastArgs a)
 {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     const bool active = i < a.N;
@@ -151,11 +153,13 @@ __global__ void __launch_bounds__(256, 4) k_step_fast_df(FastArgs a)
         bool certify = true, found = false;
         int s1 = 0, s2 = 0, s3 = 0;
         df n1, n2, den;
-        int ia = 0, ib = 0, ic = 0;
+        // Each hop needs the triangle's vertex ids and neighbour slots (SoA,
+        // loaded together so the chain per hop is two dependent loads: ids and
+        // neighbours, then the coordinates) and the high parts of the vertex
+        // coordinates.
+        int ia = a.tv[0][j], ib = a.tv[1][j], ic = a.tv[2][j];
+        int na = a.tn[0][j], nb = a.tn[1][j], nc = a.tn[2][j];
         for (;;) {
-            ia = a.tv[0][j];
-            ib = a.tv[1][j];
-            ic = a.tv[2][j];
             if (!certify) {
                 // FP32 hop test on the high parts, differences relative to vertex 3
                 const float2 A = a.xyh[ia], B = a.xyh[ib], C = a.xyh[ic];
@@ -165,21 +169,25 @@ __global__ void __launch_bounds__(256, 4) k_step_fast_df(FastArgs a)
                 const float o2 = __fmaf_rn(ax, xy, -__fmul_rn(ay, xx));    // ~ theta_2 * den
                 const float dn = __fmaf_rn(ax, by, -__fmul_rn(ay, bx));
                 const float o3 = dn - o1 - o2;                              // ~ theta_3 * den
-                const float sA = fabsf(ax) + fabsf(ay), sB = fabsf(bx) + fabsf(by), sX = fabsf(xx) + fabsf(xy);
-                const float e1 = hop_bound(sX + sB), e2 = hop_bound(sA + sX), ed = hop_bound(sA + sB);
-                const float e3 = ed + e1 + e2 + 0x1p-23f * (fabsf(dn) + fabsf(o1) + fabsf(o2));
-                int k = -1;
+                // one bound for all three (S covers every difference involved)
+                const float S = fabsf(ax) + fabsf(ay) + fabsf(bx) + fabsf(by) + fabsf(xx) + fabsf(xy);
+                const float e = hop_bound(S);
+                const float e3 = 3.0f * e + 0x1p-23f * (fabsf(dn) + fabsf(o1) + fabsf(o2));
+                int32_t nj = -1;
                 float best = 0.0f;
-                if (o1 < -e1) { k = 0; best = o1; }
-                if (o2 < -e2 && (k < 0 || o2 < best)) { k = 1; best = o2; }
-                if (o3 < -e3 && (k < 0 || o3 < best)) { k = 2; best = o3; }
-                if (k >= 0 && hops < cap) {
-                    const int32_t nj = a.tn[k][j];
-                    if (nj >= 0) {
-                        j = nj;
-                        ++hops;
-                        continue;
-                    }
+                if (o1 < -e) { nj = na; best = o1; }
+                if (o2 < -e && (nj == -1 || o2 < best)) { nj = nb; best = o2; }
+                if (o3 < -e3 && (nj == -1 || o3 < best)) { nj = nc; best = o3; }
+                if (nj >= 0 && hops < cap) {
+                    j = nj;
+                    ia = a.tv[0][j];
+                    ib = a.tv[1][j];
+                    ic = a.tv[2][j];
+                    na = a.tn[0][j];
+                    nb = a.tn[1][j];
+                    nc = a.tn[2][j];
+                    ++hops;
+                    continue;
                 }
                 certify = true;    // no clearly negative edge: certify this triangle
             }
@@ -202,10 +210,9 @@ __global__ void __launch_bounds__(256, 4) k_step_fast_df(FastArgs a)
             s3 = n3.h > e3 ? 1 : (n3.h < -e3 ? -1 : 2);
             if (s1 == 2 || s2 == 2 || s3 == 2) {
                 // a boundary edge with the foot on its side of the square: exactly 0
-                int32_t nb;
-                if (s1 == 2 && (nb = a.tn[0][j]) < 0 && (fside >> (-1 - nb) & 1u)) s1 = 0;
-                if (s2 == 2 && (nb = a.tn[1][j]) < 0 && (fside >> (-1 - nb) & 1u)) s2 = 0;
-                if (s3 == 2 && (nb = a.tn[2][j]) < 0 && (fside >> (-1 - nb) & 1u)) s3 = 0;
+                if (s1 == 2 && na < 0 && (fside >> (-1 - na) & 1u)) s1 = 0;
+                if (s2 == 2 && nb < 0 && (fside >> (-1 - nb) & 1u)) s2 = 0;
+                if (s3 == 2 && nc < 0 && (fside >> (-1 - nc) & 1u)) s3 = 0;
             }
             if (s1 == 2 || s2 == 2 || s3 == 2) {
                 // exact signs on the double coordinates and the exact foot
@@ -248,9 +255,15 @@ __global__ void __launch_bounds__(256, 4) k_step_fast_df(FastArgs a)
                 for (int q = 0; q < 3; ++q)
                     if (neg[q] && pick-- == 0) k = q;
             }
-            const int32_t nj = a.tn[k][j];
+            const int32_t nj = k == 0 ? na : (k == 1 ? nb : nc);
             if (nj < 0) break;         // cannot happen for a foot inside a valid mesh
             j = nj;
+            ia = a.tv[0][j];
+            ib = a.tv[1][j];
+            ic = a.tv[2][j];
+            na = a.tn[0][j];
+            nb = a.tn[1][j];
+            nc = a.tn[2][j];
             ++hops;
             certify = hops >= cap;     // FP32 hops until the cap, then certified ones
         }
@@ -283,18 +296,30 @@ __global__ void __launch_bounds__(256, 4) k_step_fast_df(FastArgs a)
     if (kStats) warp_stats(a.stats, active, hops, exact_tests, clipped_cnt, fallback_cnt, limit_cnt, filter2);
 }
 
-void launch_fast_df(const FastArgs &a, bool stats, bool debug, int block, cudaStream_t s)
+template <int kBlock, int kMinBlocks>
+static void launch_fast_df_cfg(const FastArgs &a, bool stats, bool debug, cudaStream_t s)
 {
-    if (block <= 0) block = 256;
-    if (block > 256) block = 256;
-    const unsigned grid = (unsigned)((a.N + block - 1) / block);
+    const unsigned grid = (unsigned)((a.N + kBlock - 1) / kBlock);
     if (grid == 0) return;
     if (stats) {
-        if (debug) k_step_fast_df<true, true><<<grid, block, 0, s>>>(a);
-        else k_step_fast_df<true, false><<<grid, block, 0, s>>>(a);
+        if (debug) k_step_fast_df<true, true, kBlock, kMinBlocks><<<grid, kBlock, 0, s>>>(a);
+        else k_step_fast_df<true, false, kBlock, kMinBlocks><<<grid, kBlock, 0, s>>>(a);
     } else {
-        if (debug) k_step_fast_df<false, true><<<grid, block, 0, s>>>(a);
-        else k_step_fast_df<false, false><<<grid, block, 0, s>>>(a);
+        if (debug) k_step_fast_df<false, true, kBlock, kMinBlocks><<<grid, kBlock, 0, s>>>(a);
+        else k_step_fast_df<false, false, kBlock, kMinBlocks><<<grid, kBlock, 0, s>>>(a);
+    }
+}
+
+// Launch configurations (threads per block x resident blocks per SM the
+// register budget is sized for): 0 = 256 x 4 (64 registers), 1 = 256 x 3,
+// 2 = 128 x 8, 3 = 128 x 6.
+void launch_fast_df(const FastArgs &a, bool stats, bool debug, int config, cudaStream_t s)
+{
+    switch (config) {
+    case 1: launch_fast_df_cfg<256, 3>(a, stats, debug, s); break;
+    case 2: launch_fast_df_cfg<128, 8>(a, stats, debug, s); break;
+    case 3: launch_fast_df_cfg<128, 6>(a, stats, debug, s); break;
+    default: launch_fast_df_cfg<256, 4>(a, stats, debug, s); break;
     }
 }
 

@@ -47,7 +47,9 @@ struct FastArgs {
     sl_debug dbg;
 };
 
-void launch_fast_df(const FastArgs &a, bool stats, bool debug, int block, cudaStream_t s);
+// config: launch configuration 0..3 (see step_fast.cu)
+void launch_fast_df(const FastArgs &a, bool stats, bool debug, int config, cudaStream_t s);
+constexpr int kFastConfigs = 4;
 void launch_fast_f32(const FastArgs &a, bool stats, bool debug, int block, cudaStream_t s);
 
 // value format conversions for the double-float kernel
