@@ -47,6 +47,7 @@ def parse():
     ap.add_argument("--kernel", type=int, default=0, help="SL_OPT_KERNEL (0 auto, 1 plain FP64, 2 tiled)")
     ap.add_argument("--curve", default="hilbert", choices=["none", "hilbert", "morton"])
     ap.add_argument("--config-id", type=int, default=0, help="SL_OPT_CONFIG launch configuration (0..3)")
+    ap.add_argument("--hop-budget", type=int, default=None, help="SL_OPT_HOP_BUDGET (default: library's)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
@@ -224,6 +225,8 @@ def main():
     if args.kernel:
         sl.sl_mesh_set_option(h, sl.SL_OPT_KERNEL, args.kernel)
     sl.sl_mesh_set_option(h, sl.SL_OPT_CONFIG, args.config_id)
+    if args.hop_budget is not None:
+        sl.sl_mesh_set_option(h, sl.SL_OPT_HOP_BUDGET, args.hop_budget)
     probs = sl.problems([(prob.field.kind, prob.dt, prob.field.packed())])
     vt = torch.float64 if prec == sl.SL_FP64 else torch.float32
     v0 = torch.tensor(prob.v0[perm], dtype=vt, device="cuda")

@@ -121,8 +121,12 @@ typedef enum {
     SL_OPT_KERNEL = 2,       /* 0 = auto (fast), 1 = plain FP64 kernel, 2 = fast kernel */
     SL_OPT_BLOCK = 3,        /* threads per block (0 = auto) */
     SL_OPT_TILES_PER_SM = 4, /* reserved */
-    SL_OPT_CONFIG = 5        /* launch configuration of the fast kernels, 0..3:
+    SL_OPT_CONFIG = 5,       /* launch configuration of the fast kernels, 0..3:
                                 threads per block x blocks per SM = 256x4, 256x3, 128x8, 128x6 */
+    SL_OPT_HOP_BUDGET = 6    /* FP32 walk hops a node makes in the main pass before it moves to the
+                                walk queue (a lean, fully occupied walk kernel continues it);
+                                0 = no queue (the default: on the benchmark meshes the extra resident
+                                walks thrash L1).  sl_step_noalloc never queues. */
 } sl_option;
 
 /*

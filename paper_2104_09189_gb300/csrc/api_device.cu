@@ -40,7 +40,7 @@ void free_device(sl_mesh *m)
 {
     DeviceMesh &d = m->d;
     void *ptrs[] = {d.xy, d.tv[0], d.tv[1], d.tv[2], d.tn[0], d.tn[1], d.tn[2], d.t0, d.t0_init, d.node_off,
-                    d.status, d.stats, d.probs, d.fprobs, d.xyq, d.xyh, d.g1, d.g2, d.tparams, d.dfa, d.dfb,
+                    d.status, d.stats, d.probs, d.fprobs, d.xyq, d.xyh, d.g1, d.g2, d.tparams, d.dfa, d.dfb, d.queue, d.queue_hops, d.queue_count,
                     m->host_v, m->host_v2};
     for (void *p : ptrs)
         if (p) cudaFree(p);
@@ -112,6 +112,7 @@ static sl_status upload_arrays(sl_mesh *m)
 sl_status upload(sl_mesh *m)
 {
     SL_CUDA(cudaGetDevice(&m->device));
+    SL_CUDA(cudaDeviceGetAttribute(&m->sms, cudaDevAttrMultiProcessorCount, m->device));
     DeviceMesh &d = m->d;
     const int64_t N = m->N, Nt = m->Nt;
     const size_t cs = m->precision == SL_FP64 ? 2 * sizeof(double) : 2 * sizeof(float);
@@ -309,9 +310,30 @@ static sl_status launch_step(const sl_mesh *m, const StepArgs &a, bool debug, cu
     return SL_OK;
 }
 
-static sl_status launch_fast(const sl_mesh *m, const FastArgs &a, bool debug, cudaStream_t s)
+// Walk-queue scratch of the fast kernels (allocated before any recording).
+static sl_status ensure_queue(sl_mesh *m)
 {
-    if (m->precision == SL_FP64) launch_fast_df(a, m->opt_stats != 0, debug, m->opt_config, s);
+    if (m->opt_hop_budget > 0 && !m->d.queue) {
+        SL_CUDA(cudaMalloc(&m->d.queue, sizeof(int32_t) * m->N));
+        SL_CUDA(cudaMalloc(&m->d.queue_hops, sizeof(uint32_t) * m->N));
+        SL_CUDA(cudaMalloc(&m->d.queue_count, sizeof(uint32_t)));
+    }
+    return SL_OK;
+}
+
+static sl_status launch_fast(sl_mesh *m, const FastArgs &a0, bool debug, cudaStream_t s)
+{
+    FastArgs a = a0;
+    if (m->opt_hop_budget > 0) {
+        // long walks continue in the walk kernel (queue scratch owned by the mesh)
+        if (!m->d.queue) return fail(SL_E_STATE, "walk queue not allocated");
+        a.queue = m->d.queue;
+        a.queue_hops = m->d.queue_hops;
+        a.queue_count = m->d.queue_count;
+        a.hop_budget = m->opt_hop_budget;
+        SL_CUDA(cudaMemsetAsync(m->d.queue_count, 0, sizeof(uint32_t), s));
+    }
+    if (m->precision == SL_FP64) launch_fast_df(a, m->opt_stats != 0, debug, m->opt_config, m->sms, s);
     else return fail(SL_E_STATE, "no FP32 kernel is built into this library yet");
     SL_CUDA(cudaGetLastError());
     return SL_OK;
@@ -362,6 +384,7 @@ static sl_status run_steps(sl_mesh *m, const sl_problem *probs, int64_t n0, int3
     }
     if (fast) {
         sl_status st = ensure_tables(m, probs, s);
+        if (st == SL_OK) st = ensure_queue(m);
         if (st != SL_OK) return st;
     }
     const size_t elem = m->precision == SL_FP64 ? sizeof(double) : sizeof(float);
@@ -485,6 +508,7 @@ extern "C" sl_status sl_step(sl_mesh *m, const sl_problem *probs, int64_t n, con
         return st;
     }
     st = ensure_tables(m, probs, s);
+    if (st == SL_OK) st = ensure_queue(m);
     if (st != SL_OK) return st;
     std::vector<FastProb> fh(m->n_problems);
     fill_fast(m, host.data(), fh.data());

@@ -400,6 +400,10 @@ extern "C" sl_status sl_mesh_set_option(sl_mesh *m, int32_t option, int64_t valu
         if (value < 0 || value > 64) return sl::fail(SL_E_ARG, "tiles per SM out of range");
         m->opt_tiles_per_sm = (int32_t)value;
         break;
+    case SL_OPT_HOP_BUDGET:
+        if (value < 0 || value > (1 << 30)) return sl::fail(SL_E_ARG, "hop budget out of range");
+        m->opt_hop_budget = (int32_t)value;
+        break;
     case SL_OPT_CONFIG:
         if (value < 0 || value > 3) return sl::fail(SL_E_ARG, "launch configuration must be 0..3");
         m->opt_config = (int32_t)value;

@@ -204,7 +204,7 @@ extern "C" sl_status sl_step_noalloc(sl_mesh *m, const sl_problem *probs, int64_
     a.N = m->N;
     a.status = m->d.status;
     a.stats = m->d.stats;
-    launch_fast_df(a, m->opt_stats != 0, false, m->opt_config, s);
+    launch_fast_df(a, m->opt_stats != 0, false, m->opt_config, m->sms, s);
     launch_from_df(sc.values, v_out, m->N, s);
     e = cudaGetLastError();
     if (e != cudaSuccess) return fail(SL_E_CUDA, std::string("sl_step_noalloc: launch: ") + cudaGetErrorString(e));

@@ -45,6 +45,9 @@ struct DeviceMesh {
     void *g1 = nullptr, *g2 = nullptr;   // field node tables, float4 (hi, lo) per node
     double *tparams = nullptr;        // field parameters the tables were built from (device)
     void *dfa = nullptr, *dfb = nullptr;   // value scratch of sl_step for the fast FP64 kernel
+    int32_t *queue = nullptr;         // walk queue of the fast kernels (N node ids)
+    uint32_t *queue_hops = nullptr;   // hops made so far by each queued node
+    uint32_t *queue_count = nullptr;
 };
 
 struct GraphCache {
@@ -80,6 +83,8 @@ struct sl_mesh {
     int32_t opt_block = 0;
     int32_t opt_tiles_per_sm = 0;
     int32_t opt_config = 0;           // launch configuration of the fast kernels
+    int32_t opt_hop_budget = 0;       // FP32 hops before a walk moves to the walk kernel (0 = never)
+    int32_t sms = 0;                  // multiprocessors of the device
     bool stepped = false;
     std::vector<double> table_key;    // field parameters of the current node tables
     sl::DeviceMesh d;

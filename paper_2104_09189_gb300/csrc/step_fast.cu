@@ -125,138 +125,255 @@ __device__ __forceinline__ float hop_bound(float S) { return S * __fmaf_rn(S, 0x
 //  within 2^-45 relative: 2^-45 S + 2^-44 S^2.
 __device__ __forceinline__ float cert_bound(float S) { return S * __fmaf_rn(S, 0x1p-44f, 0x1p-45f); }
 
+struct NodeCounters {
+    uint32_t hops = 0, exact = 0, clipped = 0, fallback = 0, limit = 0, filter2 = 0;
+};
+
+// One node of the step.  c.hops holds the hops already made (spilled nodes
+// resume in the finish pass).  With kSpill the node gives up after
+// a.hop_budget FP32 hops: it stores its current triangle in T^0 and returns
+// false; otherwise it completes (value, T^0, debug outputs) and returns true.
+template <bool kDebug, bool kSpill>
+__device__ __forceinline__ bool step_node(const FastArgs &a, int64_t i, NodeCounters &c)
+{
+    const int pi = a.nprob == 1 ? 0 : problem_of(a.node_off, a.nprob, i);
+    const FastProb &P = a.probs[pi];
+    const float4 xq = a.xyq[i];
+    const df x = df_make(xq.x, xq.z), y = df_make(xq.y, xq.w);
+    df X, Y;
+    foot_df(P, a, i, x, y, X, Y);
+    uint32_t flags = 0;
+    if (clip_df(x, y, X, Y)) {
+        flags |= SL_NODE_CLIPPED;
+        c.clipped = 1;
+    }
+    // sides of the square the foot lies on exactly (bit = boundary side code)
+    const uint32_t fside = (df_is(X, 0.0f) ? 1u : 0u) | (df_is(X, 1.0f) ? 2u : 0u) | (df_is(Y, 0.0f) ? 4u : 0u) |
+                           (df_is(Y, 1.0f) ? 8u : 0u);
+
+    int32_t j = a.t0[i];
+    const int32_t jstart = j;
+    const uint32_t cap = (uint32_t)a.walk_cap;
+    uint32_t &hops = c.hops;
+    bool certify = true, found = false;
+    int s1 = 0, s2 = 0, s3 = 0;
+    df n1, n2, den;
+    // Each hop needs the triangle's vertex ids and neighbour slots (SoA,
+    // loaded together so the chain per hop is two dependent loads: ids and
+    // neighbours, then the coordinates) and the high parts of the vertex
+    // coordinates.
+    int ia = a.tv[0][j], ib = a.tv[1][j], ic = a.tv[2][j];
+    int na = a.tn[0][j], nb = a.tn[1][j], nc = a.tn[2][j];
+    for (;;) {
+        if (!certify) {
+            if (kSpill && hops >= (uint32_t)a.hop_budget) {
+                // a long walk: leave it to the walk kernel (high occupancy)
+                if (j != jstart) a.t0[i] = j;
+                return false;
+            }
+            // FP32 hop test on the high parts, differences relative to vertex 3
+            const float2 A = a.xyh[ia], B = a.xyh[ib], C = a.xyh[ic];
+            const float ax = A.x - C.x, ay = A.y - C.y, bx = B.x - C.x, by = B.y - C.y;
+            const float xx = X.h - C.x, xy = Y.h - C.y;
+            const float o1 = __fmaf_rn(xx, by, -__fmul_rn(xy, bx));    // ~ theta_1 * den
+            const float o2 = __fmaf_rn(ax, xy, -__fmul_rn(ay, xx));    // ~ theta_2 * den
+            const float dn = __fmaf_rn(ax, by, -__fmul_rn(ay, bx));
+            const float o3 = dn - o1 - o2;                              // ~ theta_3 * den
+            // one bound for all three (S covers every difference involved)
+            const float S = fabsf(ax) + fabsf(ay) + fabsf(bx) + fabsf(by) + fabsf(xx) + fabsf(xy);
+            const float e = hop_bound(S);
+            const float e3 = 3.0f * e + 0x1p-23f * (fabsf(dn) + fabsf(o1) + fabsf(o2));
+            int32_t nj = -1;
+            float best = 0.0f;
+            if (o1 < -e) { nj = na; best = o1; }
+            if (o2 < -e && (nj == -1 || o2 < best)) { nj = nb; best = o2; }
+            if (o3 < -e3 && (nj == -1 || o3 < best)) { nj = nc; best = o3; }
+            if (nj >= 0 && hops < cap) {
+                j = nj;
+                ia = a.tv[0][j];
+                ib = a.tv[1][j];
+                ic = a.tv[2][j];
+                na = a.tn[0][j];
+                nb = a.tn[1][j];
+                nc = a.tn[2][j];
+                ++hops;
+                continue;
+            }
+            certify = true;    // no clearly negative edge: certify this triangle
+        }
+        // certified test in double-float, relative to vertex 3
+        const float4 A = a.xyq[ia], B = a.xyq[ib], C = a.xyq[ic];
+        const df cxh = df_make(C.x, C.z), cyh = df_make(C.y, C.w);
+        const df dAx = df_sub(df_make(A.x, A.z), cxh), dAy = df_sub(df_make(A.y, A.w), cyh);
+        const df dBx = df_sub(df_make(B.x, B.z), cxh), dBy = df_sub(df_make(B.y, B.w), cyh);
+        const df dXx = df_sub(X, cxh), dXy = df_sub(Y, cyh);
+        n1 = df_cross(dXx, dXy, dBx, dBy);      // orient(B, C, X): sign of theta_1
+        n2 = df_cross(dAx, dAy, dXx, dXy);      // orient(C, A, X): sign of theta_2
+        den = df_cross(dAx, dAy, dBx, dBy);     // orient(A, B, C) > 0
+        const df n3 = df_sub(df_sub(den, n1), n2);
+        const float sA = fabsf(dAx.h) + fabsf(dAy.h), sB = fabsf(dBx.h) + fabsf(dBy.h);
+        const float sX = fabsf(dXx.h) + fabsf(dXy.h);
+        const float e1 = cert_bound(sX + sB), e2 = cert_bound(sA + sX), ed = cert_bound(sA + sB);
+        const float e3 = ed + e1 + e2 + 0x1p-45f * (fabsf(den.h) + fabsf(n1.h) + fabsf(n2.h));
+        s1 = n1.h > e1 ? 1 : (n1.h < -e1 ? -1 : 2);
+        s2 = n2.h > e2 ? 1 : (n2.h < -e2 ? -1 : 2);
+        s3 = n3.h > e3 ? 1 : (n3.h < -e3 ? -1 : 2);
+        if (s1 == 2 || s2 == 2 || s3 == 2) {
+            // a boundary edge with the foot on its side of the square: exactly 0
+            if (s1 == 2 && na < 0 && (fside >> (-1 - na) & 1u)) s1 = 0;
+            if (s2 == 2 && nb < 0 && (fside >> (-1 - nb) & 1u)) s2 = 0;
+            if (s3 == 2 && nc < 0 && (fside >> (-1 - nc) & 1u)) s3 = 0;
+        }
+        if (s1 == 2 || s2 == 2 || s3 == 2) {
+            // exact signs on the double coordinates and the exact foot
+            const double2 Ad = a.xyd[ia], Bd = a.xyd[ib], Cd = a.xyd[ic];
+            int stg = 0;
+            if (s1 == 2) { s1 = orient_exact_df(Bd, Cd, X.h, X.l, Y.h, Y.l, stg); c.exact += stg == 3; c.filter2 += stg == 2; }
+            if (s2 == 2) { s2 = orient_exact_df(Cd, Ad, X.h, X.l, Y.h, Y.l, stg); c.exact += stg == 3; c.filter2 += stg == 2; }
+            if (s3 == 2) { s3 = orient_exact_df(Ad, Bd, X.h, X.l, Y.h, Y.l, stg); c.exact += stg == 3; c.filter2 += stg == 2; }
+            flags |= SL_NODE_EXACT;
+            if (!(slp::in_exact_range(Ad.x) && slp::in_exact_range(Ad.y) && slp::in_exact_range(Bd.x) &&
+                  slp::in_exact_range(Bd.y) && slp::in_exact_range(Cd.x) && slp::in_exact_range(Cd.y) &&
+                  slp::in_exact_range(X.h) && slp::in_exact_range(Y.h) && slp::in_exact_range(X.l) &&
+                  slp::in_exact_range(Y.l)))
+                flags |= SL_NODE_RANGE;
+        }
+        if (s1 >= 0 && s2 >= 0 && s3 >= 0) {
+            found = true;
+            break;
+        }
+        if (hops >= 2 * cap) break;
+        int k;
+        if (hops < cap) {
+            // the paper's rule: the most negative barycentric coordinate
+            k = -1;
+            float best = 0.0f;
+            if (s1 < 0) { k = 0; best = n1.h; }
+            if (s2 < 0 && (k < 0 || n2.h < best)) { k = 1; best = n2.h; }
+            if (s3 < 0 && (k < 0 || n3.h < best)) { k = 2; best = n3.h; }
+        } else {
+            // after `cap` hops: randomised visibility walk (certified at
+            // every triangle), which terminates on any triangulation
+            if (hops == cap) {
+                c.fallback = 1;
+                flags |= SL_NODE_FALLBACK;
+            }
+            const int neg[3] = {s1 < 0, s2 < 0, s3 < 0};
+            const int nneg = neg[0] + neg[1] + neg[2];
+            int pick = (int)(mix64_dev(((uint64_t)i << 20) ^ (uint64_t)hops) % (uint64_t)nneg);
+            k = -1;
+            for (int q = 0; q < 3; ++q)
+                if (neg[q] && pick-- == 0) k = q;
+        }
+        const int32_t nj = k == 0 ? na : (k == 1 ? nb : nc);
+        if (nj < 0) break;         // cannot happen for a foot inside a valid mesh
+        j = nj;
+        ia = a.tv[0][j];
+        ib = a.tv[1][j];
+        ic = a.tv[2][j];
+        na = a.tn[0][j];
+        nb = a.tn[1][j];
+        nc = a.tn[2][j];
+        ++hops;
+        certify = hops >= cap;     // FP32 hops until the cap, then certified ones
+    }
+    if (!found) {
+        flags |= SL_NODE_WALK_LIMIT;
+        c.limit = 1;
+    }
+    if (s1 == 0 || s2 == 0 || s3 == 0) flags |= SL_NODE_DEGENERATE;
+
+    // theta_1, theta_2 by Eq. 6 and the P1 value (Remark 1), double-float
+    const df r = df_rcp(den);
+    const df th1 = df_mul(n1, r), th2 = df_mul(n2, r);
+    const float2 *vin = (const float2 *)a.vin;
+    const df v1 = dfp(vin[ia]), v2 = dfp(vin[ib]), v3 = dfp(vin[ic]);
+    const df v = df_add(v3, df_add(df_mul(th1, df_sub(v1, v3)), df_mul(th2, df_sub(v2, v3))));
+    ((float2 *)a.vout)[i] = make_float2(v.h, v.l);
+    if (j != jstart) a.t0[i] = j;
+    if (c.limit) atomicOr(a.status, 1u << SL_E_WALK_LIMIT);
+    if (flags & SL_NODE_RANGE) atomicOr(a.status, 1u << SL_E_ARG);
+    if (kDebug) {
+        if (a.dbg.feet) {
+            a.dbg.feet[2 * i] = (double)X.h + (double)X.l;
+            a.dbg.feet[2 * i + 1] = (double)Y.h + (double)Y.l;
+        }
+        if (a.dbg.tri) a.dbg.tri[i] = j;
+        if (a.dbg.moves) a.dbg.moves[i] = (int32_t)hops;
+        if (a.dbg.flags) a.dbg.flags[i] = (uint8_t)flags;
+    }
+    return true;
+}
+
 template <bool kStats, bool kDebug, int kBlock, int kMinBlocks>
 __global__ void __launch_bounds__(kBlock, kMinBlocks) k_step_fast_df(FastArgs a)
 {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     const bool active = i < a.N;
-    uint32_t hops = 0, exact_tests = 0, clipped_cnt = 0, fallback_cnt = 0, limit_cnt = 0, filter2 = 0;
+    NodeCounters c;
+    bool spilled = false;
     if (active) {
+        if (a.queue) spilled = !step_node<kDebug, true>(a, i, c);
+        else step_node<kDebug, false>(a, i, c);
+    }
+    if (a.queue) {
+        // warp-aggregated push of the long walkers onto the walk queue
+        const unsigned mask = __ballot_sync(0xffffffffu, spilled);
+        if (mask) {
+            const int lane = threadIdx.x & 31, leader = __ffs(mask) - 1;
+            uint32_t base = 0;
+            if (lane == leader) base = atomicAdd(a.queue_count, (uint32_t)__popc(mask));
+            base = __shfl_sync(0xffffffffu, base, leader);
+            if (spilled) {
+                const uint32_t q = base + (uint32_t)__popc(mask & ((1u << lane) - 1u));
+                a.queue[q] = (int32_t)i;
+                a.queue_hops[q] = c.hops;
+            }
+        }
+    }
+    if (kStats) warp_stats(a.stats, active && !spilled, spilled ? 0u : c.hops, c.exact, spilled ? 0u : c.clipped,
+                           c.fallback, c.limit, c.filter2);
+}
+
+// Walk kernel: FP32 hops for the queued long walks, at full occupancy (few
+// registers).  Stops at the first triangle with no clearly negative edge (or
+// at the cap) and leaves it in T^0 for the finish pass, which certifies it.
+template <int kBlock>
+__global__ void __launch_bounds__(kBlock, 2048 / kBlock) k_walk_fast_df(FastArgs a)
+{
+    const uint32_t count = *a.queue_count;
+    const uint32_t cap = (uint32_t)a.walk_cap;
+    for (uint32_t q = blockIdx.x * blockDim.x + threadIdx.x; q < count; q += gridDim.x * blockDim.x) {
+        const int64_t i = a.queue[q];
+        uint32_t hops = a.queue_hops[q];
         const int pi = a.nprob == 1 ? 0 : problem_of(a.node_off, a.nprob, i);
         const FastProb &P = a.probs[pi];
         const float4 xq = a.xyq[i];
         const df x = df_make(xq.x, xq.z), y = df_make(xq.y, xq.w);
         df X, Y;
         foot_df(P, a, i, x, y, X, Y);
-        uint32_t flags = 0;
-        if (clip_df(x, y, X, Y)) {
-            flags |= SL_NODE_CLIPPED;
-            clipped_cnt = 1;
-        }
-        // sides of the square the foot lies on exactly (bit = boundary side code)
-        const uint32_t fside = (df_is(X, 0.0f) ? 1u : 0u) | (df_is(X, 1.0f) ? 2u : 0u) | (df_is(Y, 0.0f) ? 4u : 0u) |
-                               (df_is(Y, 1.0f) ? 8u : 0u);
-
+        clip_df(x, y, X, Y);
+        const float fx = X.h, fy = Y.h;
         int32_t j = a.t0[i];
-        const int32_t jstart = j;
-        const uint32_t cap = (uint32_t)a.walk_cap;
-        bool certify = true, found = false;
-        int s1 = 0, s2 = 0, s3 = 0;
-        df n1, n2, den;
-        // Each hop needs the triangle's vertex ids and neighbour slots (SoA,
-        // loaded together so the chain per hop is two dependent loads: ids and
-        // neighbours, then the coordinates) and the high parts of the vertex
-        // coordinates.
         int ia = a.tv[0][j], ib = a.tv[1][j], ic = a.tv[2][j];
         int na = a.tn[0][j], nb = a.tn[1][j], nc = a.tn[2][j];
-        for (;;) {
-            if (!certify) {
-                // FP32 hop test on the high parts, differences relative to vertex 3
-                const float2 A = a.xyh[ia], B = a.xyh[ib], C = a.xyh[ic];
-                const float ax = A.x - C.x, ay = A.y - C.y, bx = B.x - C.x, by = B.y - C.y;
-                const float xx = X.h - C.x, xy = Y.h - C.y;
-                const float o1 = __fmaf_rn(xx, by, -__fmul_rn(xy, bx));    // ~ theta_1 * den
-                const float o2 = __fmaf_rn(ax, xy, -__fmul_rn(ay, xx));    // ~ theta_2 * den
-                const float dn = __fmaf_rn(ax, by, -__fmul_rn(ay, bx));
-                const float o3 = dn - o1 - o2;                              // ~ theta_3 * den
-                // one bound for all three (S covers every difference involved)
-                const float S = fabsf(ax) + fabsf(ay) + fabsf(bx) + fabsf(by) + fabsf(xx) + fabsf(xy);
-                const float e = hop_bound(S);
-                const float e3 = 3.0f * e + 0x1p-23f * (fabsf(dn) + fabsf(o1) + fabsf(o2));
-                int32_t nj = -1;
-                float best = 0.0f;
-                if (o1 < -e) { nj = na; best = o1; }
-                if (o2 < -e && (nj == -1 || o2 < best)) { nj = nb; best = o2; }
-                if (o3 < -e3 && (nj == -1 || o3 < best)) { nj = nc; best = o3; }
-                if (nj >= 0 && hops < cap) {
-                    j = nj;
-                    ia = a.tv[0][j];
-                    ib = a.tv[1][j];
-                    ic = a.tv[2][j];
-                    na = a.tn[0][j];
-                    nb = a.tn[1][j];
-                    nc = a.tn[2][j];
-                    ++hops;
-                    continue;
-                }
-                certify = true;    // no clearly negative edge: certify this triangle
-            }
-            // certified test in double-float, relative to vertex 3
-            const float4 A = a.xyq[ia], B = a.xyq[ib], C = a.xyq[ic];
-            const df cxh = df_make(C.x, C.z), cyh = df_make(C.y, C.w);
-            const df dAx = df_sub(df_make(A.x, A.z), cxh), dAy = df_sub(df_make(A.y, A.w), cyh);
-            const df dBx = df_sub(df_make(B.x, B.z), cxh), dBy = df_sub(df_make(B.y, B.w), cyh);
-            const df dXx = df_sub(X, cxh), dXy = df_sub(Y, cyh);
-            n1 = df_cross(dXx, dXy, dBx, dBy);      // orient(B, C, X): sign of theta_1
-            n2 = df_cross(dAx, dAy, dXx, dXy);      // orient(C, A, X): sign of theta_2
-            den = df_cross(dAx, dAy, dBx, dBy);     // orient(A, B, C) > 0
-            const df n3 = df_sub(df_sub(den, n1), n2);
-            const float sA = fabsf(dAx.h) + fabsf(dAy.h), sB = fabsf(dBx.h) + fabsf(dBy.h);
-            const float sX = fabsf(dXx.h) + fabsf(dXy.h);
-            const float e1 = cert_bound(sX + sB), e2 = cert_bound(sA + sX), ed = cert_bound(sA + sB);
-            const float e3 = ed + e1 + e2 + 0x1p-45f * (fabsf(den.h) + fabsf(n1.h) + fabsf(n2.h));
-            s1 = n1.h > e1 ? 1 : (n1.h < -e1 ? -1 : 2);
-            s2 = n2.h > e2 ? 1 : (n2.h < -e2 ? -1 : 2);
-            s3 = n3.h > e3 ? 1 : (n3.h < -e3 ? -1 : 2);
-            if (s1 == 2 || s2 == 2 || s3 == 2) {
-                // a boundary edge with the foot on its side of the square: exactly 0
-                if (s1 == 2 && na < 0 && (fside >> (-1 - na) & 1u)) s1 = 0;
-                if (s2 == 2 && nb < 0 && (fside >> (-1 - nb) & 1u)) s2 = 0;
-                if (s3 == 2 && nc < 0 && (fside >> (-1 - nc) & 1u)) s3 = 0;
-            }
-            if (s1 == 2 || s2 == 2 || s3 == 2) {
-                // exact signs on the double coordinates and the exact foot
-                const double2 Ad = a.xyd[ia], Bd = a.xyd[ib], Cd = a.xyd[ic];
-                int stg = 0;
-                if (s1 == 2) { s1 = orient_exact_df(Bd, Cd, X.h, X.l, Y.h, Y.l, stg); exact_tests += stg == 3; filter2 += stg == 2; }
-                if (s2 == 2) { s2 = orient_exact_df(Cd, Ad, X.h, X.l, Y.h, Y.l, stg); exact_tests += stg == 3; filter2 += stg == 2; }
-                if (s3 == 2) { s3 = orient_exact_df(Ad, Bd, X.h, X.l, Y.h, Y.l, stg); exact_tests += stg == 3; filter2 += stg == 2; }
-                flags |= SL_NODE_EXACT;
-                if (!(slp::in_exact_range(Ad.x) && slp::in_exact_range(Ad.y) && slp::in_exact_range(Bd.x) &&
-                      slp::in_exact_range(Bd.y) && slp::in_exact_range(Cd.x) && slp::in_exact_range(Cd.y) &&
-                      slp::in_exact_range(X.h) && slp::in_exact_range(Y.h) && slp::in_exact_range(X.l) &&
-                      slp::in_exact_range(Y.l)))
-                    flags |= SL_NODE_RANGE;
-            }
-            if (s1 >= 0 && s2 >= 0 && s3 >= 0) {
-                found = true;
-                break;
-            }
-            if (hops >= 2 * cap) break;
-            int k;
-            if (hops < cap) {
-                // the paper's rule: the most negative barycentric coordinate
-                k = -1;
-                float best = 0.0f;
-                if (s1 < 0) { k = 0; best = n1.h; }
-                if (s2 < 0 && (k < 0 || n2.h < best)) { k = 1; best = n2.h; }
-                if (s3 < 0 && (k < 0 || n3.h < best)) { k = 2; best = n3.h; }
-            } else {
-                // after `cap` hops: randomised visibility walk (certified at
-                // every triangle), which terminates on any triangulation
-                if (hops == cap) {
-                    fallback_cnt = 1;
-                    flags |= SL_NODE_FALLBACK;
-                }
-                const int neg[3] = {s1 < 0, s2 < 0, s3 < 0};
-                const int nneg = neg[0] + neg[1] + neg[2];
-                int pick = (int)(mix64_dev(((uint64_t)i << 20) ^ (uint64_t)hops) % (uint64_t)nneg);
-                k = -1;
-                for (int q = 0; q < 3; ++q)
-                    if (neg[q] && pick-- == 0) k = q;
-            }
-            const int32_t nj = k == 0 ? na : (k == 1 ? nb : nc);
-            if (nj < 0) break;         // cannot happen for a foot inside a valid mesh
+        while (hops < cap) {
+            const float2 A = a.xyh[ia], B = a.xyh[ib], C = a.xyh[ic];
+            const float ax = A.x - C.x, ay = A.y - C.y, bx = B.x - C.x, by = B.y - C.y;
+            const float xx = fx - C.x, xy = fy - C.y;
+            const float o1 = __fmaf_rn(xx, by, -__fmul_rn(xy, bx));
+            const float o2 = __fmaf_rn(ax, xy, -__fmul_rn(ay, xx));
+            const float dn = __fmaf_rn(ax, by, -__fmul_rn(ay, bx));
+            const float o3 = dn - o1 - o2;
+            const float S = fabsf(ax) + fabsf(ay) + fabsf(bx) + fabsf(by) + fabsf(xx) + fabsf(xy);
+            const float e = hop_bound(S);
+            const float e3 = 3.0f * e + 0x1p-23f * (fabsf(dn) + fabsf(o1) + fabsf(o2));
+            int32_t nj = -1;
+            float best = 0.0f;
+            if (o1 < -e) { nj = na; best = o1; }
+            if (o2 < -e && (nj == -1 || o2 < best)) { nj = nb; best = o2; }
+            if (o3 < -e3 && (nj == -1 || o3 < best)) { nj = nc; best = o3; }
+            if (nj < 0) break;
             j = nj;
             ia = a.tv[0][j];
             ib = a.tv[1][j];
@@ -265,39 +382,55 @@ __global__ void __launch_bounds__(kBlock, kMinBlocks) k_step_fast_df(FastArgs a)
             nb = a.tn[1][j];
             nc = a.tn[2][j];
             ++hops;
-            certify = hops >= cap;     // FP32 hops until the cap, then certified ones
         }
-        if (!found) {
-            flags |= SL_NODE_WALK_LIMIT;
-            limit_cnt = 1;
-        }
-        if (s1 == 0 || s2 == 0 || s3 == 0) flags |= SL_NODE_DEGENERATE;
+        a.t0[i] = j;
+        a.queue_hops[q] = hops;
+    }
+}
 
-        // theta_1, theta_2 by Eq. 6 and the P1 value (Remark 1), double-float
-        const df r = df_rcp(den);
-        const df th1 = df_mul(n1, r), th2 = df_mul(n2, r);
-        const float2 *vin = (const float2 *)a.vin;
-        const df v1 = dfp(vin[ia]), v2 = dfp(vin[ib]), v3 = dfp(vin[ic]);
-        const df v = df_add(v3, df_add(df_mul(th1, df_sub(v1, v3)), df_mul(th2, df_sub(v2, v3))));
-        ((float2 *)a.vout)[i] = make_float2(v.h, v.l);
-        if (j != jstart) a.t0[i] = j;
-        if (limit_cnt) atomicOr(a.status, 1u << SL_E_WALK_LIMIT);
-        if (flags & SL_NODE_RANGE) atomicOr(a.status, 1u << SL_E_ARG);
-        if (kDebug) {
-            if (a.dbg.feet) {
-                a.dbg.feet[2 * i] = (double)X.h + (double)X.l;
-                a.dbg.feet[2 * i + 1] = (double)Y.h + (double)Y.l;
-            }
-            if (a.dbg.tri) a.dbg.tri[i] = j;
-            if (a.dbg.moves) a.dbg.moves[i] = (int32_t)hops;
-            if (a.dbg.flags) a.dbg.flags[i] = (uint8_t)flags;
+// Finish pass: the queued nodes, completed from the triangle the walk
+// kernel left in T^0 (certified test, further hops if needed, value).
+template <bool kStats, bool kDebug, int kBlock>
+__global__ void __launch_bounds__(kBlock) k_finish_fast_df(FastArgs a)
+{
+    const uint32_t count = *a.queue_count;
+    NodeCounters tot;
+    uint32_t done = 0, hmax = 0;
+    for (uint32_t q = blockIdx.x * blockDim.x + threadIdx.x; q < count; q += gridDim.x * blockDim.x) {
+        NodeCounters c;
+        c.hops = a.queue_hops[q];
+        step_node<kDebug, false>(a, a.queue[q], c);
+        tot.hops += c.hops;
+        hmax = c.hops > hmax ? c.hops : hmax;
+        tot.exact += c.exact;
+        tot.clipped += c.clipped;
+        tot.fallback += c.fallback;
+        tot.limit += c.limit;
+        tot.filter2 += c.filter2;
+        ++done;
+    }
+    if (kStats) {
+        // one thread may have finished several nodes: its sums go in whole
+        const unsigned full = 0xffffffffu;
+        const unsigned n = __reduce_add_sync(full, done), h = __reduce_add_sync(full, tot.hops);
+        const unsigned hm = __reduce_max_sync(full, hmax), e = __reduce_add_sync(full, tot.exact);
+        const unsigned f2 = __reduce_add_sync(full, tot.filter2), cl = __reduce_add_sync(full, tot.clipped);
+        const unsigned fb = __reduce_add_sync(full, tot.fallback), l = __reduce_add_sync(full, tot.limit);
+        if ((threadIdx.x & 31) == 0) {
+            if (n) atomicAdd(&a.stats[0], (unsigned long long)n);
+            if (h) atomicAdd(&a.stats[1], (unsigned long long)h);
+            if (hm) atomicMax(&a.stats[2], (unsigned long long)hm);
+            if (e) atomicAdd(&a.stats[3], (unsigned long long)e);
+            if (f2) atomicAdd(&a.stats[4], (unsigned long long)f2);
+            if (cl) atomicAdd(&a.stats[5], (unsigned long long)cl);
+            if (fb) atomicAdd(&a.stats[6], (unsigned long long)fb);
+            if (l) atomicAdd(&a.stats[7], (unsigned long long)l);
         }
     }
-    if (kStats) warp_stats(a.stats, active, hops, exact_tests, clipped_cnt, fallback_cnt, limit_cnt, filter2);
 }
 
 template <int kBlock, int kMinBlocks>
-static void launch_fast_df_cfg(const FastArgs &a, bool stats, bool debug, cudaStream_t s)
+static void launch_fast_df_cfg(const FastArgs &a, bool stats, bool debug, int sms, cudaStream_t s)
 {
     const unsigned grid = (unsigned)((a.N + kBlock - 1) / kBlock);
     if (grid == 0) return;
@@ -308,18 +441,31 @@ static void launch_fast_df_cfg(const FastArgs &a, bool stats, bool debug, cudaSt
         if (debug) k_step_fast_df<false, true, kBlock, kMinBlocks><<<grid, kBlock, 0, s>>>(a);
         else k_step_fast_df<false, false, kBlock, kMinBlocks><<<grid, kBlock, 0, s>>>(a);
     }
+    if (a.queue) {
+        k_walk_fast_df<256><<<sms * 8, 256, 0, s>>>(a);
+        const unsigned g2 = (unsigned)sms * 4;
+        if (stats) {
+            if (debug) k_finish_fast_df<true, true, 256><<<g2, 256, 0, s>>>(a);
+            else k_finish_fast_df<true, false, 256><<<g2, 256, 0, s>>>(a);
+        } else {
+            if (debug) k_finish_fast_df<false, true, 256><<<g2, 256, 0, s>>>(a);
+            else k_finish_fast_df<false, false, 256><<<g2, 256, 0, s>>>(a);
+        }
+    }
 }
 
 // Launch configurations (threads per block x resident blocks per SM the
 // register budget is sized for): 0 = 256 x 4 (64 registers), 1 = 256 x 3,
-// 2 = 128 x 8, 3 = 128 x 6.
-void launch_fast_df(const FastArgs &a, bool stats, bool debug, int config, cudaStream_t s)
+// 2 = 128 x 8, 3 = 128 x 6.  With a.queue set, walks longer than
+// a.hop_budget hops continue in the walk kernel and finish in the finish pass
+// (the caller zeroes *a.queue_count before the launch).
+void launch_fast_df(const FastArgs &a, bool stats, bool debug, int config, int sms, cudaStream_t s)
 {
     switch (config) {
-    case 1: launch_fast_df_cfg<256, 3>(a, stats, debug, s); break;
-    case 2: launch_fast_df_cfg<128, 8>(a, stats, debug, s); break;
-    case 3: launch_fast_df_cfg<128, 6>(a, stats, debug, s); break;
-    default: launch_fast_df_cfg<256, 4>(a, stats, debug, s); break;
+    case 1: launch_fast_df_cfg<256, 3>(a, stats, debug, sms, s); break;
+    case 2: launch_fast_df_cfg<128, 8>(a, stats, debug, sms, s); break;
+    case 3: launch_fast_df_cfg<128, 6>(a, stats, debug, sms, s); break;
+    default: launch_fast_df_cfg<256, 4>(a, stats, debug, sms, s); break;
     }
 }
 

@@ -45,10 +45,17 @@ struct FastArgs {
     uint32_t *status;
     unsigned long long *stats;
     sl_debug dbg;
+    // walk queue (optional): walks longer than hop_budget FP32 hops are
+    // pushed here by the main kernel, continued by the walk kernel and
+    // completed by the finish pass
+    int32_t *queue;
+    uint32_t *queue_hops;
+    uint32_t *queue_count;
+    int32_t hop_budget;
 };
 
 // config: launch configuration 0..3 (see step_fast.cu)
-void launch_fast_df(const FastArgs &a, bool stats, bool debug, int config, cudaStream_t s);
+void launch_fast_df(const FastArgs &a, bool stats, bool debug, int config, int sms, cudaStream_t s);
 constexpr int kFastConfigs = 4;
 void launch_fast_f32(const FastArgs &a, bool stats, bool debug, int block, cudaStream_t s);
 
