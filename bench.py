@@ -42,7 +42,9 @@ def parse():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
-    ap.add_argument("--config", default="C3", choices=["C1", "C2", "C3", "C4"])
+    ap.add_argument("--config", default="C3", choices=["C1", "C2", "C3", "C4", "C5"])
+    ap.add_argument("--precision", default=None, choices=["fp64", "fp32"],
+                    help="precision of the batch workload C5 (default fp64)")
     ap.add_argument("--cells", type=int, default=None, help="override cells per side (smaller test runs)")
     ap.add_argument("--kernel", type=int, default=0, help="SL_OPT_KERNEL (0 auto, 1 plain FP64, 2 tiled)")
     ap.add_argument("--curve", default="hilbert", choices=["none", "hilbert", "morton"])
@@ -115,9 +117,34 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
+class Workload:
+    """The meshes, fields, time steps and initial data of one benchmark run."""
+
+    def __init__(self, name, probs, precision, n_steps, description):
+        self.name = name
+        self.probs = probs                      # list of sl_inputs.Problem
+        self.precision = precision
+        self.n_steps = n_steps
+        self.description = description
+        self.nodes = sum(p.mesh.n_nodes for p in probs)
+        self.triangles = sum(p.mesh.n_tri for p in probs)
+
+
 def build_workload(args):
+    if args.config == "C5":
+        prec = args.precision or "fp64"
+        probs = si.batch_config(256, precision=prec)
+        n = sum(p.mesh.n_nodes for p in probs)
+        desc = (f"C5: 256 jittered meshes of {min(p.mesh.n_nodes for p in probs)}-"
+                f"{max(p.mesh.n_nodes for p in probs)} nodes ({n} nodes in all), rotation / swirl / "
+                f"Fourier-8 fields, Courant 5-30, 50 steps, {prec}, curve={args.curve}")
+        return Workload("C5", probs, prec, 50, desc)
     prob = si.config(args.config, M=args.cells)
-    return prob
+    m = prob.mesh
+    desc = (f"{prob.name}: {m.M}x{m.M} {'graded ' if m.graded else ''}jittered mesh ({m.n_nodes} nodes, "
+            f"{m.n_tri} triangles), field kind {prob.field.kind}, dt={prob.dt}, {prob.n_steps} steps, "
+            f"{prob.precision}, curve={args.curve}")
+    return Workload(prob.name, [prob], prob.precision, prob.n_steps, desc)
 
 
 def measured_peaks():
@@ -128,39 +155,49 @@ def measured_peaks():
         return {"hbm_gbs": 6800.0}, "fallback"
 
 
-def cpu_sample(prob, seconds, steps=2):
+def cpu_sample(wl, seconds, steps=2):
     """Time the oracle (as it stands) on a bounded sample of the workload:
-    `steps` steps of a node range sized to about `seconds` of CPU work."""
+    `steps` steps of a node range of the first problems, sized to about
+    `seconds` of CPU work."""
     import oracle
     threads = oracle.default_threads()
-    om = oracle.OracleMesh(prob.mesh.xy, prob.mesh.tri)
-    kind, par = prob.field.kind, prob.field.packed()
-    # calibrate on a small range
-    n_cal = min(prob.mesh.n_nodes, 200_000)
-    t0 = time.perf_counter()
-    om.step(kind, par, prob.dt, 0, prob.v0, lo=0, hi=n_cal, nthreads=threads, want_feet=False)
-    rate = n_cal / max(time.perf_counter() - t0, 1e-6)
-    n_s = int(min(prob.mesh.n_nodes, max(10_000, rate * seconds / steps)))
-    lo = (prob.mesh.n_nodes - n_s) // 2
-    t0 = time.perf_counter()
-    v = prob.v0
-    for s in range(steps):
-        out, _, _, _ = om.step(kind, par, prob.dt, s, v, lo=lo, hi=lo + n_s, nthreads=threads, want_feet=False)
-    dt = time.perf_counter() - t0
-    om.close()
-    return {"value": n_s * steps / dt, "unit": "node-updates/s", "cores": threads, "kind": "oracle",
-            "sample": f"{steps} steps (n=0..{steps - 1}) of nodes [{lo}, {lo + n_s}) of {prob.mesh.n_nodes}; "
-                      f"bin grid build excluded; {threads} threads"}
+    budget = seconds
+    done_nodes, elapsed, parts = 0, 0.0, []
+    for prob in wl.probs:
+        om = oracle.OracleMesh(prob.mesh.xy, prob.mesh.tri)
+        kind, par = prob.field.kind, prob.field.packed()
+        n_cal = min(prob.mesh.n_nodes, 200_000)
+        t0 = time.perf_counter()
+        om.step(kind, par, prob.dt, 0, prob.v0, lo=0, hi=n_cal, nthreads=threads, want_feet=False)
+        rate = n_cal / max(time.perf_counter() - t0, 1e-6)
+        n_s = int(min(prob.mesh.n_nodes, max(1000, rate * budget / steps)))
+        lo = (prob.mesh.n_nodes - n_s) // 2
+        t0 = time.perf_counter()
+        for st in range(steps):
+            om.step(kind, par, prob.dt, st, prob.v0, lo=lo, hi=lo + n_s, nthreads=threads, want_feet=False)
+        dt = time.perf_counter() - t0
+        om.close()
+        done_nodes += n_s * steps
+        elapsed += dt
+        parts.append(f"{prob.name} nodes [{lo}, {lo + n_s}) of {prob.mesh.n_nodes}")
+        budget -= dt + n_s * steps / rate
+        if budget <= 0:
+            break
+    return {"value": done_nodes / elapsed, "unit": "node-updates/s", "cores": threads, "kind": "oracle",
+            "sample": f"{steps} steps (n=0..{steps - 1}) of " + "; ".join(parts[:4]) +
+                      (f" and {len(parts) - 4} more problems" if len(parts) > 4 else "") +
+                      f"; bin grid build excluded; {threads} threads"}
 
 
 def run_reference(args):
     rank, world, _ = dist_env()
     if rank != 0:
         return
-    prob = build_workload(args)
+    wl = build_workload(args)
     per_step = max(1.0, 120.0 / max(1, args.steps + args.warmup))
     import oracle
     threads = oracle.default_threads()
+    prob = wl.probs[0]
     om = oracle.OracleMesh(prob.mesh.xy, prob.mesh.tri)
     kind, par = prob.field.kind, prob.field.packed()
     n_cal = min(prob.mesh.n_nodes, 100_000)
@@ -182,21 +219,19 @@ def run_reference(args):
         "unit": "node-updates/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": 1e3 * total / len(times), "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": workload_config(args, prob),
+        "config": workload_config(args, wl),
         "cpu_baseline": {"value": value, "unit": "node-updates/s", "cores": threads, "kind": "oracle",
-                         "sample": f"each step: one SL step of nodes [0, {n_s}) of {prob.mesh.n_nodes}"},
+                         "sample": f"each step: one SL step of nodes [0, {n_s}) of {prob.name} "
+                                   f"({prob.mesh.n_nodes} nodes), {threads} threads"},
         "e2e": {"value": value, "unit": "node-updates/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
 
 
-def workload_config(args, prob):
-    m = prob.mesh
-    return {"workload": f"{prob.name}: {m.M}x{m.M} {'graded ' if m.graded else ''}jittered mesh "
-                        f"({m.n_nodes} nodes, {m.n_tri} triangles), field kind {prob.field.kind}, "
-                        f"dt={prob.dt}, {prob.n_steps} steps, {prob.precision}, curve={args.curve}",
-            "nodes": m.n_nodes, "triangles": m.n_tri, "steps_per_run": prob.n_steps,
-            "precision": prob.precision, "l2": "inputs larger than L2 (mesh + values ~1.5 GB)"}
+def workload_config(args, wl):
+    return {"workload": wl.description, "nodes": wl.nodes, "triangles": wl.triangles, "problems": len(wl.probs),
+            "steps_per_run": wl.n_steps, "precision": wl.precision,
+            "l2": "inputs larger than L2 (129 MB)" if wl.nodes * 64 > 2 * 129e6 else "inputs may fit in L2"}
 
 
 def main():
@@ -212,24 +247,25 @@ def main():
         import torch.distributed as dist
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
 
-    prob = build_workload(args)
-    mesh = prob.mesh
-    S = prob.n_steps
-    N = mesh.n_nodes
-    prec = sl.SL_FP64 if prob.precision == "fp64" else sl.SL_FP32
+    wl = build_workload(args)
+    S = wl.n_steps
+    N = wl.nodes
+    prec = sl.SL_FP64 if wl.precision == "fp64" else sl.SL_FP32
     t_setup = time.perf_counter()
-    no, to, xy, tri = sl.pack_meshes([(mesh.xy, mesh.tri)])
-    h = sl.sl_mesh_create(no, to, xy, tri, precision=prec, seed=prob.seed)
+    no, to, xy, tri = sl.pack_meshes([(p.mesh.xy, p.mesh.tri) for p in wl.probs])
+    h = sl.sl_mesh_create(no, to, xy, tri, precision=prec, seed=wl.probs[0].seed)
     curve = {"none": sl.SL_CURVE_NONE, "hilbert": sl.SL_CURVE_HILBERT, "morton": sl.SL_CURVE_MORTON}[args.curve]
-    perm, _ = sl.sl_mesh_reorder(h, curve)
+    lperm, _ = sl.sl_mesh_reorder(h, curve)
+    perm = lperm.astype(np.int64) + np.repeat(no[:-1], np.diff(no))     # global new -> old
     if args.kernel:
         sl.sl_mesh_set_option(h, sl.SL_OPT_KERNEL, args.kernel)
     sl.sl_mesh_set_option(h, sl.SL_OPT_CONFIG, args.config_id)
     if args.hop_budget is not None:
         sl.sl_mesh_set_option(h, sl.SL_OPT_HOP_BUDGET, args.hop_budget)
-    probs = sl.problems([(prob.field.kind, prob.dt, prob.field.packed())])
+    probs = sl.problems([(p.field.kind, p.dt, p.field.packed()) for p in wl.probs])
     vt = torch.float64 if prec == sl.SL_FP64 else torch.float32
-    v0 = torch.tensor(prob.v0[perm], dtype=vt, device="cuda")
+    v0_all = np.concatenate([p.v0 for p in wl.probs])
+    v0 = torch.tensor(v0_all[perm], dtype=vt, device="cuda")
     v = v0.clone()
     w = torch.empty_like(v)
     stream = torch.cuda.current_stream()
@@ -290,8 +326,41 @@ def main():
     phases = {"first_step_ms": first_ms, "later_step_ms": rest_ms,
               "note": "eager launches, one run, after the timed region"}
 
+    fp32_check = None
+    if wl.precision == "fp32" and not args.no_plain:
+        # the same workload on the FP64 mesh: the fast FP64 path (within 1e-12
+        # of the oracle) gives the error of the FP32 result; the plain FP64
+        # kernel gives the speed-up baseline
+        v32 = np.empty(N)
+        sl.sl_mesh_reset_t0(h)
+        vv = v0.clone()
+        sl.sl_run(h, probs, 0, S, vv, w, use_graph=False)
+        v32[perm] = vv.double().cpu().numpy()
+        h64 = sl.sl_mesh_create(no, to, xy, tri, precision=sl.SL_FP64, seed=wl.probs[0].seed)
+        lp64, _ = sl.sl_mesh_reorder(h64, curve)
+        perm64 = lp64.astype(np.int64) + np.repeat(no[:-1], np.diff(no))
+        a64 = torch.tensor(v0_all[perm64], dtype=torch.float64, device="cuda")
+        b64 = torch.empty_like(a64)
+        sl.sl_run(h64, probs, 0, S, a64, b64, use_graph=True)
+        v64 = np.empty(N)
+        v64[perm64] = a64.cpu().numpy()
+        err = np.abs(v32 - v64)
+        sl.sl_mesh_set_option(h64, sl.SL_OPT_KERNEL, 1)
+        a64.copy_(torch.tensor(v0_all[perm64], dtype=torch.float64, device="cuda"))
+
+        def plain_run():
+            sl.sl_mesh_reset_t0(h64)
+            sl.sl_run(h64, probs, 0, S, a64, b64, use_graph=True)
+
+        plain_run()
+        tp = timed(lambda: [plain_run() for _ in range(2)]) / 1e3
+        sl.sl_mesh_destroy(h64)
+        fp32_check = {"max_err_vs_fp64": float(err.max()), "l2_err_vs_fp64": float(np.sqrt((err ** 2).mean())),
+                      "reference": "fast FP64 GPU path on the FP64 mesh (itself within 1e-12 of the CPU oracle)",
+                      "plain_fp64_node_updates_per_s": N * S * 2 / tp}
+
     plain = None
-    if prob.precision == "fp64" and not args.no_plain and args.kernel != 1:
+    if wl.precision == "fp64" and not args.no_plain and args.kernel != 1:
         sl.sl_mesh_set_option(h, sl.SL_OPT_KERNEL, 1)
         one_run()
         k_plain = 2
@@ -303,14 +372,14 @@ def main():
     units = N * S * args.steps * world
     value = units / elapsed
     launch_s = elapsed / (args.steps * S)
-    bpn = BYTES_PER_NODE[prob.precision]
+    bpn = BYTES_PER_NODE[wl.precision]
     peaks, peak_src = measured_peaks()
     achieved_gbs = bpn * N / launch_s / 1e9
 
     # end to end through the C ABI with host buffers (pinned)
     e2e = None
     if not args.no_e2e:
-        host = torch.tensor(prob.v0[perm], dtype=vt).pin_memory()
+        host = torch.tensor(v0_all[perm], dtype=vt).pin_memory()
         hv = host.numpy()
         sl.sl_mesh_reset_t0(h)
         sl.sl_run_host(h, probs, 0, S, hv, use_graph=True)
@@ -328,7 +397,7 @@ def main():
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
-        cpu = cpu_sample(prob, args.cpu_seconds)
+        cpu = cpu_sample(wl, args.cpu_seconds)
 
     sl.sl_mesh_destroy(h)
     if rank != 0:
@@ -349,7 +418,7 @@ def main():
         "dtype": ("f64" if args.kernel == 1 else "df64 (FP32 pairs, 48-bit significand; FP64-accuracy results)")
                  if prec == sl.SL_FP64 else "f32",
         "data": "synthetic",
-        "config": workload_config(args, prob),
+        "config": workload_config(args, wl),
         "roofline": {"bound": "hbm", "achieved": achieved_gbs, "peak": peaks.get("hbm_gbs", 6800.0),
                      "unit": "GB/s", "frac": achieved_gbs / peaks.get("hbm_gbs", 6800.0), "traffic": None,
                      "peak_source": peak_src,
@@ -368,7 +437,9 @@ def main():
         "setup_s": setup_s,
         "phases": phases,
         "plain_fp64": plain,
-        "speedup_vs_plain_fp64": (value / world) / plain["value"] if plain else None,
+        "speedup_vs_plain_fp64": ((value / world) / plain["value"] if plain else
+                                  ((value / world) / fp32_check["plain_fp64_node_updates_per_s"] if fp32_check else None)),
+        "fp32_check": fp32_check,
     }
     print(json.dumps(line), flush=True)
     if dist:

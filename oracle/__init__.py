@@ -77,6 +77,7 @@ def lib():
             L.orc_locate_points.restype = I
             L.orc_margins.argtypes = [P, I64, P, P, P]
             L.orc_feet.argtypes = [I, P, D, I64, I64, P, P, P]
+            L.orc_feet_f32.argtypes = [I, P, D, I64, I64, P, P, P]
             _lib = L
     return _lib
 
@@ -113,6 +114,17 @@ def feet(kind, params, dt, n, xy):
     out = np.empty_like(xy)
     clipped = np.empty(xy.shape[0], dtype=np.uint8)
     lib().orc_feet(int(kind), _ptr(p), float(dt), int(n), xy.shape[0], _ptr(xy), _ptr(out), _ptr(clipped))
+    return out, clipped
+
+
+def feet_f32(kind, params, dt, n, xy_f32):
+    """Feet of the FP32 path (float arithmetic, see orc_feet_f32) for float
+    node coordinates; returns (float32 feet, clipped flags)."""
+    p = np.ascontiguousarray(params, dtype=np.float64)
+    xy = np.ascontiguousarray(xy_f32, dtype=np.float32)
+    out = np.empty_like(xy)
+    clipped = np.empty(xy.shape[0], dtype=np.uint8)
+    lib().orc_feet_f32(int(kind), _ptr(p), float(dt), int(n), xy.shape[0], _ptr(xy), _ptr(out), _ptr(clipped))
     return out, clipped
 
 

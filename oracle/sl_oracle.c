@@ -108,20 +108,17 @@ void orc_field(int kind, const double *p, double x, double y, double t,
     }
 }
 
-/* Euler foot (Eq. 4) followed by the boundary clip.  Returns 1 if clipped. */
-int orc_foot(int kind, const double *p, double dt, double t, double x, double y,
-             double *X, double *Y)
+/* Boundary clip (reading of Sec. 1): if q leaves [0,1]^2, stop the segment
+ * x -> q at its first boundary crossing; every coordinate that attains the
+ * crossing is set exactly to 0 or 1, the other one is clamped to [0,1].
+ * Returns 1 if q was outside. */
+static int clip_segment(double x, double y, double qx, double qy, double *X, double *Y)
 {
-    double fx, fy;
-    orc_field(kind, p, x, y, t, &fx, &fy);
-    double qx = x - dt * fx;
-    double qy = y - dt * fy;
     if (qx >= 0.0 && qx <= 1.0 && qy >= 0.0 && qy <= 1.0) {
         *X = qx;
         *Y = qy;
         return 0;
     }
-    /* stop the segment x -> q at the first crossing of the boundary */
     double dx = qx - x, dy = qy - y;
     double sx = 2.0, sy = 2.0;         /* > 1 means "this axis is not violated" */
     double bx = 0.0, by = 0.0;
@@ -141,6 +138,109 @@ int orc_foot(int kind, const double *p, double dt, double t, double x, double y,
     *X = cx;
     *Y = cy;
     return 1;
+}
+
+/* Euler foot (Eq. 4) followed by the boundary clip.  Returns 1 if clipped. */
+int orc_foot(int kind, const double *p, double dt, double t, double x, double y,
+             double *X, double *Y)
+{
+    double fx, fy;
+    orc_field(kind, p, x, y, t, &fx, &fy);
+    double qx = x - dt * fx;
+    double qy = y - dt * fy;
+    return clip_segment(x, y, qx, qy, X, Y);
+}
+
+/* Single-precision foot of the FP32 path (its triangles are compared on the
+ * same float feet).  Node coordinates are floats; the time factors and the
+ * space factors of each field are evaluated in double and rounded to float
+ * once; the Euler step then runs in float, one rounding per operation:
+ *   AFFINE    f = (c0 + c1 x) + c2 y, X = x - f, with c0 = dt (p0 + p3 t),
+ *             c1 = dt p1, c2 = dt p2 (c3..c5 alike for y)
+ *   ROTATION  X = x + c0 (y - cy), Y = y - c0 (x - cx), c0 = dt p0
+ *   SWIRL     X = x - c0 gx, c0 = dt cos(pi t / T),
+ *             g = (sin^2(pi x) sin(2 pi y), -sin^2(pi y) sin(2 pi x))
+ *   PAPER     X = x - (c0 g1x + c1 g2x), c0 = dt cos(C1 t), c1 = dt sin(C1 t),
+ *             g1 = (cos a, sin a), g2 = (-sin a, cos a), a = C0 |x - c|
+ *   FOURIER8  the same with c0 = dt cos(2 pi t), c1 = dt sin(2 pi t),
+ *             g1 = sum_m a_m cos(phi_m) h_m, g2 = -sum_m a_m sin(phi_m) h_m,
+ *             h_m = (l pi sin(k pi x) cos(l pi y), -k pi cos(k pi x) sin(l pi y))
+ * (the same field as orc_field, split into time and space factors).  A
+ * foot outside the square is clipped in double and rounded to float. */
+void orc_feet_f32(int kind, const double *p, double dt, int64_t n, int64_t npts, const float *xy, float *feet,
+                  uint8_t *clipped)
+{
+    const double t = (double)(n + 1) * dt;
+    float c[6] = {0, 0, 0, 0, 0, 0};
+    if (kind == ORC_FIELD_AFFINE) {
+        c[0] = (float)(dt * (p[0] + p[3] * t));
+        c[1] = (float)(dt * p[1]);
+        c[2] = (float)(dt * p[2]);
+        c[3] = (float)(dt * (p[4] + p[7] * t));
+        c[4] = (float)(dt * p[5]);
+        c[5] = (float)(dt * p[6]);
+    } else if (kind == ORC_FIELD_ROTATION) {
+        c[0] = (float)(dt * p[0]);
+        c[1] = (float)p[1];
+        c[2] = (float)p[2];
+    } else if (kind == ORC_FIELD_SWIRL) {
+        c[0] = (float)(dt * cos(PI * t / p[0]));
+    } else if (kind == ORC_FIELD_PAPER) {
+        c[0] = (float)(dt * cos(p[1] * t));
+        c[1] = (float)(dt * sin(p[1] * t));
+    } else if (kind == ORC_FIELD_FOURIER8) {
+        c[0] = (float)(dt * cos(2.0 * PI * t));
+        c[1] = (float)(dt * sin(2.0 * PI * t));
+    }
+    for (int64_t i = 0; i < npts; ++i) {
+        const float x = xy[2 * i], y = xy[2 * i + 1];
+        const double xd = x, yd = y;
+        float X = x, Y = y;
+        if (kind == ORC_FIELD_AFFINE) {
+            float fx = (c[0] + c[1] * x) + c[2] * y;
+            float fy = (c[3] + c[4] * x) + c[5] * y;
+            X = x - fx;
+            Y = y - fy;
+        } else if (kind == ORC_FIELD_ROTATION) {
+            X = x + c[0] * (y - c[2]);
+            Y = y - c[0] * (x - c[1]);
+        } else if (kind == ORC_FIELD_SWIRL) {
+            double sx = sin(PI * xd), sy = sin(PI * yd);
+            float gx = (float)((sx * sx) * sin(2.0 * PI * yd));
+            float gy = (float)(-(sy * sy) * sin(2.0 * PI * xd));
+            X = x - c[0] * gx;
+            Y = y - c[0] * gy;
+        } else if (kind == ORC_FIELD_PAPER) {
+            double dx = xd - p[2], dy = yd - p[3];
+            double a = p[0] * sqrt(dx * dx + dy * dy);
+            float g1x = (float)cos(a), g1y = (float)sin(a), g2x = (float)(-sin(a)), g2y = (float)cos(a);
+            X = x - (c[0] * g1x + c[1] * g2x);
+            Y = y - (c[0] * g1y + c[1] * g2y);
+        } else if (kind == ORC_FIELD_FOURIER8) {
+            double g1x = 0, g1y = 0, g2x = 0, g2y = 0;
+            for (int m = 0; m < 8; ++m) {
+                double k = p[4 * m], l = p[4 * m + 1], am = p[4 * m + 2], ph = p[4 * m + 3];
+                double hx = l * PI * sin(k * PI * xd) * cos(l * PI * yd);
+                double hy = -k * PI * cos(k * PI * xd) * sin(l * PI * yd);
+                g1x += am * cos(ph) * hx;
+                g1y += am * cos(ph) * hy;
+                g2x -= am * sin(ph) * hx;
+                g2y -= am * sin(ph) * hy;
+            }
+            X = x - (c[0] * (float)g1x + c[1] * (float)g2x);
+            Y = y - (c[0] * (float)g1y + c[1] * (float)g2y);
+        }
+        int cl = 0;
+        if (!(X >= 0.0f && X <= 1.0f && Y >= 0.0f && Y <= 1.0f)) {
+            double cx, cy;
+            cl = clip_segment(xd, yd, (double)X, (double)Y, &cx, &cy);
+            X = (float)cx;
+            Y = (float)cy;
+        }
+        feet[2 * i] = X;
+        feet[2 * i + 1] = Y;
+        if (clipped) clipped[i] = (uint8_t)cl;
+    }
 }
 
 /* ------------------------------------------------------------------ */

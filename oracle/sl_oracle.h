@@ -54,6 +54,8 @@ int orc_locate_points(const orc_mesh *m, int64_t npts, const double *q, int32_t 
 void orc_margins(const orc_mesh *m, int64_t npts, const int32_t *tri, const double *q, double *out);
 void orc_feet(int kind, const double *p, double dt, int64_t n, int64_t npts, const double *xy,
               double *feet, uint8_t *clipped);
+void orc_feet_f32(int kind, const double *p, double dt, int64_t n, int64_t npts, const float *xy, float *feet,
+                  uint8_t *clipped);
 
 #ifdef __cplusplus
 }

@@ -286,14 +286,14 @@ static sl_status ensure_tables(sl_mesh *m, const sl_problem *probs, cudaStream_t
     SL_CUDA(cudaStreamSynchronize(s));
     SL_CUDA(cudaMemcpy(m->d.tparams, key.data(), sizeof(double) * key.size(), cudaMemcpyHostToDevice));
     FieldTableArgs ta;
-    ta.xyd = (const double2 *)m->d.xy;
+    ta.xyd = m->precision == SL_FP64 ? (const double2 *)m->d.xy : nullptr;
+    ta.xyf = m->precision == SL_FP32 ? (const float2 *)m->d.xy : nullptr;
     ta.node_off = m->d.node_off;
     ta.nprob = m->n_problems;
     ta.N = m->N;
     ta.params = m->d.tparams;
     ta.g1 = (float4 *)m->d.g1;
     ta.g2 = (float4 *)m->d.g2;
-    if (m->precision == SL_FP32) return fail(SL_E_STATE, "field tables of FP32 meshes are built by the FP32 path");
     launch_field_tables(ta, s);
     SL_CUDA(cudaGetLastError());
     SL_CUDA(cudaStreamSynchronize(s));
@@ -313,7 +313,7 @@ static sl_status launch_step(const sl_mesh *m, const StepArgs &a, bool debug, cu
 // Walk-queue scratch of the fast kernels (allocated before any recording).
 static sl_status ensure_queue(sl_mesh *m)
 {
-    if (m->opt_hop_budget > 0 && !m->d.queue) {
+    if (m->opt_hop_budget > 0 && m->precision == SL_FP64 && !m->d.queue) {
         SL_CUDA(cudaMalloc(&m->d.queue, sizeof(int32_t) * m->N));
         SL_CUDA(cudaMalloc(&m->d.queue_hops, sizeof(uint32_t) * m->N));
         SL_CUDA(cudaMalloc(&m->d.queue_count, sizeof(uint32_t)));
@@ -324,7 +324,7 @@ static sl_status ensure_queue(sl_mesh *m)
 static sl_status launch_fast(sl_mesh *m, const FastArgs &a0, bool debug, cudaStream_t s)
 {
     FastArgs a = a0;
-    if (m->opt_hop_budget > 0) {
+    if (m->opt_hop_budget > 0 && m->precision == SL_FP64) {
         // long walks continue in the walk kernel (queue scratch owned by the mesh)
         if (!m->d.queue) return fail(SL_E_STATE, "walk queue not allocated");
         a.queue = m->d.queue;
@@ -334,7 +334,7 @@ static sl_status launch_fast(sl_mesh *m, const FastArgs &a0, bool debug, cudaStr
         SL_CUDA(cudaMemsetAsync(m->d.queue_count, 0, sizeof(uint32_t), s));
     }
     if (m->precision == SL_FP64) launch_fast_df(a, m->opt_stats != 0, debug, m->opt_config, m->sms, s);
-    else return fail(SL_E_STATE, "no FP32 kernel is built into this library yet");
+    else launch_fast_f32(a, m->opt_stats != 0, debug, m->opt_config, s);
     SL_CUDA(cudaGetLastError());
     return SL_OK;
 }

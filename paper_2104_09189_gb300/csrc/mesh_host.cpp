@@ -315,6 +315,8 @@ static sl_status make_host_mesh(int32_t n_problems, const int64_t *node_off, con
         delete m;
         return sl::fail(SL_E_NOMEM, "out of host memory");
     }
+    if (precision == SL_FP32)   // the mesh the FP32 path sees: coordinates rounded to float
+        for (double &v : m->xy) v = (double)(float)v;
     st = sl::build_and_validate(m, nbr);
     if (st != SL_OK) {
         delete m;

@@ -134,9 +134,8 @@ struct NodeCounters {
 // a.hop_budget FP32 hops: it stores its current triangle in T^0 and returns
 // false; otherwise it completes (value, T^0, debug outputs) and returns true.
 template <bool kDebug, bool kSpill>
-__device__ __forceinline__ bool step_node(const FastArgs &a, int64_t i, NodeCounters &c)
+__device__ __forceinline__ bool step_node(const FastArgs &a, int64_t i, int pi, NodeCounters &c)
 {
-    const int pi = a.nprob == 1 ? 0 : problem_of(a.node_off, a.nprob, i);
     const FastProb &P = a.probs[pi];
     const float4 xq = a.xyq[i];
     const df x = df_make(xq.x, xq.z), y = df_make(xq.y, xq.w);
@@ -312,9 +311,10 @@ __global__ void __launch_bounds__(kBlock, kMinBlocks) k_step_fast_df(FastArgs a)
     const bool active = i < a.N;
     NodeCounters c;
     bool spilled = false;
+    const int pi = block_problem(a.node_off, a.nprob, a.N, i);
     if (active) {
-        if (a.queue) spilled = !step_node<kDebug, true>(a, i, c);
-        else step_node<kDebug, false>(a, i, c);
+        if (a.queue) spilled = !step_node<kDebug, true>(a, i, pi, c);
+        else step_node<kDebug, false>(a, i, pi, c);
     }
     if (a.queue) {
         // warp-aggregated push of the long walkers onto the walk queue
@@ -399,7 +399,8 @@ __global__ void __launch_bounds__(kBlock) k_finish_fast_df(FastArgs a)
     for (uint32_t q = blockIdx.x * blockDim.x + threadIdx.x; q < count; q += gridDim.x * blockDim.x) {
         NodeCounters c;
         c.hops = a.queue_hops[q];
-        step_node<kDebug, false>(a, a.queue[q], c);
+        const int64_t node = a.queue[q];
+        step_node<kDebug, false>(a, node, a.nprob == 1 ? 0 : problem_of(a.node_off, a.nprob, node), c);
         tot.hops += c.hops;
         hmax = c.hops > hmax ? c.hops : hmax;
         tot.exact += c.exact;
@@ -531,7 +532,7 @@ __global__ void k_field_tables(FieldTableArgs a)
         const double *q = a.params + 49 * (int64_t)pidx;
         const int kind = (int)q[0];
         const double *p = q + 1;
-        const double2 xy = a.xyd[i];
+        const double2 xy = a.xyd ? a.xyd[i] : make_double2((double)a.xyf[i].x, (double)a.xyf[i].y);
         double g1x = 0, g1y = 0, g2x = 0, g2y = 0;
         if (kind == SL_FIELD_SWIRL) {
             double sx, cx, sy, cy;

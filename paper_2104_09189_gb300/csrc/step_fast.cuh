@@ -57,7 +57,7 @@ struct FastArgs {
 // config: launch configuration 0..3 (see step_fast.cu)
 void launch_fast_df(const FastArgs &a, bool stats, bool debug, int config, int sms, cudaStream_t s);
 constexpr int kFastConfigs = 4;
-void launch_fast_f32(const FastArgs &a, bool stats, bool debug, int block, cudaStream_t s);
+void launch_fast_f32(const FastArgs &a, bool stats, bool debug, int config, cudaStream_t s);
 
 // value format conversions for the double-float kernel
 void launch_to_df(const double *src, float2 *dst, int64_t n, cudaStream_t s);
@@ -65,7 +65,8 @@ void launch_from_df(const float2 *src, double *dst, int64_t n, cudaStream_t s);
 
 // node tables of the fields (double precision, once per field)
 struct FieldTableArgs {
-    const double2 *xyd;
+    const double2 *xyd;           // node coordinates (FP64 meshes), or NULL
+    const float2 *xyf;            // node coordinates (FP32 meshes), or NULL
     const int64_t *node_off;
     int32_t nprob;
     int64_t N;

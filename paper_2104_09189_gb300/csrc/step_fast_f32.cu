@@ -1,0 +1,255 @@
+// step_fast_f32.cu -- the FP32 step kernel.
+//
+// The same step (Euler foot at t_{n+1}, boundary clip, barycentric walk from
+// T^0_i -- strategy (b) of Sec. 3 -- and P1 interpolation, Eq. 6 and Remark
+// 1) on a mesh whose coordinates are the double coordinates rounded to
+// float, with float node values:
+//
+//  * the foot is evaluated in float with the operation order given below
+//    (X = x - k g for table fields, ...); a foot that leaves the square is
+//    clipped in double and rounded back to float (the coordinate on the
+//    boundary is exactly 0 or 1);
+//  * the coordinates are exact floats, so an FP32 orientation has the
+//    classic forward error bound (3 + 16 e) e (|t1| + |t2|), e = 2^-24
+//    (Shewchuk 1997, stage A, in single precision): each walk decision is
+//    certified in FP32 and only undecided signs fall back to the double
+//    predicate (a double filter, then an exact expansion) on the floats
+//    promoted exactly -- the located triangle contains the float foot
+//    exactly;
+//  * theta_1, theta_2 (Eq. 6, relative to vertex 3) and the P1 value are
+//    evaluated in float.
+#include "predicates.cuh"
+#include "step_common.cuh"
+#include "step_fast.cuh"
+#include "step_kernels.cuh"
+
+namespace sl {
+
+// Foot in float.  Operation order (each step one IEEE float operation):
+//   AFFINE    f = (c0 + c1 x) + c2 y,  X = x - f   (and c3..c5 for Y)
+//   ROTATION  X = x + c0 (y - c2),     Y = y - c0 (x - c1)
+//   SWIRL     X = x - c0 g1x
+//   PAPER,    X = x - (c0 g1x + c1 g2x)
+//   FOURIER8
+// with c_k = fl32 of the per-step constants and g = fl32 of the double node
+// tables.
+__device__ __forceinline__ void foot_f32(const FastProb &P, const FastArgs &a, int64_t i, float x, float y, float &X,
+                                         float &Y)
+{
+    const float c0 = P.c[0].x, c1 = P.c[1].x, c2 = P.c[2].x;
+    switch (P.kind) {
+    case SL_FIELD_AFFINE: {
+        const float c3 = P.c[3].x, c4 = P.c[4].x, c5 = P.c[5].x;
+        const float fx = __fadd_rn(__fadd_rn(c0, __fmul_rn(c1, x)), __fmul_rn(c2, y));
+        const float fy = __fadd_rn(__fadd_rn(c3, __fmul_rn(c4, x)), __fmul_rn(c5, y));
+        X = __fsub_rn(x, fx);
+        Y = __fsub_rn(y, fy);
+        break;
+    }
+    case SL_FIELD_ROTATION:
+        X = __fadd_rn(x, __fmul_rn(c0, __fsub_rn(y, c2)));
+        Y = __fsub_rn(y, __fmul_rn(c0, __fsub_rn(x, c1)));
+        break;
+    case SL_FIELD_SWIRL: {
+        const float4 g = a.g1[i];
+        X = __fsub_rn(x, __fmul_rn(c0, g.x));
+        Y = __fsub_rn(y, __fmul_rn(c0, g.y));
+        break;
+    }
+    case SL_FIELD_PAPER:
+    case SL_FIELD_FOURIER8: {
+        const float4 g = a.g1[i], q = a.g2[i];
+        X = __fsub_rn(x, __fadd_rn(__fmul_rn(c0, g.x), __fmul_rn(c1, q.x)));
+        Y = __fsub_rn(y, __fadd_rn(__fmul_rn(c0, g.y), __fmul_rn(c1, q.y)));
+        break;
+    }
+    default:
+        X = x;
+        Y = y;
+        break;
+    }
+}
+
+// Stage-A bound of an FP32 cross product of two rounded differences of
+// exact floats, with two-fold margin: 2^-22 (|t1| + |t2|).
+__device__ __forceinline__ float cross_f32(float ux, float uy, float vx, float vy, float &bound)
+{
+    const float t2 = __fmul_rn(uy, vx);
+    const float t1 = __fmul_rn(ux, vy);
+    bound = 0x1p-22f * (fabsf(t1) + fabsf(t2));
+    return __fsub_rn(t1, t2);
+}
+
+template <bool kStats, bool kDebug, int kBlock, int kMinBlocks>
+__global__ void __launch_bounds__(kBlock, kMinBlocks) k_step_fast_f32(FastArgs a)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const bool active = i < a.N;
+    uint32_t hops = 0, exact_tests = 0, clipped_cnt = 0, fallback_cnt = 0, limit_cnt = 0, fp64_tests = 0;
+    const int pi = block_problem(a.node_off, a.nprob, a.N, i);
+    if (active) {
+        const FastProb &P = a.probs[pi];
+        const float2 xf = a.xyf[i];
+        float X, Y;
+        foot_f32(P, a, i, xf.x, xf.y, X, Y);
+        uint32_t flags = 0;
+        if (!(X >= 0.0f && X <= 1.0f && Y >= 0.0f && Y <= 1.0f)) {
+            // boundary clip in double, rounded back to float
+            double cx, cy;
+            clip_to_square((double)xf.x, (double)xf.y, (double)X, (double)Y, cx, cy);
+            X = __double2float_rn(cx);
+            Y = __double2float_rn(cy);
+            flags |= SL_NODE_CLIPPED;
+            clipped_cnt = 1;
+        }
+        const uint32_t fside = (X == 0.0f ? 1u : 0u) | (X == 1.0f ? 2u : 0u) | (Y == 0.0f ? 4u : 0u) |
+                               (Y == 1.0f ? 8u : 0u);
+
+        int32_t j = a.t0[i];
+        const int32_t jstart = j;
+        const uint32_t cap = (uint32_t)a.walk_cap;
+        bool found = false;
+        int s1 = 0, s2 = 0, s3 = 0;
+        float o1 = 0.0f, o2 = 0.0f, dn = 1.0f;
+        int ia = a.tv[0][j], ib = a.tv[1][j], ic = a.tv[2][j];
+        int na = a.tn[0][j], nb = a.tn[1][j], nc = a.tn[2][j];
+        for (;;) {
+            const float2 A = a.xyf[ia], B = a.xyf[ib], C = a.xyf[ic];
+            const float ax = __fsub_rn(A.x, C.x), ay = __fsub_rn(A.y, C.y);
+            const float bx = __fsub_rn(B.x, C.x), by = __fsub_rn(B.y, C.y);
+            const float xx = __fsub_rn(X, C.x), xy = __fsub_rn(Y, C.y);
+            float e1, e2, ed;
+            o1 = cross_f32(xx, xy, bx, by, e1);     // orient(B, C, X): theta_1 * den
+            o2 = cross_f32(ax, ay, xx, xy, e2);     // orient(C, A, X): theta_2 * den
+            dn = cross_f32(ax, ay, bx, by, ed);     // orient(A, B, C) > 0
+            const float o3 = __fsub_rn(__fsub_rn(dn, o1), o2);
+            const float e3 = ed + e1 + e2 + 0x1p-23f * (fabsf(dn) + fabsf(o1) + fabsf(o2));
+            s1 = o1 > e1 ? 1 : (o1 < -e1 ? -1 : 2);
+            s2 = o2 > e2 ? 1 : (o2 < -e2 ? -1 : 2);
+            s3 = o3 > e3 ? 1 : (o3 < -e3 ? -1 : 2);
+            if (s1 == 2 || s2 == 2 || s3 == 2) {
+                // boundary edge with the foot on its side: exactly 0
+                if (s1 == 2 && na < 0 && (fside >> (-1 - na) & 1u)) s1 = 0;
+                if (s2 == 2 && nb < 0 && (fside >> (-1 - nb) & 1u)) s2 = 0;
+                if (s3 == 2 && nc < 0 && (fside >> (-1 - nc) & 1u)) s3 = 0;
+            }
+            if (s1 == 2 || s2 == 2 || s3 == 2) {
+                // the foot on a vertex (e.g. a node whose field vanishes): the
+                // two edges through that vertex have orientation exactly 0
+                const bool onA = X == A.x && Y == A.y, onB = X == B.x && Y == B.y, onC = X == C.x && Y == C.y;
+                if (s1 == 2 && (onB || onC)) s1 = 0;
+                if (s2 == 2 && (onC || onA)) s2 = 0;
+                if (s3 == 2 && (onA || onB)) s3 = 0;
+            }
+            if (s1 == 2 || s2 == 2 || s3 == 2) {
+                // double predicate on the floats promoted exactly
+                const double Xd = X, Yd = Y;
+                if (s1 == 2) {
+                    slp::OrientResult r = slp::orient(B.x, B.y, C.x, C.y, Xd, Yd);
+                    s1 = r.sign;
+                    fp64_tests += r.stage == 1;
+                    exact_tests += r.stage == 2;
+                }
+                if (s2 == 2) {
+                    slp::OrientResult r = slp::orient(C.x, C.y, A.x, A.y, Xd, Yd);
+                    s2 = r.sign;
+                    fp64_tests += r.stage == 1;
+                    exact_tests += r.stage == 2;
+                }
+                if (s3 == 2) {
+                    slp::OrientResult r = slp::orient(A.x, A.y, B.x, B.y, Xd, Yd);
+                    s3 = r.sign;
+                    fp64_tests += r.stage == 1;
+                    exact_tests += r.stage == 2;
+                }
+                flags |= SL_NODE_EXACT;
+            }
+            if (s1 >= 0 && s2 >= 0 && s3 >= 0) {
+                found = true;
+                break;
+            }
+            if (hops >= 2 * cap) break;
+            int k;
+            if (hops < cap) {
+                // the paper's rule: the most negative barycentric coordinate
+                k = -1;
+                float best = 0.0f;
+                if (s1 < 0) { k = 0; best = o1; }
+                if (s2 < 0 && (k < 0 || o2 < best)) { k = 1; best = o2; }
+                if (s3 < 0 && (k < 0 || o3 < best)) { k = 2; best = o3; }
+            } else {
+                if (hops == cap) {
+                    fallback_cnt = 1;
+                    flags |= SL_NODE_FALLBACK;
+                }
+                const int neg[3] = {s1 < 0, s2 < 0, s3 < 0};
+                const int nneg = neg[0] + neg[1] + neg[2];
+                int pick = (int)(mix64_dev(((uint64_t)i << 20) ^ (uint64_t)hops) % (uint64_t)nneg);
+                k = -1;
+                for (int q = 0; q < 3; ++q)
+                    if (neg[q] && pick-- == 0) k = q;
+            }
+            const int32_t nj = k == 0 ? na : (k == 1 ? nb : nc);
+            if (nj < 0) break;         // cannot happen for a foot inside a valid mesh
+            j = nj;
+            ia = a.tv[0][j];
+            ib = a.tv[1][j];
+            ic = a.tv[2][j];
+            na = a.tn[0][j];
+            nb = a.tn[1][j];
+            nc = a.tn[2][j];
+            ++hops;
+        }
+        if (!found) {
+            flags |= SL_NODE_WALK_LIMIT;
+            limit_cnt = 1;
+        }
+        if (s1 == 0 || s2 == 0 || s3 == 0) flags |= SL_NODE_DEGENERATE;
+
+        // theta_1, theta_2 (Eq. 6) and the P1 value (Remark 1) in float
+        const float r = __frcp_rn(dn);
+        const float th1 = __fmul_rn(o1, r), th2 = __fmul_rn(o2, r);
+        const float *vin = (const float *)a.vin;
+        const float v1 = vin[ia], v2 = vin[ib], v3 = vin[ic];
+        const float v = __fmaf_rn(th1, __fsub_rn(v1, v3), __fmaf_rn(th2, __fsub_rn(v2, v3), v3));
+        ((float *)a.vout)[i] = v;
+        if (j != jstart) a.t0[i] = j;
+        if (limit_cnt) atomicOr(a.status, 1u << SL_E_WALK_LIMIT);
+        if (kDebug) {
+            if (a.dbg.feet) {
+                a.dbg.feet[2 * i] = (double)X;
+                a.dbg.feet[2 * i + 1] = (double)Y;
+            }
+            if (a.dbg.tri) a.dbg.tri[i] = j;
+            if (a.dbg.moves) a.dbg.moves[i] = (int32_t)hops;
+            if (a.dbg.flags) a.dbg.flags[i] = (uint8_t)flags;
+        }
+    }
+    if (kStats) warp_stats(a.stats, active, hops, exact_tests, clipped_cnt, fallback_cnt, limit_cnt, fp64_tests);
+}
+
+template <int kBlock, int kMinBlocks>
+static void launch_f32_cfg(const FastArgs &a, bool stats, bool debug, cudaStream_t s)
+{
+    const unsigned grid = (unsigned)((a.N + kBlock - 1) / kBlock);
+    if (grid == 0) return;
+    if (stats) {
+        if (debug) k_step_fast_f32<true, true, kBlock, kMinBlocks><<<grid, kBlock, 0, s>>>(a);
+        else k_step_fast_f32<true, false, kBlock, kMinBlocks><<<grid, kBlock, 0, s>>>(a);
+    } else {
+        if (debug) k_step_fast_f32<false, true, kBlock, kMinBlocks><<<grid, kBlock, 0, s>>>(a);
+        else k_step_fast_f32<false, false, kBlock, kMinBlocks><<<grid, kBlock, 0, s>>>(a);
+    }
+}
+
+void launch_fast_f32(const FastArgs &a, bool stats, bool debug, int config, cudaStream_t s)
+{
+    switch (config) {
+    case 1: launch_f32_cfg<256, 3>(a, stats, debug, s); break;
+    case 2: launch_f32_cfg<128, 8>(a, stats, debug, s); break;
+    case 3: launch_f32_cfg<128, 6>(a, stats, debug, s); break;
+    default: launch_f32_cfg<256, 4>(a, stats, debug, s); break;
+    }
+}
+
+}  // namespace sl
