@@ -48,7 +48,8 @@ def parse():
     ap.add_argument("--cells", type=int, default=None, help="override cells per side (smaller test runs)")
     ap.add_argument("--kernel", type=int, default=0, help="SL_OPT_KERNEL (0 auto, 1 plain FP64, 2 tiled)")
     ap.add_argument("--curve", default="hilbert", choices=["none", "hilbert", "morton"])
-    ap.add_argument("--config-id", type=int, default=0, help="SL_OPT_CONFIG launch configuration (0..3)")
+    ap.add_argument("--config-id", type=int, default=None, help="SL_OPT_CONFIG launch configuration (0..5); "
+                    "default: chosen by sl_autotune")
     ap.add_argument("--hop-budget", type=int, default=None, help="SL_OPT_HOP_BUDGET (default: library's)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
@@ -259,7 +260,9 @@ def main():
     perm = lperm.astype(np.int64) + np.repeat(no[:-1], np.diff(no))     # global new -> old
     if args.kernel:
         sl.sl_mesh_set_option(h, sl.SL_OPT_KERNEL, args.kernel)
-    sl.sl_mesh_set_option(h, sl.SL_OPT_CONFIG, args.config_id)
+    if args.config_id is not None:
+        sl.sl_mesh_set_option(h, sl.SL_OPT_CONFIG, args.config_id)
+        sl.sl_mesh_set_option(h, sl.SL_OPT_CONFIG_FIRST, args.config_id)
     if args.hop_budget is not None:
         sl.sl_mesh_set_option(h, sl.SL_OPT_HOP_BUDGET, args.hop_budget)
     probs = sl.problems([(p.field.kind, p.dt, p.field.packed()) for p in wl.probs])
@@ -269,6 +272,9 @@ def main():
     v = v0.clone()
     w = torch.empty_like(v)
     stream = torch.cuda.current_stream()
+    tune = None
+    if args.config_id is None and args.kernel != 1:
+        tune = sl.sl_autotune(h, probs, 3, v, w)
     setup_s = time.perf_counter() - t_setup
 
     def one_run():
@@ -436,6 +442,7 @@ def main():
                  "clipped": stats["clipped"], "fallbacks": stats["fallbacks"]},
         "setup_s": setup_s,
         "phases": phases,
+        "autotune": tune,
         "plain_fp64": plain,
         "speedup_vs_plain_fp64": ((value / world) / plain["value"] if plain else
                                   ((value / world) / fp32_check["plain_fp64_node_updates_per_s"] if fp32_check else None)),

@@ -121,12 +121,16 @@ typedef enum {
     SL_OPT_KERNEL = 2,       /* 0 = auto (fast), 1 = plain FP64 kernel, 2 = fast kernel */
     SL_OPT_BLOCK = 3,        /* threads per block (0 = auto) */
     SL_OPT_TILES_PER_SM = 4, /* reserved */
-    SL_OPT_CONFIG = 5,       /* launch configuration of the fast kernels, 0..3:
-                                threads per block x blocks per SM = 256x4, 256x3, 128x8, 128x6 */
-    SL_OPT_HOP_BUDGET = 6    /* FP32 walk hops a node makes in the main pass before it moves to the
+    SL_OPT_CONFIG = 5,       /* launch configuration of the fast kernels, 0..5: threads per block x
+                                blocks per SM the registers are sized for = 256x4, 256x3, 128x8,
+                                128x6, 256x5, 128x12 (default 5) */
+    SL_OPT_HOP_BUDGET = 6,   /* FP32 walk hops a node makes in the main pass before it moves to the
                                 walk queue (a lean, fully occupied walk kernel continues it);
                                 0 = no queue (the default: on the benchmark meshes the extra resident
                                 walks thrash L1).  sl_step_noalloc never queues. */
+    SL_OPT_CONFIG_FIRST = 7  /* launch configuration for a step whose walks start at the initial
+                                incident triangles (the first step after sl_mesh_create or
+                                sl_mesh_reset_t0): long walks favour fewer resident warps (default 0) */
 } sl_option;
 
 /*
@@ -255,6 +259,32 @@ sl_status sl_run_host(sl_mesh *m, const sl_problem *probs, int64_t n0, int32_t n
  */
 sl_status sl_step_noalloc(sl_mesh *m, const sl_problem *probs, int64_t n, const double *v_in, double *v_out,
                           void *stream);
+
+/* Result of sl_autotune: chosen launch configurations and the measured
+ * times per configuration (milliseconds; -1 where not measured). */
+#define SL_TUNE_MAX_CONFIGS 8
+typedef struct {
+    int32_t config_first;                 /* chosen SL_OPT_CONFIG_FIRST */
+    int32_t config_rest;                  /* chosen SL_OPT_CONFIG */
+    int32_t n_configs;                    /* configurations measured */
+    int32_t reserved;
+    float first_ms[SL_TUNE_MAX_CONFIGS];  /* one step from the initial start triangles */
+    float rest_ms[SL_TUNE_MAX_CONFIGS];   /* mean of the later steps */
+} sl_tune;
+
+/*
+ * sl_autotune -- choose the launch configurations of the fast kernels for
+ * this mesh and these problems by measurement: for every configuration, one
+ * step from the initial start triangles and `probe_steps` later steps are
+ * timed with CUDA events on `stream`; the fastest configuration of each
+ * phase becomes SL_OPT_CONFIG_FIRST and SL_OPT_CONFIG.  v (device, N values,
+ * V^0) and v_scratch (device, N values) are used as in sl_run; v, T^0 and
+ * the statistics counters are restored before returning (the call
+ * synchronises and allocates temporary device buffers).  No counterpart in
+ * the paper: it tunes the launch shape of the fused step.
+ */
+sl_status sl_autotune(sl_mesh *m, const sl_problem *probs, int32_t probe_steps, void *v, void *v_scratch,
+                      sl_tune *out, void *stream);
 
 /* T^0 export / import (device, N int32 global triangle indices in current
  * numbering); with V^n this is the whole state of a run (resume). */

@@ -17,19 +17,20 @@ from ._build import LIB as _LIB_PATH
 __all__ = [
     "SL_OK", "SL_E_ARG", "SL_E_MESH", "SL_E_NOMEM", "SL_E_CUDA", "SL_E_WALK_LIMIT", "SL_E_STATE",
     "SL_FP64", "SL_FP32", "SL_CURVE_NONE", "SL_CURVE_HILBERT", "SL_CURVE_MORTON",
-    "SL_OPT_STATS", "SL_OPT_WALK_CAP", "SL_OPT_KERNEL", "SL_OPT_BLOCK", "SL_OPT_TILES_PER_SM", "SL_OPT_CONFIG", "SL_OPT_HOP_BUDGET",
+    "SL_OPT_STATS", "SL_OPT_WALK_CAP", "SL_OPT_KERNEL", "SL_OPT_BLOCK", "SL_OPT_TILES_PER_SM", "SL_OPT_CONFIG", "SL_OPT_HOP_BUDGET", "SL_OPT_CONFIG_FIRST",
     "SL_NODE_CLIPPED", "SL_NODE_DEGENERATE", "SL_NODE_EXACT", "SL_NODE_FALLBACK", "SL_NODE_WALK_LIMIT",
     "SL_NODE_RANGE", "SLError", "sl_problem", "problems", "pack_meshes",
     "sl_mesh_create", "sl_mesh_validate", "sl_mesh_reorder", "sl_step", "sl_run", "sl_run_host", "sl_mesh_get_t0",
     "sl_mesh_set_t0", "sl_mesh_reset_t0", "sl_mesh_status", "sl_mesh_stats", "sl_mesh_set_option", "sl_mesh_info",
     "sl_mesh_export", "sl_mesh_destroy", "sl_last_error", "library", "EXPORTED", "sl_step_noalloc",
-    "SL_NOALLOC_MAX_NODES", "SL_NOALLOC_MAX_PROBLEMS",
+    "SL_NOALLOC_MAX_NODES", "SL_NOALLOC_MAX_PROBLEMS", "sl_autotune",
 ]
 
 SL_OK, SL_E_ARG, SL_E_MESH, SL_E_NOMEM, SL_E_CUDA, SL_E_WALK_LIMIT, SL_E_STATE = range(7)
 SL_FP64, SL_FP32 = 0, 1
 SL_CURVE_NONE, SL_CURVE_HILBERT, SL_CURVE_MORTON = 0, 1, 2
-SL_OPT_STATS, SL_OPT_WALK_CAP, SL_OPT_KERNEL, SL_OPT_BLOCK, SL_OPT_TILES_PER_SM, SL_OPT_CONFIG, SL_OPT_HOP_BUDGET = range(7)
+(SL_OPT_STATS, SL_OPT_WALK_CAP, SL_OPT_KERNEL, SL_OPT_BLOCK, SL_OPT_TILES_PER_SM, SL_OPT_CONFIG, SL_OPT_HOP_BUDGET,
+ SL_OPT_CONFIG_FIRST) = range(8)
 SL_NODE_CLIPPED, SL_NODE_DEGENERATE, SL_NODE_EXACT, SL_NODE_FALLBACK, SL_NODE_WALK_LIMIT, SL_NODE_RANGE = (
     1, 2, 4, 8, 16, 32)
 SL_NPARAMS = 48
@@ -42,7 +43,7 @@ _STATUS_NAMES = {0: "SL_OK", 1: "SL_E_ARG", 2: "SL_E_MESH", 3: "SL_E_NOMEM", 4: 
 # every entry point declared in include/sl.h
 EXPORTED = ("sl_mesh_create", "sl_mesh_validate", "sl_mesh_reorder", "sl_step", "sl_run", "sl_run_host", "sl_mesh_get_t0",
             "sl_mesh_set_t0", "sl_mesh_reset_t0", "sl_mesh_status", "sl_mesh_stats", "sl_mesh_set_option", "sl_mesh_info",
-            "sl_mesh_export", "sl_mesh_destroy", "sl_last_error", "sl_step_noalloc")
+            "sl_mesh_export", "sl_mesh_destroy", "sl_last_error", "sl_step_noalloc", "sl_autotune")
 
 
 class SLError(RuntimeError):
@@ -60,6 +61,11 @@ class sl_problem(ctypes.Structure):
 class sl_debug(ctypes.Structure):
     _fields_ = [("feet", ctypes.c_void_p), ("tri", ctypes.c_void_p), ("moves", ctypes.c_void_p),
                 ("flags", ctypes.c_void_p)]
+
+
+class sl_tune(ctypes.Structure):
+    _fields_ = [("config_first", ctypes.c_int32), ("config_rest", ctypes.c_int32), ("n_configs", ctypes.c_int32),
+                ("reserved", ctypes.c_int32), ("first_ms", ctypes.c_float * 8), ("rest_ms", ctypes.c_float * 8)]
 
 
 class sl_stats(ctypes.Structure):
@@ -98,6 +104,7 @@ def library():
         "sl_mesh_info": [P, P, P, P, P],
         "sl_mesh_export": [P, P, P, P],
         "sl_step_noalloc": [P, P, I64, P, P, P],
+        "sl_autotune": [P, P, I32, P, P, P, P],
     }
     for name, args in sig.items():
         f = getattr(L, name)
@@ -292,3 +299,15 @@ def sl_step_noalloc(h, probs, n, v_in, v_out, stream=None):
     most SL_NOALLOC_MAX_NODES nodes).  For callers that cannot allocate device
     memory while stepping."""
     _check(library().sl_step_noalloc(h, probs, int(n), _ptr(v_in), _ptr(v_out), _stream(stream)))
+
+
+def sl_autotune(h, probs, probe_steps, v, v_scratch, stream=None):
+    """Time every launch configuration of the fast kernels on this mesh and
+    set the fastest (see sl.h); returns the measurements."""
+    t = sl_tune()
+    _check(library().sl_autotune(h, probs, int(probe_steps), _ptr(v), _ptr(v_scratch), ctypes.byref(t),
+                                 _stream(stream)))
+    n = t.n_configs
+    return {"config_first": t.config_first, "config_rest": t.config_rest,
+            "first_ms": [round(float(x), 4) for x in list(t.first_ms)[:n]],
+            "rest_ms": [round(float(x), 4) for x in list(t.rest_ms)[:n]]}

@@ -39,7 +39,7 @@ int32_t default_walk_cap(const sl_mesh *m)
 void free_device(sl_mesh *m)
 {
     DeviceMesh &d = m->d;
-    void *ptrs[] = {d.xy, d.tv[0], d.tv[1], d.tv[2], d.tn[0], d.tn[1], d.tn[2], d.t0, d.t0_init, d.node_off,
+    void *ptrs[] = {d.xy, d.tv[0], d.tv[1], d.tv[2], d.tn[0], d.tn[1], d.tn[2], d.t0, d.t0_init, d.t0v, d.node_off,
                     d.status, d.stats, d.probs, d.fprobs, d.xyq, d.xyh, d.g1, d.g2, d.tparams, d.dfa, d.dfb, d.queue, d.queue_hops, d.queue_count,
                     m->host_v, m->host_v2};
     for (void *p : ptrs)
@@ -106,6 +106,9 @@ static sl_status upload_arrays(sl_mesh *m)
     SL_CUDA(cudaMemcpy(d.t0, m->t0.data(), sizeof(int32_t) * N, cudaMemcpyHostToDevice));
     SL_CUDA(cudaMemcpy(d.t0_init, m->t0_init.data(), sizeof(int32_t) * N, cudaMemcpyHostToDevice));
     SL_CUDA(cudaMemcpy(d.node_off, m->node_off.data(), sizeof(int64_t) * (m->n_problems + 1), cudaMemcpyHostToDevice));
+    launch_fill_t0v(d.t0, d.tv[0], d.tv[1], d.tv[2], (int4 *)d.t0v, N, 0);
+    SL_CUDA(cudaGetLastError());
+    SL_CUDA(cudaDeviceSynchronize());
     return SL_OK;
 }
 
@@ -125,6 +128,7 @@ sl_status upload(sl_mesh *m)
     SL_CUDA(cudaMalloc(&d.t0, sizeof(int32_t) * N));
     if (m->precision == SL_FP64) SL_CUDA(cudaMalloc(&d.xyh, sizeof(float2) * N));
     SL_CUDA(cudaMalloc(&d.t0_init, sizeof(int32_t) * N));
+    SL_CUDA(cudaMalloc(&d.t0v, sizeof(int4) * N));
     SL_CUDA(cudaMalloc(&d.node_off, sizeof(int64_t) * (m->n_problems + 1)));
     SL_CUDA(cudaMalloc(&d.status, sizeof(uint32_t) * kStatusWords));
     SL_CUDA(cudaMalloc(&d.stats, sizeof(unsigned long long) * kStatCounters));
@@ -182,6 +186,7 @@ static StepArgs make_args(const sl_mesh *m, const ProbStep *probs_dev, const voi
         a.tn[k] = m->d.tn[k];
     }
     a.t0 = m->d.t0;
+    a.t0v = (int4 *)m->d.t0v;
     a.vin = vin;
     a.vout = vout;
     a.probs = probs_dev;
@@ -208,6 +213,7 @@ static FastArgs make_fast_args(const sl_mesh *m, const FastProb *fp, const void 
         a.tn[k] = m->d.tn[k];
     }
     a.t0 = m->d.t0;
+    a.t0v = (int4 *)m->d.t0v;
     a.vin = vin;
     a.vout = vout;
     a.g1 = (const float4 *)m->d.g1;
@@ -321,7 +327,7 @@ static sl_status ensure_queue(sl_mesh *m)
     return SL_OK;
 }
 
-static sl_status launch_fast(sl_mesh *m, const FastArgs &a0, bool debug, cudaStream_t s)
+static sl_status launch_fast(sl_mesh *m, const FastArgs &a0, bool debug, int config, cudaStream_t s)
 {
     FastArgs a = a0;
     if (m->opt_hop_budget > 0 && m->precision == SL_FP64) {
@@ -333,8 +339,8 @@ static sl_status launch_fast(sl_mesh *m, const FastArgs &a0, bool debug, cudaStr
         a.hop_budget = m->opt_hop_budget;
         SL_CUDA(cudaMemsetAsync(m->d.queue_count, 0, sizeof(uint32_t), s));
     }
-    if (m->precision == SL_FP64) launch_fast_df(a, m->opt_stats != 0, debug, m->opt_config, m->sms, s);
-    else launch_fast_f32(a, m->opt_stats != 0, debug, m->opt_config, s);
+    if (m->precision == SL_FP64) launch_fast_df(a, m->opt_stats != 0, debug, config, m->sms, s);
+    else launch_fast_f32(a, m->opt_stats != 0, debug, config, s);
     SL_CUDA(cudaGetLastError());
     return SL_OK;
 }
@@ -390,8 +396,12 @@ static sl_status run_steps(sl_mesh *m, const sl_problem *probs, int64_t n0, int3
     const size_t elem = m->precision == SL_FP64 ? sizeof(double) : sizeof(float);
     GraphCache &g = m->graph;
     std::vector<uint8_t> key((const uint8_t *)probs, (const uint8_t *)(probs + m->n_problems));
+    const bool first_initial = m->t0_initial;
     const bool reuse = use_graph && g.valid && g.exec && g.n0 == n0 && g.n_steps == n_steps && g.v == v &&
-                       g.v_scratch == v2 && g.probs == key && g.kernel == m->opt_kernel && g.stats == m->opt_stats;
+                       g.v_scratch == v2 && g.probs == key && g.kernel == m->opt_kernel && g.stats == m->opt_stats &&
+                       g.config == m->opt_config && g.config_first == m->opt_config_first &&
+                       g.t0_initial == first_initial;
+    auto config_of = [&](int32_t k) { return (k == 0 && first_initial) ? m->opt_config_first : m->opt_config; };
     if (!reuse) {
         // synchronous copies: a graph recorded below may replay them later
         SL_CUDA(cudaStreamSynchronize(s));
@@ -415,7 +425,7 @@ static sl_status run_steps(sl_mesh *m, const sl_problem *probs, int64_t n0, int3
             void *a = v2, *b = v;
             for (int32_t k = 0; k < n_steps; ++k) {
                 FastArgs args = make_fast_args(m, (const FastProb *)((char *)m->d.fprobs + fper * k), a, b, nullptr);
-                sl_status st = launch_fast(m, args, false, q);
+                sl_status st = launch_fast(m, args, false, config_of(k), q);
                 if (st != SL_OK) return st;
                 void *t = a;
                 a = b;
@@ -430,7 +440,7 @@ static sl_status run_steps(sl_mesh *m, const sl_problem *probs, int64_t n0, int3
             sl_status st;
             if (fast) {
                 FastArgs args = make_fast_args(m, (const FastProb *)((char *)m->d.fprobs + fper * k), a, b, nullptr);
-                st = launch_fast(m, args, false, q);
+                st = launch_fast(m, args, false, config_of(k), q);
             } else {
                 StepArgs args = make_args(m, (const ProbStep *)((char *)m->d.probs + per * k), a, b, nullptr);
                 st = launch_step(m, args, false, q);
@@ -474,6 +484,9 @@ static sl_status run_steps(sl_mesh *m, const sl_problem *probs, int64_t n0, int3
         g.probs = key;
         g.kernel = m->opt_kernel;
         g.stats = m->opt_stats;
+        g.config = m->opt_config;
+        g.config_first = m->opt_config_first;
+        g.t0_initial = first_initial;
     }
     SL_CUDA(cudaGraphLaunch((cudaGraphExec_t)g.exec, s));
     return SL_OK;
@@ -505,6 +518,7 @@ extern "C" sl_status sl_step(sl_mesh *m, const sl_problem *probs, int64_t n, con
         StepArgs a = make_args(m, (const ProbStep *)m->d.probs, v_in, v_out, dbg);
         st = launch_step(m, a, debug, s);
         m->stepped = true;
+        m->t0_initial = false;
         return st;
     }
     st = ensure_tables(m, probs, s);
@@ -522,16 +536,17 @@ extern "C" sl_status sl_step(sl_mesh *m, const sl_problem *probs, int64_t n, con
         if (!m->d.dfb) SL_CUDA(cudaMalloc(&m->d.dfb, sizeof(float2) * m->N));
         launch_to_df((const double *)v_in, (float2 *)m->d.dfa, m->N, s);
         FastArgs a = make_fast_args(m, (const FastProb *)m->d.fprobs, m->d.dfa, m->d.dfb, dbg);
-        st = launch_fast(m, a, debug, s);
+        st = launch_fast(m, a, debug, m->t0_initial ? m->opt_config_first : m->opt_config, s);
         if (st != SL_OK) return st;
         launch_from_df((const float2 *)m->d.dfb, (double *)v_out, m->N, s);
         SL_CUDA(cudaGetLastError());
     } else {
         FastArgs a = make_fast_args(m, (const FastProb *)m->d.fprobs, v_in, v_out, dbg);
-        st = launch_fast(m, a, debug, s);
+        st = launch_fast(m, a, debug, m->t0_initial ? m->opt_config_first : m->opt_config, s);
         if (st != SL_OK) return st;
     }
     m->stepped = true;
+    m->t0_initial = false;
     return SL_OK;
 }
 
@@ -548,6 +563,7 @@ extern "C" sl_status sl_run(sl_mesh *m, const sl_problem *probs, int64_t n0, int
         st = run_steps(m, probs, n0, n_steps, v, v_scratch, use_graph, s);
         if (st != SL_OK) return st;
         m->stepped = true;
+        m->t0_initial = false;
     }
     st = read_status(m, s);
     if (stats) {
@@ -574,6 +590,7 @@ extern "C" sl_status sl_run_host(sl_mesh *m, const sl_problem *probs, int64_t n0
         st = run_steps(m, probs, n0, n_steps, m->host_v, m->host_v2, use_graph, s);
         if (st != SL_OK) return st;
         m->stepped = true;
+        m->t0_initial = false;
     }
     SL_CUDA(cudaMemcpyAsync(v_host, m->host_v, bytes, cudaMemcpyDeviceToHost, s));
     st = read_status(m, s);
@@ -602,6 +619,9 @@ extern "C" sl_status sl_mesh_set_t0(sl_mesh *m, const int32_t *t0_dev, void *str
             if (h[i] < m->tri_off[p] || h[i] >= m->tri_off[p + 1])
                 return fail(SL_E_ARG, "sl_mesh_set_t0: entry " + std::to_string(i) + " is not a triangle of its problem");
     SL_CUDA(cudaMemcpyAsync(m->d.t0, t0_dev, sizeof(int32_t) * m->N, cudaMemcpyDeviceToDevice, (cudaStream_t)stream));
+    m->t0_initial = false;
+    launch_fill_t0v(m->d.t0, m->d.tv[0], m->d.tv[1], m->d.tv[2], (int4 *)m->d.t0v, m->N, (cudaStream_t)stream);
+    SL_CUDA(cudaGetLastError());
     return SL_OK;
 }
 
@@ -610,6 +630,9 @@ extern "C" sl_status sl_mesh_reset_t0(sl_mesh *m, void *stream)
     if (!m) return fail(SL_E_ARG, "sl_mesh_reset_t0: mesh is NULL");
     SL_CUDA(cudaMemcpyAsync(m->d.t0, m->d.t0_init, sizeof(int32_t) * m->N, cudaMemcpyDeviceToDevice,
                             (cudaStream_t)stream));
+    m->t0_initial = true;
+    launch_fill_t0v(m->d.t0, m->d.tv[0], m->d.tv[1], m->d.tv[2], (int4 *)m->d.t0v, m->N, (cudaStream_t)stream);
+    SL_CUDA(cudaGetLastError());
     return SL_OK;
 }
 
@@ -665,4 +688,96 @@ extern "C" void sl_mesh_destroy(sl_mesh *m)
     if (!m) return;
     free_device(m);
     delete m;
+}
+
+extern "C" sl_status sl_autotune(sl_mesh *m, const sl_problem *probs, int32_t probe_steps, void *v, void *v_scratch,
+                                 sl_tune *out, void *stream)
+{
+    if (!m || !probs || !v || !v_scratch || !out) return fail(SL_E_ARG, "sl_autotune: NULL argument");
+    if (probe_steps < 1 || probe_steps > 1000) return fail(SL_E_ARG, "sl_autotune: probe_steps must be in [1, 1000]");
+    if (!use_fast(m)) return fail(SL_E_STATE, "sl_autotune: the plain kernel has no launch configurations");
+    sl_status st = check_device(m);
+    if (st != SL_OK) return st;
+    cudaStream_t s = (cudaStream_t)stream;
+    const size_t vbytes = (m->precision == SL_FP64 ? sizeof(double) : sizeof(float)) * m->N;
+    void *v_save = nullptr, *t_save = nullptr, *s_save = nullptr;
+    cudaEvent_t e0 = nullptr, e1 = nullptr, e2 = nullptr;
+    const int32_t cfg0 = m->opt_config, cfgf0 = m->opt_config_first;
+    const bool init0 = m->t0_initial;
+    std::memset(out, 0, sizeof(*out));
+    for (int k = 0; k < SL_TUNE_MAX_CONFIGS; ++k) out->first_ms[k] = out->rest_ms[k] = -1.0f;
+    auto cleanup = [&]() {
+        if (v_save) cudaFree(v_save);
+        if (t_save) cudaFree(t_save);
+        if (s_save) cudaFree(s_save);
+        if (e0) cudaEventDestroy(e0);
+        if (e1) cudaEventDestroy(e1);
+        if (e2) cudaEventDestroy(e2);
+    };
+    auto run = [&]() -> sl_status {
+        SL_CUDA(cudaStreamSynchronize(s));
+        SL_CUDA(cudaMalloc(&v_save, vbytes));
+        SL_CUDA(cudaMalloc(&t_save, sizeof(int32_t) * m->N));
+        SL_CUDA(cudaMalloc(&s_save, sizeof(unsigned long long) * kStatCounters));
+        SL_CUDA(cudaMemcpy(v_save, v, vbytes, cudaMemcpyDeviceToDevice));
+        SL_CUDA(cudaMemcpy(t_save, m->d.t0, sizeof(int32_t) * m->N, cudaMemcpyDeviceToDevice));
+        SL_CUDA(cudaMemcpy(s_save, m->d.stats, sizeof(unsigned long long) * kStatCounters, cudaMemcpyDeviceToDevice));
+        SL_CUDA(cudaEventCreate(&e0));
+        SL_CUDA(cudaEventCreate(&e1));
+        SL_CUDA(cudaEventCreate(&e2));
+        float best_first = 1e30f, best_rest = 1e30f;
+        {   // one untimed step first: lazy module loading and first-touch costs
+            sl_status r = sl_mesh_reset_t0(m, s);
+            if (r == SL_OK) r = run_steps(m, probs, 0, 1, v, v_scratch, 0, s);
+            if (r != SL_OK) return r;
+            SL_CUDA(cudaStreamSynchronize(s));
+        }
+        for (int c = 0; c < kFastConfigs && c < SL_TUNE_MAX_CONFIGS; ++c) {
+            m->opt_config = m->opt_config_first = c;
+            SL_CUDA(cudaMemcpyAsync(v, v_save, vbytes, cudaMemcpyDeviceToDevice, s));
+            sl_status r = sl_mesh_reset_t0(m, s);
+            if (r != SL_OK) return r;
+            SL_CUDA(cudaEventRecord(e0, s));
+            r = run_steps(m, probs, 0, 1, v, v_scratch, 0, s);
+            if (r != SL_OK) return r;
+            m->t0_initial = false;
+            SL_CUDA(cudaEventRecord(e1, s));
+            r = run_steps(m, probs, 1, probe_steps, v, v_scratch, 0, s);
+            if (r != SL_OK) return r;
+            SL_CUDA(cudaEventRecord(e2, s));
+            SL_CUDA(cudaEventSynchronize(e2));
+            float f = 0.f, g = 0.f;
+            SL_CUDA(cudaEventElapsedTime(&f, e0, e1));
+            SL_CUDA(cudaEventElapsedTime(&g, e1, e2));
+            g /= (float)probe_steps;
+            out->first_ms[c] = f;
+            out->rest_ms[c] = g;
+            out->n_configs = c + 1;
+            if (f < best_first) { best_first = f; out->config_first = c; }
+            if (g < best_rest) { best_rest = g; out->config_rest = c; }
+        }
+        // restore values, T^0 and counters; keep the chosen configurations
+        SL_CUDA(cudaMemcpyAsync(v, v_save, vbytes, cudaMemcpyDeviceToDevice, s));
+        SL_CUDA(cudaMemcpyAsync(m->d.t0, t_save, sizeof(int32_t) * m->N, cudaMemcpyDeviceToDevice, s));
+        launch_fill_t0v(m->d.t0, m->d.tv[0], m->d.tv[1], m->d.tv[2], (int4 *)m->d.t0v, m->N, s);
+        SL_CUDA(cudaMemcpyAsync(m->d.stats, s_save, sizeof(unsigned long long) * kStatCounters, cudaMemcpyDeviceToDevice, s));
+        SL_CUDA(cudaMemsetAsync(m->d.status, 0, sizeof(uint32_t) * kStatusWords, s));
+        SL_CUDA(cudaStreamSynchronize(s));
+        m->opt_config = out->config_rest;
+        m->opt_config_first = out->config_first;
+        m->t0_initial = init0;
+        if (m->graph.exec) cudaGraphExecDestroy((cudaGraphExec_t)m->graph.exec);
+        m->graph = GraphCache();
+        return SL_OK;
+    };
+    st = run();
+    if (st != SL_OK) {
+        m->opt_config = cfg0;
+        m->opt_config_first = cfgf0;
+        m->t0_initial = init0;
+        if (m->graph.exec) cudaGraphExecDestroy((cudaGraphExec_t)m->graph.exec);
+        m->graph = GraphCache();
+    }
+    cleanup();
+    return st;
 }

@@ -407,8 +407,12 @@ extern "C" sl_status sl_mesh_set_option(sl_mesh *m, int32_t option, int64_t valu
         m->opt_hop_budget = (int32_t)value;
         break;
     case SL_OPT_CONFIG:
-        if (value < 0 || value > 3) return sl::fail(SL_E_ARG, "launch configuration must be 0..3");
+        if (value < 0 || value > 5) return sl::fail(SL_E_ARG, "launch configuration must be 0..5");
         m->opt_config = (int32_t)value;
+        break;
+    case SL_OPT_CONFIG_FIRST:
+        if (value < 0 || value > 5) return sl::fail(SL_E_ARG, "launch configuration must be 0..5");
+        m->opt_config_first = (int32_t)value;
         break;
     default: return sl::fail(SL_E_ARG, "unknown option");
     }

@@ -193,6 +193,7 @@ extern "C" sl_status sl_step_noalloc(sl_mesh *m, const sl_problem *probs, int64_
         a.tn[k] = m->d.tn[k];
     }
     a.t0 = m->d.t0;
+    a.t0v = (int4 *)m->d.t0v;
     a.vin = v_out;
     a.vout = sc.values;
     a.g1 = (const float4 *)m->d.g1;
@@ -209,5 +210,6 @@ extern "C" sl_status sl_step_noalloc(sl_mesh *m, const sl_problem *probs, int64_
     e = cudaGetLastError();
     if (e != cudaSuccess) return fail(SL_E_CUDA, std::string("sl_step_noalloc: launch: ") + cudaGetErrorString(e));
     m->stepped = true;
+    m->t0_initial = false;
     return SL_OK;
 }

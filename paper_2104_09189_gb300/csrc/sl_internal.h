@@ -33,6 +33,7 @@ struct DeviceMesh {
                                                     // boundary: -1 - side (0: x=0, 1: x=1, 2: y=0, 3: y=1)
     int32_t *t0 = nullptr;            // start / last foot triangle of node i (global)
     int32_t *t0_init = nullptr;       // the initial start triangles (global)
+    void *t0v = nullptr;              // int4 (T^0, its vertex ids) per node
     int64_t *node_off = nullptr;      // n_problems + 1
     uint32_t *status = nullptr;       // [0] = OR of (1 << sl_status); others reserved
     unsigned long long *stats = nullptr;   // 8 counters (sl_stats order)
@@ -59,6 +60,8 @@ struct GraphCache {
     std::vector<uint8_t> probs;       // problems the graph was recorded with
     int32_t kernel = 0;
     int32_t stats = 0;
+    int32_t config = 0, config_first = 0;
+    bool t0_initial = false;
 };
 
 }  // namespace sl
@@ -82,7 +85,9 @@ struct sl_mesh {
     int32_t opt_kernel = 0;
     int32_t opt_block = 0;
     int32_t opt_tiles_per_sm = 0;
-    int32_t opt_config = 0;           // launch configuration of the fast kernels
+    int32_t opt_config = 5;           // launch configuration of the fast kernels (later steps)
+    int32_t opt_config_first = 0;     // ... for a step whose walks start at the initial triangles
+    bool t0_initial = true;           // T^0 holds the initial start triangles
     int32_t opt_hop_budget = 0;       // FP32 hops before a walk moves to the walk kernel (0 = never)
     int32_t sms = 0;                  // multiprocessors of the device
     bool stepped = false;

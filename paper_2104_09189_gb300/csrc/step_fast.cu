@@ -150,7 +150,11 @@ __device__ __forceinline__ bool step_node(const FastArgs &a, int64_t i, int pi, 
     const uint32_t fside = (df_is(X, 0.0f) ? 1u : 0u) | (df_is(X, 1.0f) ? 2u : 0u) | (df_is(Y, 0.0f) ? 4u : 0u) |
                            (df_is(Y, 1.0f) ? 8u : 0u);
 
-    int32_t j = a.t0[i];
+    // start triangle and its vertex ids from the per-node cache (one
+    // coalesced 16-byte load: the coordinates and values of the vertices are
+    // then a single round of gathers)
+    const int4 tq = a.t0v[i];
+    int32_t j = tq.x;
     const int32_t jstart = j;
     const uint32_t cap = (uint32_t)a.walk_cap;
     uint32_t &hops = c.hops;
@@ -160,14 +164,27 @@ __device__ __forceinline__ bool step_node(const FastArgs &a, int64_t i, int pi, 
     // Each hop needs the triangle's vertex ids and neighbour slots (SoA,
     // loaded together so the chain per hop is two dependent loads: ids and
     // neighbours, then the coordinates) and the high parts of the vertex
-    // coordinates.
-    int ia = a.tv[0][j], ib = a.tv[1][j], ic = a.tv[2][j];
-    int na = a.tn[0][j], nb = a.tn[1][j], nc = a.tn[2][j];
+    // coordinates.  The start triangle's neighbour slots are loaded only when
+    // needed.
+    int ia = tq.y, ib = tq.z, ic = tq.w;
+    int na = 0, nb = 0, nc = 0;
+    bool have_nbr = false;
+    auto load_nbr = [&]() {
+        if (!have_nbr) {
+            na = a.tn[0][j];
+            nb = a.tn[1][j];
+            nc = a.tn[2][j];
+            have_nbr = true;
+        }
+    };
     for (;;) {
         if (!certify) {
             if (kSpill && hops >= (uint32_t)a.hop_budget) {
                 // a long walk: leave it to the walk kernel (high occupancy)
-                if (j != jstart) a.t0[i] = j;
+                if (j != jstart) {
+                    a.t0[i] = j;
+                    a.t0v[i] = make_int4(j, ia, ib, ic);
+                }
                 return false;
             }
             // FP32 hop test on the high parts, differences relative to vertex 3
@@ -182,6 +199,7 @@ __device__ __forceinline__ bool step_node(const FastArgs &a, int64_t i, int pi, 
             const float S = fabsf(ax) + fabsf(ay) + fabsf(bx) + fabsf(by) + fabsf(xx) + fabsf(xy);
             const float e = hop_bound(S);
             const float e3 = 3.0f * e + 0x1p-23f * (fabsf(dn) + fabsf(o1) + fabsf(o2));
+            load_nbr();
             int32_t nj = -1;
             float best = 0.0f;
             if (o1 < -e) { nj = na; best = o1; }
@@ -264,6 +282,7 @@ __device__ __forceinline__ bool step_node(const FastArgs &a, int64_t i, int pi, 
             for (int q = 0; q < 3; ++q)
                 if (neg[q] && pick-- == 0) k = q;
         }
+        load_nbr();
         const int32_t nj = k == 0 ? na : (k == 1 ? nb : nc);
         if (nj < 0) break;         // cannot happen for a foot inside a valid mesh
         j = nj;
@@ -289,7 +308,10 @@ __device__ __forceinline__ bool step_node(const FastArgs &a, int64_t i, int pi, 
     const df v1 = dfp(vin[ia]), v2 = dfp(vin[ib]), v3 = dfp(vin[ic]);
     const df v = df_add(v3, df_add(df_mul(th1, df_sub(v1, v3)), df_mul(th2, df_sub(v2, v3))));
     ((float2 *)a.vout)[i] = make_float2(v.h, v.l);
-    if (j != jstart) a.t0[i] = j;
+    if (j != jstart) {
+        a.t0[i] = j;
+        a.t0v[i] = make_int4(j, ia, ib, ic);
+    }
     if (c.limit) atomicOr(a.status, 1u << SL_E_WALK_LIMIT);
     if (flags & SL_NODE_RANGE) atomicOr(a.status, 1u << SL_E_ARG);
     if (kDebug) {
@@ -384,6 +406,7 @@ __global__ void __launch_bounds__(kBlock, 2048 / kBlock) k_walk_fast_df(FastArgs
             ++hops;
         }
         a.t0[i] = j;
+        a.t0v[i] = make_int4(j, ia, ib, ic);
         a.queue_hops[q] = hops;
     }
 }
@@ -457,7 +480,7 @@ static void launch_fast_df_cfg(const FastArgs &a, bool stats, bool debug, int sm
 
 // Launch configurations (threads per block x resident blocks per SM the
 // register budget is sized for): 0 = 256 x 4 (64 registers), 1 = 256 x 3,
-// 2 = 128 x 8, 3 = 128 x 6.  With a.queue set, walks longer than
+// 2 = 128 x 8, 3 = 128 x 6, 4 = 256 x 5, 5 = 128 x 12.  With a.queue set, walks longer than
 // a.hop_budget hops continue in the walk kernel and finish in the finish pass
 // (the caller zeroes *a.queue_count before the launch).
 void launch_fast_df(const FastArgs &a, bool stats, bool debug, int config, int sms, cudaStream_t s)
@@ -466,6 +489,8 @@ void launch_fast_df(const FastArgs &a, bool stats, bool debug, int config, int s
     case 1: launch_fast_df_cfg<256, 3>(a, stats, debug, sms, s); break;
     case 2: launch_fast_df_cfg<128, 8>(a, stats, debug, sms, s); break;
     case 3: launch_fast_df_cfg<128, 6>(a, stats, debug, sms, s); break;
+    case 4: launch_fast_df_cfg<256, 5>(a, stats, debug, sms, s); break;
+    case 5: launch_fast_df_cfg<128, 12>(a, stats, debug, sms, s); break;
     default: launch_fast_df_cfg<256, 4>(a, stats, debug, sms, s); break;
     }
 }
@@ -565,6 +590,22 @@ __global__ void k_field_tables(FieldTableArgs a)
         if (a.g1) a.g1[i] = pack_df2(g1x, g1y);
         if (a.g2) a.g2[i] = pack_df2(g2x, g2y);
     }
+}
+
+__global__ void k_fill_t0v(const int32_t *__restrict__ t0, const int32_t *__restrict__ tv0,
+                           const int32_t *__restrict__ tv1, const int32_t *__restrict__ tv2, int4 *__restrict__ t0v,
+                           int64_t n)
+{
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const int32_t j = t0[i];
+        t0v[i] = make_int4(j, tv0[j], tv1[j], tv2[j]);
+    }
+}
+
+void launch_fill_t0v(const int32_t *t0, const int32_t *tv0, const int32_t *tv1, const int32_t *tv2, int4 *t0v,
+                     int64_t n, cudaStream_t s)
+{
+    if (n > 0) k_fill_t0v<<<grid_for(n, 256), 256, 0, s>>>(t0, tv0, tv1, tv2, t0v, n);
 }
 
 void launch_field_tables(const FieldTableArgs &a, cudaStream_t s)

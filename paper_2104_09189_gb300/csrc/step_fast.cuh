@@ -34,6 +34,7 @@ struct FastArgs {
     const int32_t *tv[3];
     const int32_t *tn[3];         // -1 - side on the boundary (0: x=0, 1: x=1, 2: y=0, 3: y=1)
     int32_t *t0;
+    int4 *t0v;                    // per node: (T^0, its three vertex ids), kept in step with t0
     const void *vin;              // FP64: float2 (hi, lo) values; FP32: float values
     void *vout;
     const float4 *g1, *g2;        // field tables (hi, lo) per node, or NULL
@@ -56,7 +57,7 @@ struct FastArgs {
 
 // config: launch configuration 0..3 (see step_fast.cu)
 void launch_fast_df(const FastArgs &a, bool stats, bool debug, int config, int sms, cudaStream_t s);
-constexpr int kFastConfigs = 4;
+constexpr int kFastConfigs = 6;
 void launch_fast_f32(const FastArgs &a, bool stats, bool debug, int config, cudaStream_t s);
 
 // value format conversions for the double-float kernel
@@ -74,5 +75,9 @@ struct FieldTableArgs {
     float4 *g1, *g2;
 };
 void launch_field_tables(const FieldTableArgs &a, cudaStream_t s);
+
+// t0v[i] = (t0[i], its three vertex ids)
+void launch_fill_t0v(const int32_t *t0, const int32_t *tv0, const int32_t *tv1, const int32_t *tv2, int4 *t0v,
+                     int64_t n, cudaStream_t s);
 
 }  // namespace sl

@@ -105,14 +105,18 @@ __global__ void __launch_bounds__(kBlock, kMinBlocks) k_step_fast_f32(FastArgs a
         const uint32_t fside = (X == 0.0f ? 1u : 0u) | (X == 1.0f ? 2u : 0u) | (Y == 0.0f ? 4u : 0u) |
                                (Y == 1.0f ? 8u : 0u);
 
-        int32_t j = a.t0[i];
+        // start triangle and its vertex ids from the per-node cache; the
+        // neighbour slots of the start triangle are loaded only when needed
+        const int4 tq = a.t0v[i];
+        int32_t j = tq.x;
         const int32_t jstart = j;
         const uint32_t cap = (uint32_t)a.walk_cap;
         bool found = false;
         int s1 = 0, s2 = 0, s3 = 0;
         float o1 = 0.0f, o2 = 0.0f, dn = 1.0f;
-        int ia = a.tv[0][j], ib = a.tv[1][j], ic = a.tv[2][j];
-        int na = a.tn[0][j], nb = a.tn[1][j], nc = a.tn[2][j];
+        int ia = tq.y, ib = tq.z, ic = tq.w;
+        int na = 0, nb = 0, nc = 0;
+        bool have_nbr = false;
         for (;;) {
             const float2 A = a.xyf[ia], B = a.xyf[ib], C = a.xyf[ic];
             const float ax = __fsub_rn(A.x, C.x), ay = __fsub_rn(A.y, C.y);
@@ -127,6 +131,12 @@ __global__ void __launch_bounds__(kBlock, kMinBlocks) k_step_fast_f32(FastArgs a
             s1 = o1 > e1 ? 1 : (o1 < -e1 ? -1 : 2);
             s2 = o2 > e2 ? 1 : (o2 < -e2 ? -1 : 2);
             s3 = o3 > e3 ? 1 : (o3 < -e3 ? -1 : 2);
+            if ((s1 == 2 || s2 == 2 || s3 == 2 || s1 < 0 || s2 < 0 || s3 < 0) && !have_nbr) {
+                na = a.tn[0][j];
+                nb = a.tn[1][j];
+                nc = a.tn[2][j];
+                have_nbr = true;
+            }
             if (s1 == 2 || s2 == 2 || s3 == 2) {
                 // boundary edge with the foot on its side: exactly 0
                 if (s1 == 2 && na < 0 && (fside >> (-1 - na) & 1u)) s1 = 0;
@@ -213,7 +223,10 @@ __global__ void __launch_bounds__(kBlock, kMinBlocks) k_step_fast_f32(FastArgs a
         const float v1 = vin[ia], v2 = vin[ib], v3 = vin[ic];
         const float v = __fmaf_rn(th1, __fsub_rn(v1, v3), __fmaf_rn(th2, __fsub_rn(v2, v3), v3));
         ((float *)a.vout)[i] = v;
-        if (j != jstart) a.t0[i] = j;
+        if (j != jstart) {
+            a.t0[i] = j;
+            a.t0v[i] = make_int4(j, ia, ib, ic);
+        }
         if (limit_cnt) atomicOr(a.status, 1u << SL_E_WALK_LIMIT);
         if (kDebug) {
             if (a.dbg.feet) {
@@ -248,6 +261,8 @@ void launch_fast_f32(const FastArgs &a, bool stats, bool debug, int config, cuda
     case 1: launch_f32_cfg<256, 3>(a, stats, debug, s); break;
     case 2: launch_f32_cfg<128, 8>(a, stats, debug, s); break;
     case 3: launch_f32_cfg<128, 6>(a, stats, debug, s); break;
+    case 4: launch_f32_cfg<256, 5>(a, stats, debug, s); break;
+    case 5: launch_f32_cfg<128, 12>(a, stats, debug, s); break;
     default: launch_f32_cfg<256, 4>(a, stats, debug, s); break;
     }
 }

@@ -14,6 +14,7 @@ struct StepArgs {
     const int32_t *tv[3];         // triangle vertices (global node indices), SoA
     const int32_t *tn[3];         // neighbours (global triangle indices, -1 = boundary), SoA
     int32_t *t0;                  // start / located triangle per node (in place)
+    int4 *t0v;                    // (T^0, its vertex ids) per node, kept in step with t0
     const void *vin;              // V^n
     void *vout;                   // V^{n+1}
     const ProbStep *probs;        // per-problem data of this step (device)

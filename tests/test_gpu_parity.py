@@ -246,3 +246,26 @@ def test_bad_step_arguments():
         sl.sl_step(g.h, bad, 0, v, w)
     assert e.value.status == sl.SL_E_ARG
     g.close()
+
+
+def test_autotune_restores_state_and_keeps_results():
+    """sl_autotune measures every launch configuration, keeps the fastest
+    and leaves values, T^0 and the results of a following run unchanged."""
+    prob = si.config("C2", M=256)
+    g = GpuRun(prob.mesh, prob.field, prob.dt, curve=sl.SL_CURVE_HILBERT)
+    v = g.to_dev(prob.v0)
+    w = g.torch.empty_like(v)
+    before = v.clone()
+    tune = sl.sl_autotune(g.h, g.probs, 2, v, w)
+    assert g.torch.equal(v, before)
+    assert 0 <= tune["config_first"] < len(tune["first_ms"]) and 0 <= tune["config_rest"] < len(tune["rest_ms"])
+    assert all(t > 0 for t in tune["first_ms"] + tune["rest_ms"])
+    sl.sl_run(g.h, g.probs, 0, 5, v, w)
+    tuned = g.from_dev(v)
+    g.close()
+    ref = GpuRun(prob.mesh, prob.field, prob.dt, curve=sl.SL_CURVE_HILBERT)
+    v2 = ref.to_dev(prob.v0)
+    w2 = ref.torch.empty_like(v2)
+    sl.sl_run(ref.h, ref.probs, 0, 5, v2, w2)
+    assert np.abs(ref.from_dev(v2) - tuned).max() <= 1e-12 * np.abs(tuned).max()
+    ref.close()
