@@ -50,7 +50,6 @@ def parse():
     ap.add_argument("--curve", default="hilbert", choices=["none", "hilbert", "morton"])
     ap.add_argument("--config-id", type=int, default=None, help="SL_OPT_CONFIG launch configuration (0..5); "
                     "default: chosen by sl_autotune")
-    ap.add_argument("--hop-budget", type=int, default=None, help="SL_OPT_HOP_BUDGET (default: library's)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
@@ -263,8 +262,6 @@ def main():
     if args.config_id is not None:
         sl.sl_mesh_set_option(h, sl.SL_OPT_CONFIG, args.config_id)
         sl.sl_mesh_set_option(h, sl.SL_OPT_CONFIG_FIRST, args.config_id)
-    if args.hop_budget is not None:
-        sl.sl_mesh_set_option(h, sl.SL_OPT_HOP_BUDGET, args.hop_budget)
     probs = sl.problems([(p.field.kind, p.dt, p.field.packed()) for p in wl.probs])
     vt = torch.float64 if prec == sl.SL_FP64 else torch.float32
     v0_all = np.concatenate([p.v0 for p in wl.probs])

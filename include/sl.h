@@ -124,10 +124,7 @@ typedef enum {
     SL_OPT_CONFIG = 5,       /* launch configuration of the fast kernels, 0..5: threads per block x
                                 blocks per SM the registers are sized for = 256x4, 256x3, 128x8,
                                 128x6, 256x5, 128x12 (default 5) */
-    SL_OPT_HOP_BUDGET = 6,   /* FP32 walk hops a node makes in the main pass before it moves to the
-                                walk queue (a lean, fully occupied walk kernel continues it);
-                                0 = no queue (the default: on the benchmark meshes the extra resident
-                                walks thrash L1).  sl_step_noalloc never queues. */
+    /* 6: unused */
     SL_OPT_CONFIG_FIRST = 7  /* launch configuration for a step whose walks start at the initial
                                 incident triangles (the first step after sl_mesh_create or
                                 sl_mesh_reset_t0): long walks favour fewer resident warps (default 0) */
@@ -162,7 +159,9 @@ typedef enum {
  * strictly counter-clockwise (exact test), an edge shared by more than two
  * triangles or by two triangles with the same orientation, an inconsistent
  * supplied nbr, a boundary edge not lying on one side of the square, a node
- * outside the square or in no triangle, or a total area that is not 1.
+ * outside the square or in no triangle, or a total area that is not 1;
+ * SL_E_ARG for more than 2^31 - 1 nodes or 715 827 882 triangles (the fast
+ * kernels number the edges of triangle t as 3 t + k in int32).
  */
 sl_status sl_mesh_create(int32_t n_problems, const int64_t *node_off, const int64_t *tri_off,
                          const double *xy, const int32_t *tri, const int32_t *nbr,

@@ -17,7 +17,7 @@ from ._build import LIB as _LIB_PATH
 __all__ = [
     "SL_OK", "SL_E_ARG", "SL_E_MESH", "SL_E_NOMEM", "SL_E_CUDA", "SL_E_WALK_LIMIT", "SL_E_STATE",
     "SL_FP64", "SL_FP32", "SL_CURVE_NONE", "SL_CURVE_HILBERT", "SL_CURVE_MORTON",
-    "SL_OPT_STATS", "SL_OPT_WALK_CAP", "SL_OPT_KERNEL", "SL_OPT_BLOCK", "SL_OPT_TILES_PER_SM", "SL_OPT_CONFIG", "SL_OPT_HOP_BUDGET", "SL_OPT_CONFIG_FIRST",
+    "SL_OPT_STATS", "SL_OPT_WALK_CAP", "SL_OPT_KERNEL", "SL_OPT_BLOCK", "SL_OPT_TILES_PER_SM", "SL_OPT_CONFIG", "SL_OPT_CONFIG_FIRST",
     "SL_NODE_CLIPPED", "SL_NODE_DEGENERATE", "SL_NODE_EXACT", "SL_NODE_FALLBACK", "SL_NODE_WALK_LIMIT",
     "SL_NODE_RANGE", "SLError", "sl_problem", "problems", "pack_meshes",
     "sl_mesh_create", "sl_mesh_validate", "sl_mesh_reorder", "sl_step", "sl_run", "sl_run_host", "sl_mesh_get_t0",
@@ -29,8 +29,8 @@ __all__ = [
 SL_OK, SL_E_ARG, SL_E_MESH, SL_E_NOMEM, SL_E_CUDA, SL_E_WALK_LIMIT, SL_E_STATE = range(7)
 SL_FP64, SL_FP32 = 0, 1
 SL_CURVE_NONE, SL_CURVE_HILBERT, SL_CURVE_MORTON = 0, 1, 2
-(SL_OPT_STATS, SL_OPT_WALK_CAP, SL_OPT_KERNEL, SL_OPT_BLOCK, SL_OPT_TILES_PER_SM, SL_OPT_CONFIG, SL_OPT_HOP_BUDGET,
- SL_OPT_CONFIG_FIRST) = range(8)
+SL_OPT_STATS, SL_OPT_WALK_CAP, SL_OPT_KERNEL, SL_OPT_BLOCK, SL_OPT_TILES_PER_SM, SL_OPT_CONFIG = range(6)
+SL_OPT_CONFIG_FIRST = 7
 SL_NODE_CLIPPED, SL_NODE_DEGENERATE, SL_NODE_EXACT, SL_NODE_FALLBACK, SL_NODE_WALK_LIMIT, SL_NODE_RANGE = (
     1, 2, 4, 8, 16, 32)
 SL_NPARAMS = 48

@@ -40,7 +40,7 @@ void free_device(sl_mesh *m)
 {
     DeviceMesh &d = m->d;
     void *ptrs[] = {d.xy, d.tv[0], d.tv[1], d.tv[2], d.tn[0], d.tn[1], d.tn[2], d.t0, d.t0_init, d.t0v, d.node_off,
-                    d.status, d.stats, d.probs, d.fprobs, d.xyq, d.xyh, d.g1, d.g2, d.tparams, d.dfa, d.dfb, d.queue, d.queue_hops, d.queue_count,
+                    d.status, d.stats, d.probs, d.fprobs, d.xyq, d.xyh, d.g1, d.g2, d.tparams, d.dfa, d.dfb, d.he,
                     m->host_v, m->host_v2};
     for (void *p : ptrs)
         if (p) cudaFree(p);
@@ -103,6 +103,9 @@ static sl_status upload_arrays(sl_mesh *m)
             }
         SL_CUDA(cudaMemcpy(d.tn[k], col.data(), sizeof(int32_t) * Nt, cudaMemcpyHostToDevice));
     }
+    // half-edge walk records of the fast kernels
+    launch_build_he(d.tv, d.tn, m->precision == SL_FP64 ? (const float2 *)d.xyh : (const float2 *)d.xy, Nt,
+                    (float4 *)d.he, 0);
     SL_CUDA(cudaMemcpy(d.t0, m->t0.data(), sizeof(int32_t) * N, cudaMemcpyHostToDevice));
     SL_CUDA(cudaMemcpy(d.t0_init, m->t0_init.data(), sizeof(int32_t) * N, cudaMemcpyHostToDevice));
     SL_CUDA(cudaMemcpy(d.node_off, m->node_off.data(), sizeof(int64_t) * (m->n_problems + 1), cudaMemcpyHostToDevice));
@@ -125,6 +128,7 @@ sl_status upload(sl_mesh *m)
         SL_CUDA(cudaMalloc(&d.tv[k], sizeof(int32_t) * Nt));
         SL_CUDA(cudaMalloc(&d.tn[k], sizeof(int32_t) * Nt));
     }
+    SL_CUDA(cudaMalloc(&d.he, sizeof(float4) * 3 * Nt));
     SL_CUDA(cudaMalloc(&d.t0, sizeof(int32_t) * N));
     if (m->precision == SL_FP64) SL_CUDA(cudaMalloc(&d.xyh, sizeof(float2) * N));
     SL_CUDA(cudaMalloc(&d.t0_init, sizeof(int32_t) * N));
@@ -212,6 +216,7 @@ static FastArgs make_fast_args(const sl_mesh *m, const FastProb *fp, const void 
         a.tv[k] = m->d.tv[k];
         a.tn[k] = m->d.tn[k];
     }
+    a.he = (const float4 *)m->d.he;
     a.t0 = m->d.t0;
     a.t0v = (int4 *)m->d.t0v;
     a.vin = vin;
@@ -316,30 +321,9 @@ static sl_status launch_step(const sl_mesh *m, const StepArgs &a, bool debug, cu
     return SL_OK;
 }
 
-// Walk-queue scratch of the fast kernels (allocated before any recording).
-static sl_status ensure_queue(sl_mesh *m)
+static sl_status launch_fast(sl_mesh *m, const FastArgs &a, bool debug, int config, cudaStream_t s)
 {
-    if (m->opt_hop_budget > 0 && m->precision == SL_FP64 && !m->d.queue) {
-        SL_CUDA(cudaMalloc(&m->d.queue, sizeof(int32_t) * m->N));
-        SL_CUDA(cudaMalloc(&m->d.queue_hops, sizeof(uint32_t) * m->N));
-        SL_CUDA(cudaMalloc(&m->d.queue_count, sizeof(uint32_t)));
-    }
-    return SL_OK;
-}
-
-static sl_status launch_fast(sl_mesh *m, const FastArgs &a0, bool debug, int config, cudaStream_t s)
-{
-    FastArgs a = a0;
-    if (m->opt_hop_budget > 0 && m->precision == SL_FP64) {
-        // long walks continue in the walk kernel (queue scratch owned by the mesh)
-        if (!m->d.queue) return fail(SL_E_STATE, "walk queue not allocated");
-        a.queue = m->d.queue;
-        a.queue_hops = m->d.queue_hops;
-        a.queue_count = m->d.queue_count;
-        a.hop_budget = m->opt_hop_budget;
-        SL_CUDA(cudaMemsetAsync(m->d.queue_count, 0, sizeof(uint32_t), s));
-    }
-    if (m->precision == SL_FP64) launch_fast_df(a, m->opt_stats != 0, debug, config, m->sms, s);
+    if (m->precision == SL_FP64) launch_fast_df(a, m->opt_stats != 0, debug, config, s);
     else launch_fast_f32(a, m->opt_stats != 0, debug, config, s);
     SL_CUDA(cudaGetLastError());
     return SL_OK;
@@ -390,7 +374,6 @@ static sl_status run_steps(sl_mesh *m, const sl_problem *probs, int64_t n0, int3
     }
     if (fast) {
         sl_status st = ensure_tables(m, probs, s);
-        if (st == SL_OK) st = ensure_queue(m);
         if (st != SL_OK) return st;
     }
     const size_t elem = m->precision == SL_FP64 ? sizeof(double) : sizeof(float);
@@ -522,7 +505,6 @@ extern "C" sl_status sl_step(sl_mesh *m, const sl_problem *probs, int64_t n, con
         return st;
     }
     st = ensure_tables(m, probs, s);
-    if (st == SL_OK) st = ensure_queue(m);
     if (st != SL_OK) return st;
     std::vector<FastProb> fh(m->n_problems);
     fill_fast(m, host.data(), fh.data());

@@ -286,8 +286,11 @@ static sl_status check_args(int32_t n_problems, const int64_t *node_off, const i
     for (int32_t p = 0; p < n_problems; ++p)
         if (node_off[p + 1] < node_off[p] || tri_off[p + 1] < tri_off[p])
             return sl::fail(SL_E_ARG, "offsets must be non-decreasing");
-    if (node_off[n_problems] >= ((int64_t)1 << 31) || tri_off[n_problems] >= ((int64_t)1 << 31))
-        return sl::fail(SL_E_ARG, "more than 2^31-1 nodes or triangles");
+    if (node_off[n_problems] >= ((int64_t)1 << 31))
+        return sl::fail(SL_E_ARG, "more than 2^31-1 nodes");
+    // the fast kernels number half-edges 3 t + k in int32
+    if (3 * tri_off[n_problems] >= ((int64_t)1 << 31))
+        return sl::fail(SL_E_ARG, "more than 715827882 triangles");
     return SL_OK;
 }
 
@@ -401,10 +404,6 @@ extern "C" sl_status sl_mesh_set_option(sl_mesh *m, int32_t option, int64_t valu
     case SL_OPT_TILES_PER_SM:
         if (value < 0 || value > 64) return sl::fail(SL_E_ARG, "tiles per SM out of range");
         m->opt_tiles_per_sm = (int32_t)value;
-        break;
-    case SL_OPT_HOP_BUDGET:
-        if (value < 0 || value > (1 << 30)) return sl::fail(SL_E_ARG, "hop budget out of range");
-        m->opt_hop_budget = (int32_t)value;
         break;
     case SL_OPT_CONFIG:
         if (value < 0 || value > 5) return sl::fail(SL_E_ARG, "launch configuration must be 0..5");

@@ -192,6 +192,7 @@ extern "C" sl_status sl_step_noalloc(sl_mesh *m, const sl_problem *probs, int64_
         a.tv[k] = m->d.tv[k];
         a.tn[k] = m->d.tn[k];
     }
+    a.he = (const float4 *)m->d.he;
     a.t0 = m->d.t0;
     a.t0v = (int4 *)m->d.t0v;
     a.vin = v_out;
@@ -205,7 +206,7 @@ extern "C" sl_status sl_step_noalloc(sl_mesh *m, const sl_problem *probs, int64_
     a.N = m->N;
     a.status = m->d.status;
     a.stats = m->d.stats;
-    launch_fast_df(a, m->opt_stats != 0, false, m->opt_config, m->sms, s);
+    launch_fast_df(a, m->opt_stats != 0, false, m->opt_config, s);
     launch_from_df(sc.values, v_out, m->N, s);
     e = cudaGetLastError();
     if (e != cudaSuccess) return fail(SL_E_CUDA, std::string("sl_step_noalloc: launch: ") + cudaGetErrorString(e));

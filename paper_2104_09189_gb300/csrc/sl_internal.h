@@ -46,9 +46,7 @@ struct DeviceMesh {
     void *g1 = nullptr, *g2 = nullptr;   // field node tables, float4 (hi, lo) per node
     double *tparams = nullptr;        // field parameters the tables were built from (device)
     void *dfa = nullptr, *dfb = nullptr;   // value scratch of sl_step for the fast FP64 kernel
-    int32_t *queue = nullptr;         // walk queue of the fast kernels (N node ids)
-    uint32_t *queue_hops = nullptr;   // hops made so far by each queued node
-    uint32_t *queue_count = nullptr;
+    void *he = nullptr;               // float4 half-edge walk records of the fast kernels (3 Nt)
 };
 
 struct GraphCache {
@@ -88,7 +86,6 @@ struct sl_mesh {
     int32_t opt_config = 5;           // launch configuration of the fast kernels (later steps)
     int32_t opt_config_first = 0;     // ... for a step whose walks start at the initial triangles
     bool t0_initial = true;           // T^0 holds the initial start triangles
-    int32_t opt_hop_budget = 0;       // FP32 hops before a walk moves to the walk kernel (0 = never)
     int32_t sms = 0;                  // multiprocessors of the device
     bool stepped = false;
     std::vector<double> table_key;    // field parameters of the current node tables

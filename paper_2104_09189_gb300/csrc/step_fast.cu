@@ -125,16 +125,74 @@ __device__ __forceinline__ float hop_bound(float S) { return S * __fmaf_rn(S, 0x
 //  within 2^-45 relative: 2^-45 S + 2^-44 S^2.
 __device__ __forceinline__ float cert_bound(float S) { return S * __fmaf_rn(S, 0x1p-44f, 0x1p-45f); }
 
+// Exact signs of the edges selected by `need` (bit k: the edge opposite
+// W_k) of the triangle (W0, W1, W2), on the double coordinates and the exact
+// foot.  Kept out of line: it runs for a few feet per million, and inlined
+// its expansions would raise the register count of the whole kernel.
+// Packed result: bits 2k..2k+1 the sign of edge k (0: 0, 1: +1, 2: -1),
+// bits 8..9 the tests decided by the expansion, bits 10..11 those decided by
+// the double filter, bit 12 a coordinate outside the exact range.
+__device__ __forceinline__ uint32_t exact_signs(const double2 *xyd, int w0, int w1, int w2, df X, df Y, uint32_t need)
+{
+    const double2 Ad = xyd[w0], Bd = xyd[w1], Cd = xyd[w2];
+    uint32_t out = 0, n3 = 0, n2 = 0;
+    for (int k = 0; k < 3; ++k) {
+        if (!(need >> k & 1u)) continue;
+        const double2 P = k == 0 ? Bd : (k == 1 ? Cd : Ad), Q = k == 0 ? Cd : (k == 1 ? Ad : Bd);
+        int stg = 0;
+        const int sg = orient_exact_df(P, Q, X.h, X.l, Y.h, Y.l, stg);
+        out |= (sg > 0 ? 1u : (sg < 0 ? 2u : 0u)) << (2 * k);
+        n3 += stg == 3;
+        n2 += stg == 2;
+    }
+    const bool in_range = slp::in_exact_range(Ad.x) && slp::in_exact_range(Ad.y) && slp::in_exact_range(Bd.x) &&
+                          slp::in_exact_range(Bd.y) && slp::in_exact_range(Cd.x) && slp::in_exact_range(Cd.y) &&
+                          slp::in_exact_range(X.h) && slp::in_exact_range(Y.h) && slp::in_exact_range(X.l) &&
+                          slp::in_exact_range(Y.l);
+    return out | (n3 << 8) | (n2 << 10) | (in_range ? 0u : 1u << 12);
+}
+
+__device__ __forceinline__ int unpack_sign(uint32_t r, int k)
+{
+    const uint32_t v = (r >> (2 * k)) & 3u;
+    return v == 1u ? 1 : (v == 2u ? -1 : 0);
+}
+
+// Randomised visibility walk step: a uniformly drawn negative edge (signs
+// s1..s3 of the edges opposite W0..W2, at least one negative).
+__device__ __forceinline__ int random_negative_edge(int64_t i, uint32_t hops, int s1, int s2, int s3)
+{
+    const int neg[3] = {s1 < 0, s2 < 0, s3 < 0};
+    const int nneg = neg[0] + neg[1] + neg[2];
+    int pick = (int)(mix64_dev(((uint64_t)i << 20) ^ (uint64_t)hops) % (uint64_t)nneg);
+    int k = -1;
+    for (int q = 0; q < 3; ++q)
+        if (neg[q] && pick-- == 0) k = q;
+    return k;
+}
+
 struct NodeCounters {
     uint32_t hops = 0, exact = 0, clipped = 0, fallback = 0, limit = 0, filter2 = 0;
 };
 
-// One node of the step.  c.hops holds the hops already made (spilled nodes
-// resume in the finish pass).  With kSpill the node gives up after
-// a.hop_budget FP32 hops: it stores its current triangle in T^0 and returns
-// false; otherwise it completes (value, T^0, debug outputs) and returns true.
-template <bool kDebug, bool kSpill>
-__device__ __forceinline__ bool step_node(const FastArgs &a, int64_t i, int pi, NodeCounters &c)
+// Triangle of a half-edge code h = 3 t + k (h >= 0).
+__device__ __forceinline__ int32_t tri_of(int32_t h) { return (int32_t)__umulhi((uint32_t)h, 0xAAAAAAABu) >> 1; }
+
+// One node of the step.
+//
+// FP32 walk state: the current triangle as its vertices (W0, W1, W2),
+// counter-clockwise, and the half-edge codes e0, e1 of its edges opposite
+// W0 and W1 (code 3 j + s: edge s of triangle j, opposite its vertex s).
+// Crossing an edge loads one 16-byte half-edge record (the next triangle's
+// new vertex and its two exit codes, see k_build_he), so an FP32 hop is a
+// single gather.  The edge the walk came through is never a candidate
+// again: it was crossed because the foot lies strictly beyond it, so its
+// barycentric coordinate in the new triangle is positive.  The certified
+// test and the value always take the triangle's vertices in slot order
+// (T[0][j], T[1][j], T[2][j]), so the result depends on the located triangle
+// and the foot only, not on the path of the walk.
+template <bool kDebug>
+__device__ __forceinline__ void step_node(const FastArgs &a, int64_t i, int pi, NodeCounters &c)
 {
     const FastProb &P = a.probs[pi];
     const float4 xq = a.xyq[i];
@@ -150,110 +208,61 @@ __device__ __forceinline__ bool step_node(const FastArgs &a, int64_t i, int pi, 
     const uint32_t fside = (df_is(X, 0.0f) ? 1u : 0u) | (df_is(X, 1.0f) ? 2u : 0u) | (df_is(Y, 0.0f) ? 4u : 0u) |
                            (df_is(Y, 1.0f) ? 8u : 0u);
 
-    // start triangle and its vertex ids from the per-node cache (one
-    // coalesced 16-byte load: the coordinates and values of the vertices are
-    // then a single round of gathers)
+    // start triangle and its vertex ids from the per-node cache: one
+    // coalesced 16-byte load
     const int4 tq = a.t0v[i];
-    int32_t j = tq.x;
-    const int32_t jstart = j;
+    int32_t e0 = tq.x, e1 = 0;
+    int32_t j = 0;
+    const int32_t jstart = tri_of(tq.x);
+    int w0 = tq.y, w1 = tq.z, w2 = tq.w;
+    bool ids = true;           // w0..w2 are the vertex ids of the current triangle
     const uint32_t cap = (uint32_t)a.walk_cap;
     uint32_t &hops = c.hops;
-    bool certify = true, found = false;
+    bool found = false;
     int s1 = 0, s2 = 0, s3 = 0;
     df n1, n2, den;
-    // Each hop needs the triangle's vertex ids and neighbour slots (SoA,
-    // loaded together so the chain per hop is two dependent loads: ids and
-    // neighbours, then the coordinates) and the high parts of the vertex
-    // coordinates.  The start triangle's neighbour slots are loaded only when
-    // needed.
-    int ia = tq.y, ib = tq.z, ic = tq.w;
-    int na = 0, nb = 0, nc = 0;
-    bool have_nbr = false;
-    auto load_nbr = [&]() {
-        if (!have_nbr) {
-            na = a.tn[0][j];
-            nb = a.tn[1][j];
-            nc = a.tn[2][j];
-            have_nbr = true;
-        }
-    };
     for (;;) {
-        if (!certify) {
-            if (kSpill && hops >= (uint32_t)a.hop_budget) {
-                // a long walk: leave it to the walk kernel (high occupancy)
-                if (j != jstart) {
-                    a.t0[i] = j;
-                    a.t0v[i] = make_int4(j, ia, ib, ic);
-                }
-                return false;
-            }
-            // FP32 hop test on the high parts, differences relative to vertex 3
-            const float2 A = a.xyh[ia], B = a.xyh[ib], C = a.xyh[ic];
-            const float ax = A.x - C.x, ay = A.y - C.y, bx = B.x - C.x, by = B.y - C.y;
-            const float xx = X.h - C.x, xy = Y.h - C.y;
-            const float o1 = __fmaf_rn(xx, by, -__fmul_rn(xy, bx));    // ~ theta_1 * den
-            const float o2 = __fmaf_rn(ax, xy, -__fmul_rn(ay, xx));    // ~ theta_2 * den
-            const float dn = __fmaf_rn(ax, by, -__fmul_rn(ay, bx));
-            const float o3 = dn - o1 - o2;                              // ~ theta_3 * den
-            // one bound for all three (S covers every difference involved)
-            const float S = fabsf(ax) + fabsf(ay) + fabsf(bx) + fabsf(by) + fabsf(xx) + fabsf(xy);
-            const float e = hop_bound(S);
-            const float e3 = 3.0f * e + 0x1p-23f * (fabsf(dn) + fabsf(o1) + fabsf(o2));
-            load_nbr();
-            int32_t nj = -1;
-            float best = 0.0f;
-            if (o1 < -e) { nj = na; best = o1; }
-            if (o2 < -e && (nj == -1 || o2 < best)) { nj = nb; best = o2; }
-            if (o3 < -e3 && (nj == -1 || o3 < best)) { nj = nc; best = o3; }
-            if (nj >= 0 && hops < cap) {
-                j = nj;
-                ia = a.tv[0][j];
-                ib = a.tv[1][j];
-                ic = a.tv[2][j];
-                na = a.tn[0][j];
-                nb = a.tn[1][j];
-                nc = a.tn[2][j];
-                ++hops;
-                continue;
-            }
-            certify = true;    // no clearly negative edge: certify this triangle
+        // certified test in double-float on (W0, W1, W2) = the vertices in
+        // slot order, relative to W2
+        j = tri_of(e0);
+        if (!ids) {
+            w0 = a.tv[0][j];
+            w1 = a.tv[1][j];
+            w2 = a.tv[2][j];
+            ids = true;
         }
-        // certified test in double-float, relative to vertex 3
-        const float4 A = a.xyq[ia], B = a.xyq[ib], C = a.xyq[ic];
+        const float4 A = a.xyq[w0], B = a.xyq[w1], C = a.xyq[w2];
         const df cxh = df_make(C.x, C.z), cyh = df_make(C.y, C.w);
         const df dAx = df_sub(df_make(A.x, A.z), cxh), dAy = df_sub(df_make(A.y, A.w), cyh);
         const df dBx = df_sub(df_make(B.x, B.z), cxh), dBy = df_sub(df_make(B.y, B.w), cyh);
         const df dXx = df_sub(X, cxh), dXy = df_sub(Y, cyh);
-        n1 = df_cross(dXx, dXy, dBx, dBy);      // orient(B, C, X): sign of theta_1
-        n2 = df_cross(dAx, dAy, dXx, dXy);      // orient(C, A, X): sign of theta_2
-        den = df_cross(dAx, dAy, dBx, dBy);     // orient(A, B, C) > 0
+        n1 = df_cross(dXx, dXy, dBx, dBy);      // orient(W1, W2, X): sign of theta of W0
+        n2 = df_cross(dAx, dAy, dXx, dXy);      // orient(W2, W0, X): sign of theta of W1
+        den = df_cross(dAx, dAy, dBx, dBy);     // orient(W0, W1, W2) > 0
         const df n3 = df_sub(df_sub(den, n1), n2);
         const float sA = fabsf(dAx.h) + fabsf(dAy.h), sB = fabsf(dBx.h) + fabsf(dBy.h);
         const float sX = fabsf(dXx.h) + fabsf(dXy.h);
-        const float e1 = cert_bound(sX + sB), e2 = cert_bound(sA + sX), ed = cert_bound(sA + sB);
-        const float e3 = ed + e1 + e2 + 0x1p-45f * (fabsf(den.h) + fabsf(n1.h) + fabsf(n2.h));
-        s1 = n1.h > e1 ? 1 : (n1.h < -e1 ? -1 : 2);
-        s2 = n2.h > e2 ? 1 : (n2.h < -e2 ? -1 : 2);
-        s3 = n3.h > e3 ? 1 : (n3.h < -e3 ? -1 : 2);
+        const float ea = cert_bound(sX + sB), eb = cert_bound(sA + sX), ed = cert_bound(sA + sB);
+        const float ec = ed + ea + eb + 0x1p-45f * (fabsf(den.h) + fabsf(n1.h) + fabsf(n2.h));
+        s1 = n1.h > ea ? 1 : (n1.h < -ea ? -1 : 2);
+        s2 = n2.h > eb ? 1 : (n2.h < -eb ? -1 : 2);
+        s3 = n3.h > ec ? 1 : (n3.h < -ec ? -1 : 2);
         if (s1 == 2 || s2 == 2 || s3 == 2) {
             // a boundary edge with the foot on its side of the square: exactly 0
-            if (s1 == 2 && na < 0 && (fside >> (-1 - na) & 1u)) s1 = 0;
-            if (s2 == 2 && nb < 0 && (fside >> (-1 - nb) & 1u)) s2 = 0;
-            if (s3 == 2 && nc < 0 && (fside >> (-1 - nc) & 1u)) s3 = 0;
+            if (s1 == 2) { const int32_t nb = a.tn[0][j]; if (nb < 0 && (fside >> (-1 - nb) & 1u)) s1 = 0; }
+            if (s2 == 2) { const int32_t nb = a.tn[1][j]; if (nb < 0 && (fside >> (-1 - nb) & 1u)) s2 = 0; }
+            if (s3 == 2) { const int32_t nb = a.tn[2][j]; if (nb < 0 && (fside >> (-1 - nb) & 1u)) s3 = 0; }
         }
         if (s1 == 2 || s2 == 2 || s3 == 2) {
             // exact signs on the double coordinates and the exact foot
-            const double2 Ad = a.xyd[ia], Bd = a.xyd[ib], Cd = a.xyd[ic];
-            int stg = 0;
-            if (s1 == 2) { s1 = orient_exact_df(Bd, Cd, X.h, X.l, Y.h, Y.l, stg); c.exact += stg == 3; c.filter2 += stg == 2; }
-            if (s2 == 2) { s2 = orient_exact_df(Cd, Ad, X.h, X.l, Y.h, Y.l, stg); c.exact += stg == 3; c.filter2 += stg == 2; }
-            if (s3 == 2) { s3 = orient_exact_df(Ad, Bd, X.h, X.l, Y.h, Y.l, stg); c.exact += stg == 3; c.filter2 += stg == 2; }
+            const uint32_t r = exact_signs(a.xyd, w0, w1, w2, X, Y, (s1 == 2 ? 1u : 0u) | (s2 == 2 ? 2u : 0u) | (s3 == 2 ? 4u : 0u));
+            if (s1 == 2) s1 = unpack_sign(r, 0);
+            if (s2 == 2) s2 = unpack_sign(r, 1);
+            if (s3 == 2) s3 = unpack_sign(r, 2);
+            c.exact += (r >> 8) & 3u;
+            c.filter2 += (r >> 10) & 3u;
             flags |= SL_NODE_EXACT;
-            if (!(slp::in_exact_range(Ad.x) && slp::in_exact_range(Ad.y) && slp::in_exact_range(Bd.x) &&
-                  slp::in_exact_range(Bd.y) && slp::in_exact_range(Cd.x) && slp::in_exact_range(Cd.y) &&
-                  slp::in_exact_range(X.h) && slp::in_exact_range(Y.h) && slp::in_exact_range(X.l) &&
-                  slp::in_exact_range(Y.l)))
-                flags |= SL_NODE_RANGE;
+            if (r & (1u << 12)) flags |= SL_NODE_RANGE;
         }
         if (s1 >= 0 && s2 >= 0 && s3 >= 0) {
             found = true;
@@ -275,25 +284,39 @@ __device__ __forceinline__ bool step_node(const FastArgs &a, int64_t i, int pi, 
                 c.fallback = 1;
                 flags |= SL_NODE_FALLBACK;
             }
-            const int neg[3] = {s1 < 0, s2 < 0, s3 < 0};
-            const int nneg = neg[0] + neg[1] + neg[2];
-            int pick = (int)(mix64_dev(((uint64_t)i << 20) ^ (uint64_t)hops) % (uint64_t)nneg);
-            k = -1;
-            for (int q = 0; q < 3; ++q)
-                if (neg[q] && pick-- == 0) k = q;
+            k = random_negative_edge(i, hops, s1, s2, s3);
         }
-        load_nbr();
-        const int32_t nj = k == 0 ? na : (k == 1 ? nb : nc);
-        if (nj < 0) break;         // cannot happen for a foot inside a valid mesh
-        j = nj;
-        ia = a.tv[0][j];
-        ib = a.tv[1][j];
-        ic = a.tv[2][j];
-        na = a.tn[0][j];
-        nb = a.tn[1][j];
-        nc = a.tn[2][j];
+        const float4 R = a.he[3 * j + k];
+        if (__float_as_int(R.z) < 0) break;    // a boundary edge: not for a foot inside a valid mesh
+        // the next triangle: (W2, W1, Q), (W0, W2, Q) or (W1, W0, Q)
+        float p0x = k == 1 ? A.x : (k == 0 ? C.x : B.x), p0y = k == 1 ? A.y : (k == 0 ? C.y : B.y);
+        float p1x = k == 0 ? B.x : (k == 1 ? C.x : A.x), p1y = k == 0 ? B.y : (k == 1 ? C.y : A.y);
+        float p2x = R.x, p2y = R.y;
+        e0 = __float_as_int(R.z);
+        e1 = __float_as_int(R.w);
+        ids = false;
         ++hops;
-        certify = hops >= cap;     // FP32 hops until the cap, then certified ones
+        // FP32 hops on the high parts while an edge is certainly negative
+        const float fx = X.h, fy = Y.h;
+        while (hops < cap) {
+            const float ax = p0x - p2x, ay = p0y - p2y, bx = p1x - p2x, by = p1y - p2y;
+            const float xx = fx - p2x, xy = fy - p2y;
+            const float o1 = __fmaf_rn(xx, by, -__fmul_rn(xy, bx));    // ~ theta of W0 * den
+            const float o2 = __fmaf_rn(ax, xy, -__fmul_rn(ay, xx));    // ~ theta of W1 * den
+            const float S = fabsf(ax) + fabsf(ay) + fabsf(bx) + fabsf(by) + fabsf(xx) + fabsf(xy);
+            const float e = hop_bound(S);
+            const bool c1 = o1 < -e, c2 = o2 < -e && !(c1 && o1 <= o2);
+            if (!(c1 || c2)) break;
+            const float4 Q = a.he[c2 ? e1 : e0];
+            if (__float_as_int(Q.z) < 0) break;    // a boundary edge (see above): certify instead
+            if (c2) { p1x = p2x; p1y = p2y; }
+            else { p0x = p2x; p0y = p2y; }
+            p2x = Q.x;
+            p2y = Q.y;
+            e0 = __float_as_int(Q.z);
+            e1 = __float_as_int(Q.w);
+            ++hops;
+        }
     }
     if (!found) {
         flags |= SL_NODE_WALK_LIMIT;
@@ -301,16 +324,16 @@ __device__ __forceinline__ bool step_node(const FastArgs &a, int64_t i, int pi, 
     }
     if (s1 == 0 || s2 == 0 || s3 == 0) flags |= SL_NODE_DEGENERATE;
 
-    // theta_1, theta_2 by Eq. 6 and the P1 value (Remark 1), double-float
+    // theta of W0, W1 by Eq. 6 and the P1 value (Remark 1), double-float
     const df r = df_rcp(den);
     const df th1 = df_mul(n1, r), th2 = df_mul(n2, r);
     const float2 *vin = (const float2 *)a.vin;
-    const df v1 = dfp(vin[ia]), v2 = dfp(vin[ib]), v3 = dfp(vin[ic]);
+    const df v1 = dfp(vin[w0]), v2 = dfp(vin[w1]), v3 = dfp(vin[w2]);
     const df v = df_add(v3, df_add(df_mul(th1, df_sub(v1, v3)), df_mul(th2, df_sub(v2, v3))));
     ((float2 *)a.vout)[i] = make_float2(v.h, v.l);
     if (j != jstart) {
         a.t0[i] = j;
-        a.t0v[i] = make_int4(j, ia, ib, ic);
+        a.t0v[i] = make_int4(3 * j, w0, w1, w2);
     }
     if (c.limit) atomicOr(a.status, 1u << SL_E_WALK_LIMIT);
     if (flags & SL_NODE_RANGE) atomicOr(a.status, 1u << SL_E_ARG);
@@ -323,7 +346,6 @@ __device__ __forceinline__ bool step_node(const FastArgs &a, int64_t i, int pi, 
         if (a.dbg.moves) a.dbg.moves[i] = (int32_t)hops;
         if (a.dbg.flags) a.dbg.flags[i] = (uint8_t)flags;
     }
-    return true;
 }
 
 template <bool kStats, bool kDebug, int kBlock, int kMinBlocks>
@@ -332,129 +354,13 @@ __global__ void __launch_bounds__(kBlock, kMinBlocks) k_step_fast_df(FastArgs a)
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     const bool active = i < a.N;
     NodeCounters c;
-    bool spilled = false;
     const int pi = block_problem(a.node_off, a.nprob, a.N, i);
-    if (active) {
-        if (a.queue) spilled = !step_node<kDebug, true>(a, i, pi, c);
-        else step_node<kDebug, false>(a, i, pi, c);
-    }
-    if (a.queue) {
-        // warp-aggregated push of the long walkers onto the walk queue
-        const unsigned mask = __ballot_sync(0xffffffffu, spilled);
-        if (mask) {
-            const int lane = threadIdx.x & 31, leader = __ffs(mask) - 1;
-            uint32_t base = 0;
-            if (lane == leader) base = atomicAdd(a.queue_count, (uint32_t)__popc(mask));
-            base = __shfl_sync(0xffffffffu, base, leader);
-            if (spilled) {
-                const uint32_t q = base + (uint32_t)__popc(mask & ((1u << lane) - 1u));
-                a.queue[q] = (int32_t)i;
-                a.queue_hops[q] = c.hops;
-            }
-        }
-    }
-    if (kStats) warp_stats(a.stats, active && !spilled, spilled ? 0u : c.hops, c.exact, spilled ? 0u : c.clipped,
-                           c.fallback, c.limit, c.filter2);
-}
-
-// Walk kernel: FP32 hops for the queued long walks, at full occupancy (few
-// registers).  Stops at the first triangle with no clearly negative edge (or
-// at the cap) and leaves it in T^0 for the finish pass, which certifies it.
-template <int kBlock>
-__global__ void __launch_bounds__(kBlock, 2048 / kBlock) k_walk_fast_df(FastArgs a)
-{
-    const uint32_t count = *a.queue_count;
-    const uint32_t cap = (uint32_t)a.walk_cap;
-    for (uint32_t q = blockIdx.x * blockDim.x + threadIdx.x; q < count; q += gridDim.x * blockDim.x) {
-        const int64_t i = a.queue[q];
-        uint32_t hops = a.queue_hops[q];
-        const int pi = a.nprob == 1 ? 0 : problem_of(a.node_off, a.nprob, i);
-        const FastProb &P = a.probs[pi];
-        const float4 xq = a.xyq[i];
-        const df x = df_make(xq.x, xq.z), y = df_make(xq.y, xq.w);
-        df X, Y;
-        foot_df(P, a, i, x, y, X, Y);
-        clip_df(x, y, X, Y);
-        const float fx = X.h, fy = Y.h;
-        int32_t j = a.t0[i];
-        int ia = a.tv[0][j], ib = a.tv[1][j], ic = a.tv[2][j];
-        int na = a.tn[0][j], nb = a.tn[1][j], nc = a.tn[2][j];
-        while (hops < cap) {
-            const float2 A = a.xyh[ia], B = a.xyh[ib], C = a.xyh[ic];
-            const float ax = A.x - C.x, ay = A.y - C.y, bx = B.x - C.x, by = B.y - C.y;
-            const float xx = fx - C.x, xy = fy - C.y;
-            const float o1 = __fmaf_rn(xx, by, -__fmul_rn(xy, bx));
-            const float o2 = __fmaf_rn(ax, xy, -__fmul_rn(ay, xx));
-            const float dn = __fmaf_rn(ax, by, -__fmul_rn(ay, bx));
-            const float o3 = dn - o1 - o2;
-            const float S = fabsf(ax) + fabsf(ay) + fabsf(bx) + fabsf(by) + fabsf(xx) + fabsf(xy);
-            const float e = hop_bound(S);
-            const float e3 = 3.0f * e + 0x1p-23f * (fabsf(dn) + fabsf(o1) + fabsf(o2));
-            int32_t nj = -1;
-            float best = 0.0f;
-            if (o1 < -e) { nj = na; best = o1; }
-            if (o2 < -e && (nj == -1 || o2 < best)) { nj = nb; best = o2; }
-            if (o3 < -e3 && (nj == -1 || o3 < best)) { nj = nc; best = o3; }
-            if (nj < 0) break;
-            j = nj;
-            ia = a.tv[0][j];
-            ib = a.tv[1][j];
-            ic = a.tv[2][j];
-            na = a.tn[0][j];
-            nb = a.tn[1][j];
-            nc = a.tn[2][j];
-            ++hops;
-        }
-        a.t0[i] = j;
-        a.t0v[i] = make_int4(j, ia, ib, ic);
-        a.queue_hops[q] = hops;
-    }
-}
-
-// Finish pass: the queued nodes, completed from the triangle the walk
-// kernel left in T^0 (certified test, further hops if needed, value).
-template <bool kStats, bool kDebug, int kBlock>
-__global__ void __launch_bounds__(kBlock) k_finish_fast_df(FastArgs a)
-{
-    const uint32_t count = *a.queue_count;
-    NodeCounters tot;
-    uint32_t done = 0, hmax = 0;
-    for (uint32_t q = blockIdx.x * blockDim.x + threadIdx.x; q < count; q += gridDim.x * blockDim.x) {
-        NodeCounters c;
-        c.hops = a.queue_hops[q];
-        const int64_t node = a.queue[q];
-        step_node<kDebug, false>(a, node, a.nprob == 1 ? 0 : problem_of(a.node_off, a.nprob, node), c);
-        tot.hops += c.hops;
-        hmax = c.hops > hmax ? c.hops : hmax;
-        tot.exact += c.exact;
-        tot.clipped += c.clipped;
-        tot.fallback += c.fallback;
-        tot.limit += c.limit;
-        tot.filter2 += c.filter2;
-        ++done;
-    }
-    if (kStats) {
-        // one thread may have finished several nodes: its sums go in whole
-        const unsigned full = 0xffffffffu;
-        const unsigned n = __reduce_add_sync(full, done), h = __reduce_add_sync(full, tot.hops);
-        const unsigned hm = __reduce_max_sync(full, hmax), e = __reduce_add_sync(full, tot.exact);
-        const unsigned f2 = __reduce_add_sync(full, tot.filter2), cl = __reduce_add_sync(full, tot.clipped);
-        const unsigned fb = __reduce_add_sync(full, tot.fallback), l = __reduce_add_sync(full, tot.limit);
-        if ((threadIdx.x & 31) == 0) {
-            if (n) atomicAdd(&a.stats[0], (unsigned long long)n);
-            if (h) atomicAdd(&a.stats[1], (unsigned long long)h);
-            if (hm) atomicMax(&a.stats[2], (unsigned long long)hm);
-            if (e) atomicAdd(&a.stats[3], (unsigned long long)e);
-            if (f2) atomicAdd(&a.stats[4], (unsigned long long)f2);
-            if (cl) atomicAdd(&a.stats[5], (unsigned long long)cl);
-            if (fb) atomicAdd(&a.stats[6], (unsigned long long)fb);
-            if (l) atomicAdd(&a.stats[7], (unsigned long long)l);
-        }
-    }
+    if (active) step_node<kDebug>(a, i, pi, c);
+    if (kStats) warp_stats(a.stats, active, c.hops, c.exact, c.clipped, c.fallback, c.limit, c.filter2);
 }
 
 template <int kBlock, int kMinBlocks>
-static void launch_fast_df_cfg(const FastArgs &a, bool stats, bool debug, int sms, cudaStream_t s)
+static void launch_fast_df_cfg(const FastArgs &a, bool stats, bool debug, cudaStream_t s)
 {
     const unsigned grid = (unsigned)((a.N + kBlock - 1) / kBlock);
     if (grid == 0) return;
@@ -465,33 +371,20 @@ static void launch_fast_df_cfg(const FastArgs &a, bool stats, bool debug, int sm
         if (debug) k_step_fast_df<false, true, kBlock, kMinBlocks><<<grid, kBlock, 0, s>>>(a);
         else k_step_fast_df<false, false, kBlock, kMinBlocks><<<grid, kBlock, 0, s>>>(a);
     }
-    if (a.queue) {
-        k_walk_fast_df<256><<<sms * 8, 256, 0, s>>>(a);
-        const unsigned g2 = (unsigned)sms * 4;
-        if (stats) {
-            if (debug) k_finish_fast_df<true, true, 256><<<g2, 256, 0, s>>>(a);
-            else k_finish_fast_df<true, false, 256><<<g2, 256, 0, s>>>(a);
-        } else {
-            if (debug) k_finish_fast_df<false, true, 256><<<g2, 256, 0, s>>>(a);
-            else k_finish_fast_df<false, false, 256><<<g2, 256, 0, s>>>(a);
-        }
-    }
 }
 
 // Launch configurations (threads per block x resident blocks per SM the
 // register budget is sized for): 0 = 256 x 4 (64 registers), 1 = 256 x 3,
-// 2 = 128 x 8, 3 = 128 x 6, 4 = 256 x 5, 5 = 128 x 12.  With a.queue set, walks longer than
-// a.hop_budget hops continue in the walk kernel and finish in the finish pass
-// (the caller zeroes *a.queue_count before the launch).
-void launch_fast_df(const FastArgs &a, bool stats, bool debug, int config, int sms, cudaStream_t s)
+// 2 = 128 x 8, 3 = 128 x 6, 4 = 256 x 5, 5 = 128 x 12.
+void launch_fast_df(const FastArgs &a, bool stats, bool debug, int config, cudaStream_t s)
 {
     switch (config) {
-    case 1: launch_fast_df_cfg<256, 3>(a, stats, debug, sms, s); break;
-    case 2: launch_fast_df_cfg<128, 8>(a, stats, debug, sms, s); break;
-    case 3: launch_fast_df_cfg<128, 6>(a, stats, debug, sms, s); break;
-    case 4: launch_fast_df_cfg<256, 5>(a, stats, debug, sms, s); break;
-    case 5: launch_fast_df_cfg<128, 12>(a, stats, debug, sms, s); break;
-    default: launch_fast_df_cfg<256, 4>(a, stats, debug, sms, s); break;
+    case 1: launch_fast_df_cfg<256, 3>(a, stats, debug, s); break;
+    case 2: launch_fast_df_cfg<128, 8>(a, stats, debug, s); break;
+    case 3: launch_fast_df_cfg<128, 6>(a, stats, debug, s); break;
+    case 4: launch_fast_df_cfg<256, 5>(a, stats, debug, s); break;
+    case 5: launch_fast_df_cfg<128, 12>(a, stats, debug, s); break;
+    default: launch_fast_df_cfg<256, 4>(a, stats, debug, s); break;
     }
 }
 
@@ -598,8 +491,50 @@ __global__ void k_fill_t0v(const int32_t *__restrict__ t0, const int32_t *__rest
 {
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
         const int32_t j = t0[i];
-        t0v[i] = make_int4(j, tv0[j], tv1[j], tv2[j]);
+        t0v[i] = make_int4(3 * j, tv0[j], tv1[j], tv2[j]);
     }
+}
+
+struct HalfEdgeArgs {
+    const int32_t *tv[3];
+    const int32_t *tn[3];
+    const float2 *xyc;
+    int64_t nt;
+    float4 *he;
+};
+
+__global__ void k_build_he(HalfEdgeArgs a)
+{
+    const int64_t nh = 3 * a.nt;
+    for (int64_t h = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; h < nh; h += (int64_t)gridDim.x * blockDim.x) {
+        const int32_t t = (int32_t)(h / 3), k = (int32_t)(h - 3 * (int64_t)t);
+        const int32_t u = a.tn[k][t];
+        float4 r = make_float4(__int_as_float(0x7fc00000), __int_as_float(0x7fc00000), __int_as_float(u),
+                               __int_as_float(u));
+        if (u >= 0) {
+            int kp = 0;
+            if (a.tn[1][u] == t) kp = 1;
+            else if (a.tn[2][u] == t) kp = 2;
+            const float2 q = a.xyc[a.tv[kp][u]];
+            r = make_float4(q.x, q.y, __int_as_float(3 * u + (kp == 2 ? 0 : kp + 1)),
+                            __int_as_float(3 * u + (kp == 0 ? 2 : kp - 1)));
+        }
+        a.he[h] = r;
+    }
+}
+
+void launch_build_he(const int32_t *const tv[3], const int32_t *const tn[3], const float2 *xyc, int64_t nt,
+                     float4 *he, cudaStream_t s)
+{
+    HalfEdgeArgs a;
+    for (int k = 0; k < 3; ++k) {
+        a.tv[k] = tv[k];
+        a.tn[k] = tn[k];
+    }
+    a.xyc = xyc;
+    a.nt = nt;
+    a.he = he;
+    if (nt > 0) k_build_he<<<grid_for(3 * nt, 256), 256, 0, s>>>(a);
 }
 
 void launch_fill_t0v(const int32_t *t0, const int32_t *tv0, const int32_t *tv1, const int32_t *tv2, int4 *t0v,

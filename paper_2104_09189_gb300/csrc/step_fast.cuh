@@ -33,8 +33,10 @@ struct FastArgs {
     const float2 *xyh;            // FP64 meshes: high parts (xh, yh) for the FP32 hop tests
     const int32_t *tv[3];
     const int32_t *tn[3];         // -1 - side on the boundary (0: x=0, 1: x=1, 2: y=0, 3: y=1)
+    const float4 *he;             // half-edge walk records, 3 per triangle (k_build_he)
     int32_t *t0;
-    int4 *t0v;                    // per node: (T^0, its three vertex ids), kept in step with t0
+    int4 *t0v;                    // per node: (3 T^0, T[0][T^0], T[1][T^0], T[2][T^0]), kept in
+                                  // step with t0
     const void *vin;              // FP64: float2 (hi, lo) values; FP32: float values
     void *vout;
     const float4 *g1, *g2;        // field tables (hi, lo) per node, or NULL
@@ -46,17 +48,10 @@ struct FastArgs {
     uint32_t *status;
     unsigned long long *stats;
     sl_debug dbg;
-    // walk queue (optional): walks longer than hop_budget FP32 hops are
-    // pushed here by the main kernel, continued by the walk kernel and
-    // completed by the finish pass
-    int32_t *queue;
-    uint32_t *queue_hops;
-    uint32_t *queue_count;
-    int32_t hop_budget;
 };
 
-// config: launch configuration 0..3 (see step_fast.cu)
-void launch_fast_df(const FastArgs &a, bool stats, bool debug, int config, int sms, cudaStream_t s);
+// config: launch configuration 0..kFastConfigs-1 (see step_fast.cu)
+void launch_fast_df(const FastArgs &a, bool stats, bool debug, int config, cudaStream_t s);
 constexpr int kFastConfigs = 6;
 void launch_fast_f32(const FastArgs &a, bool stats, bool debug, int config, cudaStream_t s);
 
@@ -76,7 +71,17 @@ struct FieldTableArgs {
 };
 void launch_field_tables(const FieldTableArgs &a, cudaStream_t s);
 
-// t0v[i] = (t0[i], its three vertex ids)
+// Half-edge walk records, he[3 t + k] for the edge of triangle t opposite its
+// vertex k.  Interior edge, u = tn[k][t], k' the slot of t in u's neighbours:
+//   (Qx, Qy, e0', e1') with Q = tv[k'][u] (coordinates: xyh for FP64 meshes,
+//   the float coordinates for FP32 meshes), e0' = 3u + (k'+1) mod 3 and
+//   e1' = 3u + (k'+2) mod 3 as int bits: the walk state of u entered
+//   through this edge is (W0, W1, W2) = (T[k'+1][u], T[k'+2][u], Q).
+// Boundary edge: (NaN, NaN, code, code) with the side code tn[k][t] < 0.
+void launch_build_he(const int32_t *const tv[3], const int32_t *const tn[3], const float2 *xyc, int64_t nt,
+                     float4 *he, cudaStream_t s);
+
+// t0v[i] = (3 t0[i], its three vertex ids in slot order)
 void launch_fill_t0v(const int32_t *t0, const int32_t *tv0, const int32_t *tv1, const int32_t *tv2, int4 *t0v,
                      int64_t n, cudaStream_t s);
 

@@ -80,6 +80,17 @@ __device__ __forceinline__ float cross_f32(float ux, float uy, float vx, float v
     return __fsub_rn(t1, t2);
 }
 
+// Triangle of a half-edge code h = 3 t + k (h >= 0).
+__device__ __forceinline__ int32_t tri_of_f32(int32_t h) { return (int32_t)__umulhi((uint32_t)h, 0xAAAAAAABu) >> 1; }
+
+// Walk state as in the double-float kernel: the current triangle's vertices
+// (W0, W1, W2), counter-clockwise, as float coordinates, and the half-edge
+// codes e0, e1, e2 of its edges opposite W0, W1, W2 (code 3 j + s: edge s of
+// triangle j).  A hop loads one 16-byte half-edge record (k_build_he).  After
+// a hop the edge the walk came through (opposite W2) is not tested: its
+// orientation was certified negative from the other side, so here it is
+// positive.  The value is evaluated with the located triangle's vertices in
+// slot order, so it does not depend on the path of the walk.
 template <bool kStats, bool kDebug, int kBlock, int kMinBlocks>
 __global__ void __launch_bounds__(kBlock, kMinBlocks) k_step_fast_f32(FastArgs a)
 {
@@ -105,43 +116,43 @@ __global__ void __launch_bounds__(kBlock, kMinBlocks) k_step_fast_f32(FastArgs a
         const uint32_t fside = (X == 0.0f ? 1u : 0u) | (X == 1.0f ? 2u : 0u) | (Y == 0.0f ? 4u : 0u) |
                                (Y == 1.0f ? 8u : 0u);
 
-        // start triangle and its vertex ids from the per-node cache; the
-        // neighbour slots of the start triangle are loaded only when needed
+        // start state from the per-node cache (T^0 and its vertex ids)
         const int4 tq = a.t0v[i];
-        int32_t j = tq.x;
-        const int32_t jstart = j;
+        int32_t e0 = tq.x, e1, e2;
+        {
+            const int32_t j0 = tri_of_f32(e0), s0 = e0 - 3 * j0;
+            e1 = 3 * j0 + (s0 == 2 ? 0 : s0 + 1);
+            e2 = 3 * j0 + (s0 == 0 ? 2 : s0 - 1);
+        }
+        float2 A = a.xyf[tq.y], B = a.xyf[tq.z], C = a.xyf[tq.w];
+        bool moved = false;
         const uint32_t cap = (uint32_t)a.walk_cap;
         bool found = false;
         int s1 = 0, s2 = 0, s3 = 0;
         float o1 = 0.0f, o2 = 0.0f, dn = 1.0f;
-        int ia = tq.y, ib = tq.z, ic = tq.w;
-        int na = 0, nb = 0, nc = 0;
-        bool have_nbr = false;
         for (;;) {
-            const float2 A = a.xyf[ia], B = a.xyf[ib], C = a.xyf[ic];
             const float ax = __fsub_rn(A.x, C.x), ay = __fsub_rn(A.y, C.y);
             const float bx = __fsub_rn(B.x, C.x), by = __fsub_rn(B.y, C.y);
             const float xx = __fsub_rn(X, C.x), xy = __fsub_rn(Y, C.y);
-            float e1, e2, ed;
-            o1 = cross_f32(xx, xy, bx, by, e1);     // orient(B, C, X): theta_1 * den
-            o2 = cross_f32(ax, ay, xx, xy, e2);     // orient(C, A, X): theta_2 * den
-            dn = cross_f32(ax, ay, bx, by, ed);     // orient(A, B, C) > 0
-            const float o3 = __fsub_rn(__fsub_rn(dn, o1), o2);
-            const float e3 = ed + e1 + e2 + 0x1p-23f * (fabsf(dn) + fabsf(o1) + fabsf(o2));
-            s1 = o1 > e1 ? 1 : (o1 < -e1 ? -1 : 2);
-            s2 = o2 > e2 ? 1 : (o2 < -e2 ? -1 : 2);
-            s3 = o3 > e3 ? 1 : (o3 < -e3 ? -1 : 2);
-            if ((s1 == 2 || s2 == 2 || s3 == 2 || s1 < 0 || s2 < 0 || s3 < 0) && !have_nbr) {
-                na = a.tn[0][j];
-                nb = a.tn[1][j];
-                nc = a.tn[2][j];
-                have_nbr = true;
+            float eb1, eb2, ed;
+            o1 = cross_f32(xx, xy, bx, by, eb1);    // orient(W1, W2, X): theta of W0 * den
+            o2 = cross_f32(ax, ay, xx, xy, eb2);    // orient(W2, W0, X): theta of W1 * den
+            dn = cross_f32(ax, ay, bx, by, ed);     // orient(W0, W1, W2) > 0
+            float o3 = 1.0f;
+            s1 = o1 > eb1 ? 1 : (o1 < -eb1 ? -1 : 2);
+            s2 = o2 > eb2 ? 1 : (o2 < -eb2 ? -1 : 2);
+            s3 = 1;
+            if (!moved) {
+                o3 = __fsub_rn(__fsub_rn(dn, o1), o2);
+                const float eb3 = ed + eb1 + eb2 + 0x1p-23f * (fabsf(dn) + fabsf(o1) + fabsf(o2));
+                s3 = o3 > eb3 ? 1 : (o3 < -eb3 ? -1 : 2);
             }
             if (s1 == 2 || s2 == 2 || s3 == 2) {
-                // boundary edge with the foot on its side: exactly 0
-                if (s1 == 2 && na < 0 && (fside >> (-1 - na) & 1u)) s1 = 0;
-                if (s2 == 2 && nb < 0 && (fside >> (-1 - nb) & 1u)) s2 = 0;
-                if (s3 == 2 && nc < 0 && (fside >> (-1 - nc) & 1u)) s3 = 0;
+                // boundary edge with the foot on its side: exactly 0 (the
+                // record of a boundary half-edge holds its side code)
+                if (s1 == 2) { const int nb = __float_as_int(a.he[e0].z); if (nb < 0 && (fside >> (-1 - nb) & 1u)) s1 = 0; }
+                if (s2 == 2) { const int nb = __float_as_int(a.he[e1].z); if (nb < 0 && (fside >> (-1 - nb) & 1u)) s2 = 0; }
+                if (s3 == 2) { const int nb = __float_as_int(a.he[e2].z); if (nb < 0 && (fside >> (-1 - nb) & 1u)) s3 = 0; }
             }
             if (s1 == 2 || s2 == 2 || s3 == 2) {
                 // the foot on a vertex (e.g. a node whose field vanishes): the
@@ -199,15 +210,20 @@ __global__ void __launch_bounds__(kBlock, kMinBlocks) k_step_fast_f32(FastArgs a
                 for (int q = 0; q < 3; ++q)
                     if (neg[q] && pick-- == 0) k = q;
             }
-            const int32_t nj = k == 0 ? na : (k == 1 ? nb : nc);
-            if (nj < 0) break;         // cannot happen for a foot inside a valid mesh
-            j = nj;
-            ia = a.tv[0][j];
-            ib = a.tv[1][j];
-            ic = a.tv[2][j];
-            na = a.tn[0][j];
-            nb = a.tn[1][j];
-            nc = a.tn[2][j];
+            const float4 R = a.he[k == 0 ? e0 : (k == 1 ? e1 : e2)];
+            if (__float_as_int(R.z) < 0) break;    // a boundary edge: not for a foot inside a valid mesh
+            // the next triangle: (W2, W1, Q), (W0, W2, Q) or (W1, W0, Q)
+            if (k == 0) A = C;
+            else if (k == 1) B = C;
+            else {
+                const float2 t = A;
+                A = B;
+                B = t;
+            }
+            C = make_float2(R.x, R.y);
+            e0 = __float_as_int(R.z);
+            e1 = __float_as_int(R.w);
+            moved = true;
             ++hops;
         }
         if (!found) {
@@ -216,16 +232,36 @@ __global__ void __launch_bounds__(kBlock, kMinBlocks) k_step_fast_f32(FastArgs a
         }
         if (s1 == 0 || s2 == 0 || s3 == 0) flags |= SL_NODE_DEGENERATE;
 
-        // theta_1, theta_2 (Eq. 6) and the P1 value (Remark 1) in float
+        // the located triangle in slot order: its vertex ids and the
+        // numerators of Eq. 6 relative to its vertex 2
+        int w0 = tq.y, w1 = tq.z, w2 = tq.w;
+        const int32_t j = tri_of_f32(e0);
+        if (moved) {
+            w0 = a.tv[0][j];
+            w1 = a.tv[1][j];
+            w2 = a.tv[2][j];
+            // (W0, W1, W2) = slots (s, s+1, s+2)
+            const int32_t s = e0 - 3 * j;
+            const float2 V0 = s == 0 ? A : (s == 1 ? C : B), V1 = s == 0 ? B : (s == 1 ? A : C);
+            const float2 V2 = s == 0 ? C : (s == 1 ? B : A);
+            const float ax = __fsub_rn(V0.x, V2.x), ay = __fsub_rn(V0.y, V2.y);
+            const float bx = __fsub_rn(V1.x, V2.x), by = __fsub_rn(V1.y, V2.y);
+            const float xx = __fsub_rn(X, V2.x), xy = __fsub_rn(Y, V2.y);
+            float eb;
+            o1 = cross_f32(xx, xy, bx, by, eb);
+            o2 = cross_f32(ax, ay, xx, xy, eb);
+            dn = cross_f32(ax, ay, bx, by, eb);
+        }
+        // theta of W0, W1 (Eq. 6) and the P1 value (Remark 1) in float
         const float r = __frcp_rn(dn);
         const float th1 = __fmul_rn(o1, r), th2 = __fmul_rn(o2, r);
         const float *vin = (const float *)a.vin;
-        const float v1 = vin[ia], v2 = vin[ib], v3 = vin[ic];
+        const float v1 = vin[w0], v2 = vin[w1], v3 = vin[w2];
         const float v = __fmaf_rn(th1, __fsub_rn(v1, v3), __fmaf_rn(th2, __fsub_rn(v2, v3), v3));
         ((float *)a.vout)[i] = v;
-        if (j != jstart) {
+        if (moved) {
             a.t0[i] = j;
-            a.t0v[i] = make_int4(j, ia, ib, ic);
+            a.t0v[i] = make_int4(3 * j, w0, w1, w2);
         }
         if (limit_cnt) atomicOr(a.status, 1u << SL_E_WALK_LIMIT);
         if (kDebug) {
