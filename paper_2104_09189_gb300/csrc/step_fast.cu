@@ -127,13 +127,16 @@ __device__ __forceinline__ float cert_bound(float S) { return S * __fmaf_rn(S, 0
 
 // Exact signs of the edges selected by `need` (bit k: the edge opposite
 // W_k) of the triangle (W0, W1, W2), on the double coordinates and the exact
-// foot.  Kept out of line: it runs for a few feet per million, and inlined
-// its expansions would raise the register count of the whole kernel.
+// foot (one inlined copy of the staged predicate for all three edges).
 // Packed result: bits 2k..2k+1 the sign of edge k (0: 0, 1: +1, 2: -1),
 // bits 8..9 the tests decided by the expansion, bits 10..11 those decided by
 // the double filter, bit 12 a coordinate outside the exact range.
 __device__ __forceinline__ uint32_t exact_signs(const double2 *xyd, int w0, int w1, int w2, df X, df Y, uint32_t need)
 {
+    // The foot is loop-invariant: without this barrier the compiler hoists
+    // its float -> double conversions (FP64-pipe work) out of the rare branch
+    // that calls this function into every node's path.
+    asm volatile("" : "+f"(X.h), "+f"(X.l), "+f"(Y.h), "+f"(Y.l));
     const double2 Ad = xyd[w0], Bd = xyd[w1], Cd = xyd[w2];
     uint32_t out = 0, n3 = 0, n2 = 0;
     for (int k = 0; k < 3; ++k) {

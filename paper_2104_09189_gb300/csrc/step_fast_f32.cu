@@ -163,8 +163,12 @@ __global__ void __launch_bounds__(kBlock, kMinBlocks) k_step_fast_f32(FastArgs a
                 if (s3 == 2 && (onA || onB)) s3 = 0;
             }
             if (s1 == 2 || s2 == 2 || s3 == 2) {
-                // double predicate on the floats promoted exactly
-                const double Xd = X, Yd = Y;
+                // double predicate on the floats promoted exactly (the
+                // barrier keeps the conversions of the loop-invariant foot
+                // inside this rare branch)
+                float xb = X, yb = Y;
+                asm volatile("" : "+f"(xb), "+f"(yb));
+                const double Xd = xb, Yd = yb;
                 if (s1 == 2) {
                     slp::OrientResult r = slp::orient(B.x, B.y, C.x, C.y, Xd, Yd);
                     s1 = r.sign;
