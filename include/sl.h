@@ -123,7 +123,7 @@ typedef enum {
     SL_OPT_TILES_PER_SM = 4, /* reserved */
     SL_OPT_CONFIG = 5,       /* launch configuration of the fast kernels, 0..5: threads per block x
                                 blocks per SM the registers are sized for = 256x4, 256x3, 128x8,
-                                128x6, 256x5, 128x12 (default 5) */
+                                128x9, 256x5, 128x12 (default 5) */
     /* 6: unused */
     SL_OPT_CONFIG_FIRST = 7  /* launch configuration for a step whose walks start at the initial
                                 incident triangles (the first step after sl_mesh_create or

@@ -207,16 +207,11 @@ __device__ __forceinline__ void step_node(const FastArgs &a, int64_t i, int pi, 
         flags |= SL_NODE_CLIPPED;
         c.clipped = 1;
     }
-    // sides of the square the foot lies on exactly (bit = boundary side code)
-    const uint32_t fside = (df_is(X, 0.0f) ? 1u : 0u) | (df_is(X, 1.0f) ? 2u : 0u) | (df_is(Y, 0.0f) ? 4u : 0u) |
-                           (df_is(Y, 1.0f) ? 8u : 0u);
-
     // start triangle and its vertex ids from the per-node cache: one
     // coalesced 16-byte load
     const int4 tq = a.t0v[i];
     int32_t e0 = tq.x, e1 = 0;
     int32_t j = 0;
-    const int32_t jstart = tri_of(tq.x);
     int w0 = tq.y, w1 = tq.z, w2 = tq.w;
     bool ids = true;           // w0..w2 are the vertex ids of the current triangle
     const uint32_t cap = (uint32_t)a.walk_cap;
@@ -252,6 +247,9 @@ __device__ __forceinline__ void step_node(const FastArgs &a, int64_t i, int pi, 
         s3 = n3.h > ec ? 1 : (n3.h < -ec ? -1 : 2);
         if (s1 == 2 || s2 == 2 || s3 == 2) {
             // a boundary edge with the foot on its side of the square: exactly 0
+            // (fside: the sides the foot lies on, bit = boundary side code)
+            const uint32_t fside = (df_is(X, 0.0f) ? 1u : 0u) | (df_is(X, 1.0f) ? 2u : 0u) |
+                                   (df_is(Y, 0.0f) ? 4u : 0u) | (df_is(Y, 1.0f) ? 8u : 0u);
             if (s1 == 2) { const int32_t nb = a.tn[0][j]; if (nb < 0 && (fside >> (-1 - nb) & 1u)) s1 = 0; }
             if (s2 == 2) { const int32_t nb = a.tn[1][j]; if (nb < 0 && (fside >> (-1 - nb) & 1u)) s2 = 0; }
             if (s3 == 2) { const int32_t nb = a.tn[2][j]; if (nb < 0 && (fside >> (-1 - nb) & 1u)) s3 = 0; }
@@ -291,9 +289,11 @@ __device__ __forceinline__ void step_node(const FastArgs &a, int64_t i, int pi, 
         }
         const float4 R = a.he[3 * j + k];
         if (__float_as_int(R.z) < 0) break;    // a boundary edge: not for a foot inside a valid mesh
-        // the next triangle: (W2, W1, Q), (W0, W2, Q) or (W1, W0, Q)
-        float p0x = k == 1 ? A.x : (k == 0 ? C.x : B.x), p0y = k == 1 ? A.y : (k == 0 ? C.y : B.y);
-        float p1x = k == 0 ? B.x : (k == 1 ? C.x : A.x), p1y = k == 0 ? B.y : (k == 1 ? C.y : A.y);
+        // the next triangle: (W2, W1, Q), (W0, W2, Q) or (W1, W0, Q); the
+        // high parts of the kept vertices are reloaded (L1 hits) rather than
+        // kept live through the certified test
+        const float2 P0 = a.xyh[k == 1 ? w0 : (k == 0 ? w2 : w1)], P1 = a.xyh[k == 0 ? w1 : (k == 1 ? w2 : w0)];
+        float p0x = P0.x, p0y = P0.y, p1x = P1.x, p1y = P1.y;
         float p2x = R.x, p2y = R.y;
         e0 = __float_as_int(R.z);
         e1 = __float_as_int(R.w);
@@ -334,7 +334,7 @@ __device__ __forceinline__ void step_node(const FastArgs &a, int64_t i, int pi, 
     const df v1 = dfp(vin[w0]), v2 = dfp(vin[w1]), v3 = dfp(vin[w2]);
     const df v = df_add(v3, df_add(df_mul(th1, df_sub(v1, v3)), df_mul(th2, df_sub(v2, v3))));
     ((float2 *)a.vout)[i] = make_float2(v.h, v.l);
-    if (j != jstart) {
+    if (hops > 0) {
         a.t0[i] = j;
         a.t0v[i] = make_int4(3 * j, w0, w1, w2);
     }
@@ -378,13 +378,13 @@ static void launch_fast_df_cfg(const FastArgs &a, bool stats, bool debug, cudaSt
 
 // Launch configurations (threads per block x resident blocks per SM the
 // register budget is sized for): 0 = 256 x 4 (64 registers), 1 = 256 x 3,
-// 2 = 128 x 8, 3 = 128 x 6, 4 = 256 x 5, 5 = 128 x 12.
+// 2 = 128 x 8, 3 = 128 x 9 (56 registers), 4 = 256 x 5, 5 = 128 x 12.
 void launch_fast_df(const FastArgs &a, bool stats, bool debug, int config, cudaStream_t s)
 {
     switch (config) {
     case 1: launch_fast_df_cfg<256, 3>(a, stats, debug, s); break;
     case 2: launch_fast_df_cfg<128, 8>(a, stats, debug, s); break;
-    case 3: launch_fast_df_cfg<128, 6>(a, stats, debug, s); break;
+    case 3: launch_fast_df_cfg<128, 9>(a, stats, debug, s); break;
     case 4: launch_fast_df_cfg<256, 5>(a, stats, debug, s); break;
     case 5: launch_fast_df_cfg<128, 12>(a, stats, debug, s); break;
     default: launch_fast_df_cfg<256, 4>(a, stats, debug, s); break;

@@ -229,6 +229,27 @@ __global__ void __launch_bounds__(kBlock, kMinBlocks) k_step_fast_f32(FastArgs a
             e1 = __float_as_int(R.w);
             moved = true;
             ++hops;
+            // lean hops: the two exits of the entered triangle, taken while
+            // one is certainly negative (the same stage-A bound); the full
+            // test above decides where no edge is certainly negative
+            while (hops < cap) {
+                const float ax = __fsub_rn(A.x, C.x), ay = __fsub_rn(A.y, C.y);
+                const float bx = __fsub_rn(B.x, C.x), by = __fsub_rn(B.y, C.y);
+                const float xx = __fsub_rn(X, C.x), xy = __fsub_rn(Y, C.y);
+                float eb1, eb2;
+                const float q1 = cross_f32(xx, xy, bx, by, eb1);
+                const float q2 = cross_f32(ax, ay, xx, xy, eb2);
+                const bool c1 = q1 < -eb1, c2 = q2 < -eb2 && !(c1 && q1 <= q2);
+                if (!(c1 || c2)) break;
+                const float4 Q = a.he[c2 ? e1 : e0];
+                if (__float_as_int(Q.z) < 0) break;    // a boundary edge: not for a foot inside a valid mesh
+                if (c2) B = C;
+                else A = C;
+                C = make_float2(Q.x, Q.y);
+                e0 = __float_as_int(Q.z);
+                e1 = __float_as_int(Q.w);
+                ++hops;
+            }
         }
         if (!found) {
             flags |= SL_NODE_WALK_LIMIT;
@@ -300,7 +321,7 @@ void launch_fast_f32(const FastArgs &a, bool stats, bool debug, int config, cuda
     switch (config) {
     case 1: launch_f32_cfg<256, 3>(a, stats, debug, s); break;
     case 2: launch_f32_cfg<128, 8>(a, stats, debug, s); break;
-    case 3: launch_f32_cfg<128, 6>(a, stats, debug, s); break;
+    case 3: launch_f32_cfg<128, 9>(a, stats, debug, s); break;
     case 4: launch_f32_cfg<256, 5>(a, stats, debug, s); break;
     case 5: launch_f32_cfg<128, 12>(a, stats, debug, s); break;
     default: launch_f32_cfg<256, 4>(a, stats, debug, s); break;
