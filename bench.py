@@ -64,6 +64,29 @@ def dist_env():
     return rank, world, local
 
 
+def max_over_ranks(dist, seconds, device):
+    """The slowest rank's timed region (every rank gets the same value)."""
+    import torch
+    if dist is None:
+        return seconds
+    t = torch.tensor([seconds], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_value(nodes_per_rank, steps_per_run, runs, world, seconds):
+    """node-updates/s of the whole job: every rank advances its own copy of
+    the workload (replicas, weak scaling), timed by the slowest rank."""
+    return nodes_per_rank * steps_per_run * runs * world / seconds
+
+
+def launches_per_run(steps_per_run, double_float):
+    """Kernels one timed run launches: the start-cache fill after the T^0
+    reset, one step kernel per step and, for the double-float path, the value
+    conversions to and from (hi, lo) pairs."""
+    return steps_per_run + 1 + (2 if double_float else 0)
+
+
 class ClockSampler:
     """nvidia-smi clocks and throttle reasons sampled every 200 ms."""
     FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
@@ -306,10 +329,7 @@ def main():
         dist.barrier()
     elapsed = ev0.elapsed_time(ev1) / 1e3
     clocks = sampler.stop()
-    if dist:
-        tt = torch.tensor([elapsed], dtype=torch.float64, device="cuda")
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        elapsed = float(tt.item())
+    elapsed = max_over_ranks(dist, elapsed, "cuda")
 
     # phases: the first step (walks start at the initial incident triangles)
     # and the remaining steps (walks start at the previous foot triangles)
@@ -372,8 +392,7 @@ def main():
                  "kernel": "plain FP64 step (one thread per node, all arithmetic in double)"}
         sl.sl_mesh_set_option(h, sl.SL_OPT_KERNEL, args.kernel)
 
-    units = N * S * args.steps * world
-    value = units / elapsed
+    value = whole_job_value(N, S, args.steps, world, elapsed)
     launch_s = elapsed / (args.steps * S)
     bpn = BYTES_PER_NODE[wl.precision]
     peaks, peak_src = measured_peaks()
@@ -432,7 +451,7 @@ def main():
                      "launch_ms": launch_s * 1e3},
         "cpu_baseline": cpu,
         "e2e": e2e,
-        "gpu_launches": args.steps * (S + (2 if (prec == sl.SL_FP64 and args.kernel != 1) else 0)),
+        "gpu_launches": args.steps * launches_per_run(S, prec == sl.SL_FP64 and args.kernel != 1),
         "clocks": clocks,
         "walk": {"first_run_mean_hops_per_node_update": stats["walk_moves"] / max(1, stats["node_updates"]),
                  "max_hops": stats["max_moves"], "exact_tests": stats["exact_tests"],
