@@ -54,6 +54,11 @@ def parse():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-plain", action="store_true", help="skip the plain FP64 kernel comparison")
+    ap.add_argument("--study", choices=["courant"], default=None,
+                    help="the paper's walk study (Sec. 4): mean hops per node-update and time per step "
+                         "against the Courant number for each start strategy; prints one JSON line")
+    ap.add_argument("--study-cells", type=int, default=386,
+                    help="cells per side of the study mesh (386: 1.5e5 nodes, the paper's size)")
     return ap.parse_args()
 
 
@@ -257,10 +262,75 @@ def workload_config(args, wl):
             "l2": "inputs larger than L2 (129 MB)" if wl.nodes * 64 > 2 * 129e6 else "inputs may fit in L2"}
 
 
+STUDY_ALPHAS = (0.25, 0.5, 1, 2, 4, 6, 8, 10, 12, 14, 16, 18, 20)
+
+
+def run_study(args):
+    """Dependence on the Courant number (Sec. 4): the paper's rotating field
+    f = (cos(C0 |x - c| + C1 t), sin(...)), |f| = 1, L_x = C0 = 2 pi and
+    L_t = C1 in {2 pi, 8 pi}; dt = alpha dx, ceil(1/dt) steps over t in
+    [0, 1]; nodes whose foot leaves the domain excluded; hops averaged over
+    the located node-updates.  Strategy (a) starts every walk at the node's
+    own incident triangle, (b) at the previous step's foot triangle."""
+    import torch
+    import paper_2104_09189_gb300 as sl
+    rank, world, local = dist_env()
+    if rank != 0:
+        return
+    torch.cuda.set_device(local)
+    M = args.study_cells
+    mesh = si.grid_mesh(M, 0.25, 7)
+    no, to, xy, tri = sl.pack_meshes([(mesh.xy, mesh.tri)])
+    h = sl.sl_mesh_create(no, to, xy, tri, precision=sl.SL_FP64, seed=7)
+    node_perm, _ = sl.sl_mesh_reorder(h, sl.SL_CURVE_HILBERT)
+    sl.sl_mesh_set_option(h, sl.SL_OPT_OUTSIDE, 1)
+    sl.sl_mesh_set_option(h, sl.SL_OPT_STATS, 1)
+    v0 = torch.tensor(si.cosine_bump(mesh.xy, 0.5, 0.75, 0.15)[node_perm], dtype=torch.float64, device="cuda")
+    v = v0.clone()
+    w = torch.empty_like(v)
+    stream = torch.cuda.current_stream()
+    rows = []
+    for lt_name, lt in (("2pi", 2 * np.pi), ("8pi", 8 * np.pi)):
+        f = si.paper_field(2 * np.pi, lt)
+        for alpha in STUDY_ALPHAS:
+            dt = alpha / M
+            S = int(np.ceil(1.0 / dt))
+            probs = sl.problems([(f.kind, dt, f.packed())])
+            for strategy, name in ((1, "a"), (0, "b")):
+                sl.sl_mesh_set_option(h, sl.SL_OPT_STRATEGY, strategy)
+                sl.sl_mesh_stats(h, reset=True)
+                v.copy_(v0)
+                sl.sl_run(h, probs, 0, S, v, w, use_graph=True)       # records the graph; statistics
+                st = sl.sl_mesh_stats(h, reset=True)
+                sl.sl_mesh_reset_t0(h)
+                v.copy_(v0)
+                torch.cuda.synchronize()
+                e0 = torch.cuda.Event(enable_timing=True)
+                e1 = torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                sl.sl_run(h, probs, 0, S, v, w, use_graph=True)
+                e1.record(stream)
+                torch.cuda.synchronize()
+                ms = e0.elapsed_time(e1)
+                located = st["node_updates"] - st["excluded"]
+                rows.append({"Lt": lt_name, "alpha": alpha, "strategy": name, "steps": S,
+                             "mean_hops": st["walk_moves"] / max(1, located),
+                             "excluded_fraction": st["excluded"] / max(1, st["node_updates"]),
+                             "ms_per_step": ms / S, "ns_per_located_node_update": 1e6 * ms / max(1, located)})
+    sl.sl_mesh_destroy(h)
+    print(json.dumps({"study": "courant", "source": "Sec. 4, dependence on the Courant number",
+                      "mesh": {"cells": M, "nodes": mesh.n_nodes, "triangles": mesh.n_tri, "jitter": 0.25,
+                               "dx": 1.0 / M, "curve": "hilbert"},
+                      "field": "paper (cos(C0|x-c|+C1 t), sin(...)), C0 = 2 pi, c = (0.5, 0.5)",
+                      "outside": "excluded", "precision": "fp64 (double-float kernel)", "rows": rows}), flush=True)
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         return run_reference(args)
+    if args.study:
+        return run_study(args)
     import torch
     import paper_2104_09189_gb300 as sl
     rank, world, local = dist_env()

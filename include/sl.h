@@ -86,7 +86,9 @@ enum {
     SL_NODE_EXACT = 4,        /* an orientation sign needed the exact stage */
     SL_NODE_FALLBACK = 8,     /* the walk hit its hop cap and used the fallback walk */
     SL_NODE_WALK_LIMIT = 16,  /* the fallback failed too: the value is not valid */
-    SL_NODE_RANGE = 32        /* a coordinate outside the exact predicate's range */
+    SL_NODE_RANGE = 32,       /* a coordinate outside the exact predicate's range */
+    SL_NODE_EXCLUDED = 64     /* SL_OPT_OUTSIDE = 1: the Euler foot left the square, so the node
+                                 was excluded (V^{n+1}_i = V^n_i, no walk, T^0_i unchanged) */
 };
 
 typedef struct sl_mesh sl_mesh;   /* opaque; owns device mesh arrays and T^0 */
@@ -112,6 +114,7 @@ typedef struct {
     uint64_t clipped;        /* feet clipped to the boundary */
     uint64_t fallbacks;      /* walks that switched to the fallback rule */
     uint64_t walk_limit;     /* walks that failed */
+    uint64_t excluded;       /* nodes excluded (SL_OPT_OUTSIDE = 1); node_updates counts them too */
 } sl_stats;
 
 /* Tunable options (sl_mesh_set_option) */
@@ -125,9 +128,16 @@ typedef enum {
                                 blocks per SM the registers are sized for = 256x4, 256x3, 128x8,
                                 128x9, 256x5, 128x12 (default 5) */
     /* 6: unused */
-    SL_OPT_CONFIG_FIRST = 7  /* launch configuration for a step whose walks start at the initial
+    SL_OPT_CONFIG_FIRST = 7, /* launch configuration for a step whose walks start at the initial
                                 incident triangles (the first step after sl_mesh_create or
                                 sl_mesh_reset_t0): long walks favour fewer resident warps (default 0) */
+    SL_OPT_STRATEGY = 8,     /* start triangle of the walks (Sec. 3): 0 = strategy (b), the triangle
+                                found at the previous step (default); 1 = strategy (a), the node's own
+                                incident triangle at every step (T^0 is never overwritten).  Setting
+                                it resets T^0 to the initial incident triangles (synchronises). */
+    SL_OPT_OUTSIDE = 9       /* feet that leave the square: 0 = clip them to the boundary (default);
+                                1 = exclude the node, as the paper's experiments do (Sec. 4):
+                                V^{n+1}_i = V^n_i, flag SL_NODE_EXCLUDED */
 } sl_option;
 
 /*

@@ -26,6 +26,7 @@ _lib = None
 FLAG_CLIPPED = 1
 FLAG_DEGENERATE = 2
 FLAG_MULTI = 4
+FLAG_EXCLUDED = 8
 
 
 def build(force=False):
@@ -69,6 +70,8 @@ def lib():
             L.orc_tri_margin.restype = D
             L.orc_step_range.argtypes = [P, I, P, D, I64, P, P, P, P, P, I64, I64, I]
             L.orc_step_range.restype = I
+            L.orc_step_range_x.argtypes = [P, I, P, D, I64, P, P, P, P, P, I64, I64, I, I]
+            L.orc_step_range_x.restype = I
             L.orc_step.argtypes = [P, I, P, D, I64, P, P, P, P, P, I]
             L.orc_step.restype = I
             L.orc_run.argtypes = [P, I, P, D, I64, I, P, P, I]
@@ -175,9 +178,11 @@ class OracleMesh:
         lib().orc_margins(self._h, q.shape[0], _ptr(tri), _ptr(q), _ptr(out))
         return out
 
-    def step(self, kind, params, dt, n, vin, lo=0, hi=None, nthreads=None, want_feet=True):
+    def step(self, kind, params, dt, n, vin, lo=0, hi=None, nthreads=None, want_feet=True, exclude=False):
         """One step n -> n+1 on nodes [lo, hi).  Returns (vout, tri, flags, feet)
-        restricted to that range."""
+        restricted to that range.  exclude: nodes whose Euler foot leaves the
+        square keep their value (flag FLAG_EXCLUDED, tri -1) instead of being
+        clipped (Sec. 4)."""
         hi = self.n if hi is None else hi
         cnt = hi - lo
         p = np.ascontiguousarray(params, dtype=np.float64)
@@ -186,21 +191,22 @@ class OracleMesh:
         tri = np.full(self.n, -1, dtype=np.int32)
         flags = np.zeros(self.n, dtype=np.uint8)
         ft = np.zeros((self.n, 2), dtype=np.float64) if want_feet else None
-        err = lib().orc_step_range(self._h, int(kind), _ptr(p), float(dt), int(n), _ptr(vin), _ptr(vout),
-                                   _ptr(ft), _ptr(tri), _ptr(flags), int(lo), int(hi),
-                                   int(nthreads or default_threads()))
+        err = lib().orc_step_range_x(self._h, int(kind), _ptr(p), float(dt), int(n), _ptr(vin), _ptr(vout),
+                                     _ptr(ft), _ptr(tri), _ptr(flags), int(lo), int(hi),
+                                     int(nthreads or default_threads()), 1 if exclude else 0)
         if err:
             raise RuntimeError("oracle: a foot lies in no triangle (mesh does not cover the square)")
         sl = slice(lo, hi)
         return vout[sl], tri[sl], flags[sl], (ft[sl] if want_feet else None)
 
-    def run(self, kind, params, dt, n0, nsteps, v, nthreads=None, record=False):
+    def run(self, kind, params, dt, n0, nsteps, v, nthreads=None, record=False, exclude=False):
         """nsteps steps from V^{n0}.  Returns V^{n0+nsteps} (and, with record,
         the list of (V, tri, flags, feet) after every step)."""
         v = np.array(v, dtype=np.float64, copy=True)
         hist = []
         for s in range(nsteps):
-            vout, tri, flags, ft = self.step(kind, params, dt, n0 + s, v, nthreads=nthreads, want_feet=record)
+            vout, tri, flags, ft = self.step(kind, params, dt, n0 + s, v, nthreads=nthreads, want_feet=record,
+                                             exclude=exclude)
             v = vout.copy()
             if record:
                 hist.append((v.copy(), tri.copy(), flags.copy(), ft.copy()))

@@ -576,6 +576,7 @@ typedef struct {
     int32_t *tri;
     uint8_t *flags;
     int64_t lo, hi;
+    int exclude;
     int err;
 } step_job;
 
@@ -585,6 +586,20 @@ static void *step_worker(void *arg)
     const orc_mesh *m = J->m;
     for (int64_t i = J->lo; i < J->hi; ++i) {
         double X, Y;
+        if (J->exclude) {
+            /* Sec. 4: nodes whose Euler foot leaves the domain are excluded
+             * from the computation; V keeps its value there */
+            double fx, fy;
+            orc_field(J->kind, J->p, m->xy[2 * i], m->xy[2 * i + 1], J->t, &fx, &fy);
+            const double qx = m->xy[2 * i] - J->dt * fx, qy = m->xy[2 * i + 1] - J->dt * fy;
+            if (!(qx >= 0.0 && qx <= 1.0 && qy >= 0.0 && qy <= 1.0)) {
+                if (J->vout) J->vout[i] = J->vin[i];
+                if (J->feet) { J->feet[2 * i] = qx; J->feet[2 * i + 1] = qy; }
+                if (J->tri) J->tri[i] = -1;
+                if (J->flags) J->flags[i] = (uint8_t)ORC_FLAG_EXCLUDED;
+                continue;
+            }
+        }
         int clipped = orc_foot(J->kind, J->p, J->dt, J->t, m->xy[2 * i], m->xy[2 * i + 1], &X, &Y);
         int32_t j;
         int f;
@@ -629,8 +644,16 @@ int orc_step_range(const orc_mesh *m, int kind, const double *p, double dt, int6
                    const double *vin, double *vout, double *feet, int32_t *tri, uint8_t *flags,
                    int64_t lo, int64_t hi, int nthreads)
 {
+    return orc_step_range_x(m, kind, p, dt, n, vin, vout, feet, tri, flags, lo, hi, nthreads, 0);
+}
+
+int orc_step_range_x(const orc_mesh *m, int kind, const double *p, double dt, int64_t n,
+                     const double *vin, double *vout, double *feet, int32_t *tri, uint8_t *flags,
+                     int64_t lo, int64_t hi, int nthreads, int exclude)
+{
     step_job J;
     memset(&J, 0, sizeof(J));
+    J.exclude = exclude;
     J.m = m;
     J.kind = kind;
     J.p = p;

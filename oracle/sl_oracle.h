@@ -24,7 +24,8 @@ enum {
 enum {
     ORC_FLAG_CLIPPED = 1,     /* the Euler foot left the square and was clipped */
     ORC_FLAG_DEGENERATE = 2,  /* the foot lies on an edge line of its triangle */
-    ORC_FLAG_MULTI = 4        /* more than one triangle contains the foot */
+    ORC_FLAG_MULTI = 4,       /* more than one triangle contains the foot */
+    ORC_FLAG_EXCLUDED = 8     /* exclusion mode: the Euler foot left the square (Sec. 4) */
 };
 
 typedef struct orc_mesh orc_mesh;
@@ -45,6 +46,12 @@ double orc_tri_margin(const orc_mesh *m, int32_t j, double X, double Y);
 int orc_step_range(const orc_mesh *m, int kind, const double *p, double dt, int64_t n,
                    const double *vin, double *vout, double *feet, int32_t *tri, uint8_t *flags,
                    int64_t lo, int64_t hi, int nthreads);
+/* The same with exclusion (exclude != 0): a node whose Euler foot leaves the
+ * square keeps V^n (vout[i] = vin[i]), tri -1, flag ORC_FLAG_EXCLUDED, feet =
+ * the unclipped foot (the paper's experiments, Sec. 4). */
+int orc_step_range_x(const orc_mesh *m, int kind, const double *p, double dt, int64_t n,
+                     const double *vin, double *vout, double *feet, int32_t *tri, uint8_t *flags,
+                     int64_t lo, int64_t hi, int nthreads, int exclude);
 int orc_step(const orc_mesh *m, int kind, const double *p, double dt, int64_t n,
              const double *vin, double *vout, double *feet, int32_t *tri, uint8_t *flags,
              int nthreads);

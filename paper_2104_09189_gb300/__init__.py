@@ -17,9 +17,10 @@ from ._build import LIB as _LIB_PATH
 __all__ = [
     "SL_OK", "SL_E_ARG", "SL_E_MESH", "SL_E_NOMEM", "SL_E_CUDA", "SL_E_WALK_LIMIT", "SL_E_STATE",
     "SL_FP64", "SL_FP32", "SL_CURVE_NONE", "SL_CURVE_HILBERT", "SL_CURVE_MORTON",
-    "SL_OPT_STATS", "SL_OPT_WALK_CAP", "SL_OPT_KERNEL", "SL_OPT_BLOCK", "SL_OPT_TILES_PER_SM", "SL_OPT_CONFIG", "SL_OPT_CONFIG_FIRST",
+    "SL_OPT_STATS", "SL_OPT_WALK_CAP", "SL_OPT_KERNEL", "SL_OPT_BLOCK", "SL_OPT_TILES_PER_SM", "SL_OPT_CONFIG",
+    "SL_OPT_CONFIG_FIRST", "SL_OPT_STRATEGY", "SL_OPT_OUTSIDE",
     "SL_NODE_CLIPPED", "SL_NODE_DEGENERATE", "SL_NODE_EXACT", "SL_NODE_FALLBACK", "SL_NODE_WALK_LIMIT",
-    "SL_NODE_RANGE", "SLError", "sl_problem", "problems", "pack_meshes",
+    "SL_NODE_RANGE", "SL_NODE_EXCLUDED", "SLError", "sl_problem", "problems", "pack_meshes",
     "sl_mesh_create", "sl_mesh_validate", "sl_mesh_reorder", "sl_step", "sl_run", "sl_run_host", "sl_mesh_get_t0",
     "sl_mesh_set_t0", "sl_mesh_reset_t0", "sl_mesh_status", "sl_mesh_stats", "sl_mesh_set_option", "sl_mesh_info",
     "sl_mesh_export", "sl_mesh_destroy", "sl_last_error", "library", "EXPORTED", "sl_step_noalloc",
@@ -30,9 +31,10 @@ SL_OK, SL_E_ARG, SL_E_MESH, SL_E_NOMEM, SL_E_CUDA, SL_E_WALK_LIMIT, SL_E_STATE =
 SL_FP64, SL_FP32 = 0, 1
 SL_CURVE_NONE, SL_CURVE_HILBERT, SL_CURVE_MORTON = 0, 1, 2
 SL_OPT_STATS, SL_OPT_WALK_CAP, SL_OPT_KERNEL, SL_OPT_BLOCK, SL_OPT_TILES_PER_SM, SL_OPT_CONFIG = range(6)
-SL_OPT_CONFIG_FIRST = 7
+SL_OPT_CONFIG_FIRST, SL_OPT_STRATEGY, SL_OPT_OUTSIDE = 7, 8, 9
 SL_NODE_CLIPPED, SL_NODE_DEGENERATE, SL_NODE_EXACT, SL_NODE_FALLBACK, SL_NODE_WALK_LIMIT, SL_NODE_RANGE = (
     1, 2, 4, 8, 16, 32)
+SL_NODE_EXCLUDED = 64
 SL_NPARAMS = 48
 SL_NOALLOC_MAX_NODES = 1 << 20
 SL_NOALLOC_MAX_PROBLEMS = 256
@@ -70,7 +72,8 @@ class sl_tune(ctypes.Structure):
 
 class sl_stats(ctypes.Structure):
     _fields_ = [(n, ctypes.c_uint64) for n in ("node_updates", "walk_moves", "max_moves", "exact_tests",
-                                                "filter2_tests", "clipped", "fallbacks", "walk_limit")]
+                                                "filter2_tests", "clipped", "fallbacks", "walk_limit",
+                                                "excluded")]
 
     def as_dict(self):
         return {n: int(getattr(self, n)) for n, _ in self._fields_}

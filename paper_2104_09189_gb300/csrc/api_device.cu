@@ -201,6 +201,8 @@ static StepArgs make_args(const sl_mesh *m, const ProbStep *probs_dev, const voi
     a.status = m->d.status;
     a.stats = m->d.stats;
     if (dbg) a.dbg = *dbg;
+    a.keep_t0 = m->opt_strategy == 1;
+    a.exclude = m->opt_outside == 1;
     return a;
 }
 
@@ -231,6 +233,8 @@ static FastArgs make_fast_args(const sl_mesh *m, const FastProb *fp, const void 
     a.status = m->d.status;
     a.stats = m->d.stats;
     if (dbg) a.dbg = *dbg;
+    a.keep_t0 = m->opt_strategy == 1;
+    a.exclude = m->opt_outside == 1;
     return a;
 }
 
@@ -618,6 +622,16 @@ extern "C" sl_status sl_mesh_reset_t0(sl_mesh *m, void *stream)
     return SL_OK;
 }
 
+// T^0 back to the initial incident triangles, synchronously (option changes).
+sl_status sl::reset_t0_sync(sl_mesh *m)
+{
+    SL_CUDA(cudaSetDevice(m->device));
+    sl_status st = sl_mesh_reset_t0(m, nullptr);
+    if (st != SL_OK) return st;
+    SL_CUDA(cudaDeviceSynchronize());
+    return SL_OK;
+}
+
 extern "C" sl_status sl_mesh_status(sl_mesh *m, void *stream)
 {
     if (!m) return fail(SL_E_ARG, "sl_mesh_status: mesh is NULL");
@@ -644,6 +658,7 @@ extern "C" sl_status sl_mesh_stats(sl_mesh *m, sl_stats *out, int32_t reset, voi
         out->clipped = c[5];
         out->fallbacks = c[6];
         out->walk_limit = c[7];
+        out->excluded = c[8];
     }
     return SL_OK;
 }

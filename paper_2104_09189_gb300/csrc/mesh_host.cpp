@@ -413,6 +413,17 @@ extern "C" sl_status sl_mesh_set_option(sl_mesh *m, int32_t option, int64_t valu
         if (value < 0 || value > 5) return sl::fail(SL_E_ARG, "launch configuration must be 0..5");
         m->opt_config_first = (int32_t)value;
         break;
+    case SL_OPT_STRATEGY: {
+        if (value != 0 && value != 1) return sl::fail(SL_E_ARG, "strategy must be 0 (b) or 1 (a)");
+        m->opt_strategy = (int32_t)value;
+        sl_status st = sl::reset_t0_sync(m);
+        if (st != SL_OK) return st;
+        break;
+    }
+    case SL_OPT_OUTSIDE:
+        if (value != 0 && value != 1) return sl::fail(SL_E_ARG, "outside mode must be 0 (clip) or 1 (exclude)");
+        m->opt_outside = (int32_t)value;
+        break;
     default: return sl::fail(SL_E_ARG, "unknown option");
     }
     m->graph.valid = false;   // recorded launches may depend on options

@@ -206,6 +206,8 @@ extern "C" sl_status sl_step_noalloc(sl_mesh *m, const sl_problem *probs, int64_
     a.N = m->N;
     a.status = m->d.status;
     a.stats = m->d.stats;
+    a.keep_t0 = m->opt_strategy == 1;
+    a.exclude = m->opt_outside == 1;
     launch_fast_df(a, m->opt_stats != 0, false, m->opt_config, s);
     launch_from_df(sc.values, v_out, m->N, s);
     e = cudaGetLastError();

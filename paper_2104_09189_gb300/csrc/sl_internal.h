@@ -85,6 +85,8 @@ struct sl_mesh {
     int32_t opt_tiles_per_sm = 0;
     int32_t opt_config = 5;           // launch configuration of the fast kernels (later steps)
     int32_t opt_config_first = 0;     // ... for a step whose walks start at the initial triangles
+    int32_t opt_strategy = 0;         // 0 = strategy (b), 1 = strategy (a) (T^0 never overwritten)
+    int32_t opt_outside = 0;          // 0 = clip feet that leave the square, 1 = exclude the node
     bool t0_initial = true;           // T^0 holds the initial start triangles
     int32_t sms = 0;                  // multiprocessors of the device
     bool stepped = false;
@@ -103,5 +105,6 @@ sl_status reorder_host(sl_mesh *m, int32_t curve, int32_t *node_perm, int32_t *t
 // device side (step.cu)
 sl_status upload(sl_mesh *m);
 void free_device(sl_mesh *m);
+sl_status reset_t0_sync(sl_mesh *m);
 int32_t default_walk_cap(const sl_mesh *m);
 }  // namespace sl

@@ -23,7 +23,7 @@ struct ProbStep {
 };
 
 // Device status word bits and counters
-enum { kStatusWords = 4, kStatCounters = 8 };
+enum { kStatusWords = 4, kStatCounters = 9 };
 
 // f(x, t_{n+1}) at a node, in double precision, in the evaluation order of
 // the field definitions listed in sl.h.  Intrinsics with explicit rounding

@@ -175,7 +175,7 @@ __device__ __forceinline__ int random_negative_edge(int64_t i, uint32_t hops, in
 }
 
 struct NodeCounters {
-    uint32_t hops = 0, exact = 0, clipped = 0, fallback = 0, limit = 0, filter2 = 0;
+    uint32_t hops = 0, exact = 0, clipped = 0, fallback = 0, limit = 0, filter2 = 0, excluded = 0;
 };
 
 // Triangle of a half-edge code h = 3 t + k (h >= 0).
@@ -203,6 +203,22 @@ __device__ __forceinline__ void step_node(const FastArgs &a, int64_t i, int pi, 
     df X, Y;
     foot_df(P, a, i, x, y, X, Y);
     uint32_t flags = 0;
+    if (a.exclude && (df_neg_strict(X) || df_gt1(X) || df_neg_strict(Y) || df_gt1(Y))) {
+        // the paper's experiments exclude nodes whose foot leaves the domain
+        // (Sec. 4): V unchanged, no walk, T^0 unchanged
+        ((float2 *)a.vout)[i] = ((const float2 *)a.vin)[i];
+        c.excluded = 1;
+        if (kDebug) {
+            if (a.dbg.feet) {
+                a.dbg.feet[2 * i] = (double)X.h + (double)X.l;
+                a.dbg.feet[2 * i + 1] = (double)Y.h + (double)Y.l;
+            }
+            if (a.dbg.tri) a.dbg.tri[i] = -1;
+            if (a.dbg.moves) a.dbg.moves[i] = 0;
+            if (a.dbg.flags) a.dbg.flags[i] = (uint8_t)SL_NODE_EXCLUDED;
+        }
+        return;
+    }
     if (clip_df(x, y, X, Y)) {
         flags |= SL_NODE_CLIPPED;
         c.clipped = 1;
@@ -334,7 +350,7 @@ __device__ __forceinline__ void step_node(const FastArgs &a, int64_t i, int pi, 
     const df v1 = dfp(vin[w0]), v2 = dfp(vin[w1]), v3 = dfp(vin[w2]);
     const df v = df_add(v3, df_add(df_mul(th1, df_sub(v1, v3)), df_mul(th2, df_sub(v2, v3))));
     ((float2 *)a.vout)[i] = make_float2(v.h, v.l);
-    if (hops > 0) {
+    if (hops > 0 && !a.keep_t0) {
         a.t0[i] = j;
         a.t0v[i] = make_int4(3 * j, w0, w1, w2);
     }
@@ -359,7 +375,7 @@ __global__ void __launch_bounds__(kBlock, kMinBlocks) k_step_fast_df(FastArgs a)
     NodeCounters c;
     const int pi = block_problem(a.node_off, a.nprob, a.N, i);
     if (active) step_node<kDebug>(a, i, pi, c);
-    if (kStats) warp_stats(a.stats, active, c.hops, c.exact, c.clipped, c.fallback, c.limit, c.filter2);
+    if (kStats) warp_stats(a.stats, active, c.hops, c.exact, c.clipped, c.fallback, c.limit, c.filter2, c.excluded);
 }
 
 template <int kBlock, int kMinBlocks>

@@ -48,6 +48,8 @@ struct FastArgs {
     uint32_t *status;
     unsigned long long *stats;
     sl_debug dbg;
+    int32_t keep_t0;              // strategy (a): T^0 is never overwritten
+    int32_t exclude;              // nodes whose foot leaves the square are excluded (Sec. 4)
 };
 
 // config: launch configuration 0..kFastConfigs-1 (see step_fast.cu)

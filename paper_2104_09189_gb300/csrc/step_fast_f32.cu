@@ -97,6 +97,7 @@ __global__ void __launch_bounds__(kBlock, kMinBlocks) k_step_fast_f32(FastArgs a
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     const bool active = i < a.N;
     uint32_t hops = 0, exact_tests = 0, clipped_cnt = 0, fallback_cnt = 0, limit_cnt = 0, fp64_tests = 0;
+    uint32_t excluded_cnt = 0;
     const int pi = block_problem(a.node_off, a.nprob, a.N, i);
     if (active) {
         const FastProb &P = a.probs[pi];
@@ -104,7 +105,23 @@ __global__ void __launch_bounds__(kBlock, kMinBlocks) k_step_fast_f32(FastArgs a
         float X, Y;
         foot_f32(P, a, i, xf.x, xf.y, X, Y);
         uint32_t flags = 0;
-        if (!(X >= 0.0f && X <= 1.0f && Y >= 0.0f && Y <= 1.0f)) {
+        bool excluded = false;
+        if (!(X >= 0.0f && X <= 1.0f && Y >= 0.0f && Y <= 1.0f) && a.exclude) {
+            // the paper's experiments exclude nodes whose foot leaves the
+            // domain (Sec. 4): V unchanged, no walk, T^0 unchanged
+            ((float *)a.vout)[i] = ((const float *)a.vin)[i];
+            excluded_cnt = 1;
+            excluded = true;
+            if (kDebug) {
+                if (a.dbg.feet) {
+                    a.dbg.feet[2 * i] = (double)X;
+                    a.dbg.feet[2 * i + 1] = (double)Y;
+                }
+                if (a.dbg.tri) a.dbg.tri[i] = -1;
+                if (a.dbg.moves) a.dbg.moves[i] = 0;
+                if (a.dbg.flags) a.dbg.flags[i] = (uint8_t)SL_NODE_EXCLUDED;
+            }
+        } else if (!(X >= 0.0f && X <= 1.0f && Y >= 0.0f && Y <= 1.0f)) {
             // boundary clip in double, rounded back to float
             double cx, cy;
             clip_to_square((double)xf.x, (double)xf.y, (double)X, (double)Y, cx, cy);
@@ -113,193 +130,205 @@ __global__ void __launch_bounds__(kBlock, kMinBlocks) k_step_fast_f32(FastArgs a
             flags |= SL_NODE_CLIPPED;
             clipped_cnt = 1;
         }
-        const uint32_t fside = (X == 0.0f ? 1u : 0u) | (X == 1.0f ? 2u : 0u) | (Y == 0.0f ? 4u : 0u) |
-                               (Y == 1.0f ? 8u : 0u);
+        if (!excluded) {
+            const uint32_t fside = (X == 0.0f ? 1u : 0u) | (X == 1.0f ? 2u : 0u) | (Y == 0.0f ? 4u : 0u) |
+                                   (Y == 1.0f ? 8u : 0u);
 
-        // start state from the per-node cache (T^0 and its vertex ids)
-        const int4 tq = a.t0v[i];
-        int32_t e0 = tq.x, e1, e2;
-        {
-            const int32_t j0 = tri_of_f32(e0), s0 = e0 - 3 * j0;
-            e1 = 3 * j0 + (s0 == 2 ? 0 : s0 + 1);
-            e2 = 3 * j0 + (s0 == 0 ? 2 : s0 - 1);
-        }
-        float2 A = a.xyf[tq.y], B = a.xyf[tq.z], C = a.xyf[tq.w];
-        bool moved = false;
-        const uint32_t cap = (uint32_t)a.walk_cap;
-        bool found = false;
-        int s1 = 0, s2 = 0, s3 = 0;
-        float o1 = 0.0f, o2 = 0.0f, dn = 1.0f;
-        for (;;) {
-            const float ax = __fsub_rn(A.x, C.x), ay = __fsub_rn(A.y, C.y);
-            const float bx = __fsub_rn(B.x, C.x), by = __fsub_rn(B.y, C.y);
-            const float xx = __fsub_rn(X, C.x), xy = __fsub_rn(Y, C.y);
-            float eb1, eb2, ed;
-            o1 = cross_f32(xx, xy, bx, by, eb1);    // orient(W1, W2, X): theta of W0 * den
-            o2 = cross_f32(ax, ay, xx, xy, eb2);    // orient(W2, W0, X): theta of W1 * den
-            dn = cross_f32(ax, ay, bx, by, ed);     // orient(W0, W1, W2) > 0
-            float o3 = 1.0f;
-            s1 = o1 > eb1 ? 1 : (o1 < -eb1 ? -1 : 2);
-            s2 = o2 > eb2 ? 1 : (o2 < -eb2 ? -1 : 2);
-            s3 = 1;
-            if (!moved) {
-                o3 = __fsub_rn(__fsub_rn(dn, o1), o2);
-                const float eb3 = ed + eb1 + eb2 + 0x1p-23f * (fabsf(dn) + fabsf(o1) + fabsf(o2));
-                s3 = o3 > eb3 ? 1 : (o3 < -eb3 ? -1 : 2);
+            // start state from the per-node cache (T^0 and its vertex ids)
+            const int4 tq = a.t0v[i];
+            int32_t e0 = tq.x, e1, e2;
+            {
+                const int32_t j0 = tri_of_f32(e0), s0 = e0 - 3 * j0;
+                e1 = 3 * j0 + (s0 == 2 ? 0 : s0 + 1);
+                e2 = 3 * j0 + (s0 == 0 ? 2 : s0 - 1);
             }
-            if (s1 == 2 || s2 == 2 || s3 == 2) {
-                // boundary edge with the foot on its side: exactly 0 (the
-                // record of a boundary half-edge holds its side code)
-                if (s1 == 2) { const int nb = __float_as_int(a.he[e0].z); if (nb < 0 && (fside >> (-1 - nb) & 1u)) s1 = 0; }
-                if (s2 == 2) { const int nb = __float_as_int(a.he[e1].z); if (nb < 0 && (fside >> (-1 - nb) & 1u)) s2 = 0; }
-                if (s3 == 2) { const int nb = __float_as_int(a.he[e2].z); if (nb < 0 && (fside >> (-1 - nb) & 1u)) s3 = 0; }
-            }
-            if (s1 == 2 || s2 == 2 || s3 == 2) {
-                // the foot on a vertex (e.g. a node whose field vanishes): the
-                // two edges through that vertex have orientation exactly 0
-                const bool onA = X == A.x && Y == A.y, onB = X == B.x && Y == B.y, onC = X == C.x && Y == C.y;
-                if (s1 == 2 && (onB || onC)) s1 = 0;
-                if (s2 == 2 && (onC || onA)) s2 = 0;
-                if (s3 == 2 && (onA || onB)) s3 = 0;
-            }
-            if (s1 == 2 || s2 == 2 || s3 == 2) {
-                // double predicate on the floats promoted exactly (the
-                // barrier keeps the conversions of the loop-invariant foot
-                // inside this rare branch)
-                float xb = X, yb = Y;
-                asm volatile("" : "+f"(xb), "+f"(yb));
-                const double Xd = xb, Yd = yb;
-                if (s1 == 2) {
-                    slp::OrientResult r = slp::orient(B.x, B.y, C.x, C.y, Xd, Yd);
-                    s1 = r.sign;
-                    fp64_tests += r.stage == 1;
-                    exact_tests += r.stage == 2;
-                }
-                if (s2 == 2) {
-                    slp::OrientResult r = slp::orient(C.x, C.y, A.x, A.y, Xd, Yd);
-                    s2 = r.sign;
-                    fp64_tests += r.stage == 1;
-                    exact_tests += r.stage == 2;
-                }
-                if (s3 == 2) {
-                    slp::OrientResult r = slp::orient(A.x, A.y, B.x, B.y, Xd, Yd);
-                    s3 = r.sign;
-                    fp64_tests += r.stage == 1;
-                    exact_tests += r.stage == 2;
-                }
-                flags |= SL_NODE_EXACT;
-            }
-            if (s1 >= 0 && s2 >= 0 && s3 >= 0) {
-                found = true;
-                break;
-            }
-            if (hops >= 2 * cap) break;
-            int k;
-            if (hops < cap) {
-                // the paper's rule: the most negative barycentric coordinate
-                k = -1;
-                float best = 0.0f;
-                if (s1 < 0) { k = 0; best = o1; }
-                if (s2 < 0 && (k < 0 || o2 < best)) { k = 1; best = o2; }
-                if (s3 < 0 && (k < 0 || o3 < best)) { k = 2; best = o3; }
-            } else {
-                if (hops == cap) {
-                    fallback_cnt = 1;
-                    flags |= SL_NODE_FALLBACK;
-                }
-                const int neg[3] = {s1 < 0, s2 < 0, s3 < 0};
-                const int nneg = neg[0] + neg[1] + neg[2];
-                int pick = (int)(mix64_dev(((uint64_t)i << 20) ^ (uint64_t)hops) % (uint64_t)nneg);
-                k = -1;
-                for (int q = 0; q < 3; ++q)
-                    if (neg[q] && pick-- == 0) k = q;
-            }
-            const float4 R = a.he[k == 0 ? e0 : (k == 1 ? e1 : e2)];
-            if (__float_as_int(R.z) < 0) break;    // a boundary edge: not for a foot inside a valid mesh
-            // the next triangle: (W2, W1, Q), (W0, W2, Q) or (W1, W0, Q)
-            if (k == 0) A = C;
-            else if (k == 1) B = C;
-            else {
-                const float2 t = A;
-                A = B;
-                B = t;
-            }
-            C = make_float2(R.x, R.y);
-            e0 = __float_as_int(R.z);
-            e1 = __float_as_int(R.w);
-            moved = true;
-            ++hops;
-            // lean hops: the two exits of the entered triangle, taken while
-            // one is certainly negative (the same stage-A bound); the full
-            // test above decides where no edge is certainly negative
-            while (hops < cap) {
+            float2 A = a.xyf[tq.y], B = a.xyf[tq.z], C = a.xyf[tq.w];
+            bool moved = false;
+            const uint32_t cap = (uint32_t)a.walk_cap;
+            bool found = false;
+            int s1 = 0, s2 = 0, s3 = 0;
+            float o1 = 0.0f, o2 = 0.0f, dn = 1.0f;
+            for (;;) {
                 const float ax = __fsub_rn(A.x, C.x), ay = __fsub_rn(A.y, C.y);
                 const float bx = __fsub_rn(B.x, C.x), by = __fsub_rn(B.y, C.y);
                 const float xx = __fsub_rn(X, C.x), xy = __fsub_rn(Y, C.y);
-                float eb1, eb2;
-                const float q1 = cross_f32(xx, xy, bx, by, eb1);
-                const float q2 = cross_f32(ax, ay, xx, xy, eb2);
-                const bool c1 = q1 < -eb1, c2 = q2 < -eb2 && !(c1 && q1 <= q2);
-                if (!(c1 || c2)) break;
-                const float4 Q = a.he[c2 ? e1 : e0];
-                if (__float_as_int(Q.z) < 0) break;    // a boundary edge: not for a foot inside a valid mesh
-                if (c2) B = C;
-                else A = C;
-                C = make_float2(Q.x, Q.y);
-                e0 = __float_as_int(Q.z);
-                e1 = __float_as_int(Q.w);
+                float eb1, eb2, ed;
+                o1 = cross_f32(xx, xy, bx, by, eb1);    // orient(W1, W2, X): theta of W0 * den
+                o2 = cross_f32(ax, ay, xx, xy, eb2);    // orient(W2, W0, X): theta of W1 * den
+                dn = cross_f32(ax, ay, bx, by, ed);     // orient(W0, W1, W2) > 0
+                float o3 = 1.0f;
+                s1 = o1 > eb1 ? 1 : (o1 < -eb1 ? -1 : 2);
+                s2 = o2 > eb2 ? 1 : (o2 < -eb2 ? -1 : 2);
+                s3 = 1;
+                if (!moved) {
+                    o3 = __fsub_rn(__fsub_rn(dn, o1), o2);
+                    const float eb3 = ed + eb1 + eb2 + 0x1p-23f * (fabsf(dn) + fabsf(o1) + fabsf(o2));
+                    s3 = o3 > eb3 ? 1 : (o3 < -eb3 ? -1 : 2);
+                }
+                if (s1 == 2 || s2 == 2 || s3 == 2) {
+                    // boundary edge with the foot on its side: exactly 0 (the
+                    // record of a boundary half-edge holds its side code)
+                    if (s1 == 2) {
+                        const int nb = __float_as_int(a.he[e0].z);
+                        if (nb < 0 && (fside >> (-1 - nb) & 1u)) s1 = 0;
+                    }
+                    if (s2 == 2) {
+                        const int nb = __float_as_int(a.he[e1].z);
+                        if (nb < 0 && (fside >> (-1 - nb) & 1u)) s2 = 0;
+                    }
+                    if (s3 == 2) {
+                        const int nb = __float_as_int(a.he[e2].z);
+                        if (nb < 0 && (fside >> (-1 - nb) & 1u)) s3 = 0;
+                    }
+                }
+                if (s1 == 2 || s2 == 2 || s3 == 2) {
+                    // the foot on a vertex (e.g. a node whose field vanishes): the
+                    // two edges through that vertex have orientation exactly 0
+                    const bool onA = X == A.x && Y == A.y, onB = X == B.x && Y == B.y, onC = X == C.x && Y == C.y;
+                    if (s1 == 2 && (onB || onC)) s1 = 0;
+                    if (s2 == 2 && (onC || onA)) s2 = 0;
+                    if (s3 == 2 && (onA || onB)) s3 = 0;
+                }
+                if (s1 == 2 || s2 == 2 || s3 == 2) {
+                    // double predicate on the floats promoted exactly (the
+                    // barrier keeps the conversions of the loop-invariant foot
+                    // inside this rare branch)
+                    float xb = X, yb = Y;
+                    asm volatile("" : "+f"(xb), "+f"(yb));
+                    const double Xd = xb, Yd = yb;
+                    if (s1 == 2) {
+                        slp::OrientResult r = slp::orient(B.x, B.y, C.x, C.y, Xd, Yd);
+                        s1 = r.sign;
+                        fp64_tests += r.stage == 1;
+                        exact_tests += r.stage == 2;
+                    }
+                    if (s2 == 2) {
+                        slp::OrientResult r = slp::orient(C.x, C.y, A.x, A.y, Xd, Yd);
+                        s2 = r.sign;
+                        fp64_tests += r.stage == 1;
+                        exact_tests += r.stage == 2;
+                    }
+                    if (s3 == 2) {
+                        slp::OrientResult r = slp::orient(A.x, A.y, B.x, B.y, Xd, Yd);
+                        s3 = r.sign;
+                        fp64_tests += r.stage == 1;
+                        exact_tests += r.stage == 2;
+                    }
+                    flags |= SL_NODE_EXACT;
+                }
+                if (s1 >= 0 && s2 >= 0 && s3 >= 0) {
+                    found = true;
+                    break;
+                }
+                if (hops >= 2 * cap) break;
+                int k;
+                if (hops < cap) {
+                    // the paper's rule: the most negative barycentric coordinate
+                    k = -1;
+                    float best = 0.0f;
+                    if (s1 < 0) { k = 0; best = o1; }
+                    if (s2 < 0 && (k < 0 || o2 < best)) { k = 1; best = o2; }
+                    if (s3 < 0 && (k < 0 || o3 < best)) { k = 2; best = o3; }
+                } else {
+                    if (hops == cap) {
+                        fallback_cnt = 1;
+                        flags |= SL_NODE_FALLBACK;
+                    }
+                    const int neg[3] = {s1 < 0, s2 < 0, s3 < 0};
+                    const int nneg = neg[0] + neg[1] + neg[2];
+                    int pick = (int)(mix64_dev(((uint64_t)i << 20) ^ (uint64_t)hops) % (uint64_t)nneg);
+                    k = -1;
+                    for (int q = 0; q < 3; ++q)
+                        if (neg[q] && pick-- == 0) k = q;
+                }
+                const float4 R = a.he[k == 0 ? e0 : (k == 1 ? e1 : e2)];
+                if (__float_as_int(R.z) < 0) break;    // a boundary edge: not for a foot inside a valid mesh
+                // the next triangle: (W2, W1, Q), (W0, W2, Q) or (W1, W0, Q)
+                if (k == 0) A = C;
+                else if (k == 1) B = C;
+                else {
+                    const float2 t = A;
+                    A = B;
+                    B = t;
+                }
+                C = make_float2(R.x, R.y);
+                e0 = __float_as_int(R.z);
+                e1 = __float_as_int(R.w);
+                moved = true;
                 ++hops;
+                // lean hops: the two exits of the entered triangle, taken while
+                // one is certainly negative (the same stage-A bound); the full
+                // test above decides where no edge is certainly negative
+                while (hops < cap) {
+                    const float ax = __fsub_rn(A.x, C.x), ay = __fsub_rn(A.y, C.y);
+                    const float bx = __fsub_rn(B.x, C.x), by = __fsub_rn(B.y, C.y);
+                    const float xx = __fsub_rn(X, C.x), xy = __fsub_rn(Y, C.y);
+                    float eb1, eb2;
+                    const float q1 = cross_f32(xx, xy, bx, by, eb1);
+                    const float q2 = cross_f32(ax, ay, xx, xy, eb2);
+                    const bool c1 = q1 < -eb1, c2 = q2 < -eb2 && !(c1 && q1 <= q2);
+                    if (!(c1 || c2)) break;
+                    const float4 Q = a.he[c2 ? e1 : e0];
+                    if (__float_as_int(Q.z) < 0) break;    // a boundary edge: not for a foot inside a valid mesh
+                    if (c2) B = C;
+                    else A = C;
+                    C = make_float2(Q.x, Q.y);
+                    e0 = __float_as_int(Q.z);
+                    e1 = __float_as_int(Q.w);
+                    ++hops;
+                }
             }
-        }
-        if (!found) {
-            flags |= SL_NODE_WALK_LIMIT;
-            limit_cnt = 1;
-        }
-        if (s1 == 0 || s2 == 0 || s3 == 0) flags |= SL_NODE_DEGENERATE;
+            if (!found) {
+                flags |= SL_NODE_WALK_LIMIT;
+                limit_cnt = 1;
+            }
+            if (s1 == 0 || s2 == 0 || s3 == 0) flags |= SL_NODE_DEGENERATE;
 
-        // the located triangle in slot order: its vertex ids and the
-        // numerators of Eq. 6 relative to its vertex 2
-        int w0 = tq.y, w1 = tq.z, w2 = tq.w;
-        const int32_t j = tri_of_f32(e0);
-        if (moved) {
-            w0 = a.tv[0][j];
-            w1 = a.tv[1][j];
-            w2 = a.tv[2][j];
-            // (W0, W1, W2) = slots (s, s+1, s+2)
-            const int32_t s = e0 - 3 * j;
-            const float2 V0 = s == 0 ? A : (s == 1 ? C : B), V1 = s == 0 ? B : (s == 1 ? A : C);
-            const float2 V2 = s == 0 ? C : (s == 1 ? B : A);
-            const float ax = __fsub_rn(V0.x, V2.x), ay = __fsub_rn(V0.y, V2.y);
-            const float bx = __fsub_rn(V1.x, V2.x), by = __fsub_rn(V1.y, V2.y);
-            const float xx = __fsub_rn(X, V2.x), xy = __fsub_rn(Y, V2.y);
-            float eb;
-            o1 = cross_f32(xx, xy, bx, by, eb);
-            o2 = cross_f32(ax, ay, xx, xy, eb);
-            dn = cross_f32(ax, ay, bx, by, eb);
-        }
-        // theta of W0, W1 (Eq. 6) and the P1 value (Remark 1) in float
-        const float r = __frcp_rn(dn);
-        const float th1 = __fmul_rn(o1, r), th2 = __fmul_rn(o2, r);
-        const float *vin = (const float *)a.vin;
-        const float v1 = vin[w0], v2 = vin[w1], v3 = vin[w2];
-        const float v = __fmaf_rn(th1, __fsub_rn(v1, v3), __fmaf_rn(th2, __fsub_rn(v2, v3), v3));
-        ((float *)a.vout)[i] = v;
-        if (moved) {
-            a.t0[i] = j;
-            a.t0v[i] = make_int4(3 * j, w0, w1, w2);
-        }
-        if (limit_cnt) atomicOr(a.status, 1u << SL_E_WALK_LIMIT);
-        if (kDebug) {
-            if (a.dbg.feet) {
-                a.dbg.feet[2 * i] = (double)X;
-                a.dbg.feet[2 * i + 1] = (double)Y;
+            // the located triangle in slot order: its vertex ids and the
+            // numerators of Eq. 6 relative to its vertex 2
+            int w0 = tq.y, w1 = tq.z, w2 = tq.w;
+            const int32_t j = tri_of_f32(e0);
+            if (moved) {
+                w0 = a.tv[0][j];
+                w1 = a.tv[1][j];
+                w2 = a.tv[2][j];
+                // (W0, W1, W2) = slots (s, s+1, s+2)
+                const int32_t s = e0 - 3 * j;
+                const float2 V0 = s == 0 ? A : (s == 1 ? C : B), V1 = s == 0 ? B : (s == 1 ? A : C);
+                const float2 V2 = s == 0 ? C : (s == 1 ? B : A);
+                const float ax = __fsub_rn(V0.x, V2.x), ay = __fsub_rn(V0.y, V2.y);
+                const float bx = __fsub_rn(V1.x, V2.x), by = __fsub_rn(V1.y, V2.y);
+                const float xx = __fsub_rn(X, V2.x), xy = __fsub_rn(Y, V2.y);
+                float eb;
+                o1 = cross_f32(xx, xy, bx, by, eb);
+                o2 = cross_f32(ax, ay, xx, xy, eb);
+                dn = cross_f32(ax, ay, bx, by, eb);
             }
-            if (a.dbg.tri) a.dbg.tri[i] = j;
-            if (a.dbg.moves) a.dbg.moves[i] = (int32_t)hops;
-            if (a.dbg.flags) a.dbg.flags[i] = (uint8_t)flags;
+            // theta of W0, W1 (Eq. 6) and the P1 value (Remark 1) in float
+            const float r = __frcp_rn(dn);
+            const float th1 = __fmul_rn(o1, r), th2 = __fmul_rn(o2, r);
+            const float *vin = (const float *)a.vin;
+            const float v1 = vin[w0], v2 = vin[w1], v3 = vin[w2];
+            const float v = __fmaf_rn(th1, __fsub_rn(v1, v3), __fmaf_rn(th2, __fsub_rn(v2, v3), v3));
+            ((float *)a.vout)[i] = v;
+            if (moved && !a.keep_t0) {
+                a.t0[i] = j;
+                a.t0v[i] = make_int4(3 * j, w0, w1, w2);
+            }
+            if (limit_cnt) atomicOr(a.status, 1u << SL_E_WALK_LIMIT);
+            if (kDebug) {
+                if (a.dbg.feet) {
+                    a.dbg.feet[2 * i] = (double)X;
+                    a.dbg.feet[2 * i + 1] = (double)Y;
+                }
+                if (a.dbg.tri) a.dbg.tri[i] = j;
+                if (a.dbg.moves) a.dbg.moves[i] = (int32_t)hops;
+                if (a.dbg.flags) a.dbg.flags[i] = (uint8_t)flags;
+            }
         }
     }
-    if (kStats) warp_stats(a.stats, active, hops, exact_tests, clipped_cnt, fallback_cnt, limit_cnt, fp64_tests);
+    if (kStats)
+        warp_stats(a.stats, active, hops, exact_tests, clipped_cnt, fallback_cnt, limit_cnt, fp64_tests, excluded_cnt);
 }
 
 template <int kBlock, int kMinBlocks>

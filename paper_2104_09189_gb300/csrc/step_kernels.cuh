@@ -25,6 +25,8 @@ struct StepArgs {
     uint32_t *status;             // deferred status bits
     unsigned long long *stats;    // counters in sl_stats order
     sl_debug dbg;                 // optional per-node outputs (device pointers)
+    int32_t keep_t0;              // strategy (a): T^0 is never overwritten
+    int32_t exclude;              // nodes whose foot leaves the square are excluded (Sec. 4)
 };
 
 __device__ __forceinline__ uint64_t mix64_dev(uint64_t z)
@@ -37,7 +39,7 @@ __device__ __forceinline__ uint64_t mix64_dev(uint64_t z)
 // Warp-aggregated counters: one atomic per warp and counter.
 __device__ __forceinline__ void warp_stats(unsigned long long *stats, bool active, uint32_t hops,
                                            uint32_t exact_tests, uint32_t clipped, uint32_t fallback,
-                                           uint32_t limit, uint32_t filter2 = 0)
+                                           uint32_t limit, uint32_t filter2 = 0, uint32_t excluded = 0)
 {
     const unsigned full = 0xffffffffu;
     unsigned n = __reduce_add_sync(full, active ? 1u : 0u);
@@ -48,6 +50,7 @@ __device__ __forceinline__ void warp_stats(unsigned long long *stats, bool activ
     unsigned c = __reduce_add_sync(full, clipped);
     unsigned fb = __reduce_add_sync(full, fallback);
     unsigned l = __reduce_add_sync(full, limit);
+    unsigned x = __reduce_add_sync(full, excluded);
     if ((threadIdx.x & 31) == 0) {
         if (n) atomicAdd(&stats[0], (unsigned long long)n);
         if (h) atomicAdd(&stats[1], (unsigned long long)h);
@@ -57,6 +60,7 @@ __device__ __forceinline__ void warp_stats(unsigned long long *stats, bool activ
         if (c) atomicAdd(&stats[5], (unsigned long long)c);
         if (fb) atomicAdd(&stats[6], (unsigned long long)fb);
         if (l) atomicAdd(&stats[7], (unsigned long long)l);
+        if (x) atomicAdd(&stats[8], (unsigned long long)x);
     }
 }
 

@@ -20,16 +20,38 @@ __global__ void __launch_bounds__(256) k_step_plain_f64(StepArgs a)
 {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     bool active = i < a.N;
-    uint32_t hops = 0, exact_tests = 0, clipped_cnt = 0, fallback_cnt = 0, limit_cnt = 0;
+    uint32_t hops = 0, exact_tests = 0, clipped_cnt = 0, fallback_cnt = 0, limit_cnt = 0, excluded_cnt = 0;
+    const double *vin = (const double *)a.vin;
+    double X = 0.0, Y = 0.0;
+    bool clipped = false;
     if (active) {
         const int pi = a.nprob == 1 ? 0 : problem_of(a.node_off, a.nprob, i);
         const ProbStep &P = a.probs[pi];
-        const double2 *xy = (const double2 *)a.xy;
-        const double *vin = (const double *)a.vin;
-        const double2 xi = xy[i];
-        double fx, fy, X, Y;
+        const double2 xi = ((const double2 *)a.xy)[i];
+        double fx, fy;
         field_f64(P, xi.x, xi.y, fx, fy);
-        const bool clipped = foot_clip_f64(xi.x, xi.y, P.dt, fx, fy, X, Y);
+        const double qx = __dsub_rn(xi.x, __dmul_rn(P.dt, fx)), qy = __dsub_rn(xi.y, __dmul_rn(P.dt, fy));
+        if (a.exclude && !(qx >= 0.0 && qx <= 1.0 && qy >= 0.0 && qy <= 1.0)) {
+            // the paper's experiments exclude nodes whose foot leaves the
+            // domain (Sec. 4): V unchanged, no walk, T^0 unchanged
+            ((double *)a.vout)[i] = vin[i];
+            excluded_cnt = 1;
+            if (kDebug) {
+                if (a.dbg.feet) {
+                    a.dbg.feet[2 * i] = qx;
+                    a.dbg.feet[2 * i + 1] = qy;
+                }
+                if (a.dbg.tri) a.dbg.tri[i] = -1;
+                if (a.dbg.moves) a.dbg.moves[i] = 0;
+                if (a.dbg.flags) a.dbg.flags[i] = (uint8_t)SL_NODE_EXCLUDED;
+            }
+            active = false;
+        } else {
+            clipped = clip_to_square(xi.x, xi.y, qx, qy, X, Y);
+        }
+    }
+    if (active) {
+        const double2 *xy = (const double2 *)a.xy;
         uint32_t flags = clipped ? SL_NODE_CLIPPED : 0u;
         clipped_cnt = clipped;
 
@@ -104,8 +126,10 @@ __global__ void __launch_bounds__(256) k_step_plain_f64(StepArgs a)
         const int ia = a.tv[0][j], ib = a.tv[1][j], ic = a.tv[2][j];
         const double v = __dadd_rn(__dadd_rn(__dmul_rn(th1, vin[ia]), __dmul_rn(th2, vin[ib])), __dmul_rn(th3, vin[ic]));
         ((double *)a.vout)[i] = v;
-        a.t0[i] = j;
-        a.t0v[i] = make_int4(3 * j, ia, ib, ic);     // the start state of the fast kernels
+        if (!a.keep_t0) {
+            a.t0[i] = j;
+            a.t0v[i] = make_int4(3 * j, ia, ib, ic);     // the start state of the fast kernels
+        }
         if (limit_cnt) atomicOr(a.status, 1u << SL_E_WALK_LIMIT);
         if (flags & SL_NODE_RANGE) atomicOr(a.status, 1u << SL_E_ARG);
         if (kDebug) {
@@ -118,7 +142,8 @@ __global__ void __launch_bounds__(256) k_step_plain_f64(StepArgs a)
             if (a.dbg.flags) a.dbg.flags[i] = (uint8_t)flags;
         }
     }
-    if (kStats) warp_stats(a.stats, active, hops, exact_tests, clipped_cnt, fallback_cnt, limit_cnt);
+    if (kStats)
+        warp_stats(a.stats, i < a.N, hops, exact_tests, clipped_cnt, fallback_cnt, limit_cnt, 0, excluded_cnt);
 }
 
 void launch_plain_f64(const StepArgs &a, bool stats, bool debug, int block, cudaStream_t s)

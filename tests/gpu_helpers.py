@@ -66,7 +66,8 @@ class GpuRun:
         feet = np.empty((N, 2))
         feet[self.node_perm] = dbg["feet"].cpu().numpy().reshape(N, 2)
         tri = np.empty(N, dtype=np.int64)
-        tri[self.node_perm] = self.tri_perm[dbg["tri"].cpu().numpy()]
+        d = dbg["tri"].cpu().numpy()
+        tri[self.node_perm] = np.where(d < 0, -1, self.tri_perm[np.maximum(d, 0)])   # -1: excluded
         moves = np.empty(N, dtype=np.int64)
         moves[self.node_perm] = dbg["moves"].cpu().numpy()
         flags = np.empty(N, dtype=np.uint8)

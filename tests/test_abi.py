@@ -112,3 +112,30 @@ def test_bad_arguments():
     _expect(sl.SL_E_ARG, lambda: sl.sl_mesh_validate(np.array([1, m.n_nodes]), np.array([0, m.n_tri]), m.xy, m.tri))
     _expect(sl.SL_E_ARG, lambda: sl.sl_mesh_validate(np.array([0, m.n_nodes, 3]), np.array([0, m.n_tri, 2]),
                                                       m.xy, m.tri))
+
+
+def test_python_constants_match_the_header_enums():
+    # every "SL_NAME = value" enumerator of include/sl.h has the same value in
+    # the binding (options, node flags, field kinds, statuses, ...)
+    import re
+    hdr = open(os.path.join(ROOT, "include", "sl.h")).read()
+    hdr = re.sub(r"/\*.*?\*/", " ", hdr, flags=re.S)     # comments mention values too
+    pairs = re.findall(r"\b(SL_[A-Z0-9_]+)\s*=\s*(\d+)", hdr)
+    assert len(pairs) > 20
+    missing = []
+    for name, val in pairs:
+        if hasattr(sl, name):
+            assert getattr(sl, name) == int(val), name
+        else:
+            missing.append(name)
+    # field kinds live on the input side; everything else must be exported
+    assert all(n.startswith("SL_FIELD_") for n in missing), missing
+
+
+def test_stats_struct_matches_the_header():
+    import re
+    hdr = open(os.path.join(ROOT, "include", "sl.h")).read()
+    body = hdr[hdr.index("typedef struct {\n    uint64_t node_updates;"):]
+    body = body[:body.index("} sl_stats;")]
+    names = re.findall(r"uint64_t\s+(\w+);", body)
+    assert [n for n, _ in sl.sl_stats._fields_] == names

@@ -1,0 +1,154 @@
+"""GPU tests of the paper's experimental setup (Sec. 4): exclusion of the
+nodes whose foot leaves the domain, and the start strategies (a) and (b) of
+Sec. 3.  Results must not depend on the strategy: the walk locates the
+triangle that contains the foot whichever triangle it starts from."""
+import numpy as np
+import pytest
+
+import oracle
+import paper_2104_09189_gb300 as sl
+import sl_inputs as si
+from gpu_helpers import FOOT_DELTA, REL_TOL_FP64, GpuRun
+
+pytestmark = pytest.mark.gpu
+
+
+def _bump(xy):
+    return np.exp(-((xy[:, 0] - 0.45) ** 2 + (xy[:, 1] - 0.6) ** 2) / (2 * 0.12 ** 2))
+
+
+@pytest.mark.parametrize("kernel", [1, 2], ids=["plain", "fast"])
+def test_exclusion_matches_the_oracle(kernel):
+    m = si.grid_mesh(96, 0.25, 11)
+    f = si.paper_field(2 * np.pi, 2 * np.pi)
+    dt = 0.04
+    om = oracle.OracleMesh(m.xy, m.tri)
+    g = GpuRun(m, f, dt, curve=sl.SL_CURVE_HILBERT, kernel=kernel)
+    sl.sl_mesh_set_option(g.h, sl.SL_OPT_OUTSIDE, 1)
+    sl.sl_mesh_set_option(g.h, sl.SL_OPT_STATS, 1)
+    sl.sl_mesh_stats(g.h, reset=True)
+    vo = _bump(m.xy)
+    v = g.to_dev(vo)
+    n_out = 0
+    for n in range(4):
+        v_prev = g.from_dev(v)
+        v, res = g.step(n, v)
+        ov, otri, ofl, oft = om.step(f.kind, f.packed(), dt, n, vo, exclude=True)
+        out = (ofl & oracle.FLAG_EXCLUDED) != 0
+        gout = (res["flags"] & sl.SL_NODE_EXCLUDED) != 0
+        # no unclipped foot within rounding of the boundary, so the decisions agree exactly
+        margin = np.minimum(np.minimum(np.abs(oft[:, 0]), np.abs(oft[:, 0] - 1)),
+                            np.minimum(np.abs(oft[:, 1]), np.abs(oft[:, 1] - 1)))
+        assert margin.min() > 1e-12
+        assert np.array_equal(out, gout)
+        assert out.sum() > 0.02 * m.n_nodes
+        n_out += int(out.sum())
+        # excluded: V unchanged (bitwise in double; the fast kernel carries
+        # values as (hi, lo) float pairs, a 48-bit significand)
+        if kernel == 1:
+            assert np.array_equal(res["v"][out], v_prev[out])
+        else:
+            assert np.all(np.abs(res["v"][out] - v_prev[out]) <= 2.0 ** -46 * np.abs(v_prev[out]))
+        assert np.all(res["tri"][out] == -1)
+        keep = ~out
+        err = np.abs(res["v"][keep] - ov[keep]).max() / np.abs(ov).max()
+        assert err <= REL_TOL_FP64
+        safe = keep & (om.margins(np.where(keep, otri, 0).astype(np.int32), oft) > FOOT_DELTA)
+        assert np.array_equal(res["tri"][safe], otri[safe])
+        vo = ov
+    st = sl.sl_mesh_stats(g.h)
+    assert st["excluded"] == n_out
+    assert st["node_updates"] == 4 * m.n_nodes
+    g.close()
+
+
+@pytest.mark.parametrize("prec", [sl.SL_FP64, sl.SL_FP32], ids=["fp64", "fp32"])
+def test_strategy_a_locates_the_same_triangles_with_more_hops(prec):
+    # Courant 6.4: (a) walks ~ the whole characteristic every step, (b) only
+    # the foot's drift ~ L_t dt^2 / h (Sec. 4)
+    m = si.grid_mesh(128, 0.25, 12)
+    f = si.paper_field(2 * np.pi, 2 * np.pi)
+    dt = 0.05
+    runs = {}
+    for strategy in (0, 1):
+        g = GpuRun(m, f, dt, curve=sl.SL_CURVE_HILBERT, precision=prec)
+        sl.sl_mesh_set_option(g.h, sl.SL_OPT_STRATEGY, strategy)
+        t0_init = g.torch.empty(m.n_nodes, dtype=g.torch.int32, device=g.dev)
+        sl.sl_mesh_get_t0(g.h, t0_init)
+        v = g.to_dev(_bump(m.xy))
+        hist = []
+        for n in range(6):
+            v, res = g.step(n, v)
+            hist.append(res)
+        t0_end = g.torch.empty_like(t0_init)
+        sl.sl_mesh_get_t0(g.h, t0_end)
+        runs[strategy] = (hist, bool(g.torch.equal(t0_init, t0_end)))
+        g.close()
+    hb, b_kept = runs[0]
+    ha, a_kept = runs[1]
+    assert a_kept and not b_kept          # (a) never overwrites T^0 (Sec. 3); (b) does
+    for n, (rb, ra) in enumerate(zip(hb, ha)):
+        clean = ((rb["flags"] | ra["flags"]) & sl.SL_NODE_DEGENERATE) == 0
+        assert np.array_equal(rb["tri"][clean], ra["tri"][clean])
+        tol = REL_TOL_FP64 if prec == sl.SL_FP64 else 1e-6
+        assert np.abs(rb["v"] - ra["v"]).max() <= tol * np.abs(rb["v"]).max()
+        if n == 0:
+            # the first step: (a) and (b) coincide (Sec. 3)
+            assert np.array_equal(rb["moves"], ra["moves"])
+        else:
+            # later steps: (b) starts next to the foot, (a) at the node
+            assert ra["moves"].mean() > 1.5 * rb["moves"].mean()
+    # (a) walks the same path every step for a time-constant reach: step 1 vs
+    # step 2 hop counts differ only through the field's time dependence
+    assert ha[1]["moves"].mean() > 0.5 * ha[0]["moves"].mean()
+
+
+def test_strategy_option_resets_t0():
+    m = si.grid_mesh(48, 0.25, 13)
+    f = si.rotation_field()
+    g = GpuRun(m, f, 0.03)
+    t0_init = g.torch.empty(m.n_nodes, dtype=g.torch.int32, device=g.dev)
+    sl.sl_mesh_get_t0(g.h, t0_init)
+    v = g.to_dev(_bump(m.xy))
+    for n in range(2):
+        v, _ = g.step(n, v)
+    t0 = g.torch.empty_like(t0_init)
+    sl.sl_mesh_get_t0(g.h, t0)
+    assert not g.torch.equal(t0, t0_init)
+    sl.sl_mesh_set_option(g.h, sl.SL_OPT_STRATEGY, 1)
+    sl.sl_mesh_get_t0(g.h, t0)
+    assert g.torch.equal(t0, t0_init)
+    with pytest.raises(sl.SLError):
+        sl.sl_mesh_set_option(g.h, sl.SL_OPT_STRATEGY, 2)
+    with pytest.raises(sl.SLError):
+        sl.sl_mesh_set_option(g.h, sl.SL_OPT_OUTSIDE, 5)
+    g.close()
+
+
+def test_courant_study_shows_the_paper_trends():
+    """Sec. 4: hops of strategy (a) grow linearly with the Courant number,
+    those of (b) grow like L_t alpha^2 dx and stay below (a) while
+    L_t alpha dx < 1; a larger L_t costs (b) more hops."""
+    import json
+    import os
+    import subprocess
+    import sys
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    p = subprocess.run([sys.executable, os.path.join(root, "bench.py"), "--study", "courant", "--study-cells", "64"],
+                       capture_output=True, text=True, timeout=600, cwd=root)
+    assert p.returncode == 0, p.stderr[-2000:]
+    d = json.loads(p.stdout.strip().splitlines()[-1])
+
+    def hops(lt, strategy):
+        r = [x for x in d["rows"] if x["Lt"] == lt and x["strategy"] == strategy]
+        return np.array([x["alpha"] for x in r]), np.array([x["mean_hops"] for x in r])
+
+    al, a2 = hops("2pi", "a")
+    _, b2 = hops("2pi", "b")
+    _, b8 = hops("8pi", "b")
+    big = al >= 1
+    assert np.all(np.diff(a2[big]) > 0)
+    mid = (al >= 2) & (al <= 6)              # L_t alpha dx < 1 for L_t = 2 pi, dx = 1/64
+    assert np.all(b2[mid] < a2[mid])
+    assert b8[mid].mean() > b2[mid].mean()
+    assert all(0.0 <= x["excluded_fraction"] < 1.0 for x in d["rows"])

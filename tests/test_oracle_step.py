@@ -223,3 +223,51 @@ def test_fp32_feet_agree_with_double_feet(fld, dt):
         for i in np.nonzero(c32)[0]:
             X, Y = f32[i]
             assert X in (0.0, 1.0) or Y in (0.0, 1.0)
+
+
+def test_exclusion_keeps_the_value_of_nodes_whose_foot_leaves():
+    """Sec. 4 excludes the nodes whose Euler foot leaves the domain.  A
+    translation by (+0.25, 0) (f = (-0.25, 0), dt = 1) sends exactly the
+    nodes with x > 0.75 out: those keep V^n and are flagged, the others get
+    the clip-mode result bitwise (their feet are inside, so nothing else
+    changes)."""
+    m, om = _mesh()
+    p = np.zeros(48)
+    p[0] = -0.25
+    v0 = np.sin(3.0 * m.xy[:, 0]) + m.xy[:, 1] ** 2
+    vx, tri_x, fl_x, ft_x = om.step(si.FIELD_AFFINE, p, 1.0, 0, v0, exclude=True)
+    vc, tri_c, fl_c, _ = om.step(si.FIELD_AFFINE, p, 1.0, 0, v0)
+    x = m.xy[:, 0]
+    out = (fl_x & oracle.FLAG_EXCLUDED) != 0
+    assert np.all(out[x > 0.75 + 1e-12]) and not np.any(out[x < 0.75 - 1e-12])
+    assert 0.1 * m.n_nodes < out.sum() < 0.4 * m.n_nodes
+    assert np.array_equal(vx[out], v0[out])
+    assert np.all(tri_x[out] == -1)
+    # excluded feet are reported unclipped: outside the square, on the translated node
+    assert np.all(ft_x[out, 0] > 1.0) and np.allclose(ft_x[out, 0], x[out] + 0.25, atol=1e-15)
+    keep = ~out
+    assert np.array_equal(vx[keep], vc[keep]) and np.array_equal(tri_x[keep], tri_c[keep])
+    assert np.all((fl_c[keep] & oracle.FLAG_CLIPPED) == 0)
+
+
+def test_exclusion_of_the_paper_field_matches_the_unclipped_feet():
+    """The paper's rotating field (Sec. 4) with a large step: a node is
+    excluded exactly when its unclipped Euler foot (Eq. 4) lies outside the
+    square, and the exclusion does not depend on V."""
+    m, om = _mesh()
+    f = si.paper_field(2 * np.pi, 2 * np.pi)
+    dt = 0.05
+    v0 = np.cos(2.0 * m.xy[:, 0]) * m.xy[:, 1]
+    _, _, flags, feet = om.step(f.kind, f.packed(), dt, 2, v0, exclude=True)
+    t = 3 * dt
+    r = np.hypot(m.xy[:, 0] - 0.5, m.xy[:, 1] - 0.5)
+    qx = m.xy[:, 0] - dt * np.cos(2 * np.pi * r + 2 * np.pi * t)
+    qy = m.xy[:, 1] - dt * np.sin(2 * np.pi * r + 2 * np.pi * t)
+    margin = np.minimum(np.minimum(np.abs(qx), np.abs(qx - 1)), np.minimum(np.abs(qy), np.abs(qy - 1)))
+    outside = ~((qx >= 0) & (qx <= 1) & (qy >= 0) & (qy <= 1))
+    sure = margin > 1e-12
+    out = (flags & oracle.FLAG_EXCLUDED) != 0
+    assert out.sum() > 0
+    assert np.array_equal(out[sure], outside[sure])
+    _, _, flags2, _ = om.step(f.kind, f.packed(), dt, 2, 2.0 * v0 + 1.0, exclude=True)
+    assert np.array_equal(flags, flags2)
