@@ -303,7 +303,7 @@ __device__ __forceinline__ void step_node(const FastArgs &a, int64_t i, int pi, 
             }
             k = random_negative_edge(i, hops, s1, s2, s3);
         }
-        const float4 R = a.he[3 * j + k];
+        const float4 R = __ldg(&a.he[3 * j + k]);
         if (__float_as_int(R.z) < 0) break;    // a boundary edge: not for a foot inside a valid mesh
         // the next triangle: (W2, W1, Q), (W0, W2, Q) or (W1, W0, Q); the
         // high parts of the kept vertices are reloaded (L1 hits) rather than
@@ -326,7 +326,7 @@ __device__ __forceinline__ void step_node(const FastArgs &a, int64_t i, int pi, 
             const float e = hop_bound(S);
             const bool c1 = o1 < -e, c2 = o2 < -e && !(c1 && o1 <= o2);
             if (!(c1 || c2)) break;
-            const float4 Q = a.he[c2 ? e1 : e0];
+            const float4 Q = __ldg(&a.he[c2 ? e1 : e0]);
             if (__float_as_int(Q.z) < 0) break;    // a boundary edge (see above): certify instead
             if (c2) { p1x = p2x; p1y = p2y; }
             else { p0x = p2x; p0y = p2y; }

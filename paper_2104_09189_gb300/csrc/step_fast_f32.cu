@@ -169,15 +169,15 @@ __global__ void __launch_bounds__(kBlock, kMinBlocks) k_step_fast_f32(FastArgs a
                     // boundary edge with the foot on its side: exactly 0 (the
                     // record of a boundary half-edge holds its side code)
                     if (s1 == 2) {
-                        const int nb = __float_as_int(a.he[e0].z);
+                        const int nb = __float_as_int(__ldg(&a.he[e0]).z);
                         if (nb < 0 && (fside >> (-1 - nb) & 1u)) s1 = 0;
                     }
                     if (s2 == 2) {
-                        const int nb = __float_as_int(a.he[e1].z);
+                        const int nb = __float_as_int(__ldg(&a.he[e1]).z);
                         if (nb < 0 && (fside >> (-1 - nb) & 1u)) s2 = 0;
                     }
                     if (s3 == 2) {
-                        const int nb = __float_as_int(a.he[e2].z);
+                        const int nb = __float_as_int(__ldg(&a.he[e2]).z);
                         if (nb < 0 && (fside >> (-1 - nb) & 1u)) s3 = 0;
                     }
                 }
@@ -241,7 +241,7 @@ __global__ void __launch_bounds__(kBlock, kMinBlocks) k_step_fast_f32(FastArgs a
                     for (int q = 0; q < 3; ++q)
                         if (neg[q] && pick-- == 0) k = q;
                 }
-                const float4 R = a.he[k == 0 ? e0 : (k == 1 ? e1 : e2)];
+                const float4 R = __ldg(&a.he[k == 0 ? e0 : (k == 1 ? e1 : e2)]);
                 if (__float_as_int(R.z) < 0) break;    // a boundary edge: not for a foot inside a valid mesh
                 // the next triangle: (W2, W1, Q), (W0, W2, Q) or (W1, W0, Q)
                 if (k == 0) A = C;
@@ -268,7 +268,7 @@ __global__ void __launch_bounds__(kBlock, kMinBlocks) k_step_fast_f32(FastArgs a
                     const float q2 = cross_f32(ax, ay, xx, xy, eb2);
                     const bool c1 = q1 < -eb1, c2 = q2 < -eb2 && !(c1 && q1 <= q2);
                     if (!(c1 || c2)) break;
-                    const float4 Q = a.he[c2 ? e1 : e0];
+                    const float4 Q = __ldg(&a.he[c2 ? e1 : e0]);
                     if (__float_as_int(Q.z) < 0) break;    // a boundary edge: not for a foot inside a valid mesh
                     if (c2) B = C;
                     else A = C;
