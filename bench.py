@@ -54,9 +54,11 @@ def parse():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-plain", action="store_true", help="skip the plain FP64 kernel comparison")
-    ap.add_argument("--study", choices=["courant"], default=None,
-                    help="the paper's walk study (Sec. 4): mean hops per node-update and time per step "
-                         "against the Courant number for each start strategy; prints one JSON line")
+    ap.add_argument("--study", choices=["courant", "structured"], default=None,
+                    help="the paper's studies (Sec. 4), one JSON line: 'courant' = mean hops per "
+                         "node-update and time per step against the Courant number for strategies (a) "
+                         "and (b); 'structured' = walk (b) against the direct location on the "
+                         "structured Courant grid at alpha = 5, N = 1e6..8e6")
     ap.add_argument("--study-cells", type=int, default=386,
                     help="cells per side of the study mesh (386: 1.5e5 nodes, the paper's size)")
     return ap.parse_args()
@@ -325,10 +327,82 @@ def run_study(args):
                       "outside": "excluded", "precision": "fp64 (double-float kernel)", "rows": rows}), flush=True)
 
 
+def _timed_run(sl, torch, h, probs, S, v, v0, w):
+    """One S-step run (graph) for the statistics, then the same run timed
+    with CUDA events.  Returns (ms, stats of the first run)."""
+    stream = torch.cuda.current_stream()
+    sl.sl_mesh_stats(h, reset=True)
+    sl.sl_mesh_reset_t0(h)
+    v.copy_(v0)
+    sl.sl_run(h, probs, 0, S, v, w, use_graph=True)
+    st = sl.sl_mesh_stats(h, reset=True)
+    sl.sl_mesh_reset_t0(h)
+    v.copy_(v0)
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    sl.sl_run(h, probs, 0, S, v, w, use_graph=True)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1), st
+
+
+def run_study_structured(args):
+    """Comparison with a structured grid (Sec. 4): on the Courant grid of M x M
+    cells the foot's triangle has a direct formula; the paper times it against
+    the walk (b) at L_x = L_t = 2 pi, alpha = 5, N from 1e6 to 8e6, location
+    plus barycentric coordinates included.  Here each arm is the full step
+    (foot, location, P1) with feet outside excluded: walk (b) on a jittered
+    mesh of the same size, walk (b) on the Courant grid, and the direct
+    location on the Courant grid (strategy 2, a certified walk from the
+    formula's triangle)."""
+    import torch
+    import paper_2104_09189_gb300 as sl
+    rank, world, local = dist_env()
+    if rank != 0:
+        return
+    torch.cuda.set_device(local)
+    f = si.paper_field(2 * np.pi, 2 * np.pi)
+    rows = []
+    for M in (1000, 1414, 2000, 2828):
+        dt = 5.0 / M
+        S = int(np.ceil(1.0 / dt))
+        probs = sl.problems([(f.kind, dt, f.packed())])
+        for mesh_name, mesh in (("jittered", si.grid_mesh(M, 0.25, 17)), ("courant", si.courant_grid(M))):
+            no, to, xy, tri = sl.pack_meshes([(mesh.xy, mesh.tri)])
+            h = sl.sl_mesh_create(no, to, xy, tri, precision=sl.SL_FP64, seed=17)
+            node_perm, _ = sl.sl_mesh_reorder(h, sl.SL_CURVE_HILBERT)
+            sl.sl_mesh_set_option(h, sl.SL_OPT_OUTSIDE, 1)
+            sl.sl_mesh_set_option(h, sl.SL_OPT_STATS, 1)
+            v0 = torch.tensor(si.cosine_bump(mesh.xy, 0.5, 0.75, 0.15)[node_perm], dtype=torch.float64,
+                              device="cuda")
+            v = v0.clone()
+            w = torch.empty_like(v)
+            arms = [("walk_b", 0)] + ([("direct", 2)] if mesh_name == "courant" else [])
+            for arm, strategy in arms:
+                sl.sl_mesh_set_option(h, sl.SL_OPT_STRATEGY, strategy)
+                ms, st = _timed_run(sl, torch, h, probs, S, v, v0, w)
+                located = st["node_updates"] - st["excluded"]
+                rows.append({"cells": M, "nodes": mesh.n_nodes, "mesh": mesh_name, "location": arm, "steps": S,
+                             "mean_hops": st["walk_moves"] / max(1, located),
+                             "excluded_fraction": st["excluded"] / max(1, st["node_updates"]),
+                             "ms_per_step": ms / S, "ns_per_located_node_update": 1e6 * ms / max(1, located)})
+            sl.sl_mesh_destroy(h)
+            del v, w, v0
+            torch.cuda.empty_cache()
+    print(json.dumps({"study": "structured", "source": "Sec. 4, comparison with a structured grid",
+                      "field": "paper (cos(C0|x-c|+C1 t), sin(...)), C0 = C1 = 2 pi, c = (0.5, 0.5)",
+                      "alpha": 5, "outside": "excluded", "precision": "fp64 (double-float kernel)",
+                      "rows": rows}), flush=True)
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         return run_reference(args)
+    if args.study == "structured":
+        return run_study_structured(args)
     if args.study:
         return run_study(args)
     import torch

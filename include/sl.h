@@ -133,8 +133,13 @@ typedef enum {
                                 sl_mesh_reset_t0): long walks favour fewer resident warps (default 0) */
     SL_OPT_STRATEGY = 8,     /* start triangle of the walks (Sec. 3): 0 = strategy (b), the triangle
                                 found at the previous step (default); 1 = strategy (a), the node's own
-                                incident triangle at every step (T^0 is never overwritten).  Setting
-                                it resets T^0 to the initial incident triangles (synchronises). */
+                                incident triangle at every step (T^0 is never overwritten); 2 = the
+                                direct location of Sec. 4 on a structured Courant grid (one problem
+                                of M x M cells, each split along its (l,m)-(l+1,m+1) diagonal, any
+                                numbering; SL_E_ARG for other meshes): the walk starts at the triangle
+                                the formula gives for the foot and corrects it if rounding put the
+                                guess next door.  Setting it resets T^0 to the initial incident
+                                triangles (synchronises). */
     SL_OPT_OUTSIDE = 9       /* feet that leave the square: 0 = clip them to the boundary (default);
                                 1 = exclude the node, as the paper's experiments do (Sec. 4):
                                 V^{n+1}_i = V^n_i, flag SL_NODE_EXCLUDED */

@@ -40,7 +40,7 @@ void free_device(sl_mesh *m)
 {
     DeviceMesh &d = m->d;
     void *ptrs[] = {d.xy, d.tv[0], d.tv[1], d.tv[2], d.tn[0], d.tn[1], d.tn[2], d.t0, d.t0_init, d.t0v, d.node_off,
-                    d.status, d.stats, d.probs, d.fprobs, d.xyq, d.xyh, d.g1, d.g2, d.tparams, d.dfa, d.dfb, d.he,
+                    d.status, d.stats, d.probs, d.fprobs, d.xyq, d.xyh, d.g1, d.g2, d.tparams, d.dfa, d.dfb, d.he, d.grid_t0v,
                     m->host_v, m->host_v2};
     for (void *p : ptrs)
         if (p) cudaFree(p);
@@ -201,8 +201,10 @@ static StepArgs make_args(const sl_mesh *m, const ProbStep *probs_dev, const voi
     a.status = m->d.status;
     a.stats = m->d.stats;
     if (dbg) a.dbg = *dbg;
-    a.keep_t0 = m->opt_strategy == 1;
+    a.keep_t0 = m->opt_strategy != 0;
     a.exclude = m->opt_outside == 1;
+    a.grid_M = m->opt_strategy == 2 ? m->grid_M : 0;
+    a.grid_t0v = (const int4 *)m->d.grid_t0v;
     return a;
 }
 
@@ -233,8 +235,10 @@ static FastArgs make_fast_args(const sl_mesh *m, const FastProb *fp, const void 
     a.status = m->d.status;
     a.stats = m->d.stats;
     if (dbg) a.dbg = *dbg;
-    a.keep_t0 = m->opt_strategy == 1;
+    a.keep_t0 = m->opt_strategy != 0;
     a.exclude = m->opt_outside == 1;
+    a.grid_M = m->opt_strategy == 2 ? m->grid_M : 0;
+    a.grid_t0v = (const int4 *)m->d.grid_t0v;
     return a;
 }
 
@@ -622,6 +626,24 @@ extern "C" sl_status sl_mesh_reset_t0(sl_mesh *m, void *stream)
     return SL_OK;
 }
 
+// Start states of the structured-grid triangles (direct location, Sec. 4):
+// slot 2 (M m + l) + (lower ? 1 : 0) -> (3 t, T[0][t], T[1][t], T[2][t]).
+sl_status sl::upload_grid_table(sl_mesh *m, const std::vector<int32_t> &slot_tri)
+{
+    SL_CUDA(cudaSetDevice(m->device));
+    std::vector<int4> h(slot_tri.size());
+    for (size_t k = 0; k < slot_tri.size(); ++k) {
+        const int32_t t = slot_tri[k];
+        h[k] = make_int4(3 * t, m->tri[3 * (size_t)t], m->tri[3 * (size_t)t + 1], m->tri[3 * (size_t)t + 2]);
+    }
+    if (m->d.grid_t0v) cudaFree(m->d.grid_t0v);
+    m->d.grid_t0v = nullptr;
+    SL_CUDA(cudaMalloc(&m->d.grid_t0v, sizeof(int4) * h.size()));
+    SL_CUDA(cudaMemcpy(m->d.grid_t0v, h.data(), sizeof(int4) * h.size(), cudaMemcpyHostToDevice));
+    m->graph.valid = false;
+    return SL_OK;
+}
+
 // T^0 back to the initial incident triangles, synchronously (option changes).
 sl_status sl::reset_t0_sync(sl_mesh *m)
 {
@@ -677,7 +699,10 @@ extern "C" sl_status sl_mesh_reorder(sl_mesh *m, int32_t curve, int32_t *node_pe
     if (st != SL_OK) return st;
     if (m->graph.exec) cudaGraphExecDestroy((cudaGraphExec_t)m->graph.exec);
     m->graph = GraphCache();
-    return upload_arrays(m);
+    st = upload_arrays(m);
+    // the structured-grid table follows the triangle numbering
+    if (st == SL_OK && m->opt_strategy == 2) st = sl_mesh_set_option(m, SL_OPT_STRATEGY, 2);
+    return st;
 }
 
 extern "C" void sl_mesh_destroy(sl_mesh *m)

@@ -384,6 +384,49 @@ extern "C" sl_status sl_mesh_export(const sl_mesh *m, double *xy, int32_t *tri, 
     return SL_OK;
 }
 
+// The structured Courant grid of Sec. 4: one problem of M x M square cells
+// of [0,1]^2, each split into its upper triangle (l,m), (l+1,m+1), (l,m+1)
+// and its lower triangle (l,m), (l+1,m), (l+1,m+1).  Fills slot_tri[2 (M m +
+// l) + (upper ? 0 : 1)] with the current index of that triangle, identifying
+// every triangle by its vertices (any numbering), or fails.
+static sl_status courant_slots(const sl_mesh *m, int32_t &M, std::vector<int32_t> &slot_tri)
+{
+    if (m->n_problems != 1) return sl::fail(SL_E_ARG, "direct location needs a single-problem mesh");
+    M = m->cells.empty() ? 0 : m->cells[0];
+    if (M < 1 || m->Nt != 2 * (int64_t)M * M || m->N != (int64_t)(M + 1) * (M + 1))
+        return sl::fail(SL_E_ARG, "direct location: the mesh is not a structured Courant grid (sizes)");
+    slot_tri.assign((size_t)2 * M * M, -1);
+    auto grid = [&](int32_t v, int64_t &gi, int64_t &gj) {
+        const double gx = m->xy[2 * (size_t)v] * M, gy = m->xy[2 * (size_t)v + 1] * M;
+        gi = std::llround(gx);
+        gj = std::llround(gy);
+        return std::fabs(gx - (double)gi) <= 1e-3 && std::fabs(gy - (double)gj) <= 1e-3;   // float-rounded meshes too
+    };
+    for (int64_t t = 0; t < m->Nt; ++t) {
+        int64_t gi[3], gj[3];
+        for (int k = 0; k < 3; ++k)
+            if (!grid(m->tri[3 * t + k], gi[k], gj[k]))
+                return sl::fail(SL_E_ARG, "direct location: a node is not a grid point");
+        const int64_t l = std::min(std::min(gi[0], gi[1]), gi[2]), mm = std::min(std::min(gj[0], gj[1]), gj[2]);
+        if (l < 0 || mm < 0 || l >= M || mm >= M) return sl::fail(SL_E_ARG, "direct location: bad cell");
+        // upper: the corner (l+1, m) is missing; lower: the corner (l, m+1)
+        bool has10 = false, has01 = false, has00 = false, has11 = false;
+        for (int k = 0; k < 3; ++k) {
+            const int64_t di = gi[k] - l, dj = gj[k] - mm;
+            has00 |= di == 0 && dj == 0;
+            has11 |= di == 1 && dj == 1;
+            has10 |= di == 1 && dj == 0;
+            has01 |= di == 0 && dj == 1;
+        }
+        if (!(has00 && has11 && (has10 != has01)))
+            return sl::fail(SL_E_ARG, "direct location: a triangle is not half of a grid cell split along (l,m)-(l+1,m+1)");
+        const size_t slot = 2 * (size_t)(M * mm + l) + (has01 ? 0 : 1);
+        if (slot_tri[slot] >= 0) return sl::fail(SL_E_ARG, "direct location: two triangles in one half cell");
+        slot_tri[slot] = (int32_t)t;
+    }
+    return SL_OK;
+}
+
 extern "C" sl_status sl_mesh_set_option(sl_mesh *m, int32_t option, int64_t value)
 {
     if (!m) return sl::fail(SL_E_ARG, "sl_mesh_set_option: mesh is NULL");
@@ -414,7 +457,15 @@ extern "C" sl_status sl_mesh_set_option(sl_mesh *m, int32_t option, int64_t valu
         m->opt_config_first = (int32_t)value;
         break;
     case SL_OPT_STRATEGY: {
-        if (value != 0 && value != 1) return sl::fail(SL_E_ARG, "strategy must be 0 (b) or 1 (a)");
+        if (value < 0 || value > 2) return sl::fail(SL_E_ARG, "strategy must be 0 (b), 1 (a) or 2 (direct)");
+        if (value == 2) {
+            int32_t M = 0;
+            std::vector<int32_t> slots;
+            sl_status st = courant_slots(m, M, slots);
+            if (st == SL_OK) st = sl::upload_grid_table(m, slots);
+            if (st != SL_OK) return st;
+            m->grid_M = M;
+        }
         m->opt_strategy = (int32_t)value;
         sl_status st = sl::reset_t0_sync(m);
         if (st != SL_OK) return st;

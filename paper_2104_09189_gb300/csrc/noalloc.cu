@@ -206,8 +206,10 @@ extern "C" sl_status sl_step_noalloc(sl_mesh *m, const sl_problem *probs, int64_
     a.N = m->N;
     a.status = m->d.status;
     a.stats = m->d.stats;
-    a.keep_t0 = m->opt_strategy == 1;
+    a.keep_t0 = m->opt_strategy != 0;
     a.exclude = m->opt_outside == 1;
+    a.grid_M = m->opt_strategy == 2 ? m->grid_M : 0;
+    a.grid_t0v = (const int4 *)m->d.grid_t0v;
     launch_fast_df(a, m->opt_stats != 0, false, m->opt_config, s);
     launch_from_df(sc.values, v_out, m->N, s);
     e = cudaGetLastError();

@@ -223,9 +223,10 @@ __device__ __forceinline__ void step_node(const FastArgs &a, int64_t i, int pi, 
         flags |= SL_NODE_CLIPPED;
         c.clipped = 1;
     }
-    // start triangle and its vertex ids from the per-node cache: one
-    // coalesced 16-byte load
-    const int4 tq = a.t0v[i];
+    // start triangle and its vertex ids from the per-node cache (one
+    // coalesced 16-byte load), or from the direct location on a structured
+    // grid
+    const int4 tq = a.grid_M > 0 ? __ldg(&a.grid_t0v[grid_slot(X.h, Y.h, a.grid_M)]) : a.t0v[i];
     int32_t e0 = tq.x, e1 = 0;
     int32_t j = 0;
     int w0 = tq.y, w1 = tq.z, w2 = tq.w;

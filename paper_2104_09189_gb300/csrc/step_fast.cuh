@@ -48,8 +48,10 @@ struct FastArgs {
     uint32_t *status;
     unsigned long long *stats;
     sl_debug dbg;
-    int32_t keep_t0;              // strategy (a): T^0 is never overwritten
+    int32_t keep_t0;              // strategy (a) or direct location: T^0 is never overwritten
     int32_t exclude;              // nodes whose foot leaves the square are excluded (Sec. 4)
+    int32_t grid_M;               // > 0: start at the direct location on the structured grid (Sec. 4)
+    const int4 *grid_t0v;         // start state of structured triangle 2 (M m + l) + (lower ? 1 : 0)
 };
 
 // config: launch configuration 0..kFastConfigs-1 (see step_fast.cu)

@@ -135,7 +135,7 @@ __global__ void __launch_bounds__(kBlock, kMinBlocks) k_step_fast_f32(FastArgs a
                                    (Y == 1.0f ? 8u : 0u);
 
             // start state from the per-node cache (T^0 and its vertex ids)
-            const int4 tq = a.t0v[i];
+            const int4 tq = a.grid_M > 0 ? __ldg(&a.grid_t0v[grid_slot(X, Y, a.grid_M)]) : a.t0v[i];
             int32_t e0 = tq.x, e1, e2;
             {
                 const int32_t j0 = tri_of_f32(e0), s0 = e0 - 3 * j0;

@@ -25,8 +25,10 @@ struct StepArgs {
     uint32_t *status;             // deferred status bits
     unsigned long long *stats;    // counters in sl_stats order
     sl_debug dbg;                 // optional per-node outputs (device pointers)
-    int32_t keep_t0;              // strategy (a): T^0 is never overwritten
+    int32_t keep_t0;              // strategy (a) or direct location: T^0 is never overwritten
     int32_t exclude;              // nodes whose foot leaves the square are excluded (Sec. 4)
+    int32_t grid_M;               // > 0: start at the direct location on the structured grid (Sec. 4)
+    const int4 *grid_t0v;         // start state of structured triangle 2 (M m + l) + (lower ? 1 : 0)
 };
 
 __device__ __forceinline__ uint64_t mix64_dev(uint64_t z)
@@ -62,6 +64,17 @@ __device__ __forceinline__ void warp_stats(unsigned long long *stats, bool activ
         if (l) atomicAdd(&stats[7], (unsigned long long)l);
         if (x) atomicAdd(&stats[8], (unsigned long long)x);
     }
+}
+
+// The triangle of the structured Courant grid (M cells per side of [0,1]^2)
+// that the paper's direct formula (Sec. 4) gives for the point (x, y):
+// cell (l, m) = (floor(x M), floor(y M)) clamped to the grid, upper triangle
+// when x M - l < y M - m.  Returns the slot 2 (M m + l) + (upper ? 0 : 1).
+__device__ __forceinline__ int grid_slot(float x, float y, int M)
+{
+    const float gx = x * (float)M, gy = y * (float)M;
+    const int l = min(max((int)floorf(gx), 0), M - 1), m = min(max((int)floorf(gy), 0), M - 1);
+    return 2 * (M * m + l) + (gx - (float)l < gy - (float)m ? 0 : 1);
 }
 
 void launch_plain_f64(const StepArgs &a, bool stats, bool debug, int block, cudaStream_t s);

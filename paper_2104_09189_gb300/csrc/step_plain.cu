@@ -55,7 +55,7 @@ __global__ void __launch_bounds__(256) k_step_plain_f64(StepArgs a)
         uint32_t flags = clipped ? SL_NODE_CLIPPED : 0u;
         clipped_cnt = clipped;
 
-        int32_t j = a.t0[i];
+        int32_t j = a.grid_M > 0 ? a.grid_t0v[grid_slot((float)X, (float)Y, a.grid_M)].x / 3 : a.t0[i];
         int s1 = 0, s2 = 0, s3 = 0;
         bool found = false;
         const uint32_t cap = (uint32_t)a.walk_cap;

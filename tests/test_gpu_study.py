@@ -152,3 +152,71 @@ def test_courant_study_shows_the_paper_trends():
     assert np.all(b2[mid] < a2[mid])
     assert b8[mid].mean() > b2[mid].mean()
     assert all(0.0 <= x["excluded_fraction"] < 1.0 for x in d["rows"])
+
+
+@pytest.mark.parametrize("kernel,prec,curve,shuffle", [
+    (2, sl.SL_FP64, sl.SL_CURVE_HILBERT, False),
+    (1, sl.SL_FP64, sl.SL_CURVE_NONE, False),
+    (2, sl.SL_FP64, sl.SL_CURVE_NONE, True),
+    (0, sl.SL_FP32, sl.SL_CURVE_MORTON, False),
+], ids=["fast-hilbert", "plain", "fast-shuffled", "fp32-morton"])
+def test_direct_location_on_the_courant_grid(kernel, prec, curve, shuffle):
+    """Strategy 2: the walk starts at the triangle of the paper's direct
+    formula (Sec. 4); results equal the oracle's and almost no walk is left."""
+    from sl_inputs.meshes import shuffled
+    M = 80
+    m = si.courant_grid(M)
+    if shuffle:
+        m = shuffled(m, 5)
+    f = si.paper_field(2 * np.pi, 2 * np.pi)
+    dt = 5.0 / M
+    om = oracle.OracleMesh(m.xy, m.tri)
+    g = GpuRun(m, f, dt, curve=curve, kernel=kernel, precision=prec)
+    sl.sl_mesh_set_option(g.h, sl.SL_OPT_STRATEGY, 2)
+    sl.sl_mesh_set_option(g.h, sl.SL_OPT_OUTSIDE, 1)
+    vo = _bump(m.xy)
+    v = g.to_dev(vo)
+    hops = []
+    for n in range(3):
+        v, res = g.step(n, v)
+        if prec == sl.SL_FP64:
+            ov, otri, ofl, oft = om.step(f.kind, f.packed(), dt, n, vo, exclude=True)
+            out = (ofl & oracle.FLAG_EXCLUDED) != 0
+            assert np.array_equal(out, (res["flags"] & sl.SL_NODE_EXCLUDED) != 0)
+            keep = ~out
+            assert np.abs(res["v"][keep] - ov[keep]).max() <= REL_TOL_FP64 * np.abs(ov).max()
+            safe = keep & (om.margins(np.where(keep, otri, 0).astype(np.int32), oft) > FOOT_DELTA)
+            assert np.array_equal(res["tri"][safe], otri[safe])
+            vo = ov
+        else:
+            # FP32: the oracle's own float feet (the FP32 path's operation
+            # order), located exactly on the float-rounded mesh; a node is
+            # excluded when its float foot leaves the square
+            xy32 = m.xy.astype(np.float32)
+            om32 = oracle.OracleMesh(xy32.astype(np.float64), m.tri)
+            f32, outside = oracle.feet_f32(f.kind, f.packed(), dt, n, xy32)
+            out = outside != 0
+            assert np.array_equal(out, (res["flags"] & sl.SL_NODE_EXCLUDED) != 0)
+            keep = ~out
+            ft = f32.astype(np.float64)[keep]
+            tri_o, _ = om32.locate(ft)
+            safe = om32.margins(tri_o.astype(np.int32), ft) > FOOT_DELTA
+            assert np.array_equal(res["tri"][keep][safe], tri_o[safe])
+            om32.close()
+        hops.append(res["moves"][(res["flags"] & sl.SL_NODE_EXCLUDED) == 0].mean())
+    assert max(hops) < 0.01
+    g.close()
+
+
+def test_direct_location_rejects_other_meshes():
+    m = si.grid_mesh(32, 0.25, 3)
+    g = GpuRun(m, si.rotation_field(), 0.01)
+    with pytest.raises(sl.SLError):
+        sl.sl_mesh_set_option(g.h, sl.SL_OPT_STRATEGY, 2)
+    g.close()
+    # a Courant grid keeps its table through a renumbering
+    c = si.courant_grid(24)
+    g = GpuRun(c, si.rotation_field(), 0.01)
+    sl.sl_mesh_set_option(g.h, sl.SL_OPT_STRATEGY, 2)
+    sl.sl_mesh_reorder(g.h, sl.SL_CURVE_HILBERT)
+    g.close()
