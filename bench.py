@@ -273,7 +273,9 @@ def run_study(args):
     L_t = C1 in {2 pi, 8 pi}; dt = alpha dx, ceil(1/dt) steps over t in
     [0, 1]; nodes whose foot leaves the domain excluded; hops averaged over
     the located node-updates.  Strategy (a) starts every walk at the node's
-    own incident triangle, (b) at the previous step's foot triangle."""
+    own incident triangle, (b) at the previous step's foot triangle, (c) at
+    the triangle just located for the node's parent in a breadth-first
+    spanning tree (one launch per tree level, no graph)."""
     import torch
     import paper_2104_09189_gb300 as sl
     rank, world, local = dist_env()
@@ -298,7 +300,7 @@ def run_study(args):
             dt = alpha / M
             S = int(np.ceil(1.0 / dt))
             probs = sl.problems([(f.kind, dt, f.packed())])
-            for strategy, name in ((1, "a"), (0, "b")):
+            for strategy, name in ((1, "a"), (0, "b"), (3, "c")):
                 sl.sl_mesh_set_option(h, sl.SL_OPT_STRATEGY, strategy)
                 sl.sl_mesh_stats(h, reset=True)
                 v.copy_(v0)

@@ -138,8 +138,12 @@ typedef enum {
                                 of M x M cells, each split along its (l,m)-(l+1,m+1) diagonal, any
                                 numbering; SL_E_ARG for other meshes): the walk starts at the triangle
                                 the formula gives for the foot and corrects it if rounding put the
-                                guess next door.  Setting it resets T^0 to the initial incident
-                                triangles (synchronises). */
+                                guess next door; 3 = strategy (c), the triangle just located for
+                                the node's parent in a breadth-first spanning tree of the node
+                                graph rooted at the node nearest (0.5, 0.5) (Sec. 3, 4): one launch
+                                per tree level and step, no graph (sl_run's use_graph is ignored);
+                                T^0_i holds the node's own foot triangle after each step.  Setting
+                                it resets T^0 to the initial incident triangles (synchronises). */
     SL_OPT_OUTSIDE = 9       /* feet that leave the square: 0 = clip them to the boundary (default);
                                 1 = exclude the node, as the paper's experiments do (Sec. 4):
                                 V^{n+1}_i = V^n_i, flag SL_NODE_EXCLUDED */

@@ -40,7 +40,7 @@ void free_device(sl_mesh *m)
 {
     DeviceMesh &d = m->d;
     void *ptrs[] = {d.xy, d.tv[0], d.tv[1], d.tv[2], d.tn[0], d.tn[1], d.tn[2], d.t0, d.t0_init, d.t0v, d.node_off,
-                    d.status, d.stats, d.probs, d.fprobs, d.xyq, d.xyh, d.g1, d.g2, d.tparams, d.dfa, d.dfb, d.he, d.grid_t0v,
+                    d.status, d.stats, d.probs, d.fprobs, d.xyq, d.xyh, d.g1, d.g2, d.tparams, d.dfa, d.dfb, d.he, d.grid_t0v, d.tree_order, d.tree_parent,
                     m->host_v, m->host_v2};
     for (void *p : ptrs)
         if (p) cudaFree(p);
@@ -201,10 +201,11 @@ static StepArgs make_args(const sl_mesh *m, const ProbStep *probs_dev, const voi
     a.status = m->d.status;
     a.stats = m->d.stats;
     if (dbg) a.dbg = *dbg;
-    a.keep_t0 = m->opt_strategy != 0;
+    a.keep_t0 = m->opt_strategy == 1 || m->opt_strategy == 2;   // (a), direct: T^0 kept
     a.exclude = m->opt_outside == 1;
     a.grid_M = m->opt_strategy == 2 ? m->grid_M : 0;
     a.grid_t0v = (const int4 *)m->d.grid_t0v;
+    a.count = m->N;     // every node; the level launches of strategy (c) narrow it
     return a;
 }
 
@@ -235,10 +236,11 @@ static FastArgs make_fast_args(const sl_mesh *m, const FastProb *fp, const void 
     a.status = m->d.status;
     a.stats = m->d.stats;
     if (dbg) a.dbg = *dbg;
-    a.keep_t0 = m->opt_strategy != 0;
+    a.keep_t0 = m->opt_strategy == 1 || m->opt_strategy == 2;   // (a), direct: T^0 kept
     a.exclude = m->opt_outside == 1;
     a.grid_M = m->opt_strategy == 2 ? m->grid_M : 0;
     a.grid_t0v = (const int4 *)m->d.grid_t0v;
+    a.count = m->N;     // every node; the level launches of strategy (c) narrow it
     return a;
 }
 
@@ -321,18 +323,40 @@ static sl_status ensure_tables(sl_mesh *m, const sl_problem *probs, cudaStream_t
     return SL_OK;
 }
 
+// Strategy (c): one launch per spanning-tree level, in level order, so that
+// every node starts from its parent's triangle of the same step.
+template <class Args, class Launch>
+static void for_levels(const sl_mesh *m, const Args &a0, Launch launch)
+{
+    if (m->opt_strategy != 3) {
+        launch(a0);
+        return;
+    }
+    Args a = a0;
+    a.order = m->d.tree_order;
+    a.parent = m->d.tree_parent;
+    const std::vector<int64_t> &off = m->tree_level_off;
+    for (size_t k = 0; k + 1 < off.size(); ++k) {
+        a.base = off[k];
+        a.count = off[k + 1] - off[k];
+        launch(a);
+    }
+}
+
 static sl_status launch_step(const sl_mesh *m, const StepArgs &a, bool debug, cudaStream_t s)
 {
     if (m->precision != SL_FP64) return fail(SL_E_STATE, "the plain kernel is FP64 only");
-    launch_plain_f64(a, m->opt_stats != 0, debug, m->opt_block, s);
+    for_levels(m, a, [&](const StepArgs &x) { launch_plain_f64(x, m->opt_stats != 0, debug, m->opt_block, s); });
     SL_CUDA(cudaGetLastError());
     return SL_OK;
 }
 
 static sl_status launch_fast(sl_mesh *m, const FastArgs &a, bool debug, int config, cudaStream_t s)
 {
-    if (m->precision == SL_FP64) launch_fast_df(a, m->opt_stats != 0, debug, config, s);
-    else launch_fast_f32(a, m->opt_stats != 0, debug, config, s);
+    for_levels(m, a, [&](const FastArgs &x) {
+        if (m->precision == SL_FP64) launch_fast_df(x, m->opt_stats != 0, debug, config, s);
+        else launch_fast_f32(x, m->opt_stats != 0, debug, config, s);
+    });
     SL_CUDA(cudaGetLastError());
     return SL_OK;
 }
@@ -373,6 +397,9 @@ static sl_status run_steps(sl_mesh *m, const sl_problem *probs, int64_t n0, int3
                            int32_t use_graph, cudaStream_t s)
 {
     const bool fast = use_fast(m);
+    // strategy (c) launches once per spanning-tree level and step: far too
+    // many nodes for a graph on large meshes, so it always runs eagerly
+    if (m->opt_strategy == 3) use_graph = 0;
     const size_t per = sizeof(ProbStep) * m->n_problems;
     const size_t fper = sizeof(FastProb) * m->n_problems;
     std::vector<ProbStep> host((size_t)m->n_problems * (size_t)n_steps);
@@ -644,6 +671,18 @@ sl_status sl::upload_grid_table(sl_mesh *m, const std::vector<int32_t> &slot_tri
     return SL_OK;
 }
 
+// Spanning tree of strategy (c) on the device (node order by level, parents).
+sl_status sl::upload_tree(sl_mesh *m, const std::vector<int32_t> &order, const std::vector<int32_t> &parent)
+{
+    SL_CUDA(cudaSetDevice(m->device));
+    if (!m->d.tree_order) SL_CUDA(cudaMalloc(&m->d.tree_order, sizeof(int32_t) * m->N));
+    if (!m->d.tree_parent) SL_CUDA(cudaMalloc(&m->d.tree_parent, sizeof(int32_t) * m->N));
+    SL_CUDA(cudaMemcpy(m->d.tree_order, order.data(), sizeof(int32_t) * m->N, cudaMemcpyHostToDevice));
+    SL_CUDA(cudaMemcpy(m->d.tree_parent, parent.data(), sizeof(int32_t) * m->N, cudaMemcpyHostToDevice));
+    m->graph.valid = false;
+    return SL_OK;
+}
+
 // T^0 back to the initial incident triangles, synchronously (option changes).
 sl_status sl::reset_t0_sync(sl_mesh *m)
 {
@@ -701,7 +740,8 @@ extern "C" sl_status sl_mesh_reorder(sl_mesh *m, int32_t curve, int32_t *node_pe
     m->graph = GraphCache();
     st = upload_arrays(m);
     // the structured-grid table follows the triangle numbering
-    if (st == SL_OK && m->opt_strategy == 2) st = sl_mesh_set_option(m, SL_OPT_STRATEGY, 2);
+    if (st == SL_OK && (m->opt_strategy == 2 || m->opt_strategy == 3))
+        st = sl_mesh_set_option(m, SL_OPT_STRATEGY, m->opt_strategy);
     return st;
 }
 

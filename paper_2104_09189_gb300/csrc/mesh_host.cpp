@@ -457,7 +457,15 @@ extern "C" sl_status sl_mesh_set_option(sl_mesh *m, int32_t option, int64_t valu
         m->opt_config_first = (int32_t)value;
         break;
     case SL_OPT_STRATEGY: {
-        if (value < 0 || value > 2) return sl::fail(SL_E_ARG, "strategy must be 0 (b), 1 (a) or 2 (direct)");
+        if (value < 0 || value > 3) return sl::fail(SL_E_ARG, "strategy must be 0 (b), 1 (a), 2 (direct) or 3 (c)");
+        if (value == 3) {
+            std::vector<int32_t> order, parent;
+            std::vector<int64_t> level_off;
+            sl_status st = sl::build_tree(m, order, level_off, parent);
+            if (st == SL_OK) st = sl::upload_tree(m, order, parent);
+            if (st != SL_OK) return st;
+            m->tree_level_off = level_off;
+        }
         if (value == 2) {
             int32_t M = 0;
             std::vector<int32_t> slots;

@@ -154,6 +154,8 @@ extern "C" sl_status sl_step_noalloc(sl_mesh *m, const sl_problem *probs, int64_
     if ((const void *)v_in == (const void *)v_out) return fail(SL_E_ARG, "sl_step_noalloc: v_in and v_out must not alias");
     if (n < 0) return fail(SL_E_ARG, "sl_step_noalloc: n must be >= 0");
     if (m->precision != SL_FP64) return fail(SL_E_ARG, "sl_step_noalloc: FP64 meshes only");
+    if (m->opt_strategy == 3)
+        return fail(SL_E_STATE, "sl_step_noalloc: strategy (c) needs one launch per tree level (use sl_step)");
     if (m->N > kNoAllocMaxNodes)
         return fail(SL_E_ARG, "sl_step_noalloc: the mesh has " + std::to_string(m->N) + " nodes; the static scratch holds at most " +
                                   std::to_string(kNoAllocMaxNodes) + " (use sl_step)");
@@ -206,10 +208,11 @@ extern "C" sl_status sl_step_noalloc(sl_mesh *m, const sl_problem *probs, int64_
     a.N = m->N;
     a.status = m->d.status;
     a.stats = m->d.stats;
-    a.keep_t0 = m->opt_strategy != 0;
+    a.keep_t0 = m->opt_strategy == 1 || m->opt_strategy == 2;   // (a), direct: T^0 kept
     a.exclude = m->opt_outside == 1;
     a.grid_M = m->opt_strategy == 2 ? m->grid_M : 0;
     a.grid_t0v = (const int4 *)m->d.grid_t0v;
+    a.count = m->N;
     launch_fast_df(a, m->opt_stats != 0, false, m->opt_config, s);
     launch_from_df(sc.values, v_out, m->N, s);
     e = cudaGetLastError();

@@ -35,6 +35,8 @@ struct DeviceMesh {
     int32_t *t0_init = nullptr;       // the initial start triangles (global)
     void *t0v = nullptr;              // int4 (T^0, its vertex ids) per node
     void *grid_t0v = nullptr;         // int4 start state per structured-grid triangle (strategy 2)
+    int32_t *tree_order = nullptr;    // strategy (c): nodes by spanning-tree level (N)
+    int32_t *tree_parent = nullptr;   // strategy (c): parent of every node (N; the root its own)
     int64_t *node_off = nullptr;      // n_problems + 1
     uint32_t *status = nullptr;       // [0] = OR of (1 << sl_status); others reserved
     unsigned long long *stats = nullptr;   // 8 counters (sl_stats order)
@@ -87,8 +89,10 @@ struct sl_mesh {
     int32_t opt_config = 5;           // launch configuration of the fast kernels (later steps)
     int32_t opt_config_first = 0;     // ... for a step whose walks start at the initial triangles
     int32_t opt_strategy = 0;         // 0 = strategy (b), 1 = strategy (a) (T^0 never overwritten),
-                                      // 2 = direct location on a structured Courant grid
+                                      // 2 = direct location on a structured Courant grid,
+                                      // 3 = strategy (c) (spanning-tree parent's triangle)
     int32_t grid_M = 0;               // cells per side when the mesh is a structured Courant grid
+    std::vector<int64_t> tree_level_off;   // strategy (c): level k = tree_order[off[k], off[k+1])
     int32_t opt_outside = 0;          // 0 = clip feet that leave the square, 1 = exclude the node
     bool t0_initial = true;           // T^0 holds the initial start triangles
     int32_t sms = 0;                  // multiprocessors of the device
@@ -110,5 +114,8 @@ sl_status upload(sl_mesh *m);
 void free_device(sl_mesh *m);
 sl_status reset_t0_sync(sl_mesh *m);
 sl_status upload_grid_table(sl_mesh *m, const std::vector<int32_t> &slot_tri);
+sl_status build_tree(const sl_mesh *m, std::vector<int32_t> &order, std::vector<int64_t> &level_off,
+                     std::vector<int32_t> &parent);
+sl_status upload_tree(sl_mesh *m, const std::vector<int32_t> &order, const std::vector<int32_t> &parent);
 int32_t default_walk_cap(const sl_mesh *m);
 }  // namespace sl

@@ -46,6 +46,18 @@ __device__ __forceinline__ df df_div(df a, df b)
     return q;
 }
 
+// The clip and the exclusion decide on the foot rounded to double, the
+// precision Eq. 4 is evaluated in: a double-float coordinate above 1 by at
+// most half an ulp of 1 in double (2^-53, ties to even) rounds to exactly 1
+// and lies on the boundary.  (Below 1 and near 0 the double-float and double
+// decisions already agree.)  Without this, a boundary node whose velocity is
+// tangent to within 1e-16 could be clipped by one arithmetic and not by the
+// other, and the clip moves the foot by a whole step.
+__device__ __forceinline__ void round_boundary(df &X)
+{
+    if (X.h == 1.0f && X.l > 0.0f && X.l <= 0x1p-53f) X.l = 0.0f;
+}
+
 // Boundary clip of the Euler foot q of node x, in double-float: if q leaves
 // [0,1]^2 the segment x -> q stops at its first boundary crossing; the
 // coordinates that attain the crossing become exactly 0 or 1, the other one
@@ -194,7 +206,7 @@ __device__ __forceinline__ int32_t tri_of(int32_t h) { return (int32_t)__umulhi(
 // test and the value always take the triangle's vertices in slot order
 // (T[0][j], T[1][j], T[2][j]), so the result depends on the located triangle
 // and the foot only, not on the path of the walk.
-template <bool kDebug>
+template <bool kDebug, bool kExt>
 __device__ __forceinline__ void step_node(const FastArgs &a, int64_t i, int pi, NodeCounters &c)
 {
     const FastProb &P = a.probs[pi];
@@ -202,12 +214,19 @@ __device__ __forceinline__ void step_node(const FastArgs &a, int64_t i, int pi, 
     const df x = df_make(xq.x, xq.z), y = df_make(xq.y, xq.w);
     df X, Y;
     foot_df(P, a, i, x, y, X, Y);
+    round_boundary(X);
+    round_boundary(Y);
     uint32_t flags = 0;
-    if (a.exclude && (df_neg_strict(X) || df_gt1(X) || df_neg_strict(Y) || df_gt1(Y))) {
+    if (kExt && a.exclude && (df_neg_strict(X) || df_gt1(X) || df_neg_strict(Y) || df_gt1(Y))) {
         // the paper's experiments exclude nodes whose foot leaves the domain
         // (Sec. 4): V unchanged, no walk, T^0 unchanged
         ((float2 *)a.vout)[i] = ((const float2 *)a.vin)[i];
         c.excluded = 1;
+        if (a.parent) {
+            // strategy (c): the children start where this node would have
+            a.t0[i] = a.t0[a.parent[i]];
+            a.t0v[i] = a.t0v[a.parent[i]];
+        }
         if (kDebug) {
             if (a.dbg.feet) {
                 a.dbg.feet[2 * i] = (double)X.h + (double)X.l;
@@ -226,7 +245,8 @@ __device__ __forceinline__ void step_node(const FastArgs &a, int64_t i, int pi, 
     // start triangle and its vertex ids from the per-node cache (one
     // coalesced 16-byte load), or from the direct location on a structured
     // grid
-    const int4 tq = a.grid_M > 0 ? __ldg(&a.grid_t0v[grid_slot(X.h, Y.h, a.grid_M)]) : a.t0v[i];
+    const int4 tq = kExt && a.grid_M > 0 ? __ldg(&a.grid_t0v[grid_slot(X.h, Y.h, a.grid_M)])
+                                         : a.t0v[kExt && a.parent ? (int64_t)a.parent[i] : i];
     int32_t e0 = tq.x, e1 = 0;
     int32_t j = 0;
     int w0 = tq.y, w1 = tq.z, w2 = tq.w;
@@ -351,7 +371,7 @@ __device__ __forceinline__ void step_node(const FastArgs &a, int64_t i, int pi, 
     const df v1 = dfp(vin[w0]), v2 = dfp(vin[w1]), v3 = dfp(vin[w2]);
     const df v = df_add(v3, df_add(df_mul(th1, df_sub(v1, v3)), df_mul(th2, df_sub(v2, v3))));
     ((float2 *)a.vout)[i] = make_float2(v.h, v.l);
-    if (hops > 0 && !a.keep_t0) {
+    if ((hops > 0 || (kExt && a.parent)) && !(kExt && a.keep_t0)) {
         a.t0[i] = j;
         a.t0v[i] = make_int4(3 * j, w0, w1, w2);
     }
@@ -368,28 +388,33 @@ __device__ __forceinline__ void step_node(const FastArgs &a, int64_t i, int pi, 
     }
 }
 
-template <bool kStats, bool kDebug, int kBlock, int kMinBlocks>
+// kExt: the variant with the options of the paper's experiments (exclusion,
+// strategies (a), (c) and the direct structured-grid start); the default
+// variant compiles them out and keeps its registers for the walk.
+template <bool kStats, bool kDebug, int kBlock, int kMinBlocks, bool kExt>
 __global__ void __launch_bounds__(kBlock, kMinBlocks) k_step_fast_df(FastArgs a)
 {
-    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    const bool active = i < a.N;
+    const int64_t i = kExt ? node_of_thread(a) : (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const bool active = kExt ? i >= 0 : i < a.N;
     NodeCounters c;
-    const int pi = block_problem(a.node_off, a.nprob, a.N, i);
-    if (active) step_node<kDebug>(a, i, pi, c);
+    // a spanning-tree level mixes problems within a block: search per node
+    const int pi = kExt && a.order ? (active && a.nprob > 1 ? problem_of(a.node_off, a.nprob, i) : 0)
+                                   : block_problem(a.node_off, a.nprob, a.N, i);
+    if (active) step_node<kDebug, kExt>(a, i, pi, c);
     if (kStats) warp_stats(a.stats, active, c.hops, c.exact, c.clipped, c.fallback, c.limit, c.filter2, c.excluded);
 }
 
-template <int kBlock, int kMinBlocks>
+template <int kBlock, int kMinBlocks, bool kExt = false>
 static void launch_fast_df_cfg(const FastArgs &a, bool stats, bool debug, cudaStream_t s)
 {
-    const unsigned grid = (unsigned)((a.N + kBlock - 1) / kBlock);
+    const unsigned grid = (unsigned)((a.count + kBlock - 1) / kBlock);
     if (grid == 0) return;
     if (stats) {
-        if (debug) k_step_fast_df<true, true, kBlock, kMinBlocks><<<grid, kBlock, 0, s>>>(a);
-        else k_step_fast_df<true, false, kBlock, kMinBlocks><<<grid, kBlock, 0, s>>>(a);
+        if (debug) k_step_fast_df<true, true, kBlock, kMinBlocks, kExt><<<grid, kBlock, 0, s>>>(a);
+        else k_step_fast_df<true, false, kBlock, kMinBlocks, kExt><<<grid, kBlock, 0, s>>>(a);
     } else {
-        if (debug) k_step_fast_df<false, true, kBlock, kMinBlocks><<<grid, kBlock, 0, s>>>(a);
-        else k_step_fast_df<false, false, kBlock, kMinBlocks><<<grid, kBlock, 0, s>>>(a);
+        if (debug) k_step_fast_df<false, true, kBlock, kMinBlocks, kExt><<<grid, kBlock, 0, s>>>(a);
+        else k_step_fast_df<false, false, kBlock, kMinBlocks, kExt><<<grid, kBlock, 0, s>>>(a);
     }
 }
 
@@ -398,6 +423,11 @@ static void launch_fast_df_cfg(const FastArgs &a, bool stats, bool debug, cudaSt
 // 2 = 128 x 8, 3 = 128 x 9 (56 registers), 4 = 256 x 5, 5 = 128 x 12.
 void launch_fast_df(const FastArgs &a, bool stats, bool debug, int config, cudaStream_t s)
 {
+    if (a.exclude || a.order || a.grid_M > 0 || a.keep_t0) {
+        // the experiment options: one configuration (128 x 8, 64 registers)
+        launch_fast_df_cfg<128, 8, true>(a, stats, debug, s);
+        return;
+    }
     switch (config) {
     case 1: launch_fast_df_cfg<256, 3>(a, stats, debug, s); break;
     case 2: launch_fast_df_cfg<128, 8>(a, stats, debug, s); break;

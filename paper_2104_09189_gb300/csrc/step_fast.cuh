@@ -52,6 +52,12 @@ struct FastArgs {
     int32_t exclude;              // nodes whose foot leaves the square are excluded (Sec. 4)
     int32_t grid_M;               // > 0: start at the direct location on the structured grid (Sec. 4)
     const int4 *grid_t0v;         // start state of structured triangle 2 (M m + l) + (lower ? 1 : 0)
+    // strategy (c): the launch covers the nodes order[base, base + count) (one
+    // spanning-tree level) and each starts at its parent's T^0; otherwise
+    // order is NULL and the launch covers nodes [0, count)
+    const int32_t *order;
+    const int32_t *parent;
+    int64_t base, count;
 };
 
 // config: launch configuration 0..kFastConfigs-1 (see step_fast.cu)

@@ -91,14 +91,19 @@ __device__ __forceinline__ int32_t tri_of_f32(int32_t h) { return (int32_t)__umu
 // orientation was certified negative from the other side, so here it is
 // positive.  The value is evaluated with the located triangle's vertices in
 // slot order, so it does not depend on the path of the walk.
-template <bool kStats, bool kDebug, int kBlock, int kMinBlocks>
+// kExt: the variant with the options of the paper's experiments (exclusion,
+// strategies (a), (c) and the direct structured-grid start); the default
+// variant compiles them out.
+template <bool kStats, bool kDebug, int kBlock, int kMinBlocks, bool kExt>
 __global__ void __launch_bounds__(kBlock, kMinBlocks) k_step_fast_f32(FastArgs a)
 {
-    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    const bool active = i < a.N;
+    const int64_t i = kExt ? node_of_thread(a) : (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const bool active = kExt ? i >= 0 : i < a.N;
     uint32_t hops = 0, exact_tests = 0, clipped_cnt = 0, fallback_cnt = 0, limit_cnt = 0, fp64_tests = 0;
     uint32_t excluded_cnt = 0;
-    const int pi = block_problem(a.node_off, a.nprob, a.N, i);
+    // a spanning-tree level mixes problems within a block: search per node
+    const int pi = kExt && a.order ? (active && a.nprob > 1 ? problem_of(a.node_off, a.nprob, i) : 0)
+                                   : block_problem(a.node_off, a.nprob, a.N, i);
     if (active) {
         const FastProb &P = a.probs[pi];
         const float2 xf = a.xyf[i];
@@ -106,12 +111,17 @@ __global__ void __launch_bounds__(kBlock, kMinBlocks) k_step_fast_f32(FastArgs a
         foot_f32(P, a, i, xf.x, xf.y, X, Y);
         uint32_t flags = 0;
         bool excluded = false;
-        if (!(X >= 0.0f && X <= 1.0f && Y >= 0.0f && Y <= 1.0f) && a.exclude) {
+        if (kExt && a.exclude && !(X >= 0.0f && X <= 1.0f && Y >= 0.0f && Y <= 1.0f)) {
             // the paper's experiments exclude nodes whose foot leaves the
             // domain (Sec. 4): V unchanged, no walk, T^0 unchanged
             ((float *)a.vout)[i] = ((const float *)a.vin)[i];
             excluded_cnt = 1;
             excluded = true;
+            if (a.parent) {
+                // strategy (c): the children start where this node would have
+                a.t0[i] = a.t0[a.parent[i]];
+                a.t0v[i] = a.t0v[a.parent[i]];
+            }
             if (kDebug) {
                 if (a.dbg.feet) {
                     a.dbg.feet[2 * i] = (double)X;
@@ -135,7 +145,8 @@ __global__ void __launch_bounds__(kBlock, kMinBlocks) k_step_fast_f32(FastArgs a
                                    (Y == 1.0f ? 8u : 0u);
 
             // start state from the per-node cache (T^0 and its vertex ids)
-            const int4 tq = a.grid_M > 0 ? __ldg(&a.grid_t0v[grid_slot(X, Y, a.grid_M)]) : a.t0v[i];
+            const int4 tq = kExt && a.grid_M > 0 ? __ldg(&a.grid_t0v[grid_slot(X, Y, a.grid_M)])
+                                                 : a.t0v[kExt && a.parent ? (int64_t)a.parent[i] : i];
             int32_t e0 = tq.x, e1, e2;
             {
                 const int32_t j0 = tri_of_f32(e0), s0 = e0 - 3 * j0;
@@ -311,7 +322,7 @@ __global__ void __launch_bounds__(kBlock, kMinBlocks) k_step_fast_f32(FastArgs a
             const float v1 = vin[w0], v2 = vin[w1], v3 = vin[w2];
             const float v = __fmaf_rn(th1, __fsub_rn(v1, v3), __fmaf_rn(th2, __fsub_rn(v2, v3), v3));
             ((float *)a.vout)[i] = v;
-            if (moved && !a.keep_t0) {
+            if ((moved || (kExt && a.parent)) && !(kExt && a.keep_t0)) {
                 a.t0[i] = j;
                 a.t0v[i] = make_int4(3 * j, w0, w1, w2);
             }
@@ -331,22 +342,27 @@ __global__ void __launch_bounds__(kBlock, kMinBlocks) k_step_fast_f32(FastArgs a
         warp_stats(a.stats, active, hops, exact_tests, clipped_cnt, fallback_cnt, limit_cnt, fp64_tests, excluded_cnt);
 }
 
-template <int kBlock, int kMinBlocks>
+template <int kBlock, int kMinBlocks, bool kExt = false>
 static void launch_f32_cfg(const FastArgs &a, bool stats, bool debug, cudaStream_t s)
 {
-    const unsigned grid = (unsigned)((a.N + kBlock - 1) / kBlock);
+    const unsigned grid = (unsigned)((a.count + kBlock - 1) / kBlock);
     if (grid == 0) return;
     if (stats) {
-        if (debug) k_step_fast_f32<true, true, kBlock, kMinBlocks><<<grid, kBlock, 0, s>>>(a);
-        else k_step_fast_f32<true, false, kBlock, kMinBlocks><<<grid, kBlock, 0, s>>>(a);
+        if (debug) k_step_fast_f32<true, true, kBlock, kMinBlocks, kExt><<<grid, kBlock, 0, s>>>(a);
+        else k_step_fast_f32<true, false, kBlock, kMinBlocks, kExt><<<grid, kBlock, 0, s>>>(a);
     } else {
-        if (debug) k_step_fast_f32<false, true, kBlock, kMinBlocks><<<grid, kBlock, 0, s>>>(a);
-        else k_step_fast_f32<false, false, kBlock, kMinBlocks><<<grid, kBlock, 0, s>>>(a);
+        if (debug) k_step_fast_f32<false, true, kBlock, kMinBlocks, kExt><<<grid, kBlock, 0, s>>>(a);
+        else k_step_fast_f32<false, false, kBlock, kMinBlocks, kExt><<<grid, kBlock, 0, s>>>(a);
     }
 }
 
 void launch_fast_f32(const FastArgs &a, bool stats, bool debug, int config, cudaStream_t s)
 {
+    if (a.exclude || a.order || a.grid_M > 0 || a.keep_t0) {
+        // the experiment options: one configuration (128 x 8)
+        launch_f32_cfg<128, 8, true>(a, stats, debug, s);
+        return;
+    }
     switch (config) {
     case 1: launch_f32_cfg<256, 3>(a, stats, debug, s); break;
     case 2: launch_f32_cfg<128, 8>(a, stats, debug, s); break;

@@ -29,6 +29,12 @@ struct StepArgs {
     int32_t exclude;              // nodes whose foot leaves the square are excluded (Sec. 4)
     int32_t grid_M;               // > 0: start at the direct location on the structured grid (Sec. 4)
     const int4 *grid_t0v;         // start state of structured triangle 2 (M m + l) + (lower ? 1 : 0)
+    // strategy (c): the launch covers the nodes order[base, base + count) (one
+    // spanning-tree level) and each starts at its parent's T^0; otherwise
+    // order is NULL and the launch covers nodes [0, count)
+    const int32_t *order;
+    const int32_t *parent;
+    int64_t base, count;
 };
 
 __device__ __forceinline__ uint64_t mix64_dev(uint64_t z)
@@ -75,6 +81,16 @@ __device__ __forceinline__ int grid_slot(float x, float y, int M)
     const float gx = x * (float)M, gy = y * (float)M;
     const int l = min(max((int)floorf(gx), 0), M - 1), m = min(max((int)floorf(gy), 0), M - 1);
     return 2 * (M * m + l) + (gx - (float)l < gy - (float)m ? 0 : 1);
+}
+
+// The node a thread of a step kernel works on (-1: none): thread t of the
+// launch takes node t, or order[base + t] for a spanning-tree level.
+template <class Args>
+__device__ __forceinline__ int64_t node_of_thread(const Args &a)
+{
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= a.count) return -1;
+    return a.order ? (int64_t)a.order[a.base + t] : t;
 }
 
 void launch_plain_f64(const StepArgs &a, bool stats, bool debug, int block, cudaStream_t s);

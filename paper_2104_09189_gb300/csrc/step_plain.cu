@@ -18,8 +18,8 @@ namespace sl {
 template <bool kStats, bool kDebug>
 __global__ void __launch_bounds__(256) k_step_plain_f64(StepArgs a)
 {
-    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    bool active = i < a.N;
+    const int64_t i = node_of_thread(a);
+    bool active = i >= 0;
     uint32_t hops = 0, exact_tests = 0, clipped_cnt = 0, fallback_cnt = 0, limit_cnt = 0, excluded_cnt = 0;
     const double *vin = (const double *)a.vin;
     double X = 0.0, Y = 0.0;
@@ -36,6 +36,11 @@ __global__ void __launch_bounds__(256) k_step_plain_f64(StepArgs a)
             // domain (Sec. 4): V unchanged, no walk, T^0 unchanged
             ((double *)a.vout)[i] = vin[i];
             excluded_cnt = 1;
+            if (a.parent) {
+                // strategy (c): the children start where this node would have
+                a.t0[i] = a.t0[a.parent[i]];
+                a.t0v[i] = a.t0v[a.parent[i]];
+            }
             if (kDebug) {
                 if (a.dbg.feet) {
                     a.dbg.feet[2 * i] = qx;
@@ -55,7 +60,8 @@ __global__ void __launch_bounds__(256) k_step_plain_f64(StepArgs a)
         uint32_t flags = clipped ? SL_NODE_CLIPPED : 0u;
         clipped_cnt = clipped;
 
-        int32_t j = a.grid_M > 0 ? a.grid_t0v[grid_slot((float)X, (float)Y, a.grid_M)].x / 3 : a.t0[i];
+        int32_t j = a.grid_M > 0 ? a.grid_t0v[grid_slot((float)X, (float)Y, a.grid_M)].x / 3
+                                 : a.t0[a.parent ? (int64_t)a.parent[i] : i];
         int s1 = 0, s2 = 0, s3 = 0;
         bool found = false;
         const uint32_t cap = (uint32_t)a.walk_cap;
@@ -143,14 +149,14 @@ __global__ void __launch_bounds__(256) k_step_plain_f64(StepArgs a)
         }
     }
     if (kStats)
-        warp_stats(a.stats, i < a.N, hops, exact_tests, clipped_cnt, fallback_cnt, limit_cnt, 0, excluded_cnt);
+        warp_stats(a.stats, i >= 0, hops, exact_tests, clipped_cnt, fallback_cnt, limit_cnt, 0, excluded_cnt);
 }
 
 void launch_plain_f64(const StepArgs &a, bool stats, bool debug, int block, cudaStream_t s)
 {
     if (block <= 0) block = 256;
     if (block > 256) block = 256;
-    const unsigned grid = (unsigned)((a.N + block - 1) / block);
+    const unsigned grid = (unsigned)((a.count + block - 1) / block);
     if (grid == 0) return;
     if (stats) {
         if (debug) k_step_plain_f64<true, true><<<grid, block, 0, s>>>(a);

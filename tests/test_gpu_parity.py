@@ -269,3 +269,29 @@ def test_autotune_restores_state_and_keeps_results():
     sl.sl_run(ref.h, ref.probs, 0, 5, v2, w2)
     assert np.abs(ref.from_dev(v2) - tuned).max() <= 1e-12 * np.abs(tuned).max()
     ref.close()
+
+
+@pytest.mark.parametrize("kernel", [1, 2], ids=["plain", "fast"])
+@pytest.mark.parametrize("fx", [-1e-17, 1e-17])
+def test_boundary_nodes_with_nearly_tangent_velocity(kernel, fx):
+    """A boundary node whose velocity is tangent to within 1e-17: x - dt f_x
+    rounds (in double, Eq. 4) onto the boundary or across it.  The clip is
+    discontinuous there, so the fast kernel must decide on the foot rounded
+    to double like the oracle: the same nodes are clipped and the values
+    agree."""
+    mesh = si.grid_mesh(40, 0.25, 9)
+    p = np.zeros(48)
+    p[0], p[4] = fx, -1.0                     # f = (fx, -1): feet move up by dt
+    fld = si.Field(si.FIELD_AFFINE, p, 1.0)
+    dt = 0.05
+    om = oracle.OracleMesh(mesh.xy, mesh.tri)
+    g = GpuRun(mesh, fld, dt, curve=sl.SL_CURVE_HILBERT, kernel=kernel)
+    v0 = np.cos(2.0 * mesh.xy[:, 0]) + mesh.xy[:, 1] ** 2
+    v = g.to_dev(v0)
+    v, res = g.step(0, v)
+    ov, otri, ofl, oft = om.step(fld.kind, fld.packed(), dt, 0, v0)
+    on_side = (mesh.xy[:, 0] == 0.0) | (mesh.xy[:, 0] == 1.0)
+    assert on_side.sum() > 40
+    assert np.array_equal((res["flags"] & sl.SL_NODE_CLIPPED) != 0, (ofl & oracle.FLAG_CLIPPED) != 0)
+    assert np.abs(res["v"] - ov).max() <= 1e-12 * np.abs(ov).max()
+    g.close()

@@ -151,6 +151,11 @@ def test_courant_study_shows_the_paper_trends():
     mid = (al >= 2) & (al <= 6)              # L_t alpha dx < 1 for L_t = 2 pi, dx = 1/64
     assert np.all(b2[mid] < a2[mid])
     assert b8[mid].mean() > b2[mid].mean()
+    # (c): nearly flat in alpha while L_x dt < 1 (the uniform bound of Sec. 3)
+    _, c2 = hops("2pi", "c")
+    flat = (al >= 1) & (al <= 6)
+    assert c2[flat].max() < 2.0 * c2[flat].min() + 0.5
+    assert np.all(c2[al >= 8] < a2[al >= 8])
     assert all(0.0 <= x["excluded_fraction"] < 1.0 for x in d["rows"])
 
 
@@ -220,3 +225,60 @@ def test_direct_location_rejects_other_meshes():
     sl.sl_mesh_set_option(g.h, sl.SL_OPT_STRATEGY, 2)
     sl.sl_mesh_reorder(g.h, sl.SL_CURVE_HILBERT)
     g.close()
+
+
+@pytest.mark.parametrize("kernel,prec", [(2, sl.SL_FP64), (1, sl.SL_FP64), (0, sl.SL_FP32)],
+                         ids=["fast", "plain", "fp32"])
+def test_strategy_c_matches_the_oracle_and_walks_little(kernel, prec):
+    """Strategy (c) (Sec. 3): every node starts at its spanning-tree parent's
+    triangle of the same step.  Results equal the oracle's, T^0 holds every
+    node's own foot triangle, and the walks stay short (the feet of
+    neighbouring nodes are within (1 + L_x dt) dx of each other)."""
+    m = si.grid_mesh(72, 0.25, 21)
+    f = si.paper_field(2 * np.pi, 2 * np.pi)
+    dt = 6.0 / 72
+    om = oracle.OracleMesh(m.xy, m.tri)
+    g = GpuRun(m, f, dt, curve=sl.SL_CURVE_HILBERT, kernel=kernel, precision=prec)
+    sl.sl_mesh_set_option(g.h, sl.SL_OPT_STRATEGY, 3)
+    vo = _bump(m.xy)
+    v = g.to_dev(vo)
+    t0 = g.torch.empty(m.n_nodes, dtype=g.torch.int32, device=g.dev)
+    for n in range(3):
+        v, res = g.step(n, v)
+        if prec == sl.SL_FP64:
+            ov, otri, ofl, oft = om.step(f.kind, f.packed(), dt, n, vo)
+            assert np.abs(res["v"] - ov).max() <= REL_TOL_FP64 * np.abs(ov).max()
+            safe = om.margins(otri.astype(np.int32), oft) > FOOT_DELTA
+            assert np.array_equal(res["tri"][safe], otri[safe])
+            vo = ov
+        # T^0_i is the triangle located for node i (Algorithm 1, strategy (c))
+        sl.sl_mesh_get_t0(g.h, t0)
+        got = np.empty(m.n_nodes, dtype=np.int64)
+        got[g.node_perm] = g.tri_perm[t0.cpu().numpy()]
+        assert np.array_equal(got, res["tri"])
+        if n > 0:
+            assert res["moves"].mean() < 3.0
+    g.close()
+
+
+def test_strategy_c_on_a_batch_with_exclusion():
+    """Tree levels of several problems run together; exclusion passes the
+    parent's start on to the children.  Values equal the oracle's."""
+    probs = si.batch_config(5, nmin=2e3, nmax=3e4, steps=3)
+    meshes = [(p.mesh.xy, p.mesh.tri) for p in probs]
+    no, to, xy, tri = sl.pack_meshes(meshes)
+    import torch
+    h = sl.sl_mesh_create(no, to, xy, tri)
+    sl.sl_mesh_set_option(h, sl.SL_OPT_STRATEGY, 3)
+    sl.sl_mesh_set_option(h, sl.SL_OPT_OUTSIDE, 1)
+    pr = sl.problems([(p.field.kind, 2.0 * p.dt, p.field.packed()) for p in probs])
+    v = torch.tensor(np.concatenate([p.v0 for p in probs]), dtype=torch.float64, device="cuda:0")
+    w = torch.empty_like(v)
+    sl.sl_run(h, pr, 0, 3, v, w, use_graph=True)        # (c) runs eagerly whatever use_graph says
+    got = v.cpu().numpy()
+    sl.sl_mesh_destroy(h)
+    for k, p in enumerate(probs):
+        om = oracle.OracleMesh(p.mesh.xy, p.mesh.tri)
+        want = om.run(p.field.kind, p.field.packed(), 2.0 * p.dt, 0, 3, p.v0, exclude=True)
+        seg = got[no[k]:no[k + 1]]
+        assert np.abs(seg - want).max() <= 1e-12 * np.abs(want).max()
