@@ -177,6 +177,31 @@ def build_workload(args):
     return Workload(prob.name, [prob], prob.precision, prob.n_steps, desc)
 
 
+TRAFFIC_SOURCES = ("step_fast.cu", "step_fast.cuh", "df.cuh", "predicates.cuh", "step_common.cuh", "step_kernels.cuh")
+
+
+def committed_traffic(workload_key):
+    """DRAM bytes per launch of the dominant kernel from the committed ncu
+    summary (profiles/k_step_fast_df_c3_traffic.md), or None when the kernel
+    sources changed since that capture or the workload differs."""
+    import hashlib
+    here = os.path.dirname(os.path.abspath(__file__))
+    path = os.path.join(here, "profiles", "k_step_fast_df_c3_traffic.md")
+    if not os.path.exists(path):
+        return None
+    fields = {}
+    for line in open(path):
+        if ":" in line and not line.startswith(("|", "#", " ", "`")):
+            k, v = line.split(":", 1)
+            fields[k.strip()] = v.strip()
+    h = hashlib.sha256()
+    for f in TRAFFIC_SOURCES:
+        h.update(open(os.path.join(here, "paper_2104_09189_gb300", "csrc", f), "rb").read())
+    if fields.get("source_sha256") != h.hexdigest() or fields.get("workload") != workload_key:
+        return None
+    return float(fields["traffic_bytes_per_launch"])
+
+
 def measured_peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -588,7 +613,9 @@ def main():
         "data": "synthetic",
         "config": workload_config(args, wl),
         "roofline": {"bound": "hbm", "achieved": achieved_gbs, "peak": peaks.get("hbm_gbs", 6800.0),
-                     "unit": "GB/s", "frac": achieved_gbs / peaks.get("hbm_gbs", 6800.0), "traffic": None,
+                     "unit": "GB/s", "frac": achieved_gbs / peaks.get("hbm_gbs", 6800.0),
+                     "traffic": (committed_traffic(f"{args.config} {wl.precision}")
+                                 if args.kernel != 1 and args.cells is None else None),
                      "peak_source": peak_src,
                      "algorithmic_bytes_per_node": bpn,
                      "kernel": ("k_step_plain_f64" if args.kernel == 1 else
