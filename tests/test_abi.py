@@ -139,3 +139,19 @@ def test_stats_struct_matches_the_header():
     body = body[:body.index("} sl_stats;")]
     names = re.findall(r"uint64_t\s+(\w+);", body)
     assert [n for n, _ in sl.sl_stats._fields_] == names
+
+
+def test_size_limits_are_rejected_before_any_array_is_read():
+    # int32 node ids and int32 half-edge codes (3 t + k): more than 2^31 - 1
+    # nodes or 715 827 882 triangles is SL_E_ARG; the check runs on the
+    # offsets alone (the arrays passed here are tiny and never read)
+    L = sl.library()
+    xy = np.zeros(8, dtype=np.float64)
+    tri = np.zeros(6, dtype=np.int32)
+    for n_nodes, n_tri in [(1 << 31, 2), (4, 715827883), (4, 1 << 30)]:
+        no = np.array([0, n_nodes], dtype=np.int64)
+        to = np.array([0, n_tri], dtype=np.int64)
+        st = L.sl_mesh_validate(1, no.ctypes.data, to.ctypes.data, xy.ctypes.data, tri.ctypes.data, None, 1,
+                                None, None)
+        assert st == sl.SL_E_ARG, (n_nodes, n_tri)
+        assert "more than" in sl.sl_last_error()
