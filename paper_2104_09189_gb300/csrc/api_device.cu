@@ -28,6 +28,18 @@ static void split_df(double v, float2 &o)
     o.y = (float)(v - (double)h);
 }
 
+// A coordinate in [0,1] as g + l: g = v rounded to the grid of 2^-24 (a float,
+// exactly), l = fl32(v - g), |l| <= 2^-25, |v - g - l| <= 2^-49.  Differences
+// of the g parts of two coordinates are exact in float (multiples of 2^-24
+// below 1 in magnitude), which is what the certified test of the fast kernel
+// builds on.
+static void split_grid(double v, float2 &o)
+{
+    const double g = std::nearbyint(v * 16777216.0) / 16777216.0;
+    o.x = (float)g;
+    o.y = (float)(v - g);
+}
+
 int32_t default_walk_cap(const sl_mesh *m)
 {
     int32_t M = 1;
@@ -60,12 +72,13 @@ static sl_status upload_arrays(sl_mesh *m)
     const int64_t N = m->N, Nt = m->Nt;
     if (m->precision == SL_FP64) {
         SL_CUDA(cudaMemcpy(d.xy, m->xy.data(), sizeof(double) * 2 * N, cudaMemcpyHostToDevice));
-        // (hi, lo) float pairs of the coordinates for the double-float kernel
+        // (grid, remainder) float pairs of the coordinates for the double-float
+        // kernel (split_grid); their grid parts are also the hop coordinates
         std::vector<float4> q(N);
         for (int64_t i = 0; i < N; ++i) {
             float2 a, b;
-            split_df(m->xy[2 * i], a);
-            split_df(m->xy[2 * i + 1], b);
+            split_grid(m->xy[2 * i], a);
+            split_grid(m->xy[2 * i + 1], b);
             q[i] = make_float4(a.x, b.x, a.y, b.y);
         }
         SL_CUDA(cudaMemcpy(d.xyq, q.data(), sizeof(float4) * N, cudaMemcpyHostToDevice));

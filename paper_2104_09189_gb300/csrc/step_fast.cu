@@ -125,17 +125,70 @@ __device__ __forceinline__ void foot_df(const FastProb &P, const FastArgs &a, in
     }
 }
 
-// Error bounds.  Coordinates are stored as hi + lo floats within 2^-48 of
-// the double coordinates (|coord| <= 1); the foot is exactly X.h + X.l.
-//  FP32 hop test on the high parts: every difference is within
-//  2^-24 + 2^-24 |d| of the exact one, so a cross product of differences
-//  whose |.|-sum is at most S is within 2^-23 S + 2^-22 S^2 (two-fold
-//  margins); theta_3's numerator (den - n1 - n2) adds the three errors and
-//  two roundings.
+// Error bound of the FP32 hop test.  Node coordinates are stored as a grid
+// part (the coordinate rounded to the grid of 2^-24, also the hop
+// coordinate) and a remainder; the foot is exactly X.h + X.l and the hop test
+// uses X.h.  Every hop coordinate is within 2^-25 of the exact one, so every
+// difference is within 2^-24 + 2^-24 |d| of the exact difference, and a cross
+// product of differences whose |.|-sum is at most S is within
+// 2^-23 S + 2^-22 S^2 (two-fold margins).
 __device__ __forceinline__ float hop_bound(float S) { return S * __fmaf_rn(S, 0x1p-22f, 0x1p-23f) + 0x1p-46f; }
-//  double-float certification: differences within 2^-46, products and sums
-//  within 2^-45 relative: 2^-45 S + 2^-44 S^2.
-__device__ __forceinline__ float cert_bound(float S) { return S * __fmaf_rn(S, 0x1p-44f, 0x1p-45f); }
+
+// Coordinates in the certified test are pairs g + r: g on the grid of 2^-24
+// (mesh nodes are stored so, the foot is converted by to_grid), |r| <= 2^-24,
+// the pair within 2^-49 of the coordinate.  A difference of two such pairs is
+// (g1 - g2) + (r1 - r2): the first difference is exact in float, the second
+// is rounded once (|r1 - r2| <= 2^-23, error <= 2^-48).
+struct gd {
+    float g, r;
+};
+
+__device__ __forceinline__ gd gd_sub(float g1, float r1, float g2, float r2)
+{
+    gd d;
+    d.g = __fsub_rn(g1, g2);
+    d.r = __fsub_rn(r1, r2);
+    return d;
+}
+
+// x = g + r with g = x rounded to the grid of 2^-24 (x in [0, 1]): the
+// scaling by 2^24 and back is exact, and so is x.h - g.
+__device__ __forceinline__ void to_grid(df x, float &g, float &r)
+{
+    g = __fmul_rn(rintf(__fmul_rn(x.h, 16777216.0f)), 0x1p-24f);
+    r = __fadd_rn(__fsub_rn(x.h, g), x.l);
+}
+
+// u_x v_y - u_y v_x for differences u, v in the pair form, as a normalised
+// double-float: the products of the grid parts with their exact FMA
+// remainders, the cross terms accumulated by FMA, the two products summed by
+// TwoSum.  Error bound (S = |u_x.g| + |u_y.g| + |v_x.g| + |v_y.g|): the input
+// pairs are within 3 * 2^-49 of the exact differences (at most 2^-47 S),
+// every remainder |r| <= 2^-23 makes each FMA's rounding at most
+// 2^-24 (2^-24 |p| + 2^-23 (|u.g| + |v.g|)), and the final additions add
+// 2^-47 (|p| + |q| + S); with |p| + |q| <= S^2 / 4 everything stays below
+// cert_bound_g(S) = 2^-44 S + 2^-44 S^2 + 2^-64.
+__device__ __forceinline__ df cross_gd(gd ux, gd uy, gd vx, gd vy)
+{
+    const float p = __fmul_rn(ux.g, vy.g);
+    float e = __fmaf_rn(ux.g, vy.g, -p);
+    e = __fmaf_rn(ux.g, vy.r, e);
+    e = __fmaf_rn(ux.r, vy.g, e);
+    e = __fmaf_rn(ux.r, vy.r, e);
+    const float q = __fmul_rn(uy.g, vx.g);
+    float f = __fmaf_rn(uy.g, vx.g, -q);
+    f = __fmaf_rn(uy.g, vx.r, f);
+    f = __fmaf_rn(uy.r, vx.g, f);
+    f = __fmaf_rn(uy.r, vx.r, f);
+    float s, t;
+    two_sum_f(p, -q, s, t);
+    t = __fadd_rn(t, __fsub_rn(e, f));
+    df n;
+    fast_two_sum_f(s, t, n.h, n.l);
+    return n;
+}
+
+__device__ __forceinline__ float cert_bound_g(float S) { return S * __fmaf_rn(S, 0x1p-44f, 0x1p-44f) + 0x1p-64f; }
 
 // Exact signs of the edges selected by `need` (bit k: the edge opposite
 // W_k) of the triangle (W0, W1, W2), on the double coordinates and the exact
@@ -242,6 +295,11 @@ __device__ __forceinline__ void step_node(const FastArgs &a, int64_t i, int pi, 
         flags |= SL_NODE_CLIPPED;
         c.clipped = 1;
     }
+    // the foot in the (grid, remainder) form of the certified test
+    float Xg, Xr, Yg, Yr;
+    to_grid(X, Xg, Xr);
+    to_grid(Y, Yg, Yr);
+
     // start triangle and its vertex ids from the per-node cache (one
     // coalesced 16-byte load), or from the direct location on a structured
     // grid
@@ -266,22 +324,31 @@ __device__ __forceinline__ void step_node(const FastArgs &a, int64_t i, int pi, 
             w2 = a.tv[2][j];
             ids = true;
         }
+        // vertices as (grid, remainder) pairs: (gx, gy, rx, ry)
         const float4 A = a.xyq[w0], B = a.xyq[w1], C = a.xyq[w2];
-        const df cxh = df_make(C.x, C.z), cyh = df_make(C.y, C.w);
-        const df dAx = df_sub(df_make(A.x, A.z), cxh), dAy = df_sub(df_make(A.y, A.w), cyh);
-        const df dBx = df_sub(df_make(B.x, B.z), cxh), dBy = df_sub(df_make(B.y, B.w), cyh);
-        const df dXx = df_sub(X, cxh), dXy = df_sub(Y, cyh);
-        n1 = df_cross(dXx, dXy, dBx, dBy);      // orient(W1, W2, X): sign of theta of W0
-        n2 = df_cross(dAx, dAy, dXx, dXy);      // orient(W2, W0, X): sign of theta of W1
-        den = df_cross(dAx, dAy, dBx, dBy);     // orient(W0, W1, W2) > 0
-        const df n3 = df_sub(df_sub(den, n1), n2);
-        const float sA = fabsf(dAx.h) + fabsf(dAy.h), sB = fabsf(dBx.h) + fabsf(dBy.h);
-        const float sX = fabsf(dXx.h) + fabsf(dXy.h);
-        const float ea = cert_bound(sX + sB), eb = cert_bound(sA + sX), ed = cert_bound(sA + sB);
-        const float ec = ed + ea + eb + 0x1p-45f * (fabsf(den.h) + fabsf(n1.h) + fabsf(n2.h));
+        const gd dAx = gd_sub(A.x, A.z, C.x, C.z), dAy = gd_sub(A.y, A.w, C.y, C.w);
+        const gd dBx = gd_sub(B.x, B.z, C.x, C.z), dBy = gd_sub(B.y, B.w, C.y, C.w);
+        const gd dXx = gd_sub(Xg, Xr, C.x, C.z), dXy = gd_sub(Yg, Yr, C.y, C.w);
+        n1 = cross_gd(dXx, dXy, dBx, dBy);      // orient(W1, W2, X): sign of theta of W0
+        n2 = cross_gd(dAx, dAy, dXx, dXy);      // orient(W2, W0, X): sign of theta of W1
+        den = cross_gd(dAx, dAy, dBx, dBy);     // orient(W0, W1, W2) > 0
+        const float sA = fabsf(dAx.g) + fabsf(dAy.g), sB = fabsf(dBx.g) + fabsf(dBy.g);
+        const float sX = fabsf(dXx.g) + fabsf(dXy.g);
+        const float ea = cert_bound_g(sX + sB), eb = cert_bound_g(sA + sX), ed = cert_bound_g(sA + sB);
         s1 = n1.h > ea ? 1 : (n1.h < -ea ? -1 : 2);
         s2 = n2.h > eb ? 1 : (n2.h < -eb ? -1 : 2);
-        s3 = n3.h > ec ? 1 : (n3.h < -ec ? -1 : 2);
+        // theta of W2's numerator den - n1 - n2: first from the high parts
+        // (the low parts and two roundings add at most 2^-22 of the terms),
+        // in double-float only when that cannot decide
+        float n3h = __fsub_rn(__fsub_rn(den.h, n1.h), n2.h);
+        const float e3 = ed + ea + eb + 0x1p-22f * (fabsf(den.h) + fabsf(n1.h) + fabsf(n2.h));
+        s3 = n3h > e3 ? 1 : (n3h < -e3 ? -1 : 2);
+        if (s3 == 2) {
+            const df n3 = df_sub(df_sub(den, n1), n2);
+            const float ec = ed + ea + eb + 0x1p-45f * (fabsf(den.h) + fabsf(n1.h) + fabsf(n2.h));
+            n3h = n3.h;
+            s3 = n3.h > ec ? 1 : (n3.h < -ec ? -1 : 2);
+        }
         if (s1 == 2 || s2 == 2 || s3 == 2) {
             // a boundary edge with the foot on its side of the square: exactly 0
             // (fside: the sides the foot lies on, bit = boundary side code)
@@ -314,7 +381,7 @@ __device__ __forceinline__ void step_node(const FastArgs &a, int64_t i, int pi, 
             float best = 0.0f;
             if (s1 < 0) { k = 0; best = n1.h; }
             if (s2 < 0 && (k < 0 || n2.h < best)) { k = 1; best = n2.h; }
-            if (s3 < 0 && (k < 0 || n3.h < best)) { k = 2; best = n3.h; }
+            if (s3 < 0 && (k < 0 || n3h < best)) { k = 2; best = n3h; }
         } else {
             // after `cap` hops: randomised visibility walk (certified at
             // every triangle), which terminates on any triangulation
