@@ -546,7 +546,7 @@ double orc_interp(const orc_mesh *m, int32_t j, double X, double Y, const double
 }
 
 /* Smallest signed distance from (X, Y) to the three edge lines of triangle j
- * (positive inside).  Used by tests to judge near-degenerate feet. */
+ * (positive inside).  Used by tests to classify near-degenerate feet. */
 double orc_tri_margin(const orc_mesh *m, int32_t j, double X, double Y)
 {
     const int32_t *t = m->tri + 3 * (int64_t)j;

@@ -295,10 +295,18 @@ __device__ __forceinline__ void step_node(const FastArgs &a, int64_t i, int pi, 
         flags |= SL_NODE_CLIPPED;
         c.clipped = 1;
     }
-    // the foot in the (grid, remainder) form of the certified test
-    float Xg, Xr, Yg, Yr;
-    to_grid(X, Xg, Xr);
-    to_grid(Y, Yg, Yr);
+    // From here on the foot is its (grid, remainder) form, Xg + Xr exactly:
+    // within 2^-49 of the double-float foot, and the form the certified test
+    // needs (the exact stage takes any float pair).  The boundary decisions
+    // above are not affected: 0 and 1 are grid points.
+    {
+        float g, r;
+        to_grid(X, g, r);
+        X = df_make(g, r);
+        to_grid(Y, g, r);
+        Y = df_make(g, r);
+    }
+    const float &Xg = X.h, &Xr = X.l, &Yg = Y.h, &Yr = Y.l;
 
     // start triangle and its vertex ids from the per-node cache (one
     // coalesced 16-byte load), or from the direct location on a structured
@@ -431,12 +439,29 @@ __device__ __forceinline__ void step_node(const FastArgs &a, int64_t i, int pi, 
     }
     if (s1 == 0 || s2 == 0 || s3 == 0) flags |= SL_NODE_DEGENERATE;
 
-    // theta of W0, W1 by Eq. 6 and the P1 value (Remark 1), double-float
-    const df r = df_rcp(den);
-    const df th1 = df_mul(n1, r), th2 = df_mul(n2, r);
+    // the P1 value (Remark 1) with the barycentric coordinates of Eq. 6,
+    // theta_k = n_k / den:  V = v3 + (n1 (v1 - v3) + n2 (v2 - v3)) / den, in
+    // double-float: the value differences from a TwoSum of the high parts,
+    // the products from their exact FMA remainders, one division
     const float2 *vin = (const float2 *)a.vin;
-    const df v1 = dfp(vin[w0]), v2 = dfp(vin[w1]), v3 = dfp(vin[w2]);
-    const df v = df_add(v3, df_add(df_mul(th1, df_sub(v1, v3)), df_mul(th2, df_sub(v2, v3))));
+    const float2 V1 = vin[w0], V2 = vin[w1], V3 = vin[w2];
+    float d1h, d1l, d2h, d2l;
+    two_sum_f(V1.x, -V3.x, d1h, d1l);
+    d1l = __fadd_rn(d1l, __fsub_rn(V1.y, V3.y));
+    two_sum_f(V2.x, -V3.x, d2h, d2l);
+    d2l = __fadd_rn(d2l, __fsub_rn(V2.y, V3.y));
+    const float p1 = __fmul_rn(n1.h, d1h), p2 = __fmul_rn(n2.h, d2h);
+    float q1 = __fmaf_rn(n1.h, d1h, -p1), q2 = __fmaf_rn(n2.h, d2h, -p2);
+    q1 = __fmaf_rn(n1.h, d1l, q1);
+    q1 = __fmaf_rn(n1.l, d1h, q1);
+    q2 = __fmaf_rn(n2.h, d2l, q2);
+    q2 = __fmaf_rn(n2.l, d2h, q2);
+    float ws, wt;
+    two_sum_f(p1, p2, ws, wt);
+    wt = __fadd_rn(wt, __fadd_rn(q1, q2));
+    df w;
+    fast_two_sum_f(ws, wt, w.h, w.l);
+    const df v = df_add(dfp(V3), df_mul(w, df_rcp(den)));
     ((float2 *)a.vout)[i] = make_float2(v.h, v.l);
     if ((hops > 0 || (kExt && a.parent)) && !(kExt && a.keep_t0)) {
         a.t0[i] = j;
