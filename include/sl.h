@@ -144,9 +144,15 @@ typedef enum {
                                 per tree level and step, no graph (sl_run's use_graph is ignored);
                                 T^0_i holds the node's own foot triangle after each step.  Setting
                                 it resets T^0 to the initial incident triangles (synchronises). */
-    SL_OPT_OUTSIDE = 9       /* feet that leave the square: 0 = clip them to the boundary (default);
+    SL_OPT_OUTSIDE = 9,      /* feet that leave the square: 0 = clip them to the boundary (default);
                                 1 = exclude the node, as the paper's experiments do (Sec. 4):
                                 V^{n+1}_i = V^n_i, flag SL_NODE_EXCLUDED */
+    SL_OPT_SPLIT = 10        /* FP64 meshes, strategy (b), feet clipped: 0 = one fused kernel per
+                                step (default); 1 = two passes per step: a lean pass finishes
+                                every node whose foot is certainly inside its start triangle and
+                                queues the others for the full kernel (fewer registers where the
+                                feet move little).  Results are identical.  Never used for a step
+                                from the initial start triangles.  sl_autotune sets it. */
 } sl_option;
 
 /*
@@ -285,9 +291,10 @@ typedef struct {
     int32_t config_first;                 /* chosen SL_OPT_CONFIG_FIRST */
     int32_t config_rest;                  /* chosen SL_OPT_CONFIG */
     int32_t n_configs;                    /* configurations measured */
-    int32_t reserved;
+    int32_t split;                        /* chosen SL_OPT_SPLIT (FP64 meshes) */
     float first_ms[SL_TUNE_MAX_CONFIGS];  /* one step from the initial start triangles */
     float rest_ms[SL_TUNE_MAX_CONFIGS];   /* mean of the later steps */
+    float split_ms[SL_TUNE_MAX_CONFIGS];  /* mean of the later steps, split (FP64 meshes) */
 } sl_tune;
 
 /*
@@ -295,7 +302,9 @@ typedef struct {
  * this mesh and these problems by measurement: for every configuration, one
  * step from the initial start triangles and `probe_steps` later steps are
  * timed with CUDA events on `stream`; the fastest configuration of each
- * phase becomes SL_OPT_CONFIG_FIRST and SL_OPT_CONFIG.  v (device, N values,
+ * phase becomes SL_OPT_CONFIG_FIRST and SL_OPT_CONFIG.  On FP64 meshes the
+ * later steps are also timed split (SL_OPT_SPLIT = 1) in every
+ * configuration, and the faster form is kept.  v (device, N values,
  * V^0) and v_scratch (device, N values) are used as in sl_run; v, T^0 and
  * the statistics counters are restored before returning (the call
  * synchronises and allocates temporary device buffers).  No counterpart in

@@ -18,7 +18,7 @@ __all__ = [
     "SL_OK", "SL_E_ARG", "SL_E_MESH", "SL_E_NOMEM", "SL_E_CUDA", "SL_E_WALK_LIMIT", "SL_E_STATE",
     "SL_FP64", "SL_FP32", "SL_CURVE_NONE", "SL_CURVE_HILBERT", "SL_CURVE_MORTON",
     "SL_OPT_STATS", "SL_OPT_WALK_CAP", "SL_OPT_KERNEL", "SL_OPT_BLOCK", "SL_OPT_TILES_PER_SM", "SL_OPT_CONFIG",
-    "SL_OPT_CONFIG_FIRST", "SL_OPT_STRATEGY", "SL_OPT_OUTSIDE",
+    "SL_OPT_CONFIG_FIRST", "SL_OPT_STRATEGY", "SL_OPT_OUTSIDE", "SL_OPT_SPLIT",
     "SL_NODE_CLIPPED", "SL_NODE_DEGENERATE", "SL_NODE_EXACT", "SL_NODE_FALLBACK", "SL_NODE_WALK_LIMIT",
     "SL_NODE_RANGE", "SL_NODE_EXCLUDED", "SLError", "sl_problem", "problems", "pack_meshes",
     "sl_mesh_create", "sl_mesh_validate", "sl_mesh_reorder", "sl_step", "sl_run", "sl_run_host", "sl_mesh_get_t0",
@@ -31,7 +31,7 @@ SL_OK, SL_E_ARG, SL_E_MESH, SL_E_NOMEM, SL_E_CUDA, SL_E_WALK_LIMIT, SL_E_STATE =
 SL_FP64, SL_FP32 = 0, 1
 SL_CURVE_NONE, SL_CURVE_HILBERT, SL_CURVE_MORTON = 0, 1, 2
 SL_OPT_STATS, SL_OPT_WALK_CAP, SL_OPT_KERNEL, SL_OPT_BLOCK, SL_OPT_TILES_PER_SM, SL_OPT_CONFIG = range(6)
-SL_OPT_CONFIG_FIRST, SL_OPT_STRATEGY, SL_OPT_OUTSIDE = 7, 8, 9
+SL_OPT_CONFIG_FIRST, SL_OPT_STRATEGY, SL_OPT_OUTSIDE, SL_OPT_SPLIT = 7, 8, 9, 10
 SL_NODE_CLIPPED, SL_NODE_DEGENERATE, SL_NODE_EXACT, SL_NODE_FALLBACK, SL_NODE_WALK_LIMIT, SL_NODE_RANGE = (
     1, 2, 4, 8, 16, 32)
 SL_NODE_EXCLUDED = 64
@@ -67,7 +67,8 @@ class sl_debug(ctypes.Structure):
 
 class sl_tune(ctypes.Structure):
     _fields_ = [("config_first", ctypes.c_int32), ("config_rest", ctypes.c_int32), ("n_configs", ctypes.c_int32),
-                ("reserved", ctypes.c_int32), ("first_ms", ctypes.c_float * 8), ("rest_ms", ctypes.c_float * 8)]
+                ("split", ctypes.c_int32), ("first_ms", ctypes.c_float * 8), ("rest_ms", ctypes.c_float * 8),
+                ("split_ms", ctypes.c_float * 8)]
 
 
 class sl_stats(ctypes.Structure):
@@ -311,6 +312,7 @@ def sl_autotune(h, probs, probe_steps, v, v_scratch, stream=None):
     _check(library().sl_autotune(h, probs, int(probe_steps), _ptr(v), _ptr(v_scratch), ctypes.byref(t),
                                  _stream(stream)))
     n = t.n_configs
-    return {"config_first": t.config_first, "config_rest": t.config_rest,
+    return {"config_first": t.config_first, "config_rest": t.config_rest, "split": t.split,
             "first_ms": [round(float(x), 4) for x in list(t.first_ms)[:n]],
-            "rest_ms": [round(float(x), 4) for x in list(t.rest_ms)[:n]]}
+            "rest_ms": [round(float(x), 4) for x in list(t.rest_ms)[:n]],
+            "split_ms": [round(float(x), 4) for x in list(t.split_ms)[:n] if x >= 0]}

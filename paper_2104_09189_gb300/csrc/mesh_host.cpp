@@ -479,6 +479,10 @@ extern "C" sl_status sl_mesh_set_option(sl_mesh *m, int32_t option, int64_t valu
         if (st != SL_OK) return st;
         break;
     }
+    case SL_OPT_SPLIT:
+        if (value != 0 && value != 1) return sl::fail(SL_E_ARG, "split must be 0 or 1");
+        m->opt_split = (int32_t)value;
+        break;
     case SL_OPT_OUTSIDE:
         if (value != 0 && value != 1) return sl::fail(SL_E_ARG, "outside mode must be 0 (clip) or 1 (exclude)");
         m->opt_outside = (int32_t)value;

@@ -35,6 +35,8 @@ struct DeviceMesh {
     int32_t *t0_init = nullptr;       // the initial start triangles (global)
     void *t0v = nullptr;              // int4 (T^0, its vertex ids) per node
     void *grid_t0v = nullptr;         // int4 start state per structured-grid triangle (strategy 2)
+    int32_t *queue = nullptr;         // split steps: nodes left to the finish pass (N)
+    uint32_t *queue_count = nullptr;
     int32_t *tree_order = nullptr;    // strategy (c): nodes by spanning-tree level (N)
     int32_t *tree_parent = nullptr;   // strategy (c): parent of every node (N; the root its own)
     int64_t *node_off = nullptr;      // n_problems + 1
@@ -61,7 +63,7 @@ struct GraphCache {
     std::vector<uint8_t> probs;       // problems the graph was recorded with
     int32_t kernel = 0;
     int32_t stats = 0;
-    int32_t config = 0, config_first = 0;
+    int32_t config = 0, config_first = 0, split = 0;
     bool t0_initial = false;
 };
 
@@ -94,6 +96,7 @@ struct sl_mesh {
     int32_t grid_M = 0;               // cells per side when the mesh is a structured Courant grid
     std::vector<int64_t> tree_level_off;   // strategy (c): level k = tree_order[off[k], off[k+1])
     int32_t opt_outside = 0;          // 0 = clip feet that leave the square, 1 = exclude the node
+    int32_t opt_split = 0;            // 1 = split steps (settle pass + finish pass), FP64 meshes
     bool t0_initial = true;           // T^0 holds the initial start triangles
     int32_t sms = 0;                  // multiprocessors of the device
     bool stepped = false;

@@ -239,6 +239,86 @@ __device__ __forceinline__ int random_negative_edge(int64_t i, uint32_t hops, in
     return k;
 }
 
+// The three barycentric numerators of the foot X (pair form) in the triangle
+// (A, B, C) (vertex pairs (gx, gy, rx, ry)), relative to C, with their
+// certification bounds:  n1 = orient(B, C, X) (theta of A), n2 = orient(C, A,
+// X) (theta of B), den = orient(A, B, C) > 0, and theta of C's numerator
+// den - n1 - n2 from the high parts, n3h, with its bound e3 (the low parts
+// and two roundings add at most 2^-22 of the terms).
+struct Certified {
+    df n1, n2, den;
+    float ea, eb, ed, n3h, e3;
+};
+
+__device__ __forceinline__ Certified certify(float4 A, float4 B, float4 C, float Xg, float Xr, float Yg, float Yr)
+{
+    const gd dAx = gd_sub(A.x, A.z, C.x, C.z), dAy = gd_sub(A.y, A.w, C.y, C.w);
+    const gd dBx = gd_sub(B.x, B.z, C.x, C.z), dBy = gd_sub(B.y, B.w, C.y, C.w);
+    const gd dXx = gd_sub(Xg, Xr, C.x, C.z), dXy = gd_sub(Yg, Yr, C.y, C.w);
+    Certified t;
+    t.n1 = cross_gd(dXx, dXy, dBx, dBy);
+    t.n2 = cross_gd(dAx, dAy, dXx, dXy);
+    t.den = cross_gd(dAx, dAy, dBx, dBy);
+    const float sA = fabsf(dAx.g) + fabsf(dAy.g), sB = fabsf(dBx.g) + fabsf(dBy.g);
+    const float sX = fabsf(dXx.g) + fabsf(dXy.g);
+    t.ea = cert_bound_g(sX + sB);
+    t.eb = cert_bound_g(sA + sX);
+    t.ed = cert_bound_g(sA + sB);
+    t.n3h = __fsub_rn(__fsub_rn(t.den.h, t.n1.h), t.n2.h);
+    t.e3 = t.ed + t.ea + t.eb + 0x1p-22f * (fabsf(t.den.h) + fabsf(t.n1.h) + fabsf(t.n2.h));
+    return t;
+}
+
+// The P1 value (Remark 1) with the barycentric coordinates of Eq. 6,
+// theta_k = n_k / den:  V = v3 + (n1 (v1 - v3) + n2 (v2 - v3)) / den, in
+// double-float: the value differences from a TwoSum of the high parts, the
+// products from their exact FMA remainders, one division.
+__device__ __forceinline__ float2 p1_value(const FastArgs &a, int w0, int w1, int w2, df n1, df n2, df den)
+{
+    const float2 *vin = (const float2 *)a.vin;
+    const float2 V1 = vin[w0], V2 = vin[w1], V3 = vin[w2];
+    float d1h, d1l, d2h, d2l;
+    two_sum_f(V1.x, -V3.x, d1h, d1l);
+    d1l = __fadd_rn(d1l, __fsub_rn(V1.y, V3.y));
+    two_sum_f(V2.x, -V3.x, d2h, d2l);
+    d2l = __fadd_rn(d2l, __fsub_rn(V2.y, V3.y));
+    const float p1 = __fmul_rn(n1.h, d1h), p2 = __fmul_rn(n2.h, d2h);
+    float q1 = __fmaf_rn(n1.h, d1h, -p1), q2 = __fmaf_rn(n2.h, d2h, -p2);
+    q1 = __fmaf_rn(n1.h, d1l, q1);
+    q1 = __fmaf_rn(n1.l, d1h, q1);
+    q2 = __fmaf_rn(n2.h, d2l, q2);
+    q2 = __fmaf_rn(n2.l, d2h, q2);
+    float ws, wt;
+    two_sum_f(p1, p2, ws, wt);
+    wt = __fadd_rn(wt, __fadd_rn(q1, q2));
+    df w;
+    fast_two_sum_f(ws, wt, w.h, w.l);
+    const df v = df_add(dfp(V3), df_mul(w, df_rcp(den)));
+    return make_float2(v.h, v.l);
+}
+
+// The foot of node i for this step: Euler (Eq. 4) in double-float, decided
+// against the boundary in double rounding, clipped, and returned in the
+// (grid, remainder) form of the certified test.  Returns true when clipped.
+__device__ __forceinline__ bool foot_pair(const FastArgs &a, int64_t i, const FastProb &P, df &X, df &Y)
+{
+    const float4 xq = a.xyq[i];
+    const df x = df_make(xq.x, xq.z), y = df_make(xq.y, xq.w);
+    foot_df(P, a, i, x, y, X, Y);
+    round_boundary(X);
+    round_boundary(Y);
+    return clip_df(x, y, X, Y);
+}
+
+__device__ __forceinline__ void foot_to_grid(df &X, df &Y)
+{
+    float g, r;
+    to_grid(X, g, r);
+    X = df_make(g, r);
+    to_grid(Y, g, r);
+    Y = df_make(g, r);
+}
+
 struct NodeCounters {
     uint32_t hops = 0, exact = 0, clipped = 0, fallback = 0, limit = 0, filter2 = 0, excluded = 0;
 };
@@ -334,23 +414,15 @@ __device__ __forceinline__ void step_node(const FastArgs &a, int64_t i, int pi, 
         }
         // vertices as (grid, remainder) pairs: (gx, gy, rx, ry)
         const float4 A = a.xyq[w0], B = a.xyq[w1], C = a.xyq[w2];
-        const gd dAx = gd_sub(A.x, A.z, C.x, C.z), dAy = gd_sub(A.y, A.w, C.y, C.w);
-        const gd dBx = gd_sub(B.x, B.z, C.x, C.z), dBy = gd_sub(B.y, B.w, C.y, C.w);
-        const gd dXx = gd_sub(Xg, Xr, C.x, C.z), dXy = gd_sub(Yg, Yr, C.y, C.w);
-        n1 = cross_gd(dXx, dXy, dBx, dBy);      // orient(W1, W2, X): sign of theta of W0
-        n2 = cross_gd(dAx, dAy, dXx, dXy);      // orient(W2, W0, X): sign of theta of W1
-        den = cross_gd(dAx, dAy, dBx, dBy);     // orient(W0, W1, W2) > 0
-        const float sA = fabsf(dAx.g) + fabsf(dAy.g), sB = fabsf(dBx.g) + fabsf(dBy.g);
-        const float sX = fabsf(dXx.g) + fabsf(dXy.g);
-        const float ea = cert_bound_g(sX + sB), eb = cert_bound_g(sA + sX), ed = cert_bound_g(sA + sB);
+        const Certified t = certify(A, B, C, Xg, Xr, Yg, Yr);
+        n1 = t.n1;
+        n2 = t.n2;
+        den = t.den;
+        const float ea = t.ea, eb = t.eb, ed = t.ed;
         s1 = n1.h > ea ? 1 : (n1.h < -ea ? -1 : 2);
         s2 = n2.h > eb ? 1 : (n2.h < -eb ? -1 : 2);
-        // theta of W2's numerator den - n1 - n2: first from the high parts
-        // (the low parts and two roundings add at most 2^-22 of the terms),
-        // in double-float only when that cannot decide
-        float n3h = __fsub_rn(__fsub_rn(den.h, n1.h), n2.h);
-        const float e3 = ed + ea + eb + 0x1p-22f * (fabsf(den.h) + fabsf(n1.h) + fabsf(n2.h));
-        s3 = n3h > e3 ? 1 : (n3h < -e3 ? -1 : 2);
+        float n3h = t.n3h;
+        s3 = n3h > t.e3 ? 1 : (n3h < -t.e3 ? -1 : 2);
         if (s3 == 2) {
             const df n3 = df_sub(df_sub(den, n1), n2);
             const float ec = ed + ea + eb + 0x1p-45f * (fabsf(den.h) + fabsf(n1.h) + fabsf(n2.h));
@@ -439,30 +511,8 @@ __device__ __forceinline__ void step_node(const FastArgs &a, int64_t i, int pi, 
     }
     if (s1 == 0 || s2 == 0 || s3 == 0) flags |= SL_NODE_DEGENERATE;
 
-    // the P1 value (Remark 1) with the barycentric coordinates of Eq. 6,
-    // theta_k = n_k / den:  V = v3 + (n1 (v1 - v3) + n2 (v2 - v3)) / den, in
-    // double-float: the value differences from a TwoSum of the high parts,
-    // the products from their exact FMA remainders, one division
-    const float2 *vin = (const float2 *)a.vin;
-    const float2 V1 = vin[w0], V2 = vin[w1], V3 = vin[w2];
-    float d1h, d1l, d2h, d2l;
-    two_sum_f(V1.x, -V3.x, d1h, d1l);
-    d1l = __fadd_rn(d1l, __fsub_rn(V1.y, V3.y));
-    two_sum_f(V2.x, -V3.x, d2h, d2l);
-    d2l = __fadd_rn(d2l, __fsub_rn(V2.y, V3.y));
-    const float p1 = __fmul_rn(n1.h, d1h), p2 = __fmul_rn(n2.h, d2h);
-    float q1 = __fmaf_rn(n1.h, d1h, -p1), q2 = __fmaf_rn(n2.h, d2h, -p2);
-    q1 = __fmaf_rn(n1.h, d1l, q1);
-    q1 = __fmaf_rn(n1.l, d1h, q1);
-    q2 = __fmaf_rn(n2.h, d2l, q2);
-    q2 = __fmaf_rn(n2.l, d2h, q2);
-    float ws, wt;
-    two_sum_f(p1, p2, ws, wt);
-    wt = __fadd_rn(wt, __fadd_rn(q1, q2));
-    df w;
-    fast_two_sum_f(ws, wt, w.h, w.l);
-    const df v = df_add(dfp(V3), df_mul(w, df_rcp(den)));
-    ((float2 *)a.vout)[i] = make_float2(v.h, v.l);
+    // the P1 value (Remark 1) with the barycentric coordinates of Eq. 6
+    ((float2 *)a.vout)[i] = p1_value(a, w0, w1, w2, n1, n2, den);
     if ((hops > 0 || (kExt && a.parent)) && !(kExt && a.keep_t0)) {
         a.t0[i] = j;
         a.t0v[i] = make_int4(3 * j, w0, w1, w2);
@@ -494,6 +544,136 @@ __global__ void __launch_bounds__(kBlock, kMinBlocks) k_step_fast_df(FastArgs a)
                                    : block_problem(a.node_off, a.nprob, a.N, i);
     if (active) step_node<kDebug, kExt>(a, i, pi, c);
     if (kStats) warp_stats(a.stats, active, c.hops, c.exact, c.clipped, c.fallback, c.limit, c.filter2, c.excluded);
+}
+
+// Settle pass of a split step: the nodes whose foot is certainly inside the
+// start triangle (all three signs certified positive, no hop, no exact
+// stage) are finished here with a lean kernel; every other node is appended
+// to the queue for the finish pass, which runs the full node step on it.  The
+// foot, the certified test and the value are the same functions as in
+// step_node, so the split does not change any result.
+template <bool kDebug>
+__device__ __forceinline__ bool settle_node(const FastArgs &a, int64_t i, int pi, NodeCounters &c)
+{
+    const FastProb &P = a.probs[pi];
+    df X, Y;
+    const bool clipped = foot_pair(a, i, P, X, Y);
+    foot_to_grid(X, Y);
+    const int4 tq = a.t0v[i];
+    const float4 A = a.xyq[tq.y], B = a.xyq[tq.z], C = a.xyq[tq.w];
+    const Certified t = certify(A, B, C, X.h, X.l, Y.h, Y.l);
+    if (!(t.n1.h > t.ea && t.n2.h > t.eb && t.n3h > t.e3)) return false;
+    ((float2 *)a.vout)[i] = p1_value(a, tq.y, tq.z, tq.w, t.n1, t.n2, t.den);
+    c.clipped = clipped;
+    if (kDebug) {
+        if (a.dbg.feet) {
+            a.dbg.feet[2 * i] = (double)X.h + (double)X.l;
+            a.dbg.feet[2 * i + 1] = (double)Y.h + (double)Y.l;
+        }
+        if (a.dbg.tri) a.dbg.tri[i] = tri_of(tq.x);
+        if (a.dbg.moves) a.dbg.moves[i] = 0;
+        if (a.dbg.flags) a.dbg.flags[i] = (uint8_t)(clipped ? SL_NODE_CLIPPED : 0u);
+    }
+    return true;
+}
+
+template <bool kStats, bool kDebug, int kBlock, int kMinBlocks>
+__global__ void __launch_bounds__(kBlock, kMinBlocks) k_settle_df(FastArgs a)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const bool active = i < a.N;
+    NodeCounters c;
+    const int pi = block_problem(a.node_off, a.nprob, a.N, i);
+    const bool queued = active && !settle_node<kDebug>(a, i, pi, c);
+    // warp-aggregated append to the queue of the finish pass
+    const unsigned mask = __ballot_sync(0xffffffffu, queued);
+    if (mask) {
+        const int lane = threadIdx.x & 31, leader = __ffs(mask) - 1;
+        uint32_t base = 0;
+        if (lane == leader) base = atomicAdd(a.queue_count, (uint32_t)__popc(mask));
+        base = __shfl_sync(0xffffffffu, base, leader);
+        if (queued) a.queue[base + (uint32_t)__popc(mask & ((1u << lane) - 1u))] = (int32_t)i;
+    }
+    if (kStats) warp_stats(a.stats, active && !queued, 0u, 0u, active && !queued ? c.clipped : 0u, 0u, 0u);
+}
+
+// Finish pass: the full node step (certified walk, exact stage, value) for
+// the queued nodes, a persistent grid striding over the queue.
+template <bool kStats, bool kDebug>
+__global__ void __launch_bounds__(128, 8) k_finish_df(FastArgs a)
+{
+    const uint32_t count = *a.queue_count;
+    NodeCounters tot;
+    uint32_t done = 0, hmax = 0;
+    for (uint32_t q = blockIdx.x * blockDim.x + threadIdx.x; q < count; q += gridDim.x * blockDim.x) {
+        NodeCounters c;
+        const int64_t i = a.queue[q];
+        step_node<kDebug, false>(a, i, a.nprob == 1 ? 0 : problem_of(a.node_off, a.nprob, i), c);
+        tot.hops += c.hops;
+        hmax = c.hops > hmax ? c.hops : hmax;
+        tot.exact += c.exact;
+        tot.filter2 += c.filter2;
+        tot.clipped += c.clipped;
+        tot.fallback += c.fallback;
+        tot.limit += c.limit;
+        ++done;
+    }
+    if (kStats) {
+        // a thread may have finished several nodes: its sums go in whole
+        const unsigned full = 0xffffffffu;
+        const unsigned n = __reduce_add_sync(full, done), h = __reduce_add_sync(full, tot.hops);
+        const unsigned hm = __reduce_max_sync(full, hmax), e = __reduce_add_sync(full, tot.exact);
+        const unsigned f2 = __reduce_add_sync(full, tot.filter2), cl = __reduce_add_sync(full, tot.clipped);
+        const unsigned fb = __reduce_add_sync(full, tot.fallback), l = __reduce_add_sync(full, tot.limit);
+        if ((threadIdx.x & 31) == 0) {
+            if (n) atomicAdd(&a.stats[0], (unsigned long long)n);
+            if (h) atomicAdd(&a.stats[1], (unsigned long long)h);
+            if (hm) atomicMax(&a.stats[2], (unsigned long long)hm);
+            if (e) atomicAdd(&a.stats[3], (unsigned long long)e);
+            if (f2) atomicAdd(&a.stats[4], (unsigned long long)f2);
+            if (cl) atomicAdd(&a.stats[5], (unsigned long long)cl);
+            if (fb) atomicAdd(&a.stats[6], (unsigned long long)fb);
+            if (l) atomicAdd(&a.stats[7], (unsigned long long)l);
+        }
+    }
+}
+
+template <int kBlock, int kMinBlocks>
+static void launch_split_cfg(const FastArgs &a, bool stats, bool debug, int sms, cudaStream_t s)
+{
+    const unsigned grid = (unsigned)((a.N + kBlock - 1) / kBlock);
+    if (grid == 0) return;
+    cudaMemsetAsync(a.queue_count, 0, sizeof(uint32_t), s);
+    if (stats) {
+        if (debug) k_settle_df<true, true, kBlock, kMinBlocks><<<grid, kBlock, 0, s>>>(a);
+        else k_settle_df<true, false, kBlock, kMinBlocks><<<grid, kBlock, 0, s>>>(a);
+    } else {
+        if (debug) k_settle_df<false, true, kBlock, kMinBlocks><<<grid, kBlock, 0, s>>>(a);
+        else k_settle_df<false, false, kBlock, kMinBlocks><<<grid, kBlock, 0, s>>>(a);
+    }
+    const unsigned g2 = (unsigned)(sms > 0 ? sms : 152) * 8u;
+    if (stats) {
+        if (debug) k_finish_df<true, true><<<g2, 128, 0, s>>>(a);
+        else k_finish_df<true, false><<<g2, 128, 0, s>>>(a);
+    } else {
+        if (debug) k_finish_df<false, true><<<g2, 128, 0, s>>>(a);
+        else k_finish_df<false, false><<<g2, 128, 0, s>>>(a);
+    }
+}
+
+// A split step (settle pass + finish pass over the queue); the settle pass
+// runs in launch configuration `config` (as launch_fast_df).  The caller
+// provides a.queue (N entries) and a.queue_count.
+void launch_split_df(const FastArgs &a, bool stats, bool debug, int config, int sms, cudaStream_t s)
+{
+    switch (config) {
+    case 1: launch_split_cfg<256, 3>(a, stats, debug, sms, s); break;
+    case 2: launch_split_cfg<128, 8>(a, stats, debug, sms, s); break;
+    case 3: launch_split_cfg<128, 9>(a, stats, debug, sms, s); break;
+    case 4: launch_split_cfg<256, 5>(a, stats, debug, sms, s); break;
+    case 5: launch_split_cfg<128, 12>(a, stats, debug, sms, s); break;
+    default: launch_split_cfg<256, 4>(a, stats, debug, sms, s); break;
+    }
 }
 
 template <int kBlock, int kMinBlocks, bool kExt = false>

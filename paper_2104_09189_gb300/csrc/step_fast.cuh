@@ -58,10 +58,15 @@ struct FastArgs {
     const int32_t *order;
     const int32_t *parent;
     int64_t base, count;
+    // split steps: the nodes the settle pass leaves to the finish pass
+    int32_t *queue;
+    uint32_t *queue_count;
 };
 
 // config: launch configuration 0..kFastConfigs-1 (see step_fast.cu)
 void launch_fast_df(const FastArgs &a, bool stats, bool debug, int config, cudaStream_t s);
+// a split step: lean settle pass (configuration `config`) + finish pass
+void launch_split_df(const FastArgs &a, bool stats, bool debug, int config, int sms, cudaStream_t s);
 constexpr int kFastConfigs = 6;
 void launch_fast_f32(const FastArgs &a, bool stats, bool debug, int config, cudaStream_t s);
 

@@ -297,3 +297,49 @@ def test_boundary_nodes_with_nearly_tangent_velocity(kernel, fx):
     assert np.array_equal((res["flags"] & sl.SL_NODE_CLIPPED) != 0, (ofl & oracle.FLAG_CLIPPED) != 0)
     assert np.abs(res["v"] - ov).max() <= 1e-12 * np.abs(ov).max()
     g.close()
+
+
+@pytest.mark.parametrize("name", ["C2", "C3"])
+def test_split_steps_are_bitwise_identical(name):
+    """SL_OPT_SPLIT: the settle pass finishes the nodes whose foot is
+    certainly inside their start triangle and the finish pass the rest, with
+    the same arithmetic as the fused kernel: values, T^0 and the walk
+    statistics are bitwise those of the fused step (moving feet: swirl;
+    stationary ones: rotation)."""
+    prob = si.config(name, M=192)
+    outs = []
+    for split in (0, 1):
+        g = GpuRun(prob.mesh, prob.field, prob.dt, curve=sl.SL_CURVE_HILBERT)
+        sl.sl_mesh_set_option(g.h, sl.SL_OPT_SPLIT, split)
+        sl.sl_mesh_set_option(g.h, sl.SL_OPT_STATS, 1)
+        v = g.to_dev(prob.v0)
+        w = g.torch.empty_like(v)
+        sl.sl_run(g.h, g.probs, 0, 6, v, w, use_graph=True)
+        t0 = g.torch.empty(prob.mesh.n_nodes, dtype=g.torch.int32, device=g.dev)
+        sl.sl_mesh_get_t0(g.h, t0)
+        st = sl.sl_mesh_stats(g.h)
+        outs.append((g.from_dev(v), t0.cpu().numpy(), st))
+        g.close()
+    (v0, t00, s0), (v1, t01, s1) = outs
+    assert np.array_equal(v0, v1)
+    assert np.array_equal(t00, t01)
+    for k in ("node_updates", "walk_moves", "max_moves", "exact_tests", "clipped", "fallbacks"):
+        assert s0[k] == s1[k], k
+
+
+def test_split_steps_match_the_oracle_with_debug_outputs():
+    prob = si.config("C2", M=128)
+    om = oracle.OracleMesh(prob.mesh.xy, prob.mesh.tri)
+    g = GpuRun(prob.mesh, prob.field, prob.dt, curve=sl.SL_CURVE_HILBERT)
+    sl.sl_mesh_set_option(g.h, sl.SL_OPT_SPLIT, 1)
+    v = g.to_dev(prob.v0)
+    vo = prob.v0
+    for n in range(4):
+        v, res = g.step(n, v)
+        ov, otri, _, oft = om.step(prob.field.kind, prob.field.packed(), prob.dt, n, vo)
+        compare_step(om, res, ov, otri, oft)
+        if n > 0:
+            assert (res["moves"] == 0).mean() > 0.05      # both passes did work
+            assert (res["moves"] > 0).mean() > 0.05
+        vo = ov
+    g.close()
