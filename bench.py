@@ -54,6 +54,8 @@ def parse():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-plain", action="store_true", help="skip the plain FP64 kernel comparison")
+    ap.add_argument("--split", type=int, choices=[0, 1], default=None,
+                    help="SL_OPT_SPLIT for the later steps (default: chosen by sl_autotune)")
     ap.add_argument("--study", choices=["courant", "structured"], default=None,
                     help="the paper's studies (Sec. 4), one JSON line: 'courant' = mean hops per "
                          "node-update and time per step against the Courant number for strategies (a) "
@@ -180,10 +182,12 @@ def build_workload(args):
 TRAFFIC_SOURCES = ("step_fast.cu", "step_fast.cuh", "df.cuh", "predicates.cuh", "step_common.cuh", "step_kernels.cuh")
 
 
-def committed_traffic(workload_key):
-    """DRAM bytes per launch of the dominant kernel from the committed ncu
+def committed_traffic(workload_key, split=0):
+    """DRAM bytes per step of the dominant kernel (the fused step kernel, or
+    the settle + finish passes of a split step) from the committed ncu
     summary (profiles/k_step_fast_df_c3_traffic.md), or None when the kernel
-    sources changed since that capture or the workload differs."""
+    sources changed since that capture, the workload differs or the form was
+    not captured."""
     import hashlib
     here = os.path.dirname(os.path.abspath(__file__))
     path = os.path.join(here, "profiles", "k_step_fast_df_c3_traffic.md")
@@ -199,7 +203,8 @@ def committed_traffic(workload_key):
         h.update(open(os.path.join(here, "paper_2104_09189_gb300", "csrc", f), "rb").read())
     if fields.get("source_sha256") != h.hexdigest() or fields.get("workload") != workload_key:
         return None
-    return float(fields["traffic_bytes_per_launch"])
+    key = "traffic_bytes_per_step_split" if split else "traffic_bytes_per_step_fused"
+    return float(fields[key]) if key in fields else None
 
 
 def measured_peaks():
@@ -466,6 +471,9 @@ def main():
     tune = None
     if args.config_id is None and args.kernel != 1:
         tune = sl.sl_autotune(h, probs, 3, v, w)
+    if args.split is not None:
+        sl.sl_mesh_set_option(h, sl.SL_OPT_SPLIT, args.split)
+    split = (args.split if args.split is not None else (tune or {}).get("split", 0)) if prec == sl.SL_FP64 else 0
     setup_s = time.perf_counter() - t_setup
 
     def one_run():
@@ -614,17 +622,19 @@ def main():
         "config": workload_config(args, wl),
         "roofline": {"bound": "hbm", "achieved": achieved_gbs, "peak": peaks.get("hbm_gbs", 6800.0),
                      "unit": "GB/s", "frac": achieved_gbs / peaks.get("hbm_gbs", 6800.0),
-                     "traffic": (committed_traffic(f"{args.config} {wl.precision}")
+                     "traffic": (committed_traffic(f"{args.config} {wl.precision}", split)
                                  if args.kernel != 1 and args.cells is None else None),
                      "peak_source": peak_src,
                      "algorithmic_bytes_per_node": bpn,
                      "kernel": ("k_step_plain_f64" if args.kernel == 1 else
-                                ("k_step_fast_df" if prec == sl.SL_FP64 else "k_step_fast_f32"))
-                               + " (one launch = one SL step over all nodes; duration = timed region / launches)",
+                                ("k_step_fast_df" + (" (later steps split: k_settle_df + k_finish_df)" if split else "")
+                                 if prec == sl.SL_FP64 else "k_step_fast_f32"))
+                               + " (one step over all nodes; duration = timed region / steps)",
                      "launch_ms": launch_s * 1e3},
         "cpu_baseline": cpu,
         "e2e": e2e,
-        "gpu_launches": args.steps * launches_per_run(S, prec == sl.SL_FP64 and args.kernel != 1),
+        "gpu_launches": args.steps * (launches_per_run(S, prec == sl.SL_FP64 and args.kernel != 1)
+                                      + (S - 1 if split else 0)),
         "clocks": clocks,
         "walk": {"first_run_mean_hops_per_node_update": stats["walk_moves"] / max(1, stats["node_updates"]),
                  "max_hops": stats["max_moves"], "exact_tests": stats["exact_tests"],
