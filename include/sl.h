@@ -294,7 +294,7 @@ typedef struct {
     int32_t split;                        /* chosen SL_OPT_SPLIT (FP64 meshes) */
     float first_ms[SL_TUNE_MAX_CONFIGS];  /* one step from the initial start triangles */
     float rest_ms[SL_TUNE_MAX_CONFIGS];   /* mean of the later steps */
-    float split_ms[SL_TUNE_MAX_CONFIGS];  /* mean of the later steps, split (FP64 meshes) */
+    float split_ms[SL_TUNE_MAX_CONFIGS];  /* [0]: mean of the later steps, split (FP64 meshes) */
 } sl_tune;
 
 /*
@@ -303,8 +303,8 @@ typedef struct {
  * step from the initial start triangles and `probe_steps` later steps are
  * timed with CUDA events on `stream`; the fastest configuration of each
  * phase becomes SL_OPT_CONFIG_FIRST and SL_OPT_CONFIG.  On FP64 meshes the
- * later steps are also timed split (SL_OPT_SPLIT = 1) in every
- * configuration, and the faster form is kept.  v (device, N values,
+ * later steps are also timed split (SL_OPT_SPLIT = 1, whose passes have a
+ * launch shape of their own), and the faster form is kept.  v (device, N values,
  * V^0) and v_scratch (device, N values) are used as in sl_run; v, T^0 and
  * the statistics counters are restored before returning (the call
  * synchronises and allocates temporary device buffers).  No counterpart in

@@ -382,7 +382,7 @@ static sl_status launch_fast(sl_mesh *m, const FastArgs &a, bool debug, int conf
         FastArgs x = a;
         x.queue = m->d.queue;
         x.queue_count = m->d.queue_count;
-        launch_split_df(x, m->opt_stats != 0, debug, config, m->sms, s);
+        launch_split_df(x, m->opt_stats != 0, debug, m->sms, s);
     } else {
         for_levels(m, a, [&](const FastArgs &x) {
             if (m->precision == SL_FP64) launch_fast_df(x, m->opt_stats != 0, debug, config, s);
@@ -855,12 +855,13 @@ extern "C" sl_status sl_autotune(sl_mesh *m, const sl_problem *probs, int32_t pr
             if (g < best_rest) { best_rest = g; out->config_rest = c; }
         }
         if (m->precision == SL_FP64) {
-            // the later steps split into a settle pass and a finish pass
+            // the later steps split into a settle pass and a finish pass (one
+            // launch shape of their own; timed once, first step as chosen)
             m->opt_split = 1;
             sl_status r = ensure_queue(m);
             if (r != SL_OK) return r;
-            for (int c = 0; c < kFastConfigs && c < SL_TUNE_MAX_CONFIGS; ++c) {
-                m->opt_config = m->opt_config_first = c;
+            for (int c = 0; c < 1; ++c) {
+                m->opt_config = m->opt_config_first = out->config_first;
                 SL_CUDA(cudaMemcpyAsync(v, v_save, vbytes, cudaMemcpyDeviceToDevice, s));
                 r = sl_mesh_reset_t0(m, s);
                 if (r != SL_OK) return r;
@@ -878,7 +879,6 @@ extern "C" sl_status sl_autotune(sl_mesh *m, const sl_problem *probs, int32_t pr
                 out->split_ms[c] = g;
                 if (g < best_rest) {
                     best_rest = g;
-                    out->config_rest = c;
                     out->split = 1;
                 }
             }

@@ -65,8 +65,8 @@ struct FastArgs {
 
 // config: launch configuration 0..kFastConfigs-1 (see step_fast.cu)
 void launch_fast_df(const FastArgs &a, bool stats, bool debug, int config, cudaStream_t s);
-// a split step: lean settle pass (configuration `config`) + finish pass
-void launch_split_df(const FastArgs &a, bool stats, bool debug, int config, int sms, cudaStream_t s);
+// a split step: lean settle pass + finish pass over its queue
+void launch_split_df(const FastArgs &a, bool stats, bool debug, int sms, cudaStream_t s);
 constexpr int kFastConfigs = 6;
 void launch_fast_f32(const FastArgs &a, bool stats, bool debug, int config, cudaStream_t s);
 
