@@ -319,6 +319,35 @@ __device__ __forceinline__ void foot_to_grid(df &X, df &Y)
     Y = df_make(g, r);
 }
 
+// FP32 hops on the high parts while one of the two exits of the current
+// triangle (W0, W1, W2) = (p0, p1, p2), entered through its third edge, is
+// certainly negative (hop_bound); e0, e1: the half-edge codes of the edges
+// opposite W0 and W1.  One 16-byte half-edge record per hop.
+__device__ __forceinline__ void lean_hops(const FastArgs &a, float fx, float fy, float &p0x, float &p0y, float &p1x,
+                                          float &p1y, float &p2x, float &p2y, int32_t &e0, int32_t &e1,
+                                          uint32_t &hops, uint32_t cap)
+{
+    while (hops < cap) {
+        const float ax = p0x - p2x, ay = p0y - p2y, bx = p1x - p2x, by = p1y - p2y;
+        const float xx = fx - p2x, xy = fy - p2y;
+        const float o1 = __fmaf_rn(xx, by, -__fmul_rn(xy, bx));    // ~ theta of W0 * den
+        const float o2 = __fmaf_rn(ax, xy, -__fmul_rn(ay, xx));    // ~ theta of W1 * den
+        const float S = fabsf(ax) + fabsf(ay) + fabsf(bx) + fabsf(by) + fabsf(xx) + fabsf(xy);
+        const float e = hop_bound(S);
+        const bool c1 = o1 < -e, c2 = o2 < -e && !(c1 && o1 <= o2);
+        if (!(c1 || c2)) break;
+        const float4 Q = __ldg(&a.he[c2 ? e1 : e0]);
+        if (__float_as_int(Q.z) < 0) break;    // a boundary edge: not for a foot inside a valid mesh
+        if (c2) { p1x = p2x; p1y = p2y; }
+        else { p0x = p2x; p0y = p2y; }
+        p2x = Q.x;
+        p2y = Q.y;
+        e0 = __float_as_int(Q.z);
+        e1 = __float_as_int(Q.w);
+        ++hops;
+    }
+}
+
 struct NodeCounters {
     uint32_t hops = 0, exact = 0, clipped = 0, fallback = 0, limit = 0, filter2 = 0, excluded = 0;
 };
@@ -402,6 +431,42 @@ __device__ __forceinline__ void step_node(const FastArgs &a, int64_t i, int pi, 
     bool found = false;
     int s1 = 0, s2 = 0, s3 = 0;
     df n1, n2, den;
+    if (cap > 0) {
+        // A foot that moved is usually clear of its start triangle: test the
+        // three edges of T^0 in FP32 first and, when one is certainly
+        // negative, hop at once (the certified test then runs where the FP32
+        // walk stops).  The vertex pairs come through L1, where a certified
+        // test of T^0 finds them again.
+        const float4 A = a.xyq[w0], B = a.xyq[w1], C = a.xyq[w2];
+        const float ax = A.x - C.x, ay = A.y - C.y, bx = B.x - C.x, by = B.y - C.y;
+        const float xx = X.h - C.x, xy = Y.h - C.y;
+        const float o1 = __fmaf_rn(xx, by, -__fmul_rn(xy, bx));
+        const float o2 = __fmaf_rn(ax, xy, -__fmul_rn(ay, xx));
+        const float dn = __fmaf_rn(ax, by, -__fmul_rn(ay, bx));
+        const float o3 = dn - o1 - o2;
+        const float S = fabsf(ax) + fabsf(ay) + fabsf(bx) + fabsf(by) + fabsf(xx) + fabsf(xy);
+        const float e = hop_bound(S);
+        const float e3 = 3.0f * e + 0x1p-23f * (fabsf(dn) + fabsf(o1) + fabsf(o2));
+        int k = -1;
+        float best = 0.0f;
+        if (o1 < -e) { k = 0; best = o1; }
+        if (o2 < -e && (k < 0 || o2 < best)) { k = 1; best = o2; }
+        if (o3 < -e3 && (k < 0 || o3 < best)) { k = 2; best = o3; }
+        if (k >= 0) {
+            const float4 R = __ldg(&a.he[tq.x + k]);
+            if (__float_as_int(R.z) >= 0) {
+                // the next triangle: (W2, W1, Q), (W0, W2, Q) or (W1, W0, Q)
+                float p0x = k == 1 ? A.x : (k == 0 ? C.x : B.x), p0y = k == 1 ? A.y : (k == 0 ? C.y : B.y);
+                float p1x = k == 0 ? B.x : (k == 1 ? C.x : A.x), p1y = k == 0 ? B.y : (k == 1 ? C.y : A.y);
+                float p2x = R.x, p2y = R.y;
+                e0 = __float_as_int(R.z);
+                e1 = __float_as_int(R.w);
+                ids = false;
+                ++hops;
+                lean_hops(a, X.h, Y.h, p0x, p0y, p1x, p1y, p2x, p2y, e0, e1, hops, cap);
+            }
+        }
+    }
     for (;;) {
         // certified test in double-float on (W0, W1, W2) = the vertices in
         // slot order, relative to W2
@@ -484,26 +549,7 @@ __device__ __forceinline__ void step_node(const FastArgs &a, int64_t i, int pi, 
         ids = false;
         ++hops;
         // FP32 hops on the high parts while an edge is certainly negative
-        const float fx = X.h, fy = Y.h;
-        while (hops < cap) {
-            const float ax = p0x - p2x, ay = p0y - p2y, bx = p1x - p2x, by = p1y - p2y;
-            const float xx = fx - p2x, xy = fy - p2y;
-            const float o1 = __fmaf_rn(xx, by, -__fmul_rn(xy, bx));    // ~ theta of W0 * den
-            const float o2 = __fmaf_rn(ax, xy, -__fmul_rn(ay, xx));    // ~ theta of W1 * den
-            const float S = fabsf(ax) + fabsf(ay) + fabsf(bx) + fabsf(by) + fabsf(xx) + fabsf(xy);
-            const float e = hop_bound(S);
-            const bool c1 = o1 < -e, c2 = o2 < -e && !(c1 && o1 <= o2);
-            if (!(c1 || c2)) break;
-            const float4 Q = __ldg(&a.he[c2 ? e1 : e0]);
-            if (__float_as_int(Q.z) < 0) break;    // a boundary edge (see above): certify instead
-            if (c2) { p1x = p2x; p1y = p2y; }
-            else { p0x = p2x; p0y = p2y; }
-            p2x = Q.x;
-            p2y = Q.y;
-            e0 = __float_as_int(Q.z);
-            e1 = __float_as_int(Q.w);
-            ++hops;
-        }
+        lean_hops(a, X.h, Y.h, p0x, p0y, p1x, p1y, p2x, p2y, e0, e1, hops, cap);
     }
     if (!found) {
         flags |= SL_NODE_WALK_LIMIT;
