@@ -528,6 +528,14 @@ def main():
     phases = {"first_step_ms": first_ms, "later_step_ms": rest_ms,
               "note": "eager launches, one run, after the timed region"}
 
+    # the effective gather roofline of a later step: a kernel making exactly
+    # its memory accesses (on the current start triangles) with no arithmetic
+    gather = None
+    if prec == sl.SL_FP64 and args.kernel != 1:
+        probe_ms = sl.sl_probe_gather(h, v, w, reps=20)
+        gather = {"probe_ms": probe_ms, "later_step_ms": rest_ms, "frac_of_gather_bound": probe_ms / rest_ms,
+                  "kernel": "k_gather_probe (node pair and start state, three vertex pairs, three values, one write)"}
+
     fp32_check = None
     if wl.precision == "fp32" and not args.no_plain:
         # the same workload on the FP64 mesh: the fast FP64 path (within 1e-12
@@ -641,6 +649,7 @@ def main():
                  "clipped": stats["clipped"], "fallbacks": stats["fallbacks"]},
         "setup_s": setup_s,
         "phases": phases,
+        "gather_probe": gather,
         "autotune": tune,
         "plain_fp64": plain,
         "speedup_vs_plain_fp64": ((value / world) / plain["value"] if plain else

@@ -313,6 +313,22 @@ typedef struct {
 sl_status sl_autotune(sl_mesh *m, const sl_problem *probs, int32_t probe_steps, void *v, void *v_scratch,
                       sl_tune *out, void *stream);
 
+/*
+ * sl_probe_gather -- the memory-system ceiling of a later step (FP64
+ * meshes): one kernel that makes exactly the memory accesses of a step in
+ * which every foot stays in its start triangle -- the node's coordinate pair
+ * and start state, the start triangle's three vertex pairs and three values,
+ * one value written -- with no arithmetic beyond summing what it read.  It
+ * runs over the mesh's current T^0, in the launch shape of the settle pass,
+ * once untimed and then `reps` times (1..1000) timed with CUDA events on
+ * `stream`; *ms_out receives the mean time per launch.  v (device, N
+ * doubles) is read as (hi, lo) float pairs; v_scratch (device, N doubles) is
+ * overwritten with meaningless values; T^0 and the statistics are not
+ * touched.  Synchronises.  No counterpart in the paper: it measures the
+ * effective gather roofline a step of this mesh is held to.
+ */
+sl_status sl_probe_gather(sl_mesh *m, const void *v, void *v_scratch, int32_t reps, float *ms_out, void *stream);
+
 /* T^0 export / import (device, N int32 global triangle indices in current
  * numbering); with V^n this is the whole state of a run (resume). */
 sl_status sl_mesh_get_t0(const sl_mesh *m, int32_t *t0_dev, void *stream);

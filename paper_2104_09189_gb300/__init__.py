@@ -24,7 +24,7 @@ __all__ = [
     "sl_mesh_create", "sl_mesh_validate", "sl_mesh_reorder", "sl_step", "sl_run", "sl_run_host", "sl_mesh_get_t0",
     "sl_mesh_set_t0", "sl_mesh_reset_t0", "sl_mesh_status", "sl_mesh_stats", "sl_mesh_set_option", "sl_mesh_info",
     "sl_mesh_export", "sl_mesh_destroy", "sl_last_error", "library", "EXPORTED", "sl_step_noalloc",
-    "SL_NOALLOC_MAX_NODES", "SL_NOALLOC_MAX_PROBLEMS", "sl_autotune",
+    "SL_NOALLOC_MAX_NODES", "SL_NOALLOC_MAX_PROBLEMS", "sl_autotune", "sl_probe_gather",
 ]
 
 SL_OK, SL_E_ARG, SL_E_MESH, SL_E_NOMEM, SL_E_CUDA, SL_E_WALK_LIMIT, SL_E_STATE = range(7)
@@ -45,7 +45,8 @@ _STATUS_NAMES = {0: "SL_OK", 1: "SL_E_ARG", 2: "SL_E_MESH", 3: "SL_E_NOMEM", 4: 
 # every entry point declared in include/sl.h
 EXPORTED = ("sl_mesh_create", "sl_mesh_validate", "sl_mesh_reorder", "sl_step", "sl_run", "sl_run_host", "sl_mesh_get_t0",
             "sl_mesh_set_t0", "sl_mesh_reset_t0", "sl_mesh_status", "sl_mesh_stats", "sl_mesh_set_option", "sl_mesh_info",
-            "sl_mesh_export", "sl_mesh_destroy", "sl_last_error", "sl_step_noalloc", "sl_autotune")
+            "sl_mesh_export", "sl_mesh_destroy", "sl_last_error", "sl_step_noalloc", "sl_autotune",
+            "sl_probe_gather")
 
 
 class SLError(RuntimeError):
@@ -109,6 +110,7 @@ def library():
         "sl_mesh_export": [P, P, P, P],
         "sl_step_noalloc": [P, P, I64, P, P, P],
         "sl_autotune": [P, P, I32, P, P, P, P],
+        "sl_probe_gather": [P, P, P, I32, P, P],
     }
     for name, args in sig.items():
         f = getattr(L, name)
@@ -303,6 +305,14 @@ def sl_step_noalloc(h, probs, n, v_in, v_out, stream=None):
     most SL_NOALLOC_MAX_NODES nodes).  For callers that cannot allocate device
     memory while stepping."""
     _check(library().sl_step_noalloc(h, probs, int(n), _ptr(v_in), _ptr(v_out), _stream(stream)))
+
+
+def sl_probe_gather(h, v, v_scratch, reps=10, stream=None):
+    """Mean time (ms) of a kernel making only the memory accesses of a steady
+    step on this mesh (see sl.h); v is read, v_scratch overwritten."""
+    ms = ctypes.c_float()
+    _check(library().sl_probe_gather(h, _ptr(v), _ptr(v_scratch), int(reps), ctypes.byref(ms), _stream(stream)))
+    return float(ms.value)
 
 
 def sl_autotune(h, probs, probe_steps, v, v_scratch, stream=None):

@@ -787,6 +787,39 @@ extern "C" void sl_mesh_destroy(sl_mesh *m)
     delete m;
 }
 
+extern "C" sl_status sl_probe_gather(sl_mesh *m, const void *v, void *v_scratch, int32_t reps, float *ms_out,
+                                     void *stream)
+{
+    if (!m || !v || !v_scratch || !ms_out) return fail(SL_E_ARG, "sl_probe_gather: NULL argument");
+    if (reps < 1 || reps > 1000) return fail(SL_E_ARG, "sl_probe_gather: reps must be in [1, 1000]");
+    if (v == v_scratch) return fail(SL_E_ARG, "sl_probe_gather: v and v_scratch must not alias");
+    if (m->precision != SL_FP64) return fail(SL_E_ARG, "sl_probe_gather: FP64 meshes only");
+    sl_status st = check_device(m);
+    if (st != SL_OK) return st;
+    cudaStream_t s = (cudaStream_t)stream;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    auto run = [&]() -> sl_status {
+        SL_CUDA(cudaEventCreate(&e0));
+        SL_CUDA(cudaEventCreate(&e1));
+        const float4 *xyq = (const float4 *)m->d.xyq;
+        const int4 *t0v = (const int4 *)m->d.t0v;
+        launch_gather_probe(xyq, t0v, (const float2 *)v, (float2 *)v_scratch, m->N, s);
+        SL_CUDA(cudaGetLastError());
+        SL_CUDA(cudaEventRecord(e0, s));
+        for (int32_t k = 0; k < reps; ++k) launch_gather_probe(xyq, t0v, (const float2 *)v, (float2 *)v_scratch, m->N, s);
+        SL_CUDA(cudaEventRecord(e1, s));
+        SL_CUDA(cudaEventSynchronize(e1));
+        float ms = 0.f;
+        SL_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+        *ms_out = ms / (float)reps;
+        return SL_OK;
+    };
+    st = run();
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    return st;
+}
+
 extern "C" sl_status sl_autotune(sl_mesh *m, const sl_problem *probs, int32_t probe_steps, void *v, void *v_scratch,
                                  sl_tune *out, void *stream)
 {

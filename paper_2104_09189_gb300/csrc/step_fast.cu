@@ -75,6 +75,13 @@ __device__ __forceinline__ bool clip_df(df x, df y, df &X, df &Y)
     const bool xfirst = !df_lt(sy, sx);       // sx <= sy
     const bool yfirst = !df_lt(sx, sy);       // sy <= sx
     const df s = xfirst ? sx : sy;
+    if (s.h == 0.0f) {
+        // a node on the side it moves out through: the foot is the node
+        // itself, kept as its own coordinate pair
+        X = x;
+        Y = y;
+        return true;
+    }
     df cx = df_add(x, df_mul(s, dx)), cy = df_add(y, df_mul(s, dy));
     if (xfirst) cx = df_make(bx, 0.0f);
     if (yfirst) cy = df_make(by, 0.0f);
@@ -273,10 +280,8 @@ __device__ __forceinline__ Certified certify(float4 A, float4 B, float4 C, float
 // theta_k = n_k / den:  V = v3 + (n1 (v1 - v3) + n2 (v2 - v3)) / den, in
 // double-float: the value differences from a TwoSum of the high parts, the
 // products from their exact FMA remainders, one division.
-__device__ __forceinline__ float2 p1_value(const FastArgs &a, int w0, int w1, int w2, df n1, df n2, df den)
+__device__ __forceinline__ float2 p1_value_of(float2 V1, float2 V2, float2 V3, df n1, df n2, df den)
 {
-    const float2 *vin = (const float2 *)a.vin;
-    const float2 V1 = vin[w0], V2 = vin[w1], V3 = vin[w2];
     float d1h, d1l, d2h, d2l;
     two_sum_f(V1.x, -V3.x, d1h, d1l);
     d1l = __fadd_rn(d1l, __fsub_rn(V1.y, V3.y));
@@ -297,17 +302,36 @@ __device__ __forceinline__ float2 p1_value(const FastArgs &a, int w0, int w1, in
     return make_float2(v.h, v.l);
 }
 
+__device__ __forceinline__ float2 p1_value(const FastArgs &a, int w0, int w1, int w2, df n1, df n2, df den)
+{
+    const float2 *vin = (const float2 *)a.vin;
+    return p1_value_of(vin[w0], vin[w1], vin[w2], n1, n2, den);
+}
+
+// A foot equal to its own node's stored coordinate pair is that node (see
+// step_node): a boundary node whose velocity points out of the square is
+// clipped at the start of its segment, and a node where the field vanishes
+// does not move.
+__device__ __forceinline__ bool foot_is_node(df x, df y, df X, df Y)
+{
+    return X.h == x.h && X.l == x.l && Y.h == y.h && Y.l == y.l;
+}
+
 // The foot of node i for this step: Euler (Eq. 4) in double-float, decided
 // against the boundary in double rounding, clipped, and returned in the
-// (grid, remainder) form of the certified test.  Returns true when clipped.
-__device__ __forceinline__ bool foot_pair(const FastArgs &a, int64_t i, const FastProb &P, df &X, df &Y)
+// (grid, remainder) form of the certified test.  Returns true when clipped;
+// at_node: the foot is the node itself.
+__device__ __forceinline__ bool foot_pair(const FastArgs &a, int64_t i, const FastProb &P, df &X, df &Y,
+                                          bool &at_node)
 {
     const float4 xq = a.xyq[i];
     const df x = df_make(xq.x, xq.z), y = df_make(xq.y, xq.w);
     foot_df(P, a, i, x, y, X, Y);
     round_boundary(X);
     round_boundary(Y);
-    return clip_df(x, y, X, Y);
+    const bool clipped = clip_df(x, y, X, Y);
+    at_node = foot_is_node(x, y, X, Y);
+    return clipped;
 }
 
 __device__ __forceinline__ void foot_to_grid(df &X, df &Y)
@@ -404,6 +428,7 @@ __device__ __forceinline__ void step_node(const FastArgs &a, int64_t i, int pi, 
         flags |= SL_NODE_CLIPPED;
         c.clipped = 1;
     }
+    const bool at_node = foot_is_node(x, y, X, Y);
     // From here on the foot is its (grid, remainder) form, Xg + Xr exactly:
     // within 2^-49 of the double-float foot, and the form the certified test
     // needs (the exact stage takes any float pair).  The boundary decisions
@@ -422,6 +447,30 @@ __device__ __forceinline__ void step_node(const FastArgs &a, int64_t i, int pi, 
     // grid
     const int4 tq = kExt && a.grid_M > 0 ? __ldg(&a.grid_t0v[grid_slot(X.h, Y.h, a.grid_M)])
                                          : a.t0v[kExt && a.parent ? (int64_t)a.parent[i] : i];
+    // A foot that is the node itself lies on a vertex: when the start
+    // triangle has node i as a vertex it contains the foot (two barycentric
+    // coordinates are zero) and the P1 value is the node's own value.  The
+    // double-float pair is only within 2^-49 of the node's double
+    // coordinate, so without this the exact stage would run on a
+    // rounding-sized offset every step.
+    if (at_node && (tq.y == (int32_t)i || tq.z == (int32_t)i || tq.w == (int32_t)i)) {
+        const int32_t j0 = tri_of(tq.x);
+        ((float2 *)a.vout)[i] = ((const float2 *)a.vin)[i];
+        if (kExt && a.parent && !a.keep_t0) {
+            a.t0[i] = j0;
+            a.t0v[i] = tq;
+        }
+        if (kDebug) {
+            if (a.dbg.feet) {
+                a.dbg.feet[2 * i] = (double)X.h + (double)X.l;
+                a.dbg.feet[2 * i + 1] = (double)Y.h + (double)Y.l;
+            }
+            if (a.dbg.tri) a.dbg.tri[i] = j0;
+            if (a.dbg.moves) a.dbg.moves[i] = 0;
+            if (a.dbg.flags) a.dbg.flags[i] = (uint8_t)(flags | SL_NODE_DEGENERATE);
+        }
+        return;
+    }
     int32_t e0 = tq.x, e1 = 0;
     int32_t j = 0;
     int w0 = tq.y, w1 = tq.z, w2 = tq.w;
@@ -592,9 +641,10 @@ __global__ void __launch_bounds__(kBlock, kMinBlocks) k_step_fast_df(FastArgs a)
     if (kStats) warp_stats(a.stats, active, c.hops, c.exact, c.clipped, c.fallback, c.limit, c.filter2, c.excluded);
 }
 
-// Settle pass of a split step: the nodes whose foot is certainly inside the
-// start triangle (all three signs certified positive, no hop, no exact
-// stage) are finished here with a lean kernel; every other node is appended
+// Settle pass of a split step: the nodes whose foot is certainly in the
+// start triangle (all three signs certified positive, or zero by a boundary
+// side code for a clipped foot; no hop, no exact stage) are finished here
+// with a lean kernel; every other node is appended
 // to the queue for the finish pass, which runs the full node step on it.  The
 // foot, the certified test and the value are the same functions as in
 // step_node, so the split does not change any result.
@@ -603,13 +653,61 @@ __device__ __forceinline__ bool settle_node(const FastArgs &a, int64_t i, int pi
 {
     const FastProb &P = a.probs[pi];
     df X, Y;
-    const bool clipped = foot_pair(a, i, P, X, Y);
+    bool at_node;
+    const bool clipped = foot_pair(a, i, P, X, Y, at_node);
     foot_to_grid(X, Y);
     const int4 tq = a.t0v[i];
     const float4 A = a.xyq[tq.y], B = a.xyq[tq.z], C = a.xyq[tq.w];
+    // the start triangle's values are read together with its vertices, not
+    // after the test: most feet stay in it, and the value then costs no
+    // further round trip to memory
+    const float2 *vin = (const float2 *)a.vin;
+    const float2 V1 = vin[tq.y], V2 = vin[tq.z], V3 = vin[tq.w];
     const Certified t = certify(A, B, C, X.h, X.l, Y.h, Y.l);
-    if (!(t.n1.h > t.ea && t.n2.h > t.eb && t.n3h > t.e3)) return false;
-    ((float2 *)a.vout)[i] = p1_value(a, tq.y, tq.z, tq.w, t.n1, t.n2, t.den);
+    bool degenerate = false;
+    if (!(t.n1.h > t.ea && t.n2.h > t.eb && t.n3h > t.e3)) {
+        if (at_node) {
+            // The foot is node i (as in step_node).  When T^0 has node i as a
+            // vertex, two of its signs are zero, so the test above cannot
+            // have passed: such a node is settled here with its own value.
+            if (tq.y != (int32_t)i && tq.z != (int32_t)i && tq.w != (int32_t)i) return false;
+            ((float2 *)a.vout)[i] = vin[i];
+            c.clipped = clipped;
+            if (kDebug) {
+                if (a.dbg.feet) {
+                    a.dbg.feet[2 * i] = (double)X.h + (double)X.l;
+                    a.dbg.feet[2 * i + 1] = (double)Y.h + (double)Y.l;
+                }
+                if (a.dbg.tri) a.dbg.tri[i] = tri_of(tq.x);
+                if (a.dbg.moves) a.dbg.moves[i] = 0;
+                if (a.dbg.flags) a.dbg.flags[i] = (uint8_t)((clipped ? SL_NODE_CLIPPED : 0u) | SL_NODE_DEGENERATE);
+            }
+            return true;
+        }
+        // A foot clipped onto a side of the square lies on the boundary edge
+        // of its triangle on that side: that sign is exactly zero (the side
+        // codes of step_node).  Any other sign that is not certainly
+        // positive leaves the node to the finish pass.
+        if (!clipped) return false;
+        const int s1 = t.n1.h > t.ea ? 1 : (t.n1.h < -t.ea ? -1 : 2);
+        const int s2 = t.n2.h > t.eb ? 1 : (t.n2.h < -t.eb ? -1 : 2);
+        int s3 = t.n3h > t.e3 ? 1 : (t.n3h < -t.e3 ? -1 : 2);
+        if (s3 == 2) {
+            const df n3 = df_sub(df_sub(t.den, t.n1), t.n2);
+            const float ec = t.ed + t.ea + t.eb + 0x1p-45f * (fabsf(t.den.h) + fabsf(t.n1.h) + fabsf(t.n2.h));
+            s3 = n3.h > ec ? 1 : (n3.h < -ec ? -1 : 2);
+        }
+        if (s1 < 0 || s2 < 0 || s3 < 0) return false;
+        const uint32_t fside = (df_is(X, 0.0f) ? 1u : 0u) | (df_is(X, 1.0f) ? 2u : 0u) |
+                               (df_is(Y, 0.0f) ? 4u : 0u) | (df_is(Y, 1.0f) ? 8u : 0u);
+        const int32_t j = tri_of(tq.x);
+        const int32_t nb1 = s1 == 2 ? a.tn[0][j] : 0, nb2 = s2 == 2 ? a.tn[1][j] : 0, nb3 = s3 == 2 ? a.tn[2][j] : 0;
+        if (s1 == 2 && !(nb1 < 0 && (fside >> (-1 - nb1) & 1u))) return false;
+        if (s2 == 2 && !(nb2 < 0 && (fside >> (-1 - nb2) & 1u))) return false;
+        if (s3 == 2 && !(nb3 < 0 && (fside >> (-1 - nb3) & 1u))) return false;
+        degenerate = true;
+    }
+    ((float2 *)a.vout)[i] = p1_value_of(V1, V2, V3, t.n1, t.n2, t.den);
     c.clipped = clipped;
     if (kDebug) {
         if (a.dbg.feet) {
@@ -618,7 +716,8 @@ __device__ __forceinline__ bool settle_node(const FastArgs &a, int64_t i, int pi
         }
         if (a.dbg.tri) a.dbg.tri[i] = tri_of(tq.x);
         if (a.dbg.moves) a.dbg.moves[i] = 0;
-        if (a.dbg.flags) a.dbg.flags[i] = (uint8_t)(clipped ? SL_NODE_CLIPPED : 0u);
+        if (a.dbg.flags)
+            a.dbg.flags[i] = (uint8_t)((clipped ? SL_NODE_CLIPPED : 0u) | (degenerate ? SL_NODE_DEGENERATE : 0u));
     }
     return true;
 }
@@ -748,6 +847,30 @@ void launch_fast_df(const FastArgs &a, bool stats, bool debug, int config, cudaS
     case 5: launch_fast_df_cfg<128, 12>(a, stats, debug, s); break;
     default: launch_fast_df_cfg<256, 4>(a, stats, debug, s); break;
     }
+}
+
+// ---------------------------------------------------------------------------
+// Gather probe: the memory accesses of a step whose feet stay in their start
+// triangles, with only a sum as arithmetic (sl_probe_gather).
+
+__global__ void __launch_bounds__(128, 14) k_gather_probe(const float4 *xyq, const int4 *t0v, const float2 *vin,
+                                                          float2 *vout, int64_t N)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= N) return;
+    const float4 xq = xyq[i];
+    const int4 tq = t0v[i];
+    const float4 A = xyq[tq.y], B = xyq[tq.z], C = xyq[tq.w];
+    const float2 V1 = vin[tq.y], V2 = vin[tq.z], V3 = vin[tq.w];
+    const float s = ((xq.x + xq.y) + (xq.z + xq.w)) + ((A.x + A.y) + (A.z + A.w)) + ((B.x + B.y) + (B.z + B.w)) +
+                    ((C.x + C.y) + (C.z + C.w)) + __int_as_float(tq.x & 0x007fffff);
+    vout[i] = make_float2((V1.x + V2.x) + (V3.x + s), (V1.y + V2.y) + V3.y);
+}
+
+void launch_gather_probe(const float4 *xyq, const int4 *t0v, const float2 *vin, float2 *vout, int64_t N,
+                         cudaStream_t s)
+{
+    if (N > 0) k_gather_probe<<<(unsigned)((N + 127) / 128), 128, 0, s>>>(xyq, t0v, vin, vout, N);
 }
 
 // ---------------------------------------------------------------------------

@@ -70,6 +70,10 @@ void launch_split_df(const FastArgs &a, bool stats, bool debug, int sms, cudaStr
 constexpr int kFastConfigs = 6;
 void launch_fast_f32(const FastArgs &a, bool stats, bool debug, int config, cudaStream_t s);
 
+// the memory accesses of a steady step with no arithmetic (sl_probe_gather)
+void launch_gather_probe(const float4 *xyq, const int4 *t0v, const float2 *vin, float2 *vout, int64_t N,
+                         cudaStream_t s);
+
 // value format conversions for the double-float kernel
 void launch_to_df(const double *src, float2 *dst, int64_t n, cudaStream_t s);
 void launch_from_df(const float2 *src, double *dst, int64_t n, cudaStream_t s);

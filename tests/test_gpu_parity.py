@@ -121,12 +121,13 @@ def test_linear_data_closed_form_on_gpu(kernel):
 
 
 def test_zero_field_leaves_values_bitwise():
-    """f = 0: every foot is its own node.  The plain kernel reproduces V bit
-    for bit and flags every foot degenerate (it lies on a vertex); the fast
-    kernel keeps coordinates as float pairs (grid part + remainder), so its
-    feet sit within 2^-48 of the nodes, and its barycentric weights are 1 and
-    0 only to about 2^-48 / h relative (the remainders' products are rounded
-    at 2^-24 of h 2^-24): the values stay within 5e-13 over three steps."""
+    """f = 0: every foot is its own node.  Both kernels return each node's
+    own value and flag every foot degenerate (it lies on a vertex of its
+    start triangle, an incident triangle of the node).  The plain kernel
+    reproduces V bit for bit; the fast kernel takes a foot equal to its
+    node's coordinate pair as the node, walks no step, and returns the value
+    as it holds it between steps, a (hi, lo) float pair: V rounded to the
+    pair, bit for bit."""
     mesh = si.grid_mesh(64, 0.25, 2)
     v0 = si.cosine_bump(mesh.xy)
     g = GpuRun(mesh, si.zero_field(), 0.1, kernel=1)
@@ -136,13 +137,22 @@ def test_zero_field_leaves_values_bitwise():
         assert np.array_equal(res["v"], v0)
         assert np.all(res["flags"] & sl.SL_NODE_DEGENERATE)
     g.close()
-    g = GpuRun(mesh, si.zero_field(), 0.1, kernel=2)
-    v_dev = g.to_dev(v0)
-    for n in range(3):
-        v_dev, res = g.step(n, v_dev)
-        assert np.abs(res["v"] - v0).max() < 5e-13
-        assert np.abs(res["feet"] - mesh.xy).max() <= 2.0 ** -48
-    g.close()
+    hi = v0.astype(np.float32).astype(np.float64)
+    v_pair = hi + (v0 - hi).astype(np.float32).astype(np.float64)
+    assert np.abs(v_pair - v0).max() <= 2.0 ** -48 * np.abs(v0).max()
+    for split in (0, 1):
+        g = GpuRun(mesh, si.zero_field(), 0.1, kernel=2)
+        sl.sl_mesh_set_option(g.h, sl.SL_OPT_SPLIT, split)
+        v_dev = g.to_dev(v0)
+        for n in range(3):
+            v_dev, res = g.step(n, v_dev)
+            assert np.array_equal(res["v"], v_pair)
+            assert np.all(res["flags"] & sl.SL_NODE_DEGENERATE)
+            assert not np.any(res["flags"] & sl.SL_NODE_EXACT)
+            assert np.all(res["moves"] == 0)
+            assert np.all(np.any(mesh.tri[res["tri"]] == np.arange(mesh.n_nodes)[:, None], axis=1))
+            assert np.abs(res["feet"] - mesh.xy).max() <= 2.0 ** -48
+        g.close()
 
 
 @pytest.mark.parametrize("kernel", [1, 2], ids=["plain", "fast"])
@@ -273,6 +283,33 @@ def test_autotune_restores_state_and_keeps_results():
     ref.close()
 
 
+def test_gather_probe_times_and_leaves_state():
+    """sl_probe_gather returns a positive mean time, reads v without
+    changing it, leaves T^0 alone and refuses bad arguments."""
+    prob = si.config("C2", M=256)
+    g = GpuRun(prob.mesh, prob.field, prob.dt, curve=sl.SL_CURVE_HILBERT)
+    v = g.to_dev(prob.v0)
+    w = g.torch.empty_like(v)
+    sl.sl_run(g.h, g.probs, 0, 3, v, w)
+    before = v.clone()
+    n = v.numel()
+    t0 = g.torch.empty(n, dtype=g.torch.int32, device="cuda")
+    sl.sl_mesh_get_t0(g.h, t0)
+    ms = sl.sl_probe_gather(g.h, v, w, reps=5)
+    assert ms > 0
+    assert g.torch.equal(v, before)
+    t1 = g.torch.empty_like(t0)
+    sl.sl_mesh_get_t0(g.h, t1)
+    assert g.torch.equal(t0, t1)
+    for reps in (0, 1001):
+        with pytest.raises(sl.SLError) as e:
+            sl.sl_probe_gather(g.h, v, w, reps=reps)
+        assert e.value.status == sl.SL_E_ARG
+    with pytest.raises(sl.SLError):
+        sl.sl_probe_gather(g.h, v, v, reps=1)
+    g.close()
+
+
 @pytest.mark.parametrize("kernel", [1, 2], ids=["plain", "fast"])
 @pytest.mark.parametrize("fx", [-1e-17, 1e-17])
 def test_boundary_nodes_with_nearly_tangent_velocity(kernel, fx):
@@ -325,6 +362,65 @@ def test_split_steps_are_bitwise_identical(name):
     assert np.array_equal(t00, t01)
     for k in ("node_updates", "walk_moves", "max_moves", "exact_tests", "clipped", "fallbacks"):
         assert s0[k] == s1[k], k
+
+
+def test_split_steps_settle_clipped_feet_like_the_fused_step():
+    """Rotation about the centre carries the corner nodes out of the square:
+    their feet are clipped onto a side, on the boundary edge of their start
+    triangle, where one sign is exactly zero.  The settle pass finishes them
+    by the boundary side codes; every debug output (foot, triangle, hops,
+    flags including DEGENERATE) is bitwise that of the fused step."""
+    prob = si.config("C3", M=160)
+    outs = []
+    for split in (0, 1):
+        g = GpuRun(prob.mesh, prob.field, prob.dt, curve=sl.SL_CURVE_HILBERT)
+        sl.sl_mesh_set_option(g.h, sl.SL_OPT_SPLIT, split)
+        v = g.to_dev(prob.v0)
+        steps = []
+        for n in range(3):
+            v, res = g.step(n, v)
+            steps.append(res)
+        outs.append(steps)
+        g.close()
+    for a, b in zip(*outs):
+        for k in ("feet", "tri", "moves", "flags", "v"):
+            assert np.array_equal(a[k], b[k]), k
+    last = outs[1][-1]
+    clipped = (last["flags"] & sl.SL_NODE_CLIPPED) != 0
+    assert clipped.sum() > 100
+    settled_on_side = clipped & (last["moves"] == 0) & ((last["flags"] & sl.SL_NODE_DEGENERATE) != 0)
+    assert settled_on_side.sum() > 0.5 * clipped.sum()
+
+
+@pytest.mark.parametrize("split", [0, 1])
+def test_boundary_nodes_moving_out_keep_their_value(split):
+    """Rotation about the centre: a boundary node whose velocity points out
+    of the square is clipped at the start of its segment (Eq. 4 with the
+    boundary clip), so its foot is the node itself.  The P1 value there is
+    the node's own value (bit for bit as the kernel holds it, a (hi, lo)
+    float pair), found in its start triangle (an incident triangle) without
+    a walk or an exact test, at every step; the oracle agrees to rounding."""
+    prob = si.config("C3", M=160)
+    mesh = prob.mesh
+    om = oracle.OracleMesh(mesh.xy, mesh.tri)
+    g = GpuRun(prob.mesh, prob.field, prob.dt, curve=sl.SL_CURVE_HILBERT)
+    sl.sl_mesh_set_option(g.h, sl.SL_OPT_SPLIT, split)
+    v = g.to_dev(prob.v0)
+    prev = prob.v0
+    for n in range(3):
+        v, res = g.step(n, v)
+        ov, otri, ofl, oft = om.step(prob.field.kind, prob.field.packed(), prob.dt, n, prev)
+        compare_step(om, res, ov, otri, oft)
+        out = np.all(oft == mesh.xy, axis=1) & ((ofl & oracle.FLAG_CLIPPED) != 0)
+        assert out.sum() > 100
+        hi = prev[out].astype(np.float32).astype(np.float64)
+        assert np.array_equal(res["v"][out], hi + (prev[out] - hi).astype(np.float32).astype(np.float64))
+        assert np.all(res["moves"][out] == 0)
+        assert not np.any(res["flags"][out] & sl.SL_NODE_EXACT)
+        assert np.all(res["flags"][out] & sl.SL_NODE_DEGENERATE)
+        assert np.all(np.any(mesh.tri[res["tri"][out]] == np.nonzero(out)[0][:, None], axis=1))
+        prev = res["v"]
+    g.close()
 
 
 def test_split_steps_match_the_oracle_with_debug_outputs():
