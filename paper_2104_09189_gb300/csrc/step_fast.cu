@@ -347,25 +347,33 @@ __device__ __forceinline__ void foot_to_grid(df &X, df &Y)
 // triangle (W0, W1, W2) = (p0, p1, p2), entered through its third edge, is
 // certainly negative (hop_bound); e0, e1: the half-edge codes of the edges
 // opposite W0 and W1.  One 16-byte half-edge record per hop.
-__device__ __forceinline__ void lean_hops(const FastArgs &a, float fx, float fy, float &p0x, float &p0y, float &p1x,
-                                          float &p1y, float &p2x, float &p2y, int32_t &e0, int32_t &e1,
-                                          uint32_t &hops, uint32_t cap)
+//
+// The loop keeps the vertices relative to the foot, a_k = W_k - X: grid
+// values minus a grid value, exact in float, so a new vertex costs two
+// subtractions and each orientation one product and one FMA:
+// orient(W1, W2, X) = a1 x a2, orient(W2, W0, X) = a2 x a0.  Each a_k is
+// within 2^-24 of the exact difference, which with the product roundings
+// stays below hop_bound(S), S = the sum of the six |a|.  The more negative
+// exit is taken (the first on a tie), as in the certified walk.  A boundary
+// record carries NaN coordinates: the next test fails and the loop ends, its
+// first code naming an edge of the triangle the walk is still in.
+__device__ __forceinline__ void lean_hops(const FastArgs &a, float fx, float fy, float p0x, float p0y, float p1x,
+                                          float p1y, float p2x, float p2y, int32_t &e0, int32_t &e1, uint32_t &hops,
+                                          uint32_t cap)
 {
+    float a0x = __fsub_rn(p0x, fx), a0y = __fsub_rn(p0y, fy), a1x = __fsub_rn(p1x, fx), a1y = __fsub_rn(p1y, fy);
+    float a2x = __fsub_rn(p2x, fx), a2y = __fsub_rn(p2y, fy);
     while (hops < cap) {
-        const float ax = p0x - p2x, ay = p0y - p2y, bx = p1x - p2x, by = p1y - p2y;
-        const float xx = fx - p2x, xy = fy - p2y;
-        const float o1 = __fmaf_rn(xx, by, -__fmul_rn(xy, bx));    // ~ theta of W0 * den
-        const float o2 = __fmaf_rn(ax, xy, -__fmul_rn(ay, xx));    // ~ theta of W1 * den
-        const float S = fabsf(ax) + fabsf(ay) + fabsf(bx) + fabsf(by) + fabsf(xx) + fabsf(xy);
-        const float e = hop_bound(S);
-        const bool c1 = o1 < -e, c2 = o2 < -e && !(c1 && o1 <= o2);
-        if (!(c1 || c2)) break;
+        const float o1 = __fmaf_rn(a1x, a2y, -__fmul_rn(a1y, a2x));    // ~ theta of W0 * den
+        const float o2 = __fmaf_rn(a2x, a0y, -__fmul_rn(a2y, a0x));    // ~ theta of W1 * den
+        const float S = fabsf(a0x) + fabsf(a0y) + fabsf(a1x) + fabsf(a1y) + fabsf(a2x) + fabsf(a2y);
+        if (!(fminf(o1, o2) < -hop_bound(S))) break;
+        const bool c2 = o2 < o1;
         const float4 Q = __ldg(&a.he[c2 ? e1 : e0]);
-        if (__float_as_int(Q.z) < 0) break;    // a boundary edge: not for a foot inside a valid mesh
-        if (c2) { p1x = p2x; p1y = p2y; }
-        else { p0x = p2x; p0y = p2y; }
-        p2x = Q.x;
-        p2y = Q.y;
+        if (c2) { a1x = a2x; a1y = a2y; }
+        else { a0x = a2x; a0y = a2y; }
+        a2x = __fsub_rn(Q.x, fx);
+        a2y = __fsub_rn(Q.y, fy);
         e0 = __float_as_int(Q.z);
         e1 = __float_as_int(Q.w);
         ++hops;
@@ -503,7 +511,7 @@ __device__ __forceinline__ void step_node(const FastArgs &a, int64_t i, int pi, 
         if (o3 < -e3 && (k < 0 || o3 < best)) { k = 2; best = o3; }
         if (k >= 0) {
             const float4 R = __ldg(&a.he[tq.x + k]);
-            if (__float_as_int(R.z) >= 0) {
+            if (!isnan(R.x)) {
                 // the next triangle: (W2, W1, Q), (W0, W2, Q) or (W1, W0, Q)
                 float p0x = k == 1 ? A.x : (k == 0 ? C.x : B.x), p0y = k == 1 ? A.y : (k == 0 ? C.y : B.y);
                 float p1x = k == 0 ? B.x : (k == 1 ? C.x : A.x), p1y = k == 0 ? B.y : (k == 1 ? C.y : A.y);
@@ -586,7 +594,7 @@ __device__ __forceinline__ void step_node(const FastArgs &a, int64_t i, int pi, 
             k = random_negative_edge(i, hops, s1, s2, s3);
         }
         const float4 R = __ldg(&a.he[3 * j + k]);
-        if (__float_as_int(R.z) < 0) break;    // a boundary edge: not for a foot inside a valid mesh
+        if (isnan(R.x)) break;    // a boundary edge: not for a foot inside a valid mesh
         // the next triangle: (W2, W1, Q), (W0, W2, Q) or (W1, W0, Q); the
         // high parts of the kept vertices are reloaded (L1 hits) rather than
         // kept live through the certified test
@@ -994,8 +1002,8 @@ __global__ void k_build_he(HalfEdgeArgs a)
     for (int64_t h = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; h < nh; h += (int64_t)gridDim.x * blockDim.x) {
         const int32_t t = (int32_t)(h / 3), k = (int32_t)(h - 3 * (int64_t)t);
         const int32_t u = a.tn[k][t];
-        float4 r = make_float4(__int_as_float(0x7fc00000), __int_as_float(0x7fc00000), __int_as_float(u),
-                               __int_as_float(u));
+        float4 r = make_float4(__int_as_float(0x7fc00000), __int_as_float(0x7fc00000),
+                               __int_as_float(3 * t + (k == 2 ? 0 : k + 1)), __int_as_float(u));
         if (u >= 0) {
             int kp = 0;
             if (a.tn[1][u] == t) kp = 1;

@@ -96,7 +96,9 @@ void launch_field_tables(const FieldTableArgs &a, cudaStream_t s);
 //   the float coordinates for FP32 meshes), e0' = 3u + (k'+1) mod 3 and
 //   e1' = 3u + (k'+2) mod 3 as int bits: the walk state of u entered
 //   through this edge is (W0, W1, W2) = (T[k'+1][u], T[k'+2][u], Q).
-// Boundary edge: (NaN, NaN, code, code) with the side code tn[k][t] < 0.
+// Boundary edge: (NaN, NaN, 3t + (k+1) mod 3, side code tn[k][t] < 0): NaN
+// coordinates end an FP32 hop loop, and the first code still names an edge
+// of t, the triangle the walk is in.
 void launch_build_he(const int32_t *const tv[3], const int32_t *const tn[3], const float2 *xyc, int64_t nt,
                      float4 *he, cudaStream_t s);
 

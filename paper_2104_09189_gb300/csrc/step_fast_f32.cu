@@ -178,17 +178,17 @@ __global__ void __launch_bounds__(kBlock, kMinBlocks) k_step_fast_f32(FastArgs a
                 }
                 if (s1 == 2 || s2 == 2 || s3 == 2) {
                     // boundary edge with the foot on its side: exactly 0 (the
-                    // record of a boundary half-edge holds its side code)
+                    // record of a boundary half-edge holds its side code last)
                     if (s1 == 2) {
-                        const int nb = __float_as_int(__ldg(&a.he[e0]).z);
+                        const int nb = __float_as_int(__ldg(&a.he[e0]).w);
                         if (nb < 0 && (fside >> (-1 - nb) & 1u)) s1 = 0;
                     }
                     if (s2 == 2) {
-                        const int nb = __float_as_int(__ldg(&a.he[e1]).z);
+                        const int nb = __float_as_int(__ldg(&a.he[e1]).w);
                         if (nb < 0 && (fside >> (-1 - nb) & 1u)) s2 = 0;
                     }
                     if (s3 == 2) {
-                        const int nb = __float_as_int(__ldg(&a.he[e2]).z);
+                        const int nb = __float_as_int(__ldg(&a.he[e2]).w);
                         if (nb < 0 && (fside >> (-1 - nb) & 1u)) s3 = 0;
                     }
                 }
@@ -253,7 +253,7 @@ __global__ void __launch_bounds__(kBlock, kMinBlocks) k_step_fast_f32(FastArgs a
                         if (neg[q] && pick-- == 0) k = q;
                 }
                 const float4 R = __ldg(&a.he[k == 0 ? e0 : (k == 1 ? e1 : e2)]);
-                if (__float_as_int(R.z) < 0) break;    // a boundary edge: not for a foot inside a valid mesh
+                if (isnan(R.x)) break;    // a boundary edge: not for a foot inside a valid mesh
                 // the next triangle: (W2, W1, Q), (W0, W2, Q) or (W1, W0, Q)
                 if (k == 0) A = C;
                 else if (k == 1) B = C;
@@ -280,7 +280,7 @@ __global__ void __launch_bounds__(kBlock, kMinBlocks) k_step_fast_f32(FastArgs a
                     const bool c1 = q1 < -eb1, c2 = q2 < -eb2 && !(c1 && q1 <= q2);
                     if (!(c1 || c2)) break;
                     const float4 Q = __ldg(&a.he[c2 ? e1 : e0]);
-                    if (__float_as_int(Q.z) < 0) break;    // a boundary edge: not for a foot inside a valid mesh
+                    if (isnan(Q.x)) break;    // a boundary edge: not for a foot inside a valid mesh
                     if (c2) B = C;
                     else A = C;
                     C = make_float2(Q.x, Q.y);
