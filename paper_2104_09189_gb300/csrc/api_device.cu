@@ -40,6 +40,16 @@ static void split_grid(double v, float2 &o)
     o.y = (float)(v - g);
 }
 
+void pack_fast_constants(int32_t kind, const double c[6], FastProb &f)
+{
+    for (int k = 0; k < 6; ++k) split_df(c[k], f.c[k]);
+    if (kind == SL_FIELD_ROTATION && c[1] >= 0.0 && c[1] <= 1.0 && c[2] >= 0.0 && c[2] <= 1.0) {
+        split_grid(c[1], f.c[1]);
+        split_grid(c[2], f.c[2]);
+        f.flags |= kFastCentreGrid;
+    }
+}
+
 int32_t default_walk_cap(const sl_mesh *m)
 {
     int32_t M = 1;
@@ -296,7 +306,7 @@ static void fill_fast(const sl_mesh *m, const ProbStep *ps, FastProb *out)
             break;
         default: break;
         }
-        for (int k = 0; k < 6; ++k) split_df(c[k], f.c[k]);
+        pack_fast_constants(q.kind, c, f);
     }
 }
 

@@ -69,13 +69,6 @@ sl_status scratch_for(int dev, DeviceScratch &out)
     return SL_OK;
 }
 
-void split_pair(double v, float2 &o)
-{
-    const float h = (float)v;
-    o.x = h;
-    o.y = (float)(v - (double)h);
-}
-
 // The per-step constants of one problem (the same formulas as sl_step).
 sl_status constants(const sl_problem &q, int64_t n, int32_t p, FastProb &f)
 {
@@ -117,7 +110,7 @@ sl_status constants(const sl_problem &q, int64_t n, int32_t p, FastProb &f)
         break;
     default: break;
     }
-    for (int k = 0; k < 6; ++k) split_pair(c[k], f.c[k]);
+    pack_fast_constants(q.kind, c, f);
     return SL_OK;
 }
 

@@ -107,8 +107,17 @@ __device__ __forceinline__ void foot_df(const FastProb &P, const FastArgs &a, in
         break;
     }
     case SL_FIELD_ROTATION:
-        X = df_add(x, df_mul(dfp(P.c[0]), df_sub(y, dfp(P.c[2]))));
-        Y = df_sub(y, df_mul(dfp(P.c[0]), df_sub(x, dfp(P.c[1]))));
+        if (P.flags & kFastCentreGrid) {
+            // node and centre in (grid, remainder) form: the grid parts
+            // subtract exactly, the remainders with one rounding (2^-49)
+            const df dy = df_make(__fsub_rn(y.h, P.c[2].x), __fsub_rn(y.l, P.c[2].y));
+            const df dx = df_make(__fsub_rn(x.h, P.c[1].x), __fsub_rn(x.l, P.c[1].y));
+            X = df_add(x, df_mul(dfp(P.c[0]), dy));
+            Y = df_sub(y, df_mul(dfp(P.c[0]), dx));
+        } else {
+            X = df_add(x, df_mul(dfp(P.c[0]), df_sub(y, dfp(P.c[2]))));
+            Y = df_sub(y, df_mul(dfp(P.c[0]), df_sub(x, dfp(P.c[1]))));
+        }
         break;
     case SL_FIELD_SWIRL: {
         const float4 g = a.g1[i];
@@ -257,23 +266,46 @@ struct Certified {
     float ea, eb, ed, n3h, e3;
 };
 
-__device__ __forceinline__ Certified certify(float4 A, float4 B, float4 C, float Xg, float Xr, float Yg, float Yr)
+// The numerators alone, with the |.|-sums of the grid differences of A, B
+// and the foot relative to C that their bounds take.
+struct Numerators {
+    df n1, n2, den;
+    float sA, sB, sX;
+};
+
+__device__ __forceinline__ Numerators numerators(float4 A, float4 B, float4 C, float Xg, float Xr, float Yg,
+                                                 float Yr)
 {
     const gd dAx = gd_sub(A.x, A.z, C.x, C.z), dAy = gd_sub(A.y, A.w, C.y, C.w);
     const gd dBx = gd_sub(B.x, B.z, C.x, C.z), dBy = gd_sub(B.y, B.w, C.y, C.w);
     const gd dXx = gd_sub(Xg, Xr, C.x, C.z), dXy = gd_sub(Yg, Yr, C.y, C.w);
-    Certified t;
+    Numerators t;
     t.n1 = cross_gd(dXx, dXy, dBx, dBy);
     t.n2 = cross_gd(dAx, dAy, dXx, dXy);
     t.den = cross_gd(dAx, dAy, dBx, dBy);
-    const float sA = fabsf(dAx.g) + fabsf(dAy.g), sB = fabsf(dBx.g) + fabsf(dBy.g);
-    const float sX = fabsf(dXx.g) + fabsf(dXy.g);
-    t.ea = cert_bound_g(sX + sB);
-    t.eb = cert_bound_g(sA + sX);
-    t.ed = cert_bound_g(sA + sB);
+    t.sA = fabsf(dAx.g) + fabsf(dAy.g);
+    t.sB = fabsf(dBx.g) + fabsf(dBy.g);
+    t.sX = fabsf(dXx.g) + fabsf(dXy.g);
+    return t;
+}
+
+__device__ __forceinline__ Certified certify_bounds(const Numerators &n)
+{
+    Certified t;
+    t.n1 = n.n1;
+    t.n2 = n.n2;
+    t.den = n.den;
+    t.ea = cert_bound_g(n.sX + n.sB);
+    t.eb = cert_bound_g(n.sA + n.sX);
+    t.ed = cert_bound_g(n.sA + n.sB);
     t.n3h = __fsub_rn(__fsub_rn(t.den.h, t.n1.h), t.n2.h);
     t.e3 = t.ed + t.ea + t.eb + 0x1p-22f * (fabsf(t.den.h) + fabsf(t.n1.h) + fabsf(t.n2.h));
     return t;
+}
+
+__device__ __forceinline__ Certified certify(float4 A, float4 B, float4 C, float Xg, float Xr, float Yg, float Yr)
+{
+    return certify_bounds(numerators(A, B, C, Xg, Xr, Yg, Yr));
 }
 
 // The P1 value (Remark 1) with the barycentric coordinates of Eq. 6,
@@ -308,30 +340,20 @@ __device__ __forceinline__ float2 p1_value(const FastArgs &a, int w0, int w1, in
     return p1_value_of(vin[w0], vin[w1], vin[w2], n1, n2, den);
 }
 
-// A foot equal to its own node's stored coordinate pair is that node (see
-// step_node): a boundary node whose velocity points out of the square is
-// clipped at the start of its segment, and a node where the field vanishes
-// does not move.
+// A foot that comes out of the foot arithmetic as its own node's stored
+// coordinate pair, bit for bit, is that node (see step_node): a boundary
+// node whose velocity points out of the square is clipped at the start of
+// its segment, and a node where the field vanishes does not move.
 __device__ __forceinline__ bool foot_is_node(df x, df y, df X, df Y)
 {
     return X.h == x.h && X.l == x.l && Y.h == y.h && Y.l == y.l;
 }
 
-// The foot of node i for this step: Euler (Eq. 4) in double-float, decided
-// against the boundary in double rounding, clipped, and returned in the
-// (grid, remainder) form of the certified test.  Returns true when clipped;
-// at_node: the foot is the node itself.
-__device__ __forceinline__ bool foot_pair(const FastArgs &a, int64_t i, const FastProb &P, df &X, df &Y,
-                                          bool &at_node)
+// A foot with both high parts strictly inside (0, 1) needs neither the
+// boundary rounding nor the clip (both act only at or beyond a side).
+__device__ __forceinline__ bool df_inside(df X, df Y)
 {
-    const float4 xq = a.xyq[i];
-    const df x = df_make(xq.x, xq.z), y = df_make(xq.y, xq.w);
-    foot_df(P, a, i, x, y, X, Y);
-    round_boundary(X);
-    round_boundary(Y);
-    const bool clipped = clip_df(x, y, X, Y);
-    at_node = foot_is_node(x, y, X, Y);
-    return clipped;
+    return X.h > 0.0f && X.h < 1.0f && Y.h > 0.0f && Y.h < 1.0f;
 }
 
 __device__ __forceinline__ void foot_to_grid(df &X, df &Y)
@@ -341,6 +363,29 @@ __device__ __forceinline__ void foot_to_grid(df &X, df &Y)
     X = df_make(g, r);
     to_grid(Y, g, r);
     Y = df_make(g, r);
+}
+
+// The foot of node i for this step: Euler (Eq. 4) in double-float, decided
+// against the boundary in double rounding, clipped, and returned in the
+// (grid, remainder) form of the certified test.  Returns true when clipped.
+// at_node: a foot on or beyond a side that is the node itself (an outward
+// boundary node); a foot inside the square is not reported here.
+__device__ __forceinline__ bool foot_pair(const FastArgs &a, int64_t i, const FastProb &P, df &X, df &Y,
+                                          bool &at_node)
+{
+    const float4 xq = a.xyq[i];
+    const df x = df_make(xq.x, xq.z), y = df_make(xq.y, xq.w);
+    foot_df(P, a, i, x, y, X, Y);
+    const bool inside = df_inside(X, Y);
+    bool clipped = false;
+    if (!inside) {
+        round_boundary(X);
+        round_boundary(Y);
+        clipped = clip_df(x, y, X, Y);
+    }
+    at_node = !inside && foot_is_node(x, y, X, Y);
+    foot_to_grid(X, Y);
+    return clipped;
 }
 
 // FP32 hops on the high parts while one of the two exits of the current
@@ -663,7 +708,6 @@ __device__ __forceinline__ bool settle_node(const FastArgs &a, int64_t i, int pi
     df X, Y;
     bool at_node;
     const bool clipped = foot_pair(a, i, P, X, Y, at_node);
-    foot_to_grid(X, Y);
     const int4 tq = a.t0v[i];
     const float4 A = a.xyq[tq.y], B = a.xyq[tq.z], C = a.xyq[tq.w];
     // the start triangle's values are read together with its vertices, not
@@ -671,13 +715,21 @@ __device__ __forceinline__ bool settle_node(const FastArgs &a, int64_t i, int pi
     // further round trip to memory
     const float2 *vin = (const float2 *)a.vin;
     const float2 V1 = vin[tq.y], V2 = vin[tq.z], V3 = vin[tq.w];
-    const Certified t = certify(A, B, C, X.h, X.l, Y.h, Y.l);
+    // One bound for the three numerators (ea, eb, ed <= E): looser than the
+    // certified test's, so a node settled here is settled there too; the
+    // few it leaves undecided take the exact decisions below.
+    const Numerators t = numerators(A, B, C, X.h, X.l, Y.h, Y.l);
+    const float E = cert_bound_g(t.sA + t.sB + t.sX);
+    const float n3h = __fsub_rn(__fsub_rn(t.den.h, t.n1.h), t.n2.h);
     bool degenerate = false;
-    if (!(t.n1.h > t.ea && t.n2.h > t.eb && t.n3h > t.e3)) {
+    if (!(fminf(t.n1.h, t.n2.h) > E &&
+          n3h > 3.0f * E + 0x1p-22f * (fabsf(t.den.h) + fabsf(t.n1.h) + fabsf(t.n2.h)))) {
         if (at_node) {
             // The foot is node i (as in step_node).  When T^0 has node i as a
             // vertex, two of its signs are zero, so the test above cannot
             // have passed: such a node is settled here with its own value.
+            // (A foot inside the square at its node, f = 0 there, is left
+            // to the finish pass, which takes the same decision.)
             if (tq.y != (int32_t)i && tq.z != (int32_t)i && tq.w != (int32_t)i) return false;
             ((float2 *)a.vout)[i] = vin[i];
             c.clipped = clipped;
@@ -697,12 +749,14 @@ __device__ __forceinline__ bool settle_node(const FastArgs &a, int64_t i, int pi
         // codes of step_node).  Any other sign that is not certainly
         // positive leaves the node to the finish pass.
         if (!clipped) return false;
-        const int s1 = t.n1.h > t.ea ? 1 : (t.n1.h < -t.ea ? -1 : 2);
-        const int s2 = t.n2.h > t.eb ? 1 : (t.n2.h < -t.eb ? -1 : 2);
-        int s3 = t.n3h > t.e3 ? 1 : (t.n3h < -t.e3 ? -1 : 2);
+        // the signs exactly as step_node's certified test takes them
+        const Certified u = certify_bounds(t);
+        const int s1 = u.n1.h > u.ea ? 1 : (u.n1.h < -u.ea ? -1 : 2);
+        const int s2 = u.n2.h > u.eb ? 1 : (u.n2.h < -u.eb ? -1 : 2);
+        int s3 = u.n3h > u.e3 ? 1 : (u.n3h < -u.e3 ? -1 : 2);
         if (s3 == 2) {
-            const df n3 = df_sub(df_sub(t.den, t.n1), t.n2);
-            const float ec = t.ed + t.ea + t.eb + 0x1p-45f * (fabsf(t.den.h) + fabsf(t.n1.h) + fabsf(t.n2.h));
+            const df n3 = df_sub(df_sub(u.den, u.n1), u.n2);
+            const float ec = u.ed + u.ea + u.eb + 0x1p-45f * (fabsf(u.den.h) + fabsf(u.n1.h) + fabsf(u.n2.h));
             s3 = n3.h > ec ? 1 : (n3.h < -ec ? -1 : 2);
         }
         if (s1 < 0 || s2 < 0 || s3 < 0) return false;

@@ -18,13 +18,23 @@ namespace sl {
 //   SWIRL     X = x - c0 g1(x)                         (c0 = dt cos(pi t / T))
 //   PAPER,    X = x - c0 g1(x) - c1 g2(x)              (c0, c1 = dt x time factors)
 //   FOURIER8
-// g1, g2 are node tables filled once per field (k_field_tables).
+// g1, g2 are node tables filled once per field (k_field_tables).  A rotation
+// centre inside the unit square is stored in (grid, remainder) form instead
+// (flag kFastCentreGrid): a node's grid part minus the centre's is then exact
+// in float, and x - c costs two additions.
 struct FastProb {
     int32_t kind;
-    int32_t pad;
+    int32_t flags;      // kFastCentreGrid
     double dt;          // only used by the clip path and the debug output
     float2 c[6];        // (hi, lo)
 };
+
+constexpr int32_t kFastCentreGrid = 1;
+
+// The six per-step constants of a problem as float pairs: (hi, lo), or for a
+// rotation centre in [0, 1]^2 the (grid, remainder) split of the node
+// coordinates (g = c rounded to the grid of 2^-24, r = fl32(c - g)).
+void pack_fast_constants(int32_t kind, const double c[6], FastProb &f);
 
 struct FastArgs {
     const float4 *xyq;            // FP64 meshes: (xh, yh, xl, yl); FP32 meshes: unused
