@@ -17,6 +17,7 @@ Launch on N GPUs with torchrun: every rank runs its own copy of the workload
 over ranks, value counts every rank's node-updates.
 """
 import argparse
+import gc
 import json
 import os
 import statistics
@@ -496,17 +497,22 @@ def main():
     if dist:
         dist.barrier()
     torch.cuda.synchronize()
-    ev0 = torch.cuda.Event(enable_timing=True)
-    ev1 = torch.cuda.Event(enable_timing=True)
-    ev0.record(stream)
-    for _ in range(args.steps):
+    # one event before each run and one after the last (the runs are timed
+    # as a whole; the per-run spread shows host stalls between runs); the
+    # collector is paused so that it cannot stall the launching thread
+    evs = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps + 1)]
+    gc.disable()
+    evs[0].record(stream)
+    for k in range(args.steps):
         sl.sl_mesh_reset_t0(h)
         sl.sl_run(h, probs, 0, S, v, w, use_graph=True)
-    ev1.record(stream)
+        evs[k + 1].record(stream)
     torch.cuda.synchronize()
+    gc.enable()
     if dist:
         dist.barrier()
-    elapsed = ev0.elapsed_time(ev1) / 1e3
+    elapsed = evs[0].elapsed_time(evs[-1]) / 1e3
+    per_run = [evs[k].elapsed_time(evs[k + 1]) for k in range(args.steps)]
     clocks = sampler.stop()
     elapsed = max_over_ranks(dist, elapsed, "cuda")
 
@@ -649,6 +655,7 @@ def main():
                  "clipped": stats["clipped"], "fallbacks": stats["fallbacks"]},
         "setup_s": setup_s,
         "phases": phases,
+        "per_run_ms": {"min": min(per_run), "median": statistics.median(per_run), "max": max(per_run)},
         "gather_probe": gather,
         "autotune": tune,
         "plain_fp64": plain,

@@ -308,10 +308,22 @@ __device__ __forceinline__ Certified certify(float4 A, float4 B, float4 C, float
     return certify_bounds(numerators(A, B, C, Xg, Xr, Yg, Yr));
 }
 
+// 1 / d to about 2^-24 relative: the hardware approximation refined by one
+// Newton step.  d is twice a triangle's area, far above the subnormal range
+// for any triangle with vertices on the grid of 2^-24.
+__device__ __forceinline__ float rcp_refined(float d)
+{
+    float r;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(d));
+    return __fmaf_rn(r, __fmaf_rn(-d, r, 1.0f), r);
+}
+
 // The P1 value (Remark 1) with the barycentric coordinates of Eq. 6,
 // theta_k = n_k / den:  V = v3 + (n1 (v1 - v3) + n2 (v2 - v3)) / den, in
 // double-float: the value differences from a TwoSum of the high parts, the
-// products from their exact FMA remainders, one division.
+// products from their exact FMA remainders, and the quotient by one
+// correction step (Karp and Markstein's division: q1 = w r, the residual
+// w - q1 den from two FMAs, q2 = residual r), about 2^-45 relative.
 __device__ __forceinline__ float2 p1_value_of(float2 V1, float2 V2, float2 V3, df n1, df n2, df den)
 {
     float d1h, d1l, d2h, d2l;
@@ -328,9 +340,10 @@ __device__ __forceinline__ float2 p1_value_of(float2 V1, float2 V2, float2 V3, d
     float ws, wt;
     two_sum_f(p1, p2, ws, wt);
     wt = __fadd_rn(wt, __fadd_rn(q1, q2));
-    df w;
-    fast_two_sum_f(ws, wt, w.h, w.l);
-    const df v = df_add(dfp(V3), df_mul(w, df_rcp(den)));
+    const float r = rcp_refined(den.h);
+    const float c1 = __fmul_rn(ws, r);
+    const float rho = __fadd_rn(__fmaf_rn(-c1, den.h, ws), __fmaf_rn(-c1, den.l, wt));
+    const df v = df_add(dfp(V3), df_make(c1, __fmul_rn(rho, r)));
     return make_float2(v.h, v.l);
 }
 
