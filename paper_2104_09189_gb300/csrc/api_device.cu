@@ -232,7 +232,10 @@ static StepArgs make_args(const sl_mesh *m, const ProbStep *probs_dev, const voi
     return a;
 }
 
-static FastArgs make_fast_args(const sl_mesh *m, const FastProb *fp, const void *vin, void *vout, const sl_debug *dbg)
+// fp: the step's constants on the device; fh: the same on the host (or
+// NULL), copied into the kernel parameters for a single problem.
+static FastArgs make_fast_args(const sl_mesh *m, const FastProb *fp, const void *vin, void *vout, const sl_debug *dbg,
+                               const FastProb *fh = nullptr)
 {
     FastArgs a;
     std::memset(&a, 0, sizeof(a));
@@ -252,6 +255,10 @@ static FastArgs make_fast_args(const sl_mesh *m, const FastProb *fp, const void 
     a.g1 = (const float4 *)m->d.g1;
     a.g2 = (const float4 *)m->d.g2;
     a.probs = fp;
+    if (fh && m->n_problems == 1) {
+        a.prob0 = fh[0];
+        a.single = 1;
+    }
     a.node_off = m->d.node_off;
     a.nprob = m->n_problems;
     a.walk_cap = m->opt_walk_cap > 0 ? m->opt_walk_cap : default_walk_cap(m);
@@ -463,11 +470,12 @@ static sl_status run_steps(sl_mesh *m, const sl_problem *probs, int64_t n0, int3
                        g.config == m->opt_config && g.config_first == m->opt_config_first &&
                        g.t0_initial == first_initial && g.split == m->opt_split;
     auto config_of = [&](int32_t k) { return (k == 0 && first_initial) ? m->opt_config_first : m->opt_config; };
+    std::vector<FastProb> fh;   // the fast kernels' constants, host copy (filled when recording)
     if (!reuse) {
         // synchronous copies: a graph recorded below may replay them later
         SL_CUDA(cudaStreamSynchronize(s));
         if (fast) {
-            std::vector<FastProb> fh((size_t)m->n_problems * (size_t)n_steps);
+            fh.resize((size_t)m->n_problems * (size_t)n_steps);
             for (int32_t k = 0; k < n_steps; ++k)
                 fill_fast(m, host.data() + (size_t)k * m->n_problems, fh.data() + (size_t)k * m->n_problems);
             sl_status st = ensure_fprobs(m, fper * n_steps);
@@ -485,7 +493,8 @@ static sl_status run_steps(sl_mesh *m, const sl_problem *probs, int64_t n0, int3
             launch_to_df((const double *)v, (float2 *)v2, m->N, q);
             void *a = v2, *b = v;
             for (int32_t k = 0; k < n_steps; ++k) {
-                FastArgs args = make_fast_args(m, (const FastProb *)((char *)m->d.fprobs + fper * k), a, b, nullptr);
+                FastArgs args = make_fast_args(m, (const FastProb *)((char *)m->d.fprobs + fper * k), a, b, nullptr,
+                                               fh.data() + (size_t)k * m->n_problems);
                 sl_status st = launch_fast(m, args, false, config_of(k), k == 0 && first_initial, q);
                 if (st != SL_OK) return st;
                 void *t = a;
@@ -500,7 +509,8 @@ static sl_status run_steps(sl_mesh *m, const sl_problem *probs, int64_t n0, int3
         for (int32_t k = 0; k < n_steps; ++k) {
             sl_status st;
             if (fast) {
-                FastArgs args = make_fast_args(m, (const FastProb *)((char *)m->d.fprobs + fper * k), a, b, nullptr);
+                FastArgs args = make_fast_args(m, (const FastProb *)((char *)m->d.fprobs + fper * k), a, b, nullptr,
+                                               fh.data() + (size_t)k * m->n_problems);
                 st = launch_fast(m, args, false, config_of(k), k == 0 && first_initial, q);
             } else {
                 StepArgs args = make_args(m, (const ProbStep *)((char *)m->d.probs + per * k), a, b, nullptr);
@@ -597,13 +607,13 @@ extern "C" sl_status sl_step(sl_mesh *m, const sl_problem *probs, int64_t n, con
         if (!m->d.dfa) SL_CUDA(cudaMalloc(&m->d.dfa, sizeof(float2) * m->N));
         if (!m->d.dfb) SL_CUDA(cudaMalloc(&m->d.dfb, sizeof(float2) * m->N));
         launch_to_df((const double *)v_in, (float2 *)m->d.dfa, m->N, s);
-        FastArgs a = make_fast_args(m, (const FastProb *)m->d.fprobs, m->d.dfa, m->d.dfb, dbg);
+        FastArgs a = make_fast_args(m, (const FastProb *)m->d.fprobs, m->d.dfa, m->d.dfb, dbg, fh.data());
         st = launch_fast(m, a, debug, m->t0_initial ? m->opt_config_first : m->opt_config, m->t0_initial, s);
         if (st != SL_OK) return st;
         launch_from_df((const float2 *)m->d.dfb, (double *)v_out, m->N, s);
         SL_CUDA(cudaGetLastError());
     } else {
-        FastArgs a = make_fast_args(m, (const FastProb *)m->d.fprobs, v_in, v_out, dbg);
+        FastArgs a = make_fast_args(m, (const FastProb *)m->d.fprobs, v_in, v_out, dbg, fh.data());
         st = launch_fast(m, a, debug, m->t0_initial ? m->opt_config_first : m->opt_config, m->t0_initial, s);
         if (st != SL_OK) return st;
     }

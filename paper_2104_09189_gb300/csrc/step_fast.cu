@@ -96,9 +96,10 @@ __device__ __forceinline__ bool clip_df(df x, df y, df &X, df &Y)
 
 // Euler foot X = x - dt f(x, t_{n+1}) (Eq. 4) in double-float, with the
 // field's time factors folded into the per-step constants.
-__device__ __forceinline__ void foot_df(const FastProb &P, const FastArgs &a, int64_t i, df x, df y, df &X, df &Y)
+template <int kKind>
+__device__ __forceinline__ void foot_df_k(const FastProb &P, const FastArgs &a, int64_t i, df x, df y, df &X, df &Y)
 {
-    switch (P.kind) {
+    switch (kKind) {
     case SL_FIELD_AFFINE: {
         df fx = df_add(df_add(dfp(P.c[0]), df_mul(dfp(P.c[1]), x)), df_mul(dfp(P.c[2]), y));
         df fy = df_add(df_add(dfp(P.c[3]), df_mul(dfp(P.c[4]), x)), df_mul(dfp(P.c[5]), y));
@@ -138,6 +139,19 @@ __device__ __forceinline__ void foot_df(const FastProb &P, const FastArgs &a, in
         X = x;
         Y = y;
         break;
+    }
+}
+
+// The same for a kind known only at run time.
+__device__ __forceinline__ void foot_df(const FastProb &P, const FastArgs &a, int64_t i, df x, df y, df &X, df &Y)
+{
+    switch (P.kind) {
+    case SL_FIELD_AFFINE: foot_df_k<SL_FIELD_AFFINE>(P, a, i, x, y, X, Y); break;
+    case SL_FIELD_ROTATION: foot_df_k<SL_FIELD_ROTATION>(P, a, i, x, y, X, Y); break;
+    case SL_FIELD_SWIRL: foot_df_k<SL_FIELD_SWIRL>(P, a, i, x, y, X, Y); break;
+    case SL_FIELD_PAPER: foot_df_k<SL_FIELD_PAPER>(P, a, i, x, y, X, Y); break;
+    case SL_FIELD_FOURIER8: foot_df_k<SL_FIELD_FOURIER8>(P, a, i, x, y, X, Y); break;
+    default: foot_df_k<SL_FIELD_ZERO>(P, a, i, x, y, X, Y); break;
     }
 }
 
@@ -383,12 +397,14 @@ __device__ __forceinline__ void foot_to_grid(df &X, df &Y)
 // (grid, remainder) form of the certified test.  Returns true when clipped.
 // at_node: a foot on or beyond a side that is the node itself (an outward
 // boundary node); a foot inside the square is not reported here.
+template <int kKind>
 __device__ __forceinline__ bool foot_pair(const FastArgs &a, int64_t i, const FastProb &P, df &X, df &Y,
                                           bool &at_node)
 {
     const float4 xq = a.xyq[i];
     const df x = df_make(xq.x, xq.z), y = df_make(xq.y, xq.w);
-    foot_df(P, a, i, x, y, X, Y);
+    if (kKind < 0) foot_df(P, a, i, x, y, X, Y);
+    else foot_df_k<kKind < 0 ? 0 : kKind>(P, a, i, x, y, X, Y);
     const bool inside = df_inside(X, Y);
     bool clipped = false;
     if (!inside) {
@@ -714,13 +730,13 @@ __global__ void __launch_bounds__(kBlock, kMinBlocks) k_step_fast_df(FastArgs a)
 // to the queue for the finish pass, which runs the full node step on it.  The
 // foot, the certified test and the value are the same functions as in
 // step_node, so the split does not change any result.
-template <bool kDebug>
+template <bool kDebug, int kKind>
 __device__ __forceinline__ bool settle_node(const FastArgs &a, int64_t i, int pi, NodeCounters &c)
 {
-    const FastProb &P = a.probs[pi];
+    const FastProb &P = kKind < 0 ? a.probs[pi] : a.prob0;
     df X, Y;
     bool at_node;
-    const bool clipped = foot_pair(a, i, P, X, Y, at_node);
+    const bool clipped = foot_pair<kKind>(a, i, P, X, Y, at_node);
     const int4 tq = a.t0v[i];
     const float4 A = a.xyq[tq.y], B = a.xyq[tq.z], C = a.xyq[tq.w];
     // the start triangle's values are read together with its vertices, not
@@ -797,14 +813,16 @@ __device__ __forceinline__ bool settle_node(const FastArgs &a, int64_t i, int pi
     return true;
 }
 
-template <bool kStats, bool kDebug, int kBlock, int kMinBlocks>
+// kKind >= 0: a single problem of that field kind, whose constants come
+// from the kernel parameters (a.prob0); -1: any problems.
+template <bool kStats, bool kDebug, int kBlock, int kMinBlocks, int kKind>
 __global__ void __launch_bounds__(kBlock, kMinBlocks) k_settle_df(FastArgs a)
 {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     const bool active = i < a.N;
     NodeCounters c;
-    const int pi = block_problem(a.node_off, a.nprob, a.N, i);
-    const bool queued = active && !settle_node<kDebug>(a, i, pi, c);
+    const int pi = kKind < 0 ? block_problem(a.node_off, a.nprob, a.N, i) : 0;
+    const bool queued = active && !settle_node<kDebug, kKind>(a, i, pi, c);
     // warp-aggregated append to the queue of the finish pass
     const unsigned mask = __ballot_sync(0xffffffffu, queued);
     if (mask) {
@@ -865,11 +883,32 @@ static void launch_split_cfg(const FastArgs &a, bool stats, bool debug, int sms,
     if (grid == 0) return;
     cudaMemsetAsync(a.queue_count, 0, sizeof(uint32_t), s);
     if (stats) {
-        if (debug) k_settle_df<true, true, kBlock, kMinBlocks><<<grid, kBlock, 0, s>>>(a);
-        else k_settle_df<true, false, kBlock, kMinBlocks><<<grid, kBlock, 0, s>>>(a);
+        if (debug) k_settle_df<true, true, kBlock, kMinBlocks, -1><<<grid, kBlock, 0, s>>>(a);
+        else k_settle_df<true, false, kBlock, kMinBlocks, -1><<<grid, kBlock, 0, s>>>(a);
+    } else if (debug) {
+        k_settle_df<false, true, kBlock, kMinBlocks, -1><<<grid, kBlock, 0, s>>>(a);
+    } else if (!a.single) {
+        k_settle_df<false, false, kBlock, kMinBlocks, -1><<<grid, kBlock, 0, s>>>(a);
     } else {
-        if (debug) k_settle_df<false, true, kBlock, kMinBlocks><<<grid, kBlock, 0, s>>>(a);
-        else k_settle_df<false, false, kBlock, kMinBlocks><<<grid, kBlock, 0, s>>>(a);
+        // the timed path of a single mesh: the field kind compiled in
+        switch (a.prob0.kind) {
+        case SL_FIELD_AFFINE:
+            k_settle_df<false, false, kBlock, kMinBlocks, SL_FIELD_AFFINE><<<grid, kBlock, 0, s>>>(a);
+            break;
+        case SL_FIELD_ROTATION:
+            k_settle_df<false, false, kBlock, kMinBlocks, SL_FIELD_ROTATION><<<grid, kBlock, 0, s>>>(a);
+            break;
+        case SL_FIELD_SWIRL:
+            k_settle_df<false, false, kBlock, kMinBlocks, SL_FIELD_SWIRL><<<grid, kBlock, 0, s>>>(a);
+            break;
+        case SL_FIELD_PAPER:
+            k_settle_df<false, false, kBlock, kMinBlocks, SL_FIELD_PAPER><<<grid, kBlock, 0, s>>>(a);
+            break;
+        case SL_FIELD_FOURIER8:
+            k_settle_df<false, false, kBlock, kMinBlocks, SL_FIELD_FOURIER8><<<grid, kBlock, 0, s>>>(a);
+            break;
+        default: k_settle_df<false, false, kBlock, kMinBlocks, SL_FIELD_ZERO><<<grid, kBlock, 0, s>>>(a); break;
+        }
     }
     const unsigned g2 = (unsigned)(sms > 0 ? sms : 152) * 8u;
     if (stats) {

@@ -51,6 +51,8 @@ struct FastArgs {
     void *vout;
     const float4 *g1, *g2;        // field tables (hi, lo) per node, or NULL
     const FastProb *probs;
+    FastProb prob0;               // single: a copy of probs[0] (kernel parameter space)
+    int32_t single;               // one problem, prob0 valid
     const int64_t *node_off;
     int32_t nprob;
     int32_t walk_cap;
