@@ -723,6 +723,52 @@ __global__ void __launch_bounds__(kBlock, kMinBlocks) k_step_fast_df(FastArgs a)
     if (kStats) warp_stats(a.stats, active, c.hops, c.exact, c.clipped, c.fallback, c.limit, c.filter2, c.excluded);
 }
 
+// The settle pass's test: one bound for the three numerators (ea, eb, ed <=
+// E), looser than the certified test's, so a node settled here is settled
+// there too.
+__device__ __forceinline__ bool settle_test(const Numerators &t)
+{
+    const float E = cert_bound_g(t.sA + t.sB + t.sX);
+    const float n3h = __fsub_rn(__fsub_rn(t.den.h, t.n1.h), t.n2.h);
+    return fminf(t.n1.h, t.n2.h) > E && n3h > 3.0f * E + 0x1p-22f * (fabsf(t.den.h) + fabsf(t.n1.h) + fabsf(t.n2.h));
+}
+
+// A node the settle test left undecided: 0 = to the finish pass, 1 = settled
+// in T^0 with the barycentric value, 2 = settled with the node's own value.
+//  * The foot is node i (as in step_node).  When T^0 has node i as a vertex,
+//    two of its signs are zero, so the test cannot have passed: settled with
+//    the node's value.  (A foot inside the square at its node, f = 0 there,
+//    is left to the finish pass, which takes the same decision.)
+//  * A foot clipped onto a side of the square lies on the boundary edge of
+//    its triangle on that side: that sign is exactly zero (the side codes of
+//    step_node).  Any other sign that is not certainly positive leaves the
+//    node to the finish pass.
+__device__ __forceinline__ int settle_decide(const FastArgs &a, int64_t i, int4 tq, df X, df Y, bool clipped,
+                                             bool at_node, const Numerators &t)
+{
+    if (at_node) return (tq.y == (int32_t)i || tq.z == (int32_t)i || tq.w == (int32_t)i) ? 2 : 0;
+    if (!clipped) return 0;
+    // the signs exactly as step_node's certified test takes them
+    const Certified u = certify_bounds(t);
+    const int s1 = u.n1.h > u.ea ? 1 : (u.n1.h < -u.ea ? -1 : 2);
+    const int s2 = u.n2.h > u.eb ? 1 : (u.n2.h < -u.eb ? -1 : 2);
+    int s3 = u.n3h > u.e3 ? 1 : (u.n3h < -u.e3 ? -1 : 2);
+    if (s3 == 2) {
+        const df n3 = df_sub(df_sub(u.den, u.n1), u.n2);
+        const float ec = u.ed + u.ea + u.eb + 0x1p-45f * (fabsf(u.den.h) + fabsf(u.n1.h) + fabsf(u.n2.h));
+        s3 = n3.h > ec ? 1 : (n3.h < -ec ? -1 : 2);
+    }
+    if (s1 < 0 || s2 < 0 || s3 < 0) return 0;
+    const uint32_t fside = (df_is(X, 0.0f) ? 1u : 0u) | (df_is(X, 1.0f) ? 2u : 0u) | (df_is(Y, 0.0f) ? 4u : 0u) |
+                           (df_is(Y, 1.0f) ? 8u : 0u);
+    const int32_t j = tri_of(tq.x);
+    const int32_t nb1 = s1 == 2 ? a.tn[0][j] : 0, nb2 = s2 == 2 ? a.tn[1][j] : 0, nb3 = s3 == 2 ? a.tn[2][j] : 0;
+    if (s1 == 2 && !(nb1 < 0 && (fside >> (-1 - nb1) & 1u))) return 0;
+    if (s2 == 2 && !(nb2 < 0 && (fside >> (-1 - nb2) & 1u))) return 0;
+    if (s3 == 2 && !(nb3 < 0 && (fside >> (-1 - nb3) & 1u))) return 0;
+    return 1;
+}
+
 // Settle pass of a split step: the nodes whose foot is certainly in the
 // start triangle (all three signs certified positive, or zero by a boundary
 // side code for a clipped foot; no hop, no exact stage) are finished here
@@ -744,22 +790,12 @@ __device__ __forceinline__ bool settle_node(const FastArgs &a, int64_t i, int pi
     // further round trip to memory
     const float2 *vin = (const float2 *)a.vin;
     const float2 V1 = vin[tq.y], V2 = vin[tq.z], V3 = vin[tq.w];
-    // One bound for the three numerators (ea, eb, ed <= E): looser than the
-    // certified test's, so a node settled here is settled there too; the
-    // few it leaves undecided take the exact decisions below.
     const Numerators t = numerators(A, B, C, X.h, X.l, Y.h, Y.l);
-    const float E = cert_bound_g(t.sA + t.sB + t.sX);
-    const float n3h = __fsub_rn(__fsub_rn(t.den.h, t.n1.h), t.n2.h);
     bool degenerate = false;
-    if (!(fminf(t.n1.h, t.n2.h) > E &&
-          n3h > 3.0f * E + 0x1p-22f * (fabsf(t.den.h) + fabsf(t.n1.h) + fabsf(t.n2.h)))) {
-        if (at_node) {
-            // The foot is node i (as in step_node).  When T^0 has node i as a
-            // vertex, two of its signs are zero, so the test above cannot
-            // have passed: such a node is settled here with its own value.
-            // (A foot inside the square at its node, f = 0 there, is left
-            // to the finish pass, which takes the same decision.)
-            if (tq.y != (int32_t)i && tq.z != (int32_t)i && tq.w != (int32_t)i) return false;
+    if (!settle_test(t)) {
+        const int d = settle_decide(a, i, tq, X, Y, clipped, at_node, t);
+        if (d == 0) return false;
+        if (d == 2) {
             ((float2 *)a.vout)[i] = vin[i];
             c.clipped = clipped;
             if (kDebug) {
@@ -773,29 +809,6 @@ __device__ __forceinline__ bool settle_node(const FastArgs &a, int64_t i, int pi
             }
             return true;
         }
-        // A foot clipped onto a side of the square lies on the boundary edge
-        // of its triangle on that side: that sign is exactly zero (the side
-        // codes of step_node).  Any other sign that is not certainly
-        // positive leaves the node to the finish pass.
-        if (!clipped) return false;
-        // the signs exactly as step_node's certified test takes them
-        const Certified u = certify_bounds(t);
-        const int s1 = u.n1.h > u.ea ? 1 : (u.n1.h < -u.ea ? -1 : 2);
-        const int s2 = u.n2.h > u.eb ? 1 : (u.n2.h < -u.eb ? -1 : 2);
-        int s3 = u.n3h > u.e3 ? 1 : (u.n3h < -u.e3 ? -1 : 2);
-        if (s3 == 2) {
-            const df n3 = df_sub(df_sub(u.den, u.n1), u.n2);
-            const float ec = u.ed + u.ea + u.eb + 0x1p-45f * (fabsf(u.den.h) + fabsf(u.n1.h) + fabsf(u.n2.h));
-            s3 = n3.h > ec ? 1 : (n3.h < -ec ? -1 : 2);
-        }
-        if (s1 < 0 || s2 < 0 || s3 < 0) return false;
-        const uint32_t fside = (df_is(X, 0.0f) ? 1u : 0u) | (df_is(X, 1.0f) ? 2u : 0u) |
-                               (df_is(Y, 0.0f) ? 4u : 0u) | (df_is(Y, 1.0f) ? 8u : 0u);
-        const int32_t j = tri_of(tq.x);
-        const int32_t nb1 = s1 == 2 ? a.tn[0][j] : 0, nb2 = s2 == 2 ? a.tn[1][j] : 0, nb3 = s3 == 2 ? a.tn[2][j] : 0;
-        if (s1 == 2 && !(nb1 < 0 && (fside >> (-1 - nb1) & 1u))) return false;
-        if (s2 == 2 && !(nb2 < 0 && (fside >> (-1 - nb2) & 1u))) return false;
-        if (s3 == 2 && !(nb3 < 0 && (fside >> (-1 - nb3) & 1u))) return false;
         degenerate = true;
     }
     ((float2 *)a.vout)[i] = p1_value_of(V1, V2, V3, t.n1, t.n2, t.den);
