@@ -386,20 +386,28 @@ static sl_status ensure_queue(sl_mesh *m)
 {
     if (m->opt_split && m->precision == SL_FP64 && !m->d.queue) {
         SL_CUDA(cudaMalloc(&m->d.queue, sizeof(int32_t) * (m->N > 0 ? m->N : 1)));
-        SL_CUDA(cudaMalloc(&m->d.queue_count, sizeof(uint32_t)));
+        SL_CUDA(cudaMalloc(&m->d.queue_count, 2 * sizeof(uint32_t)));   // alternating, see launch_fast
     }
     return SL_OK;
 }
 
 // initial: the step starts from the initial start triangles (never split).
-static sl_status launch_fast(sl_mesh *m, const FastArgs &a, bool debug, int config, bool initial, cudaStream_t s)
+// split_seq: the number of split steps already enqueued in this sequence of
+// steps (NULL: a sequence of one).  Split steps use the two queue counters
+// in turn; the first one of a sequence zeroes its counter, and each finish
+// pass zeroes the counter of the next, so the steps between need no memset.
+static sl_status launch_fast(sl_mesh *m, const FastArgs &a, bool debug, int config, bool initial, cudaStream_t s,
+                             int32_t *split_seq = nullptr)
 {
     if (m->precision == SL_FP64 && m->opt_split && !initial && m->opt_strategy == 0 && !m->opt_outside) {
         if (!m->d.queue) return fail(SL_E_STATE, "split step without its queue scratch");
+        const int32_t q = split_seq ? *split_seq : 0;
         FastArgs x = a;
         x.queue = m->d.queue;
-        x.queue_count = m->d.queue_count;
-        launch_split_df(x, m->opt_stats != 0, debug, m->sms, s);
+        x.queue_count = m->d.queue_count + (q & 1);
+        x.queue_next = split_seq ? m->d.queue_count + ((q + 1) & 1) : nullptr;
+        launch_split_df(x, m->opt_stats != 0, debug, m->sms, q == 0, s);
+        if (split_seq) ++*split_seq;
     } else {
         for_levels(m, a, [&](const FastArgs &x) {
             if (m->precision == SL_FP64) launch_fast_df(x, m->opt_stats != 0, debug, config, s);
@@ -492,10 +500,11 @@ static sl_status run_steps(sl_mesh *m, const sl_problem *probs, int64_t n0, int3
             // values travel as (hi, lo) float pairs in the two caller buffers
             launch_to_df((const double *)v, (float2 *)v2, m->N, q);
             void *a = v2, *b = v;
+            int32_t split_seq = 0;
             for (int32_t k = 0; k < n_steps; ++k) {
                 FastArgs args = make_fast_args(m, (const FastProb *)((char *)m->d.fprobs + fper * k), a, b, nullptr,
                                                fh.data() + (size_t)k * m->n_problems);
-                sl_status st = launch_fast(m, args, false, config_of(k), k == 0 && first_initial, q);
+                sl_status st = launch_fast(m, args, false, config_of(k), k == 0 && first_initial, q, &split_seq);
                 if (st != SL_OK) return st;
                 void *t = a;
                 a = b;
@@ -506,12 +515,13 @@ static sl_status run_steps(sl_mesh *m, const sl_problem *probs, int64_t n0, int3
             return SL_OK;
         }
         void *a = v, *b = v2;
+        int32_t split_seq = 0;
         for (int32_t k = 0; k < n_steps; ++k) {
             sl_status st;
             if (fast) {
                 FastArgs args = make_fast_args(m, (const FastProb *)((char *)m->d.fprobs + fper * k), a, b, nullptr,
                                                fh.data() + (size_t)k * m->n_problems);
-                st = launch_fast(m, args, false, config_of(k), k == 0 && first_initial, q);
+                st = launch_fast(m, args, false, config_of(k), k == 0 && first_initial, q, &split_seq);
             } else {
                 StepArgs args = make_args(m, (const ProbStep *)((char *)m->d.probs + per * k), a, b, nullptr);
                 st = launch_step(m, args, false, q);

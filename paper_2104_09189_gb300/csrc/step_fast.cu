@@ -854,6 +854,7 @@ template <bool kStats, bool kDebug>
 __global__ void __launch_bounds__(128, 8) k_finish_df(FastArgs a)
 {
     const uint32_t count = *a.queue_count;
+    if (a.queue_next && blockIdx.x == 0 && threadIdx.x == 0) *a.queue_next = 0;
     NodeCounters tot;
     uint32_t done = 0, hmax = 0;
     for (uint32_t q = blockIdx.x * blockDim.x + threadIdx.x; q < count; q += gridDim.x * blockDim.x) {
@@ -890,11 +891,11 @@ __global__ void __launch_bounds__(128, 8) k_finish_df(FastArgs a)
 }
 
 template <int kBlock, int kMinBlocks>
-static void launch_split_cfg(const FastArgs &a, bool stats, bool debug, int sms, cudaStream_t s)
+static void launch_split_cfg(const FastArgs &a, bool stats, bool debug, int sms, bool reset, cudaStream_t s)
 {
     const unsigned grid = (unsigned)((a.N + kBlock - 1) / kBlock);
     if (grid == 0) return;
-    cudaMemsetAsync(a.queue_count, 0, sizeof(uint32_t), s);
+    if (reset) cudaMemsetAsync(a.queue_count, 0, sizeof(uint32_t), s);
     if (stats) {
         if (debug) k_settle_df<true, true, kBlock, kMinBlocks, -1><<<grid, kBlock, 0, s>>>(a);
         else k_settle_df<true, false, kBlock, kMinBlocks, -1><<<grid, kBlock, 0, s>>>(a);
@@ -934,12 +935,13 @@ static void launch_split_cfg(const FastArgs &a, bool stats, bool debug, int sms,
 }
 
 // A split step (settle pass + finish pass over the queue).  The settle pass
-// needs 34-36 registers and is bound by the latency of its gathers, so it
-// runs at 128 x 14 (56 resident warps per SM): 10 % faster than at 48.  The
-// caller provides a.queue (N entries) and a.queue_count.
-void launch_split_df(const FastArgs &a, bool stats, bool debug, int sms, cudaStream_t s)
+// needs 32 registers, so it runs at 128 x 14 (56 resident warps per SM):
+// faster than at 48 or 64.  The caller provides a.queue (N entries) and
+// a.queue_count (zeroed here when reset, else by the previous finish pass
+// through its queue_next).
+void launch_split_df(const FastArgs &a, bool stats, bool debug, int sms, bool reset, cudaStream_t s)
 {
-    launch_split_cfg<128, 14>(a, stats, debug, sms, s);
+    launch_split_cfg<128, 14>(a, stats, debug, sms, reset, s);
 }
 
 template <int kBlock, int kMinBlocks, bool kExt = false>

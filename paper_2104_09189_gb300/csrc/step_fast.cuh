@@ -73,12 +73,13 @@ struct FastArgs {
     // split steps: the nodes the settle pass leaves to the finish pass
     int32_t *queue;
     uint32_t *queue_count;
+    uint32_t *queue_next;         // split steps: the next step's counter, zeroed by the finish pass (or NULL)
 };
 
 // config: launch configuration 0..kFastConfigs-1 (see step_fast.cu)
 void launch_fast_df(const FastArgs &a, bool stats, bool debug, int config, cudaStream_t s);
 // a split step: lean settle pass + finish pass over its queue
-void launch_split_df(const FastArgs &a, bool stats, bool debug, int sms, cudaStream_t s);
+void launch_split_df(const FastArgs &a, bool stats, bool debug, int sms, bool reset, cudaStream_t s);
 constexpr int kFastConfigs = 6;
 void launch_fast_f32(const FastArgs &a, bool stats, bool debug, int config, cudaStream_t s);
 
