@@ -500,15 +500,21 @@ def main():
     # one event before each run and one after the last (the runs are timed
     # as a whole; the per-run spread shows host stalls between runs); the
     # collector is paused so that it cannot stall the launching thread
+    # runs are queued back to back (SL_OPT_ASYNC): a host stall between two
+    # launches then only eats into the queued work; the device status of all
+    # runs is checked once after the region
     evs = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps + 1)]
+    sl.sl_mesh_set_option(h, sl.SL_OPT_ASYNC, 1)
     gc.disable()
     evs[0].record(stream)
     for k in range(args.steps):
         sl.sl_mesh_reset_t0(h)
-        sl.sl_run(h, probs, 0, S, v, w, use_graph=True)
+        sl.sl_run(h, probs, 0, S, v, w, use_graph=True, stats=False)
         evs[k + 1].record(stream)
     torch.cuda.synchronize()
     gc.enable()
+    sl.sl_mesh_set_option(h, sl.SL_OPT_ASYNC, 0)
+    sl.sl_mesh_status(h)
     if dist:
         dist.barrier()
     elapsed = evs[0].elapsed_time(evs[-1]) / 1e3

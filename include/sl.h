@@ -147,12 +147,17 @@ typedef enum {
     SL_OPT_OUTSIDE = 9,      /* feet that leave the square: 0 = clip them to the boundary (default);
                                 1 = exclude the node, as the paper's experiments do (Sec. 4):
                                 V^{n+1}_i = V^n_i, flag SL_NODE_EXCLUDED */
-    SL_OPT_SPLIT = 10        /* FP64 meshes, strategy (b), feet clipped: 0 = one fused kernel per
+    SL_OPT_SPLIT = 10,       /* FP64 meshes, strategy (b), feet clipped: 0 = one fused kernel per
                                 step (default); 1 = two passes per step: a lean pass finishes
                                 every node whose foot is certainly inside its start triangle and
                                 queues the others for the full kernel (fewer registers where the
                                 feet move little).  Results are identical.  Never used for a step
                                 from the initial start triangles.  sl_autotune sets it. */
+    SL_OPT_ASYNC = 11        /* 0 = sl_run synchronises the stream and returns the device status
+                                (default); 1 = sl_run returns once its steps are enqueued when
+                                stats is NULL, and the device status is read by the next
+                                sl_mesh_status (or a synchronising sl_run).  Lets a caller queue
+                                many runs back to back. */
 } sl_option;
 
 /*
@@ -236,7 +241,8 @@ sl_status sl_step(sl_mesh *m, const sl_problem *probs, int64_t n, const void *v_
  * steps are recorded once into a CUDA graph and replayed (the graph is kept
  * in the handle and reused while n0, n_steps, the buffers and the problems
  * are unchanged).  Synchronises the stream and returns the deferred device
- * status (SL_E_WALK_LIMIT if a walk failed).  stats may be NULL.
+ * status (SL_E_WALK_LIMIT if a walk failed).  stats may be NULL; with
+ * SL_OPT_ASYNC = 1 and stats NULL it returns without synchronising.
  */
 sl_status sl_run(sl_mesh *m, const sl_problem *probs, int64_t n0, int32_t n_steps, void *v,
                  void *v_scratch, int32_t use_graph, sl_stats *stats, void *stream);

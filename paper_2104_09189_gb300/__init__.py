@@ -18,7 +18,7 @@ __all__ = [
     "SL_OK", "SL_E_ARG", "SL_E_MESH", "SL_E_NOMEM", "SL_E_CUDA", "SL_E_WALK_LIMIT", "SL_E_STATE",
     "SL_FP64", "SL_FP32", "SL_CURVE_NONE", "SL_CURVE_HILBERT", "SL_CURVE_MORTON",
     "SL_OPT_STATS", "SL_OPT_WALK_CAP", "SL_OPT_KERNEL", "SL_OPT_BLOCK", "SL_OPT_TILES_PER_SM", "SL_OPT_CONFIG",
-    "SL_OPT_CONFIG_FIRST", "SL_OPT_STRATEGY", "SL_OPT_OUTSIDE", "SL_OPT_SPLIT",
+    "SL_OPT_CONFIG_FIRST", "SL_OPT_STRATEGY", "SL_OPT_OUTSIDE", "SL_OPT_SPLIT", "SL_OPT_ASYNC",
     "SL_NODE_CLIPPED", "SL_NODE_DEGENERATE", "SL_NODE_EXACT", "SL_NODE_FALLBACK", "SL_NODE_WALK_LIMIT",
     "SL_NODE_RANGE", "SL_NODE_EXCLUDED", "SLError", "sl_problem", "problems", "pack_meshes",
     "sl_mesh_create", "sl_mesh_validate", "sl_mesh_reorder", "sl_step", "sl_run", "sl_run_host", "sl_mesh_get_t0",
@@ -31,7 +31,7 @@ SL_OK, SL_E_ARG, SL_E_MESH, SL_E_NOMEM, SL_E_CUDA, SL_E_WALK_LIMIT, SL_E_STATE =
 SL_FP64, SL_FP32 = 0, 1
 SL_CURVE_NONE, SL_CURVE_HILBERT, SL_CURVE_MORTON = 0, 1, 2
 SL_OPT_STATS, SL_OPT_WALK_CAP, SL_OPT_KERNEL, SL_OPT_BLOCK, SL_OPT_TILES_PER_SM, SL_OPT_CONFIG = range(6)
-SL_OPT_CONFIG_FIRST, SL_OPT_STRATEGY, SL_OPT_OUTSIDE, SL_OPT_SPLIT = 7, 8, 9, 10
+SL_OPT_CONFIG_FIRST, SL_OPT_STRATEGY, SL_OPT_OUTSIDE, SL_OPT_SPLIT, SL_OPT_ASYNC = 7, 8, 9, 10, 11
 SL_NODE_CLIPPED, SL_NODE_DEGENERATE, SL_NODE_EXACT, SL_NODE_FALLBACK, SL_NODE_WALK_LIMIT, SL_NODE_RANGE = (
     1, 2, 4, 8, 16, 32)
 SL_NODE_EXCLUDED = 64
@@ -253,11 +253,13 @@ def sl_step(h, probs, n, v_in, v_out, debug=None, stream=None):
                              ctypes.byref(dbg) if dbg is not None else None, _stream(stream)))
 
 
-def sl_run(h, probs, n0, n_steps, v, v_scratch, use_graph=True, stream=None):
-    st = sl_stats()
+def sl_run(h, probs, n0, n_steps, v, v_scratch, use_graph=True, stream=None, stats=True):
+    """Returns the walk statistics as a dict, or None with stats=False (which
+    with SL_OPT_ASYNC = 1 returns without synchronising)."""
+    st = sl_stats() if stats else None
     _check(library().sl_run(h, probs, int(n0), int(n_steps), _ptr(v), _ptr(v_scratch), 1 if use_graph else 0,
-                            ctypes.byref(st), _stream(stream)))
-    return st.as_dict()
+                            ctypes.byref(st) if stats else None, _stream(stream)))
+    return st.as_dict() if stats else None
 
 
 def sl_run_host(h, probs, n0, n_steps, v_host, use_graph=True, stream=None):

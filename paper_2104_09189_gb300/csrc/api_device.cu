@@ -647,6 +647,7 @@ extern "C" sl_status sl_run(sl_mesh *m, const sl_problem *probs, int64_t n0, int
         m->stepped = true;
         m->t0_initial = false;
     }
+    if (m->opt_async && !stats) return SL_OK;   // status read by sl_mesh_status
     st = read_status(m, s);
     if (stats) {
         sl_status s2 = sl_mesh_stats(m, stats, 0, stream);
@@ -710,10 +711,9 @@ extern "C" sl_status sl_mesh_set_t0(sl_mesh *m, const int32_t *t0_dev, void *str
 extern "C" sl_status sl_mesh_reset_t0(sl_mesh *m, void *stream)
 {
     if (!m) return fail(SL_E_ARG, "sl_mesh_reset_t0: mesh is NULL");
-    SL_CUDA(cudaMemcpyAsync(m->d.t0, m->d.t0_init, sizeof(int32_t) * m->N, cudaMemcpyDeviceToDevice,
-                            (cudaStream_t)stream));
     m->t0_initial = true;
-    launch_fill_t0v(m->d.t0, m->d.tv[0], m->d.tv[1], m->d.tv[2], (int4 *)m->d.t0v, m->N, (cudaStream_t)stream);
+    launch_reset_t0(m->d.t0_init, m->d.tv[0], m->d.tv[1], m->d.tv[2], m->d.t0, (int4 *)m->d.t0v, m->N,
+                    (cudaStream_t)stream);
     SL_CUDA(cudaGetLastError());
     return SL_OK;
 }

@@ -487,6 +487,10 @@ extern "C" sl_status sl_mesh_set_option(sl_mesh *m, int32_t option, int64_t valu
         if (value != 0 && value != 1) return sl::fail(SL_E_ARG, "outside mode must be 0 (clip) or 1 (exclude)");
         m->opt_outside = (int32_t)value;
         break;
+    case SL_OPT_ASYNC:
+        if (value != 0 && value != 1) return sl::fail(SL_E_ARG, "async must be 0 or 1");
+        m->opt_async = (int32_t)value;
+        return SL_OK;   // the recorded launches do not depend on it
     default: return sl::fail(SL_E_ARG, "unknown option");
     }
     m->graph.valid = false;   // recorded launches may depend on options

@@ -97,6 +97,7 @@ struct sl_mesh {
     std::vector<int64_t> tree_level_off;   // strategy (c): level k = tree_order[off[k], off[k+1])
     int32_t opt_outside = 0;          // 0 = clip feet that leave the square, 1 = exclude the node
     int32_t opt_split = 0;            // 1 = split steps (settle pass + finish pass), FP64 meshes
+    int32_t opt_async = 0;            // 1 = sl_run without stats returns unsynchronised
     bool t0_initial = true;           // T^0 holds the initial start triangles
     int32_t sms = 0;                  // multiprocessors of the device
     bool stepped = false;

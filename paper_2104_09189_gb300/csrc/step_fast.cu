@@ -1005,13 +1005,58 @@ void launch_gather_probe(const float4 *xyq, const int4 *t0v, const float2 *vin, 
 // ---------------------------------------------------------------------------
 // Value format conversions (once per run, not per step)
 
+// h = v rounded to the nearest float (ties to even) and l = v - h rounded
+// to the nearest float, from the bits of v with integer operations, for
+// 2^-74 <= |v| < 2^127 (both parts normal floats); false otherwise.  The
+// 29 mantissa bits below the float's 23 decide the rounding of h; v - h is
+// then the signed integer rem (or rem - 2^29) times 2^(e - 1075), exact, and
+// converting that integer to float rounds it once, the scaling by a power of
+// two being exact in the normal range.  GB300 converts double to float on its
+// slow FP64 pipe, so this keeps the conversion at memory speed.
+__device__ __forceinline__ bool split_double_bits(double v, float &h, float &l)
+{
+    const unsigned long long b = (unsigned long long)__double_as_longlong(v);
+    const uint32_t hi = (uint32_t)(b >> 32), lo = (uint32_t)b;
+    const int e = (int)((hi >> 20) & 0x7FFu);
+    if (e < 1075 - 126 || e > 1023 + 126) return false;
+    const uint32_t sign = hi & 0x80000000u;
+    const uint32_t top = ((hi & 0xFFFFFu) << 3) | (lo >> 29);   // the float's 23 mantissa bits
+    const uint32_t rem = lo & 0x1FFFFFFFu;                       // the 29 bits below them
+    const bool up = rem > 0x10000000u || (rem == 0x10000000u && (top & 1u));
+    const uint32_t fb = (((uint32_t)(e - 1023 + 127) << 23) | top) + (up ? 1u : 0u);   // a carry bumps the exponent
+    h = __uint_as_float(sign | fb);
+    const int32_t r = up ? (int32_t)rem - 0x20000000 : (int32_t)rem;
+    const float scale = __uint_as_float((uint32_t)(e - 1075 + 127) << 23);   // 2^(e - 1075)
+    const float m = __fmul_rn(__int2float_rn(r), scale);
+    l = sign ? -m : m;
+    return true;
+}
+
 __global__ void k_to_df(const double *__restrict__ src, float2 *__restrict__ dst, int64_t n)
 {
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
         const double v = src[i];
-        const float h = __double2float_rn(v);
-        dst[i] = make_float2(h, __double2float_rn(v - (double)h));
+        float h, l;
+        if (!split_double_bits(v, h, l)) {
+            // zero, tiny, huge or not finite: the FP64 pipe
+            h = __double2float_rn(v);
+            l = __double2float_rn(v - (double)h);
+        }
+        dst[i] = make_float2(h, l);
     }
+}
+
+// A float as a double from its bits (exact), for normal floats; NaN
+// otherwise, which sends the caller to the conversion instruction.
+__device__ __forceinline__ double widen_float_bits(float f)
+{
+    const uint32_t u = __float_as_uint(f);
+    const uint32_t ef = (u >> 23) & 0xFFu;
+    if (ef == 0u || ef == 0xFFu) return __longlong_as_double(0x7FF8000000000000ll);
+    const unsigned long long d = ((unsigned long long)(u & 0x80000000u) << 32) |
+                                 ((unsigned long long)(ef - 127u + 1023u) << 52) |
+                                 ((unsigned long long)(u & 0x7FFFFFu) << 29);
+    return __longlong_as_double((long long)d);
 }
 
 __global__ void k_from_df(const float2 *src, double *dst, int64_t n)
@@ -1019,7 +1064,10 @@ __global__ void k_from_df(const float2 *src, double *dst, int64_t n)
     // may run in place (src and dst alias, same 8-byte slots)
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
         const float2 v = src[i];
-        dst[i] = (double)v.x + (double)v.y;
+        double a = widen_float_bits(v.x), b = widen_float_bits(v.y);
+        if (a != a) a = (double)v.x;   // zero, subnormal, infinite or NaN
+        if (b != b) b = (double)v.y;
+        dst[i] = a + b;
     }
 }
 
@@ -1099,6 +1147,19 @@ __global__ void k_field_tables(FieldTableArgs a)
     }
 }
 
+// T^0 back to its initial triangles and the start-state cache with it, one
+// pass (sl_mesh_reset_t0).
+__global__ void k_reset_t0(const int32_t *__restrict__ t0_init, const int32_t *__restrict__ tv0,
+                           const int32_t *__restrict__ tv1, const int32_t *__restrict__ tv2, int32_t *__restrict__ t0,
+                           int4 *__restrict__ t0v, int64_t n)
+{
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const int32_t j = t0_init[i];
+        t0[i] = j;
+        t0v[i] = make_int4(3 * j, tv0[j], tv1[j], tv2[j]);
+    }
+}
+
 __global__ void k_fill_t0v(const int32_t *__restrict__ t0, const int32_t *__restrict__ tv0,
                            const int32_t *__restrict__ tv1, const int32_t *__restrict__ tv2, int4 *__restrict__ t0v,
                            int64_t n)
@@ -1155,6 +1216,12 @@ void launch_fill_t0v(const int32_t *t0, const int32_t *tv0, const int32_t *tv1, 
                      int64_t n, cudaStream_t s)
 {
     if (n > 0) k_fill_t0v<<<grid_for(n, 256), 256, 0, s>>>(t0, tv0, tv1, tv2, t0v, n);
+}
+
+void launch_reset_t0(const int32_t *t0_init, const int32_t *tv0, const int32_t *tv1, const int32_t *tv2, int32_t *t0,
+                     int4 *t0v, int64_t n, cudaStream_t s)
+{
+    if (n > 0) k_reset_t0<<<grid_for(n, 256), 256, 0, s>>>(t0_init, tv0, tv1, tv2, t0, t0v, n);
 }
 
 void launch_field_tables(const FieldTableArgs &a, cudaStream_t s)

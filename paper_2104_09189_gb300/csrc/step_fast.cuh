@@ -118,5 +118,8 @@ void launch_build_he(const int32_t *const tv[3], const int32_t *const tn[3], con
 // t0v[i] = (3 t0[i], its three vertex ids in slot order)
 void launch_fill_t0v(const int32_t *t0, const int32_t *tv0, const int32_t *tv1, const int32_t *tv2, int4 *t0v,
                      int64_t n, cudaStream_t s);
+// t0 = t0_init and the start-state cache with it, one pass
+void launch_reset_t0(const int32_t *t0_init, const int32_t *tv0, const int32_t *tv1, const int32_t *tv2, int32_t *t0,
+                     int4 *t0v, int64_t n, cudaStream_t s);
 
 }  // namespace sl

@@ -155,6 +155,62 @@ def test_zero_field_leaves_values_bitwise():
         g.close()
 
 
+def test_value_pairs_round_to_nearest_at_every_magnitude():
+    """The fast FP64 path carries V as (hi, lo) float pairs: hi = V rounded to
+    the nearest float (ties to even), lo = V - hi rounded likewise, and back
+    as hi + lo in double.  With f = 0 every value comes back as that round
+    trip; checked bit for bit against numpy's conversions on values of every
+    magnitude from 2^-1000 to 2^126, exact ties, both signs, zero and the
+    subnormal range, in sl_step and in a graph-recorded sl_run."""
+    mesh = si.grid_mesh(64, 0.25, 2)
+    n = mesh.n_nodes
+    rng = np.random.default_rng(7)
+    mant = rng.uniform(1.0, 2.0, n)
+    expo = rng.integers(-1000, 127, n)
+    v = np.ldexp(mant, expo) * np.where(rng.random(n) < 0.5, -1.0, 1.0)
+    # exact ties of the float rounding (a float plus half its ulp), either parity
+    k = n // 8
+    base = np.ldexp(rng.uniform(1.0, 2.0, k).astype(np.float32).astype(np.float64), rng.integers(-60, 100, k))
+    v[:k] = base + np.ldexp(np.float64(1.0), np.frexp(base)[1] - 25)
+    v[k] = 0.0
+    v[k + 1] = -0.0
+    v[k + 2] = 5e-324
+    v[k + 3] = 2.0 ** -75 * 1.75
+    v[k + 4] = 2.0 ** -74 * 1.25
+    v[k + 5] = (2.0 - 2.0 ** -52) * 2.0 ** 126
+    hi = v.astype(np.float32).astype(np.float64)
+    want = hi + (v - hi).astype(np.float32).astype(np.float64)
+    g = GpuRun(mesh, si.zero_field(), 0.1, kernel=2)
+    vd = g.to_dev(v)
+    _, res = g.step(0, vd)
+    assert np.array_equal(res["v"].view(np.int64), want.view(np.int64))
+    w = g.torch.empty_like(vd)
+    vd = g.to_dev(v)
+    sl.sl_run(g.h, g.probs, 0, 2, vd, w, use_graph=True)
+    assert np.array_equal(g.from_dev(vd).view(np.int64), want.view(np.int64))
+    g.close()
+
+
+def test_async_runs_queue_back_to_back_with_the_same_results():
+    """SL_OPT_ASYNC = 1: sl_run without statistics returns before its steps
+    finish; several runs queued back to back end with the values of
+    synchronous runs, and sl_mesh_status reports the device status."""
+    prob = si.config("C2", M=128)
+    outs = []
+    for asy in (0, 1):
+        g = GpuRun(prob.mesh, prob.field, prob.dt, curve=sl.SL_CURVE_HILBERT)
+        sl.sl_mesh_set_option(g.h, sl.SL_OPT_ASYNC, asy)
+        v = g.to_dev(prob.v0)
+        w = g.torch.empty_like(v)
+        for _ in range(3):
+            sl.sl_mesh_reset_t0(g.h)
+            assert sl.sl_run(g.h, g.probs, 0, 4, v, w, stats=False) is None
+        sl.sl_mesh_status(g.h)
+        outs.append(g.from_dev(v))
+        g.close()
+    assert np.array_equal(outs[0], outs[1])
+
+
 @pytest.mark.parametrize("kernel", [1, 2], ids=["plain", "fast"])
 def test_graph_eager_reorder_and_resume_are_bitwise_identical(kernel):
     prob = si.config("C2", M=192)
