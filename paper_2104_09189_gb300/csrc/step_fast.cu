@@ -1046,17 +1046,21 @@ __global__ void k_to_df(const double *__restrict__ src, float2 *__restrict__ dst
     }
 }
 
-// A float as a double from its bits (exact), for normal floats; NaN
-// otherwise, which sends the caller to the conversion instruction.
-__device__ __forceinline__ double widen_float_bits(float f)
+// A float as a double from its bits (exact) for zero and normal floats;
+// false for subnormal, infinite and NaN ones.
+__device__ __forceinline__ bool widen_float_bits(float f, double &d)
 {
     const uint32_t u = __float_as_uint(f);
     const uint32_t ef = (u >> 23) & 0xFFu;
-    if (ef == 0u || ef == 0xFFu) return __longlong_as_double(0x7FF8000000000000ll);
-    const unsigned long long d = ((unsigned long long)(u & 0x80000000u) << 32) |
-                                 ((unsigned long long)(ef - 127u + 1023u) << 52) |
-                                 ((unsigned long long)(u & 0x7FFFFFu) << 29);
-    return __longlong_as_double((long long)d);
+    const unsigned long long sign = (unsigned long long)(u & 0x80000000u) << 32;
+    if ((u & 0x7FFFFFFFu) == 0u) {
+        d = __longlong_as_double((long long)sign);
+        return true;
+    }
+    if (ef == 0u || ef == 0xFFu) return false;
+    d = __longlong_as_double((long long)(sign | ((unsigned long long)(ef - 127u + 1023u) << 52) |
+                                         ((unsigned long long)(u & 0x7FFFFFu) << 29)));
+    return true;
 }
 
 __global__ void k_from_df(const float2 *src, double *dst, int64_t n)
@@ -1064,9 +1068,9 @@ __global__ void k_from_df(const float2 *src, double *dst, int64_t n)
     // may run in place (src and dst alias, same 8-byte slots)
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
         const float2 v = src[i];
-        double a = widen_float_bits(v.x), b = widen_float_bits(v.y);
-        if (a != a) a = (double)v.x;   // zero, subnormal, infinite or NaN
-        if (b != b) b = (double)v.y;
+        double a, b;
+        if (!widen_float_bits(v.x, a)) a = (double)v.x;
+        if (!widen_float_bits(v.y, b)) b = (double)v.y;
         dst[i] = a + b;
     }
 }
