@@ -11,7 +11,7 @@ FOOT_DELTA = 1e-12            # feet may differ by rounding of the field's
                               # feet closer than this to an edge line may differ
 
 
-class GpuRun:
+class DeviceRun:
     """A single-problem mesh on the GPU, optionally renumbered, with the
     permutations kept so results can be compared in the original numbering."""
 

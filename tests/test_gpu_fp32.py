@@ -12,7 +12,7 @@ import pytest
 import oracle
 import paper_2104_09189_gb300 as sl
 import sl_inputs as si
-from gpu_helpers import GpuRun
+from gpu_helpers import DeviceRun
 
 pytestmark = pytest.mark.gpu
 
@@ -24,7 +24,7 @@ def _fp32_parity(prob, steps, curve=sl.SL_CURVE_HILBERT):
     xy32 = mesh.xy.astype(np.float32)
     om32 = oracle.OracleMesh(xy32.astype(np.float64), mesh.tri)
     om64 = oracle.OracleMesh(mesh.xy, mesh.tri)
-    g = GpuRun(mesh, prob.field, prob.dt, curve=curve, precision=sl.SL_FP32)
+    g = DeviceRun(mesh, prob.field, prob.dt, curve=curve, precision=sl.SL_FP32)
     v_dev = g.to_dev(prob.v0.astype(np.float32))
     v64 = prob.v0.copy()
     worst = 0.0
@@ -67,7 +67,7 @@ def test_fp32_rotation_feet_bitwise():
     for bit (same operations in the same order)."""
     prob = si.config("C3", M=128)
     mesh = prob.mesh
-    g = GpuRun(mesh, prob.field, prob.dt, curve=sl.SL_CURVE_NONE, precision=sl.SL_FP32)
+    g = DeviceRun(mesh, prob.field, prob.dt, curve=sl.SL_CURVE_NONE, precision=sl.SL_FP32)
     v_dev = g.to_dev(prob.v0.astype(np.float32))
     for n in range(3):
         v_dev, res = g.step(n, v_dev)

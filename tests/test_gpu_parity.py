@@ -10,7 +10,7 @@ import pytest
 import oracle
 import paper_2104_09189_gb300 as sl
 import sl_inputs as si
-from gpu_helpers import GpuRun, compare_step
+from gpu_helpers import DeviceRun, compare_step
 
 pytestmark = pytest.mark.gpu
 
@@ -18,7 +18,7 @@ pytestmark = pytest.mark.gpu
 def _parity_run(prob, steps, curve=sl.SL_CURVE_NONE, kernel=0, seed=1, check_every=1):
     mesh = prob.mesh
     om = oracle.OracleMesh(mesh.xy, mesh.tri)
-    g = GpuRun(mesh, prob.field, prob.dt, curve=curve, kernel=kernel, seed=seed)
+    g = DeviceRun(mesh, prob.field, prob.dt, curve=curve, kernel=kernel, seed=seed)
     v_dev = g.to_dev(prob.v0)
     v_orc = prob.v0.copy()
     worst, near_total = 0.0, 0
@@ -69,7 +69,7 @@ def test_c3_construction_rotation_parity_and_zero_hops(kernel):
     prob = si.config("C3", M=256)
     mesh = prob.mesh
     om = oracle.OracleMesh(mesh.xy, mesh.tri)
-    g = GpuRun(mesh, prob.field, prob.dt, curve=sl.SL_CURVE_HILBERT, kernel=kernel)
+    g = DeviceRun(mesh, prob.field, prob.dt, curve=sl.SL_CURVE_HILBERT, kernel=kernel)
     v_dev = g.to_dev(prob.v0)
     v_orc = prob.v0.copy()
     for n in range(4):
@@ -109,7 +109,7 @@ def test_linear_data_closed_form_on_gpu(kernel):
     p = np.zeros(48)
     p[:8] = (-k * cx, k, 0.0, 0.0, -k * cy, 0.0, k, 0.0)
     fld = si.Field(si.FIELD_AFFINE, p, 1.0)
-    g = GpuRun(mesh, fld, dt, curve=sl.SL_CURVE_HILBERT, kernel=kernel)
+    g = DeviceRun(mesh, fld, dt, curve=sl.SL_CURVE_HILBERT, kernel=kernel)
     lin = lambda q: 0.25 + q[:, 0] - 0.5 * q[:, 1]
     v = g.to_dev(lin(mesh.xy))
     w = g.torch.empty_like(v)
@@ -130,7 +130,7 @@ def test_zero_field_leaves_values_bitwise():
     pair, bit for bit."""
     mesh = si.grid_mesh(64, 0.25, 2)
     v0 = si.cosine_bump(mesh.xy)
-    g = GpuRun(mesh, si.zero_field(), 0.1, kernel=1)
+    g = DeviceRun(mesh, si.zero_field(), 0.1, kernel=1)
     v_dev = g.to_dev(v0)
     for n in range(3):
         v_dev, res = g.step(n, v_dev)
@@ -141,7 +141,7 @@ def test_zero_field_leaves_values_bitwise():
     v_pair = hi + (v0 - hi).astype(np.float32).astype(np.float64)
     assert np.abs(v_pair - v0).max() <= 2.0 ** -48 * np.abs(v0).max()
     for split in (0, 1):
-        g = GpuRun(mesh, si.zero_field(), 0.1, kernel=2)
+        g = DeviceRun(mesh, si.zero_field(), 0.1, kernel=2)
         sl.sl_mesh_set_option(g.h, sl.SL_OPT_SPLIT, split)
         v_dev = g.to_dev(v0)
         for n in range(3):
@@ -180,7 +180,7 @@ def test_value_pairs_round_to_nearest_at_every_magnitude():
     v[k + 5] = (2.0 - 2.0 ** -52) * 2.0 ** 126
     hi = v.astype(np.float32).astype(np.float64)
     want = hi + (v - hi).astype(np.float32).astype(np.float64)
-    g = GpuRun(mesh, si.zero_field(), 0.1, kernel=2)
+    g = DeviceRun(mesh, si.zero_field(), 0.1, kernel=2)
     vd = g.to_dev(v)
     _, res = g.step(0, vd)
     assert np.array_equal(res["v"].view(np.int64), want.view(np.int64))
@@ -198,7 +198,7 @@ def test_async_runs_queue_back_to_back_with_the_same_results():
     prob = si.config("C2", M=128)
     outs = []
     for asy in (0, 1):
-        g = GpuRun(prob.mesh, prob.field, prob.dt, curve=sl.SL_CURVE_HILBERT)
+        g = DeviceRun(prob.mesh, prob.field, prob.dt, curve=sl.SL_CURVE_HILBERT)
         sl.sl_mesh_set_option(g.h, sl.SL_OPT_ASYNC, asy)
         v = g.to_dev(prob.v0)
         w = g.torch.empty_like(v)
@@ -218,7 +218,7 @@ def test_graph_eager_reorder_and_resume_are_bitwise_identical(kernel):
     outs = []
     for curve, graph in [(sl.SL_CURVE_NONE, False), (sl.SL_CURVE_NONE, True), (sl.SL_CURVE_HILBERT, True),
                          (sl.SL_CURVE_MORTON, False)]:
-        g = GpuRun(mesh, prob.field, prob.dt, curve=curve, kernel=kernel)
+        g = DeviceRun(mesh, prob.field, prob.dt, curve=curve, kernel=kernel)
         v = g.to_dev(prob.v0)
         w = g.torch.empty_like(v)
         sl.sl_run(g.h, g.probs, 0, 7, v, w, use_graph=graph)
@@ -228,7 +228,7 @@ def test_graph_eager_reorder_and_resume_are_bitwise_identical(kernel):
         assert np.array_equal(o, outs[0])
     # resume: 3 steps, export T^0 and V; a new handle imports them and runs
     # 4 more steps, exactly like the first handle continuing
-    g = GpuRun(mesh, prob.field, prob.dt, kernel=kernel)
+    g = DeviceRun(mesh, prob.field, prob.dt, kernel=kernel)
     v = g.to_dev(prob.v0)
     w = g.torch.empty_like(v)
     sl.sl_run(g.h, g.probs, 0, 3, v, w)
@@ -236,7 +236,7 @@ def test_graph_eager_reorder_and_resume_are_bitwise_identical(kernel):
     sl.sl_mesh_get_t0(g.h, t0)
     v_resume = v.clone()
     sl.sl_run(g.h, g.probs, 3, 4, v, w)
-    g2 = GpuRun(mesh, prob.field, prob.dt, kernel=kernel)
+    g2 = DeviceRun(mesh, prob.field, prob.dt, kernel=kernel)
     sl.sl_mesh_set_t0(g2.h, t0)
     sl.sl_run(g2.h, g2.probs, 3, 4, v_resume, w)
     assert np.array_equal(g2.from_dev(v_resume), g.from_dev(v))
@@ -250,13 +250,13 @@ def test_graph_eager_reorder_and_resume_are_bitwise_identical(kernel):
 
 def test_run_host_matches_device_run():
     prob = si.config("C1")
-    g = GpuRun(prob.mesh, prob.field, prob.dt)
+    g = DeviceRun(prob.mesh, prob.field, prob.dt)
     v = g.to_dev(prob.v0)
     w = g.torch.empty_like(v)
     sl.sl_run(g.h, g.probs, 0, 5, v, w)
     dev_result = g.from_dev(v)
     g.close()
-    g = GpuRun(prob.mesh, prob.field, prob.dt)
+    g = DeviceRun(prob.mesh, prob.field, prob.dt)
     host = prob.v0.copy()
     sl.sl_run_host(g.h, g.probs, 0, 5, host)
     assert np.array_equal(host, dev_result)
@@ -267,7 +267,7 @@ def test_run_host_matches_device_run():
 def test_walk_cap_reports_status_without_hanging(kernel):
     """A tiny hop cap (debug knob) must end in SL_E_WALK_LIMIT, not a hang."""
     prob = si.config("C2", M=128)
-    g = GpuRun(prob.mesh, prob.field, prob.dt, kernel=kernel)
+    g = DeviceRun(prob.mesh, prob.field, prob.dt, kernel=kernel)
     sl.sl_mesh_set_option(g.h, sl.SL_OPT_WALK_CAP, 1)
     v = g.to_dev(prob.v0)
     w = g.torch.empty_like(v)
@@ -303,7 +303,7 @@ def test_batched_problems_match_single_runs(kernel):
 
 def test_bad_step_arguments():
     prob = si.config("C1", M=8)
-    g = GpuRun(prob.mesh, prob.field, prob.dt)
+    g = DeviceRun(prob.mesh, prob.field, prob.dt)
     v = g.to_dev(prob.v0)
     with pytest.raises(sl.SLError) as e:
         sl.sl_step(g.h, g.probs, 0, v, v)
@@ -320,7 +320,7 @@ def test_autotune_restores_state_and_keeps_results():
     """sl_autotune measures every launch configuration, keeps the fastest
     and leaves values, T^0 and the results of a following run unchanged."""
     prob = si.config("C2", M=256)
-    g = GpuRun(prob.mesh, prob.field, prob.dt, curve=sl.SL_CURVE_HILBERT)
+    g = DeviceRun(prob.mesh, prob.field, prob.dt, curve=sl.SL_CURVE_HILBERT)
     v = g.to_dev(prob.v0)
     w = g.torch.empty_like(v)
     before = v.clone()
@@ -331,7 +331,7 @@ def test_autotune_restores_state_and_keeps_results():
     sl.sl_run(g.h, g.probs, 0, 5, v, w)
     tuned = g.from_dev(v)
     g.close()
-    ref = GpuRun(prob.mesh, prob.field, prob.dt, curve=sl.SL_CURVE_HILBERT)
+    ref = DeviceRun(prob.mesh, prob.field, prob.dt, curve=sl.SL_CURVE_HILBERT)
     v2 = ref.to_dev(prob.v0)
     w2 = ref.torch.empty_like(v2)
     sl.sl_run(ref.h, ref.probs, 0, 5, v2, w2)
@@ -343,7 +343,7 @@ def test_gather_probe_times_and_leaves_state():
     """sl_probe_gather returns a positive mean time, reads v without
     changing it, leaves T^0 alone and refuses bad arguments."""
     prob = si.config("C2", M=256)
-    g = GpuRun(prob.mesh, prob.field, prob.dt, curve=sl.SL_CURVE_HILBERT)
+    g = DeviceRun(prob.mesh, prob.field, prob.dt, curve=sl.SL_CURVE_HILBERT)
     v = g.to_dev(prob.v0)
     w = g.torch.empty_like(v)
     sl.sl_run(g.h, g.probs, 0, 3, v, w)
@@ -380,7 +380,7 @@ def test_boundary_nodes_with_nearly_tangent_velocity(kernel, fx):
     fld = si.Field(si.FIELD_AFFINE, p, 1.0)
     dt = 0.05
     om = oracle.OracleMesh(mesh.xy, mesh.tri)
-    g = GpuRun(mesh, fld, dt, curve=sl.SL_CURVE_HILBERT, kernel=kernel)
+    g = DeviceRun(mesh, fld, dt, curve=sl.SL_CURVE_HILBERT, kernel=kernel)
     v0 = np.cos(2.0 * mesh.xy[:, 0]) + mesh.xy[:, 1] ** 2
     v = g.to_dev(v0)
     v, res = g.step(0, v)
@@ -402,7 +402,7 @@ def test_split_steps_are_bitwise_identical(name):
     prob = si.config(name, M=192)
     outs = []
     for split in (0, 1):
-        g = GpuRun(prob.mesh, prob.field, prob.dt, curve=sl.SL_CURVE_HILBERT)
+        g = DeviceRun(prob.mesh, prob.field, prob.dt, curve=sl.SL_CURVE_HILBERT)
         sl.sl_mesh_set_option(g.h, sl.SL_OPT_SPLIT, split)
         sl.sl_mesh_set_option(g.h, sl.SL_OPT_STATS, 1)
         v = g.to_dev(prob.v0)
@@ -429,7 +429,7 @@ def test_split_steps_settle_clipped_feet_like_the_fused_step():
     prob = si.config("C3", M=160)
     outs = []
     for split in (0, 1):
-        g = GpuRun(prob.mesh, prob.field, prob.dt, curve=sl.SL_CURVE_HILBERT)
+        g = DeviceRun(prob.mesh, prob.field, prob.dt, curve=sl.SL_CURVE_HILBERT)
         sl.sl_mesh_set_option(g.h, sl.SL_OPT_SPLIT, split)
         v = g.to_dev(prob.v0)
         steps = []
@@ -459,7 +459,7 @@ def test_boundary_nodes_moving_out_keep_their_value(split):
     prob = si.config("C3", M=160)
     mesh = prob.mesh
     om = oracle.OracleMesh(mesh.xy, mesh.tri)
-    g = GpuRun(prob.mesh, prob.field, prob.dt, curve=sl.SL_CURVE_HILBERT)
+    g = DeviceRun(prob.mesh, prob.field, prob.dt, curve=sl.SL_CURVE_HILBERT)
     sl.sl_mesh_set_option(g.h, sl.SL_OPT_SPLIT, split)
     v = g.to_dev(prob.v0)
     prev = prob.v0
@@ -482,7 +482,7 @@ def test_boundary_nodes_moving_out_keep_their_value(split):
 def test_split_steps_match_the_oracle_with_debug_outputs():
     prob = si.config("C2", M=128)
     om = oracle.OracleMesh(prob.mesh.xy, prob.mesh.tri)
-    g = GpuRun(prob.mesh, prob.field, prob.dt, curve=sl.SL_CURVE_HILBERT)
+    g = DeviceRun(prob.mesh, prob.field, prob.dt, curve=sl.SL_CURVE_HILBERT)
     sl.sl_mesh_set_option(g.h, sl.SL_OPT_SPLIT, 1)
     v = g.to_dev(prob.v0)
     vo = prob.v0

@@ -8,7 +8,7 @@ import pytest
 import oracle
 import paper_2104_09189_gb300 as sl
 import sl_inputs as si
-from gpu_helpers import FOOT_DELTA, REL_TOL_FP64, GpuRun
+from gpu_helpers import FOOT_DELTA, REL_TOL_FP64, DeviceRun
 
 pytestmark = pytest.mark.gpu
 
@@ -23,7 +23,7 @@ def test_exclusion_matches_the_oracle(kernel):
     f = si.paper_field(2 * np.pi, 2 * np.pi)
     dt = 0.04
     om = oracle.OracleMesh(m.xy, m.tri)
-    g = GpuRun(m, f, dt, curve=sl.SL_CURVE_HILBERT, kernel=kernel)
+    g = DeviceRun(m, f, dt, curve=sl.SL_CURVE_HILBERT, kernel=kernel)
     sl.sl_mesh_set_option(g.h, sl.SL_OPT_OUTSIDE, 1)
     sl.sl_mesh_set_option(g.h, sl.SL_OPT_STATS, 1)
     sl.sl_mesh_stats(g.h, reset=True)
@@ -71,7 +71,7 @@ def test_strategy_a_locates_the_same_triangles_with_more_hops(prec):
     dt = 0.05
     runs = {}
     for strategy in (0, 1):
-        g = GpuRun(m, f, dt, curve=sl.SL_CURVE_HILBERT, precision=prec)
+        g = DeviceRun(m, f, dt, curve=sl.SL_CURVE_HILBERT, precision=prec)
         sl.sl_mesh_set_option(g.h, sl.SL_OPT_STRATEGY, strategy)
         t0_init = g.torch.empty(m.n_nodes, dtype=g.torch.int32, device=g.dev)
         sl.sl_mesh_get_t0(g.h, t0_init)
@@ -106,7 +106,7 @@ def test_strategy_a_locates_the_same_triangles_with_more_hops(prec):
 def test_strategy_option_resets_t0():
     m = si.grid_mesh(48, 0.25, 13)
     f = si.rotation_field()
-    g = GpuRun(m, f, 0.03)
+    g = DeviceRun(m, f, 0.03)
     t0_init = g.torch.empty(m.n_nodes, dtype=g.torch.int32, device=g.dev)
     sl.sl_mesh_get_t0(g.h, t0_init)
     v = g.to_dev(_bump(m.xy))
@@ -176,7 +176,7 @@ def test_direct_location_on_the_courant_grid(kernel, prec, curve, shuffle):
     f = si.paper_field(2 * np.pi, 2 * np.pi)
     dt = 5.0 / M
     om = oracle.OracleMesh(m.xy, m.tri)
-    g = GpuRun(m, f, dt, curve=curve, kernel=kernel, precision=prec)
+    g = DeviceRun(m, f, dt, curve=curve, kernel=kernel, precision=prec)
     sl.sl_mesh_set_option(g.h, sl.SL_OPT_STRATEGY, 2)
     sl.sl_mesh_set_option(g.h, sl.SL_OPT_OUTSIDE, 1)
     vo = _bump(m.xy)
@@ -215,13 +215,13 @@ def test_direct_location_on_the_courant_grid(kernel, prec, curve, shuffle):
 
 def test_direct_location_rejects_other_meshes():
     m = si.grid_mesh(32, 0.25, 3)
-    g = GpuRun(m, si.rotation_field(), 0.01)
+    g = DeviceRun(m, si.rotation_field(), 0.01)
     with pytest.raises(sl.SLError):
         sl.sl_mesh_set_option(g.h, sl.SL_OPT_STRATEGY, 2)
     g.close()
     # a Courant grid keeps its table through a renumbering
     c = si.courant_grid(24)
-    g = GpuRun(c, si.rotation_field(), 0.01)
+    g = DeviceRun(c, si.rotation_field(), 0.01)
     sl.sl_mesh_set_option(g.h, sl.SL_OPT_STRATEGY, 2)
     sl.sl_mesh_reorder(g.h, sl.SL_CURVE_HILBERT)
     g.close()
@@ -238,7 +238,7 @@ def test_strategy_c_matches_the_oracle_and_walks_little(kernel, prec):
     f = si.paper_field(2 * np.pi, 2 * np.pi)
     dt = 6.0 / 72
     om = oracle.OracleMesh(m.xy, m.tri)
-    g = GpuRun(m, f, dt, curve=sl.SL_CURVE_HILBERT, kernel=kernel, precision=prec)
+    g = DeviceRun(m, f, dt, curve=sl.SL_CURVE_HILBERT, kernel=kernel, precision=prec)
     sl.sl_mesh_set_option(g.h, sl.SL_OPT_STRATEGY, 3)
     vo = _bump(m.xy)
     v = g.to_dev(vo)
