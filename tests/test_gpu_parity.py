@@ -280,6 +280,52 @@ def test_walk_cap_reports_status_without_hanging(kernel):
     g.close()
 
 
+def test_async_run_defers_the_walk_limit_status_to_mesh_status():
+    """With SL_OPT_ASYNC = 1 a run that hits the hop cap returns at once;
+    sl_mesh_status then reports SL_E_WALK_LIMIT, and the handle stays usable."""
+    prob = si.config("C2", M=128)
+    g = DeviceRun(prob.mesh, prob.field, prob.dt)
+    sl.sl_mesh_set_option(g.h, sl.SL_OPT_WALK_CAP, 1)
+    sl.sl_mesh_set_option(g.h, sl.SL_OPT_ASYNC, 1)
+    v = g.to_dev(prob.v0)
+    w = g.torch.empty_like(v)
+    assert sl.sl_run(g.h, g.probs, 0, 1, v, w, use_graph=False, stats=False) is None
+    with pytest.raises(sl.SLError) as e:
+        sl.sl_mesh_status(g.h)
+    assert e.value.status == sl.SL_E_WALK_LIMIT
+    sl.sl_mesh_set_option(g.h, sl.SL_OPT_WALK_CAP, 0)
+    sl.sl_run(g.h, g.probs, 1, 1, v, w, use_graph=False, stats=False)
+    sl.sl_mesh_status(g.h)
+    g.close()
+
+
+def test_split_steps_on_a_batch_are_bitwise_identical():
+    """Split steps on a batch of meshes with different fields (the settle
+    pass that finds each node's problem): values, T^0 and statistics are
+    bitwise those of the fused steps."""
+    probs = si.batch_config(6, nmin=2e3, nmax=2e4, steps=5)
+    no, to, xy, tri = sl.pack_meshes([(p.mesh.xy, p.mesh.tri) for p in probs])
+    import torch
+    pr = sl.problems([(p.field.kind, p.dt, p.field.packed()) for p in probs])
+    outs = []
+    for split in (0, 1):
+        h = sl.sl_mesh_create(no, to, xy, tri)
+        sl.sl_mesh_set_option(h, sl.SL_OPT_SPLIT, split)
+        sl.sl_mesh_set_option(h, sl.SL_OPT_STATS, 1)
+        v = torch.tensor(np.concatenate([p.v0 for p in probs]), dtype=torch.float64, device="cuda:0")
+        w = torch.empty_like(v)
+        st = sl.sl_run(h, pr, 0, 5, v, w)
+        t0 = torch.empty(v.numel(), dtype=torch.int32, device="cuda:0")
+        sl.sl_mesh_get_t0(h, t0)
+        outs.append((v.cpu().numpy(), t0.cpu().numpy(), st))
+        sl.sl_mesh_destroy(h)
+    (v0, t00, s0), (v1, t01, s1) = outs
+    assert np.array_equal(v0.view(np.int64), v1.view(np.int64))
+    assert np.array_equal(t00, t01)
+    for k in ("node_updates", "walk_moves", "max_moves", "exact_tests", "clipped", "fallbacks"):
+        assert s0[k] == s1[k], k
+
+
 @pytest.mark.parametrize("kernel", [1, 2], ids=["plain", "fast"])
 def test_batched_problems_match_single_runs(kernel):
     probs = si.batch_config(6, nmin=2e3, nmax=2e4, steps=3)
