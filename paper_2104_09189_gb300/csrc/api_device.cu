@@ -165,28 +165,34 @@ sl_status upload(sl_mesh *m)
 }
 
 // Host-side evaluation of the time factors of each field at t_{n+1}.
-static sl_status fill_step(const sl_mesh *m, const sl_problem *probs, int64_t n, ProbStep *out)
+// The constants of step n (t_{n+1} = (n+1) dt) of one problem, validated.
+static sl_status fill_step_one(const sl_problem &q, int64_t n, int32_t p, ProbStep &s)
 {
     const double pi = 3.14159265358979323846;
+    if (q.kind < SL_FIELD_ZERO || q.kind > SL_FIELD_PAPER)
+        return fail(SL_E_ARG, "problem " + std::to_string(p) + ": unknown field kind");
+    if (!(std::isfinite(q.dt) && q.dt > 0.0))
+        return fail(SL_E_ARG, "problem " + std::to_string(p) + ": dt must be finite and > 0");
+    for (int k = 0; k < SL_NPARAMS; ++k)
+        if (!std::isfinite(q.p[k])) return fail(SL_E_ARG, "problem " + std::to_string(p) + ": non-finite field parameter");
+    if (q.kind == SL_FIELD_SWIRL && q.p[0] == 0.0) return fail(SL_E_ARG, "swirl period p0 must be nonzero");
+    std::memset(&s, 0, sizeof(s));
+    s.kind = q.kind;
+    s.dt = q.dt;
+    s.t = (double)(n + 1) * q.dt;
+    std::memcpy(s.p, q.p, sizeof(s.p));
+    if (q.kind == SL_FIELD_SWIRL) s.c[0] = std::cos(pi * s.t / q.p[0]);
+    if (q.kind == SL_FIELD_FOURIER8)
+        for (int mm = 0; mm < 8; ++mm) s.c[mm] = q.p[4 * mm + 2] * std::cos(2.0 * pi * s.t + q.p[4 * mm + 3]);
+    if (q.kind == SL_FIELD_PAPER) s.c[0] = q.p[1] * s.t;
+    return SL_OK;
+}
+
+static sl_status fill_step(const sl_mesh *m, const sl_problem *probs, int64_t n, ProbStep *out)
+{
     for (int32_t p = 0; p < m->n_problems; ++p) {
-        const sl_problem &q = probs[p];
-        if (q.kind < SL_FIELD_ZERO || q.kind > SL_FIELD_PAPER)
-            return fail(SL_E_ARG, "problem " + std::to_string(p) + ": unknown field kind");
-        if (!(std::isfinite(q.dt) && q.dt > 0.0))
-            return fail(SL_E_ARG, "problem " + std::to_string(p) + ": dt must be finite and > 0");
-        for (int k = 0; k < SL_NPARAMS; ++k)
-            if (!std::isfinite(q.p[k])) return fail(SL_E_ARG, "problem " + std::to_string(p) + ": non-finite field parameter");
-        if (q.kind == SL_FIELD_SWIRL && q.p[0] == 0.0) return fail(SL_E_ARG, "swirl period p0 must be nonzero");
-        ProbStep &s = out[p];
-        std::memset(&s, 0, sizeof(s));
-        s.kind = q.kind;
-        s.dt = q.dt;
-        s.t = (double)(n + 1) * q.dt;
-        std::memcpy(s.p, q.p, sizeof(s.p));
-        if (q.kind == SL_FIELD_SWIRL) s.c[0] = std::cos(pi * s.t / q.p[0]);
-        if (q.kind == SL_FIELD_FOURIER8)
-            for (int mm = 0; mm < 8; ++mm) s.c[mm] = q.p[4 * mm + 2] * std::cos(2.0 * pi * s.t + q.p[4 * mm + 3]);
-        if (q.kind == SL_FIELD_PAPER) s.c[0] = q.p[1] * s.t;
+        const sl_status st = fill_step_one(probs[p], n, p, out[p]);
+        if (st != SL_OK) return st;
     }
     return SL_OK;
 }
@@ -277,44 +283,54 @@ static FastArgs make_fast_args(const sl_mesh *m, const FastProb *fp, const void 
 // The fast kernels are the default; SL_OPT_KERNEL = 1 selects the plain FP64 one.
 static bool use_fast(const sl_mesh *m) { return m->opt_kernel != 1 || m->precision == SL_FP32; }
 
-// Per-step constants of the fast kernels (see FastProb).
-static void fill_fast(const sl_mesh *m, const ProbStep *ps, FastProb *out)
+// Per-step constants of the fast kernels (see FastProb), of one problem.
+static void fill_fast_one(const ProbStep &q, FastProb &f)
 {
     const double pi = 3.14159265358979323846;
-    for (int32_t p = 0; p < m->n_problems; ++p) {
-        const ProbStep &q = ps[p];
-        FastProb &f = out[p];
-        std::memset(&f, 0, sizeof(f));
-        f.kind = q.kind;
-        f.dt = q.dt;
-        double c[6] = {0, 0, 0, 0, 0, 0};
-        switch (q.kind) {
-        case SL_FIELD_AFFINE:
-            c[0] = q.dt * (q.p[0] + q.p[3] * q.t);
-            c[1] = q.dt * q.p[1];
-            c[2] = q.dt * q.p[2];
-            c[3] = q.dt * (q.p[4] + q.p[7] * q.t);
-            c[4] = q.dt * q.p[5];
-            c[5] = q.dt * q.p[6];
-            break;
-        case SL_FIELD_ROTATION:
-            c[0] = q.dt * q.p[0];
-            c[1] = q.p[1];
-            c[2] = q.p[2];
-            break;
-        case SL_FIELD_SWIRL: c[0] = q.dt * q.c[0]; break;
-        case SL_FIELD_PAPER:
-            c[0] = q.dt * std::cos(q.p[1] * q.t);
-            c[1] = q.dt * std::sin(q.p[1] * q.t);
-            break;
-        case SL_FIELD_FOURIER8:
-            c[0] = q.dt * std::cos(2.0 * pi * q.t);
-            c[1] = q.dt * std::sin(2.0 * pi * q.t);
-            break;
-        default: break;
-        }
-        pack_fast_constants(q.kind, c, f);
+    std::memset(&f, 0, sizeof(f));
+    f.kind = q.kind;
+    f.dt = q.dt;
+    double c[6] = {0, 0, 0, 0, 0, 0};
+    switch (q.kind) {
+    case SL_FIELD_AFFINE:
+        c[0] = q.dt * (q.p[0] + q.p[3] * q.t);
+        c[1] = q.dt * q.p[1];
+        c[2] = q.dt * q.p[2];
+        c[3] = q.dt * (q.p[4] + q.p[7] * q.t);
+        c[4] = q.dt * q.p[5];
+        c[5] = q.dt * q.p[6];
+        break;
+    case SL_FIELD_ROTATION:
+        c[0] = q.dt * q.p[0];
+        c[1] = q.p[1];
+        c[2] = q.p[2];
+        break;
+    case SL_FIELD_SWIRL: c[0] = q.dt * q.c[0]; break;
+    case SL_FIELD_PAPER:
+        c[0] = q.dt * std::cos(q.p[1] * q.t);
+        c[1] = q.dt * std::sin(q.p[1] * q.t);
+        break;
+    case SL_FIELD_FOURIER8:
+        c[0] = q.dt * std::cos(2.0 * pi * q.t);
+        c[1] = q.dt * std::sin(2.0 * pi * q.t);
+        break;
+    default: break;
     }
+    pack_fast_constants(q.kind, c, f);
+}
+
+static void fill_fast(const sl_mesh *m, const ProbStep *ps, FastProb *out)
+{
+    for (int32_t p = 0; p < m->n_problems; ++p) fill_fast_one(ps[p], out[p]);
+}
+
+sl_status fast_constants_one(const sl_problem &q, int64_t n, int32_t p, FastProb &f)
+{
+    ProbStep s;
+    const sl_status st = fill_step_one(q, n, p, s);
+    if (st != SL_OK) return st;
+    fill_fast_one(s, f);
+    return SL_OK;
 }
 
 // Node tables of the trigonometric fields, rebuilt when the fields change.

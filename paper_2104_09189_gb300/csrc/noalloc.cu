@@ -69,51 +69,6 @@ sl_status scratch_for(int dev, DeviceScratch &out)
     return SL_OK;
 }
 
-// The per-step constants of one problem (the same formulas as sl_step).
-sl_status constants(const sl_problem &q, int64_t n, int32_t p, FastProb &f)
-{
-    const double pi = 3.14159265358979323846;
-    if (q.kind < SL_FIELD_ZERO || q.kind > SL_FIELD_PAPER)
-        return fail(SL_E_ARG, "problem " + std::to_string(p) + ": unknown field kind");
-    if (!(std::isfinite(q.dt) && q.dt > 0.0))
-        return fail(SL_E_ARG, "problem " + std::to_string(p) + ": dt must be finite and > 0");
-    for (int k = 0; k < SL_NPARAMS; ++k)
-        if (!std::isfinite(q.p[k])) return fail(SL_E_ARG, "problem " + std::to_string(p) + ": non-finite field parameter");
-    if (q.kind == SL_FIELD_SWIRL && q.p[0] == 0.0) return fail(SL_E_ARG, "swirl period p0 must be nonzero");
-    std::memset(&f, 0, sizeof(f));
-    f.kind = q.kind;
-    f.dt = q.dt;
-    const double t = (double)(n + 1) * q.dt;
-    double c[6] = {0, 0, 0, 0, 0, 0};
-    switch (q.kind) {
-    case SL_FIELD_AFFINE:
-        c[0] = q.dt * (q.p[0] + q.p[3] * t);
-        c[1] = q.dt * q.p[1];
-        c[2] = q.dt * q.p[2];
-        c[3] = q.dt * (q.p[4] + q.p[7] * t);
-        c[4] = q.dt * q.p[5];
-        c[5] = q.dt * q.p[6];
-        break;
-    case SL_FIELD_ROTATION:
-        c[0] = q.dt * q.p[0];
-        c[1] = q.p[1];
-        c[2] = q.p[2];
-        break;
-    case SL_FIELD_SWIRL: c[0] = q.dt * std::cos(pi * t / q.p[0]); break;
-    case SL_FIELD_PAPER:
-        c[0] = q.dt * std::cos(q.p[1] * t);
-        c[1] = q.dt * std::sin(q.p[1] * t);
-        break;
-    case SL_FIELD_FOURIER8:
-        c[0] = q.dt * std::cos(2.0 * pi * t);
-        c[1] = q.dt * std::sin(2.0 * pi * t);
-        break;
-    default: break;
-    }
-    pack_fast_constants(q.kind, c, f);
-    return SL_OK;
-}
-
 // Node tables of trigonometric fields must already match these problems
 // (building them would allocate).
 bool tables_ready(const sl_mesh *m, const sl_problem *probs)
@@ -167,7 +122,7 @@ extern "C" sl_status sl_step_noalloc(sl_mesh *m, const sl_problem *probs, int64_
 
     FastProb host[kNoAllocMaxProblems];
     for (int32_t p = 0; p < m->n_problems; ++p) {
-        st = constants(probs[p], n, p, host[p]);
+        st = fast_constants_one(probs[p], n, p, host[p]);
         if (st != SL_OK) return st;
     }
     cudaStream_t s = (cudaStream_t)stream;

@@ -110,11 +110,14 @@ struct sl_mesh {
 };
 
 namespace sl {
+struct FastProb;
 // host side (mesh_host.cpp)
 sl_status build_and_validate(sl_mesh *m, const int32_t *nbr_in);
 sl_status reorder_host(sl_mesh *m, int32_t curve, int32_t *node_perm, int32_t *tri_perm);
-// device side (step.cu)
+// device side (api_device.cu)
 sl_status upload(sl_mesh *m);
+// the fast kernels' constants of step n of one problem, validated as sl_step validates them
+sl_status fast_constants_one(const sl_problem &q, int64_t n, int32_t p, FastProb &f);
 void free_device(sl_mesh *m);
 sl_status reset_t0_sync(sl_mesh *m);
 sl_status upload_grid_table(sl_mesh *m, const std::vector<int32_t> &slot_tri);
