@@ -87,8 +87,10 @@ enum {
     SL_NODE_FALLBACK = 8,     /* the walk hit its hop cap and used the fallback walk */
     SL_NODE_WALK_LIMIT = 16,  /* the fallback failed too: the value is not valid */
     SL_NODE_RANGE = 32,       /* a coordinate outside the exact predicate's range */
-    SL_NODE_EXCLUDED = 64     /* SL_OPT_OUTSIDE = 1: the Euler foot left the square, so the node
+    SL_NODE_EXCLUDED = 64,    /* SL_OPT_OUTSIDE = 1: the Euler foot left the square, so the node
                                  was excluded (V^{n+1}_i = V^n_i, no walk, T^0_i unchanged) */
+    SL_NODE_PRECISE = 128     /* double-float kernel: the value was evaluated in FP64 because V^n
+                                 is steep in the located triangle (SL_OPT_PRECISE) */
 };
 
 typedef struct sl_mesh sl_mesh;   /* opaque; owns device mesh arrays and T^0 */
@@ -97,10 +99,14 @@ typedef struct sl_mesh sl_mesh;   /* opaque; owns device mesh arrays and T^0 */
  * Arrays are indexed by node in the mesh's current numbering (all problems
  * concatenated). */
 typedef struct {
-    double *feet;     /* 2N doubles: the clipped foot (x, y) of every node */
+    double *feet;     /* 2N doubles: the clipped foot (x, y) of every node, rounded to double */
     int32_t *tri;     /* N: located triangle, global index in current numbering */
     int32_t *moves;   /* N: walk hops (0 if the start triangle contains the foot) */
     uint8_t *flags;   /* N: SL_NODE_* bits */
+    double *feet_lo;  /* 2N doubles: the exact rest of the foot, so that feet + feet_lo (summed
+                         exactly, per coordinate) is the point the kernel located.  The
+                         double-float kernel holds a foot as a pair of floats, which one double
+                         cannot always represent; the plain FP64 and the FP32 kernels write 0. */
 } sl_debug;
 
 /* Counters accumulated on the device by sl_step / sl_run when enabled with
@@ -122,12 +128,11 @@ typedef enum {
     SL_OPT_STATS = 0,        /* 0/1: accumulate sl_stats counters (default 0) */
     SL_OPT_WALK_CAP = 1,     /* hops before the fallback rule (default max(64, 4 (M+1))) */
     SL_OPT_KERNEL = 2,       /* 0 = auto (fast), 1 = plain FP64 kernel, 2 = fast kernel */
-    SL_OPT_BLOCK = 3,        /* threads per block (0 = auto) */
-    SL_OPT_TILES_PER_SM = 4, /* reserved */
+    SL_OPT_BLOCK = 3,        /* threads per block of the plain FP64 kernel (0 = auto) */
+    /* 4 and 6 are not options (SL_E_ARG) */
     SL_OPT_CONFIG = 5,       /* launch configuration of the fast kernels, 0..5: threads per block x
                                 blocks per SM the registers are sized for = 256x4, 256x3, 128x8,
                                 128x9, 256x5, 128x12 (default 5) */
-    /* 6: unused */
     SL_OPT_CONFIG_FIRST = 7, /* launch configuration for a step whose walks start at the initial
                                 incident triangles (the first step after sl_mesh_create or
                                 sl_mesh_reset_t0): long walks favour fewer resident warps (default 0) */
@@ -153,11 +158,21 @@ typedef enum {
                                 queues the others for the full kernel (fewer registers where the
                                 feet move little).  Results are identical.  Never used for a step
                                 from the initial start triangles.  sl_autotune sets it. */
-    SL_OPT_ASYNC = 11        /* 0 = sl_run synchronises the stream and returns the device status
+    SL_OPT_ASYNC = 11,       /* 0 = sl_run synchronises the stream and returns the device status
                                 (default); 1 = sl_run returns once its steps are enqueued when
                                 stats is NULL, and the device status is read by the next
                                 sl_mesh_status (or a synchronising sl_run).  Lets a caller queue
                                 many runs back to back. */
+    SL_OPT_PRECISE = 12      /* FP64 meshes, double-float kernel: gradient bound G >= 0 (value
+                                units per unit length; default 32; 0 = never).  The double-float
+                                foot and barycentric coordinates carry about 2^-48 of rounding (a
+                                foot moved by a few 2^-49), so a step's value is off by about
+                                2^-46 |grad V|.  Where V^n in the located triangle is steeper
+                                than G (max_k (v_k - v_3)^2 > G^2 den, den = twice its area), the
+                                foot of an unclipped node, its barycentric coordinates (Eq. 6)
+                                and the P1 value are evaluated again in FP64 from the double
+                                coordinates, as the plain kernel does; the located triangle is
+                                the same.  Scale G with the magnitude of V. */
 } sl_option;
 
 /*
@@ -262,7 +277,10 @@ sl_status sl_run_host(sl_mesh *m, const sl_problem *probs, int64_t n0, int32_t n
 
 /*
  * sl_step_noalloc -- the same step as sl_step for FP64 meshes (double values
- * in and out), performing no device allocation.  The paper has no
+ * in and out), performing no device allocation.  It always runs the fused
+ * double-float kernel in the launch configuration sl_step would use for the
+ * step: SL_OPT_KERNEL = 1 (the plain FP64 kernel) and SL_OPT_SPLIT do not
+ * apply to it (the split form gives the same results).  The paper has no
  * counterpart: this exists for callers that cannot allocate device memory
  * while they step -- code running inside a host application whose caching
  * allocator owns the device memory, callbacks that must not synchronise the
@@ -280,7 +298,9 @@ sl_status sl_run_host(sl_mesh *m, const sl_problem *probs, int64_t n0, int32_t n
  *
  * All scratch lives in one library-owned static device array per GPU
  * (8 MiB of value pairs + 16 KiB of per-problem constants), held by every
- * GPU that loads the library until the process exits.  The first call on a
+ * GPU that loads the library until the process exits.  The step's constants
+ * reach that array in the parameters of a small kernel; no host buffer of
+ * the call is read after it returns.  The first call on a
  * device looks up the array's device address (cudaGetSymbolAddress); make
  * that first call before any stream capture.  Every call on a device shares
  * the array and overwrites what it uses, so calls that overlap on the GPU
@@ -335,8 +355,16 @@ sl_status sl_autotune(sl_mesh *m, const sl_problem *probs, int32_t probe_steps, 
  */
 sl_status sl_probe_gather(sl_mesh *m, const void *v, void *v_scratch, int32_t reps, float *ms_out, void *stream);
 
-/* T^0 export / import (device, N int32 global triangle indices in current
- * numbering); with V^n this is the whole state of a run (resume). */
+/*
+ * sl_mesh_get_t0 / sl_mesh_set_t0 -- export / import the start-triangle list
+ * T^0 of Sec. 3 (Algorithm 1 reads T^0_i as the walk's first triangle and,
+ * in strategy (b), stores the foot triangle T^f_i there).  t0_dev: device,
+ * N int32, global triangle indices in the current numbering, written (get)
+ * or read (set) on `stream`; the caller owns it.  With V^n this is the whole
+ * state of a run, so a run can stop and resume bitwise.  set validates every
+ * entry (SL_E_ARG if one is not a triangle of its node's problem; it copies
+ * T^0 through the host and synchronises) and refreshes the start-state cache.
+ */
 sl_status sl_mesh_get_t0(const sl_mesh *m, int32_t *t0_dev, void *stream);
 sl_status sl_mesh_set_t0(sl_mesh *m, const int32_t *t0_dev, void *stream);
 
@@ -347,24 +375,51 @@ sl_status sl_mesh_set_t0(sl_mesh *m, const int32_t *t0_dev, void *stream);
  * the first step). */
 sl_status sl_mesh_reset_t0(sl_mesh *m, void *stream);
 
-/* Synchronise `stream` and return (and clear) the deferred device status. */
+/*
+ * sl_mesh_status -- synchronise `stream` and return (and clear) the deferred
+ * device status: SL_E_WALK_LIMIT when a walk exceeded its hop cap and its
+ * fallback (reading c9: the paper assumes Delaunay meshes, on which the walk
+ * of Algorithm 1 always ends), SL_E_ARG when a coordinate fell outside the
+ * exact predicate's range, SL_OK otherwise.
+ */
 sl_status sl_mesh_status(sl_mesh *m, void *stream);
 
-/* Read (and with reset != 0, clear) the device counters; synchronises. */
+/*
+ * sl_mesh_stats -- read (and with reset != 0, clear) the device counters of
+ * sl_stats (out: host); synchronises `stream`.  The hop counts are the walk
+ * steps of Algorithm 1 that the paper measures (Sec. 2.2, Sec. 4: mean moves
+ * per located point); the other counters have no counterpart in the paper.
+ */
 sl_status sl_mesh_stats(sl_mesh *m, sl_stats *out, int32_t reset, void *stream);
 
+/*
+ * sl_mesh_set_option -- set one sl_option (values and ranges documented with
+ * the enum; SL_E_ARG for an unknown option or a value out of range).
+ * SL_OPT_STRATEGY selects the start strategies of Sec. 3 and the direct
+ * location of Sec. 4, SL_OPT_OUTSIDE the exclusion of Sec. 4; the others are
+ * launch and instrumentation settings with no counterpart in the paper.
+ * Host only, except SL_OPT_STRATEGY, which resets T^0 and synchronises.
+ */
 sl_status sl_mesh_set_option(sl_mesh *m, int32_t option, int64_t value);
 
-/* Sizes of the handle: n_nodes, n_tri, n_problems, precision. */
+/* sl_mesh_info -- the sizes of the handle (host outputs, each may be NULL):
+ * nodes and triangles over all problems, problems, precision.  No
+ * counterpart in the paper. */
 sl_status sl_mesh_info(const sl_mesh *m, int64_t *n_nodes, int64_t *n_tri, int32_t *n_problems,
                        int32_t *precision);
 
-/* Export the mesh in its current numbering (host arrays: 2N doubles,
- * 3Nt int32 local vertex indices, 3Nt int32 local neighbours). */
+/* sl_mesh_export -- the mesh in its current numbering: the node list V, the
+ * triangle list T and the neighbour list N of Sec. 3 (host arrays owned by
+ * the caller: xy 2N doubles, tri 3Nt int32 local vertex indices, nbr 3Nt
+ * int32 local neighbours, -1 on the boundary; each may be NULL). */
 sl_status sl_mesh_export(const sl_mesh *m, double *xy, int32_t *tri, int32_t *nbr);
 
+/* sl_mesh_destroy -- free the handle and every device buffer it owns
+ * (NULL is ignored).  No counterpart in the paper. */
 void sl_mesh_destroy(sl_mesh *m);
 
+/* sl_last_error -- the calling thread's message for its last failed call
+ * (valid until its next call).  No counterpart in the paper. */
 const char *sl_last_error(void);
 
 #ifdef __cplusplus

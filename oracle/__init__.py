@@ -57,6 +57,8 @@ def lib():
             L.orc_foot.restype = I
             L.orc_orient_sign.argtypes = [D] * 6
             L.orc_orient_sign.restype = I
+            L.orc_orient_sign2.argtypes = [D] * 8
+            L.orc_orient_sign2.restype = I
             L.orc_set_force_exact.argtypes = [I]
             L.orc_exact_calls.restype = ctypes.c_long
             L.orc_mesh_create.argtypes = [I64, I64, P, P]
@@ -66,8 +68,6 @@ def lib():
             L.orc_mesh_bins.restype = I
             L.orc_interp.argtypes = [P, ctypes.c_int32, D, D, P]
             L.orc_interp.restype = D
-            L.orc_tri_margin.argtypes = [P, ctypes.c_int32, D, D]
-            L.orc_tri_margin.restype = D
             L.orc_step_range.argtypes = [P, I, P, D, I64, P, P, P, P, P, I64, I64, I]
             L.orc_step_range.restype = I
             L.orc_step_range_x.argtypes = [P, I, P, D, I64, P, P, P, P, P, I64, I64, I, I]
@@ -78,9 +78,10 @@ def lib():
             L.orc_run.restype = I
             L.orc_locate_points.argtypes = [P, I64, P, P, P]
             L.orc_locate_points.restype = I
-            L.orc_margins.argtypes = [P, I64, P, P, P]
+            L.orc_locate_points2.argtypes = [P, I64, P, P, P, P, I]
+            L.orc_locate_points2.restype = I
+            L.orc_tri_signs2.argtypes = [P, I64, P, P, P, P, I]
             L.orc_feet.argtypes = [I, P, D, I64, I64, P, P, P]
-            L.orc_feet_f32.argtypes = [I, P, D, I64, I64, P, P, P]
             _lib = L
     return _lib
 
@@ -102,6 +103,18 @@ def orient_sign(a, b, c, force_exact=False):
         L.orc_set_force_exact(0)
 
 
+def orient_sign2(a, b, qh, ql, force_exact=False):
+    """Exact sign of orient(a, b, q) for the point q = qh + ql (the sum of
+    the two doubles of each coordinate, taken exactly)."""
+    L = lib()
+    L.orc_set_force_exact(1 if force_exact else 0)
+    try:
+        return L.orc_orient_sign2(float(a[0]), float(a[1]), float(b[0]), float(b[1]),
+                                  float(qh[0]), float(qh[1]), float(ql[0]), float(ql[1]))
+    finally:
+        L.orc_set_force_exact(0)
+
+
 def field(kind, params, x, y, t):
     p = np.ascontiguousarray(params, dtype=np.float64)
     fx = ctypes.c_double()
@@ -117,17 +130,6 @@ def feet(kind, params, dt, n, xy):
     out = np.empty_like(xy)
     clipped = np.empty(xy.shape[0], dtype=np.uint8)
     lib().orc_feet(int(kind), _ptr(p), float(dt), int(n), xy.shape[0], _ptr(xy), _ptr(out), _ptr(clipped))
-    return out, clipped
-
-
-def feet_f32(kind, params, dt, n, xy_f32):
-    """Feet of the FP32 path (float arithmetic, see orc_feet_f32) for float
-    node coordinates; returns (float32 feet, clipped flags)."""
-    p = np.ascontiguousarray(params, dtype=np.float64)
-    xy = np.ascontiguousarray(xy_f32, dtype=np.float32)
-    out = np.empty_like(xy)
-    clipped = np.empty(xy.shape[0], dtype=np.uint8)
-    lib().orc_feet_f32(int(kind), _ptr(p), float(dt), int(n), xy.shape[0], _ptr(xy), _ptr(out), _ptr(clipped))
     return out, clipped
 
 
@@ -158,25 +160,38 @@ class OracleMesh:
     def bins(self):
         return lib().orc_mesh_bins(self._h)
 
-    def locate(self, q):
+    def locate(self, q, q_lo=None, nthreads=None):
+        """Exact location of query points: the lowest-index triangle that
+        contains each point and its flags (FLAG_DEGENERATE: on an edge line
+        of that triangle; FLAG_MULTI: more than one triangle contains it).
+        With q_lo the points are q + q_lo, the sum of each coordinate's two
+        doubles taken exactly (a double-float foot)."""
         q = np.ascontiguousarray(q, dtype=np.float64).reshape(-1, 2)
+        ql = None if q_lo is None else np.ascontiguousarray(q_lo, dtype=np.float64).reshape(-1, 2)
         tri = np.empty(q.shape[0], dtype=np.int32)
         flags = np.empty(q.shape[0], dtype=np.uint8)
-        err = lib().orc_locate_points(self._h, q.shape[0], _ptr(q), _ptr(tri), _ptr(flags))
+        err = lib().orc_locate_points2(self._h, q.shape[0], _ptr(q), _ptr(ql), _ptr(tri), _ptr(flags),
+                                       int(nthreads or default_threads()))
         if err:
             raise RuntimeError("oracle: a query point lies in no triangle (mesh does not cover it)")
         return tri, flags
 
+    def signs(self, tri, q, q_lo=None, nthreads=None):
+        """Exact orientation signs of each point against the three edges of
+        the given triangle (opposite vertex 0, 1, 2): int8 (n, 3), -2 for an
+        index that is not a triangle.  The point lies in the closed triangle
+        iff all three are >= 0."""
+        tri = np.ascontiguousarray(tri, dtype=np.int32)
+        q = np.ascontiguousarray(q, dtype=np.float64).reshape(-1, 2)
+        ql = None if q_lo is None else np.ascontiguousarray(q_lo, dtype=np.float64).reshape(-1, 2)
+        out = np.empty((q.shape[0], 3), dtype=np.int8)
+        lib().orc_tri_signs2(self._h, q.shape[0], _ptr(tri), _ptr(q), _ptr(ql), _ptr(out),
+                             int(nthreads or default_threads()))
+        return out
+
     def interp(self, j, X, Y, V):
         V = np.ascontiguousarray(V, dtype=np.float64)
         return lib().orc_interp(self._h, int(j), float(X), float(Y), _ptr(V))
-
-    def margins(self, tri, q):
-        tri = np.ascontiguousarray(tri, dtype=np.int32)
-        q = np.ascontiguousarray(q, dtype=np.float64).reshape(-1, 2)
-        out = np.empty(q.shape[0], dtype=np.float64)
-        lib().orc_margins(self._h, q.shape[0], _ptr(tri), _ptr(q), _ptr(out))
-        return out
 
     def step(self, kind, params, dt, n, vin, lo=0, hi=None, nthreads=None, want_feet=True, exclude=False):
         """One step n -> n+1 on nodes [lo, hi).  Returns (vout, tri, flags, feet)

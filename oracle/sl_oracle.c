@@ -151,98 +151,6 @@ int orc_foot(int kind, const double *p, double dt, double t, double x, double y,
     return clip_segment(x, y, qx, qy, X, Y);
 }
 
-/* Single-precision foot of the FP32 path (its triangles are compared on the
- * same float feet).  Node coordinates are floats; the time factors and the
- * space factors of each field are evaluated in double and rounded to float
- * once; the Euler step then runs in float, one rounding per operation:
- *   AFFINE    f = (c0 + c1 x) + c2 y, X = x - f, with c0 = dt (p0 + p3 t),
- *             c1 = dt p1, c2 = dt p2 (c3..c5 alike for y)
- *   ROTATION  X = x + c0 (y - cy), Y = y - c0 (x - cx), c0 = dt p0
- *   SWIRL     X = x - c0 gx, c0 = dt cos(pi t / T),
- *             g = (sin^2(pi x) sin(2 pi y), -sin^2(pi y) sin(2 pi x))
- *   PAPER     X = x - (c0 g1x + c1 g2x), c0 = dt cos(C1 t), c1 = dt sin(C1 t),
- *             g1 = (cos a, sin a), g2 = (-sin a, cos a), a = C0 |x - c|
- *   FOURIER8  the same with c0 = dt cos(2 pi t), c1 = dt sin(2 pi t),
- *             g1 = sum_m a_m cos(phi_m) h_m, g2 = -sum_m a_m sin(phi_m) h_m,
- *             h_m = (l pi sin(k pi x) cos(l pi y), -k pi cos(k pi x) sin(l pi y))
- * (the same field as orc_field, split into time and space factors).  A
- * foot outside the square is clipped in double and rounded to float. */
-void orc_feet_f32(int kind, const double *p, double dt, int64_t n, int64_t npts, const float *xy, float *feet,
-                  uint8_t *clipped)
-{
-    const double t = (double)(n + 1) * dt;
-    float c[6] = {0, 0, 0, 0, 0, 0};
-    if (kind == ORC_FIELD_AFFINE) {
-        c[0] = (float)(dt * (p[0] + p[3] * t));
-        c[1] = (float)(dt * p[1]);
-        c[2] = (float)(dt * p[2]);
-        c[3] = (float)(dt * (p[4] + p[7] * t));
-        c[4] = (float)(dt * p[5]);
-        c[5] = (float)(dt * p[6]);
-    } else if (kind == ORC_FIELD_ROTATION) {
-        c[0] = (float)(dt * p[0]);
-        c[1] = (float)p[1];
-        c[2] = (float)p[2];
-    } else if (kind == ORC_FIELD_SWIRL) {
-        c[0] = (float)(dt * cos(PI * t / p[0]));
-    } else if (kind == ORC_FIELD_PAPER) {
-        c[0] = (float)(dt * cos(p[1] * t));
-        c[1] = (float)(dt * sin(p[1] * t));
-    } else if (kind == ORC_FIELD_FOURIER8) {
-        c[0] = (float)(dt * cos(2.0 * PI * t));
-        c[1] = (float)(dt * sin(2.0 * PI * t));
-    }
-    for (int64_t i = 0; i < npts; ++i) {
-        const float x = xy[2 * i], y = xy[2 * i + 1];
-        const double xd = x, yd = y;
-        float X = x, Y = y;
-        if (kind == ORC_FIELD_AFFINE) {
-            float fx = (c[0] + c[1] * x) + c[2] * y;
-            float fy = (c[3] + c[4] * x) + c[5] * y;
-            X = x - fx;
-            Y = y - fy;
-        } else if (kind == ORC_FIELD_ROTATION) {
-            X = x + c[0] * (y - c[2]);
-            Y = y - c[0] * (x - c[1]);
-        } else if (kind == ORC_FIELD_SWIRL) {
-            double sx = sin(PI * xd), sy = sin(PI * yd);
-            float gx = (float)((sx * sx) * sin(2.0 * PI * yd));
-            float gy = (float)(-(sy * sy) * sin(2.0 * PI * xd));
-            X = x - c[0] * gx;
-            Y = y - c[0] * gy;
-        } else if (kind == ORC_FIELD_PAPER) {
-            double dx = xd - p[2], dy = yd - p[3];
-            double a = p[0] * sqrt(dx * dx + dy * dy);
-            float g1x = (float)cos(a), g1y = (float)sin(a), g2x = (float)(-sin(a)), g2y = (float)cos(a);
-            X = x - (c[0] * g1x + c[1] * g2x);
-            Y = y - (c[0] * g1y + c[1] * g2y);
-        } else if (kind == ORC_FIELD_FOURIER8) {
-            double g1x = 0, g1y = 0, g2x = 0, g2y = 0;
-            for (int m = 0; m < 8; ++m) {
-                double k = p[4 * m], l = p[4 * m + 1], am = p[4 * m + 2], ph = p[4 * m + 3];
-                double hx = l * PI * sin(k * PI * xd) * cos(l * PI * yd);
-                double hy = -k * PI * cos(k * PI * xd) * sin(l * PI * yd);
-                g1x += am * cos(ph) * hx;
-                g1y += am * cos(ph) * hy;
-                g2x -= am * sin(ph) * hx;
-                g2y -= am * sin(ph) * hy;
-            }
-            X = x - (c[0] * (float)g1x + c[1] * (float)g2x);
-            Y = y - (c[0] * (float)g1y + c[1] * (float)g2y);
-        }
-        int cl = 0;
-        if (!(X >= 0.0f && X <= 1.0f && Y >= 0.0f && Y <= 1.0f)) {
-            double cx, cy;
-            cl = clip_segment(xd, yd, (double)X, (double)Y, &cx, &cy);
-            X = (float)cx;
-            Y = (float)cy;
-        }
-        feet[2 * i] = X;
-        feet[2 * i + 1] = Y;
-        if (clipped) clipped[i] = (uint8_t)cl;
-    }
-}
-
 /* ------------------------------------------------------------------ */
 /* Exact orientation sign                                               */
 /* ------------------------------------------------------------------ */
@@ -407,6 +315,69 @@ int orc_orient_sign(double ax, double ay, double bx, double by, double cx, doubl
     return orient_exact(v);
 }
 
+/* The same sign for a query point given as an unevaluated sum of two
+ * doubles per coordinate, q = (qxh + qxl, qyh + qyl), taken exactly (a
+ * double-float foot is such a sum, and one double cannot always hold it).
+ * The determinant is linear in q:
+ *   orient(a, b, q) = orient(a, b, qh) + (bx - ax) qyl - (by - ay) qxl,
+ * evaluated exactly with the multi-limb integers on all eight inputs. */
+static int orient_exact_pair(const double v[8])
+{
+    /* v = ax, ay, bx, by, qxh, qyh, qxl, qyl */
+    int64_t m[8];
+    int e[8], emin = 1 << 30;
+    for (int k = 0; k < 8; ++k) {
+        if (v[k] == 0.0) { m[k] = 0; e[k] = 0; continue; }
+        int ex;
+        double f = frexp(v[k], &ex);
+        m[k] = (int64_t)ldexp(f, 53);
+        e[k] = ex - 53;
+        if (e[k] < emin) emin = e[k];
+    }
+    big b[8];
+    for (int k = 0; k < 8; ++k) big_set_scaled(&b[k], m[k], m[k] ? e[k] - emin : 0);
+    big dbx, dby, qx, qy, dqx, dqy, t1, t2, det;
+    big_addsub(&dbx, &b[2], &b[0], -1);
+    big_addsub(&dby, &b[3], &b[1], -1);
+    big_addsub(&qx, &b[4], &b[6], 1);          /* qx = qxh + qxl exactly */
+    big_addsub(&qy, &b[5], &b[7], 1);
+    big_addsub(&dqx, &qx, &b[0], -1);
+    big_addsub(&dqy, &qy, &b[1], -1);
+    big_mul(&t1, &dbx, &dqy);
+    big_mul(&t2, &dby, &dqx);
+    big_addsub(&det, &t1, &t2, -1);
+    return det.sign;
+}
+
+/* Sign of orient(a, b, q) for q = (qxh + qxl, qyh + qyl), exact for all
+ * finite inputs.  With qxl = qyl = 0 this is orc_orient_sign(a, b, qh). */
+int orc_orient_sign2(double ax, double ay, double bx, double by, double qxh, double qyh, double qxl, double qyl)
+{
+    if (qxl == 0.0 && qyl == 0.0) return orc_orient_sign(ax, ay, bx, by, qxh, qyh);
+    if (!g_force_exact) {
+        double ex = bx - ax, ey = by - ay;
+        double t1 = ex * (qyh - ay);
+        double t2 = ey * (qxh - ax);
+        double c1 = ex * qyl;
+        double c2 = ey * qxl;
+        double det = (t1 - t2) + (c1 - c2);
+        double mag = fabs(t1) + fabs(t2) + fabs(c1) + fabs(c2);
+        /* t1, t2 carry at most 3 roundings each, c1, c2 at most 2 (the
+         * difference ex or ey and the product), and the three additions one
+         * each: |det - exact| <= (8u + O(u^2)) mag, u = 2^-53.  2^-49 mag
+         * doubles that margin; an underflowed c1 or c2 is off by at most
+         * 2^-1074, far below it while mag > 2^-900. */
+        double bound = 0x1p-49 * mag;
+        if (mag > 0x1p-900 && mag < 0x1p+900) {
+            if (det > bound) return 1;
+            if (det < -bound) return -1;
+        }
+    }
+    __atomic_fetch_add(&g_exact_calls, 1, __ATOMIC_RELAXED);
+    double v[8] = {ax, ay, bx, by, qxh, qyh, qxl, qyl};
+    return orient_exact_pair(v);
+}
+
 /* ------------------------------------------------------------------ */
 /* Mesh with a uniform bin grid                                        */
 /* ------------------------------------------------------------------ */
@@ -530,6 +501,49 @@ int orc_locate(const orc_mesh *m, double X, double Y, int32_t *tri_out, int *fla
     return best >= 0 ? 0 : -1;
 }
 
+/* The three signs of tri_signs for a query point q = qh + ql (pair form). */
+static void tri_signs2(const orc_mesh *m, int64_t j, double X, double Y, double Xl, double Yl, int s[3])
+{
+    const int32_t *t = m->tri + 3 * j;
+    double x1 = m->xy[2 * t[0]], y1 = m->xy[2 * t[0] + 1];
+    double x2 = m->xy[2 * t[1]], y2 = m->xy[2 * t[1] + 1];
+    double x3 = m->xy[2 * t[2]], y3 = m->xy[2 * t[2] + 1];
+    s[0] = orc_orient_sign2(x2, y2, x3, y3, X, Y, Xl, Yl);
+    s[1] = orc_orient_sign2(x3, y3, x1, y1, X, Y, Xl, Yl);
+    s[2] = orc_orient_sign2(x1, y1, x2, y2, X, Y, Xl, Yl);
+}
+
+/* orc_locate for the point (X + Xl, Y + Yl), taken exactly.  The bin is the
+ * one of the rounded sums: a triangle's bins cover its bounding box
+ * [bmin, bmax] through the same monotone map, and bmin <= q implies
+ * bmin <= fl(q) for a double bmin (rounding to nearest is monotone), so every
+ * containing triangle is still a candidate. */
+int orc_locate2(const orc_mesh *m, double X, double Y, double Xl, double Yl, int32_t *tri_out, int *flags)
+{
+    int B = m->B;
+    size_t b = (size_t)bin_of(Y + Yl, B) * B + bin_of(X + Xl, B);
+    int32_t best = -1;
+    int count = 0, degen = 0;
+    for (int64_t q = m->start[b]; q < m->start[b + 1]; ++q) {
+        int32_t j = m->items[q];
+        int s[3];
+        tri_signs2(m, j, X, Y, Xl, Yl, s);
+        if (s[0] >= 0 && s[1] >= 0 && s[2] >= 0) {
+            if (count == 0) {
+                best = j;
+                degen = (s[0] == 0 || s[1] == 0 || s[2] == 0);
+            }
+            count++;
+        }
+    }
+    *tri_out = best;
+    int f = 0;
+    if (degen) f |= ORC_FLAG_DEGENERATE;
+    if (count > 1) f |= ORC_FLAG_MULTI;
+    *flags = f;
+    return best >= 0 ? 0 : -1;
+}
+
 /* P1 value at (X, Y) in triangle j, by Eq. 6 and the interpolation formula
  * of Remark 1. */
 double orc_interp(const orc_mesh *m, int32_t j, double X, double Y, const double *V)
@@ -543,23 +557,6 @@ double orc_interp(const orc_mesh *m, int32_t j, double X, double Y, const double
     double th2 = ((eta3 - eta1) * (X - xi3) + (xi1 - xi3) * (Y - eta3)) / den;
     double th3 = 1.0 - th1 - th2;
     return th1 * V[t[0]] + th2 * V[t[1]] + th3 * V[t[2]];
-}
-
-/* Smallest signed distance from (X, Y) to the three edge lines of triangle j
- * (positive inside).  Used by tests to classify near-degenerate feet. */
-double orc_tri_margin(const orc_mesh *m, int32_t j, double X, double Y)
-{
-    const int32_t *t = m->tri + 3 * (int64_t)j;
-    double best = 1e300;
-    for (int k = 0; k < 3; ++k) {
-        int32_t a = t[(k + 1) % 3], b = t[(k + 2) % 3];
-        double ax = m->xy[2 * a], ay = m->xy[2 * a + 1];
-        double bx = m->xy[2 * b], by = m->xy[2 * b + 1];
-        double ex = bx - ax, ey = by - ay;
-        double d = (ex * (Y - ay) - ey * (X - ax)) / sqrt(ex * ex + ey * ey);
-        if (d < best) best = d;
-    }
-    return best;
 }
 
 /* ------------------------------------------------------------------ */
@@ -690,24 +687,104 @@ int orc_run(const orc_mesh *m, int kind, const double *p, double dt, int64_t n0,
     return 0;
 }
 
-/* Locate arbitrary query points (no foot, no clip). */
-int orc_locate_points(const orc_mesh *m, int64_t npts, const double *q, int32_t *tri, uint8_t *flags)
+/* Batch location and sign triples of query points, threaded over
+ * contiguous ranges.  Points are (q[2i] + ql[2i], q[2i+1] + ql[2i+1]),
+ * taken exactly; ql may be NULL (points q). */
+typedef struct {
+    const orc_mesh *m;
+    const double *q, *ql;
+    const int32_t *tri_in;     /* sign mode: the triangle of each point */
+    int32_t *tri;
+    uint8_t *flags;
+    int8_t *signs;             /* sign mode: 3 per point */
+    int64_t lo, hi;
+    int err;
+} point_job;
+
+static void *point_worker(void *arg)
 {
-    int err = 0;
-    for (int64_t i = 0; i < npts; ++i) {
+    point_job *J = (point_job *)arg;
+    for (int64_t i = J->lo; i < J->hi; ++i) {
+        const double X = J->q[2 * i], Y = J->q[2 * i + 1];
+        const double Xl = J->ql ? J->ql[2 * i] : 0.0, Yl = J->ql ? J->ql[2 * i + 1] : 0.0;
+        if (J->signs) {
+            int s[3] = {-2, -2, -2};          /* -2: not a triangle of the mesh */
+            const int32_t j = J->tri_in[i];
+            if (j >= 0 && j < J->m->nt) tri_signs2(J->m, j, X, Y, Xl, Yl, s);
+            for (int k = 0; k < 3; ++k) J->signs[3 * i + k] = (int8_t)s[k];
+            continue;
+        }
         int32_t j;
         int f;
-        if (orc_locate(m, q[2 * i], q[2 * i + 1], &j, &f) != 0) err = -1;
-        tri[i] = j;
-        if (flags) flags[i] = (uint8_t)f;
+        if (orc_locate2(J->m, X, Y, Xl, Yl, &j, &f) != 0) J->err = -1;
+        J->tri[i] = j;
+        if (J->flags) J->flags[i] = (uint8_t)f;
     }
+    return NULL;
+}
+
+static int run_points(point_job *tmpl, int64_t npts, int nthreads)
+{
+    if (nthreads < 1) nthreads = 1;
+    if (nthreads > 256) nthreads = 256;
+    if (npts < (int64_t)nthreads * 256) nthreads = npts > 256 ? (int)(npts / 256) : 1;
+    point_job jobs[256];
+    pthread_t th[256];
+    for (int k = 0; k < nthreads; ++k) {
+        jobs[k] = *tmpl;
+        jobs[k].lo = npts * k / nthreads;
+        jobs[k].hi = npts * (k + 1) / nthreads;
+        jobs[k].err = 0;
+    }
+    int started = 0;
+    for (int k = 1; k < nthreads; ++k) {
+        if (pthread_create(&th[k], NULL, point_worker, &jobs[k]) != 0) break;
+        started = k;
+    }
+    point_worker(&jobs[0]);
+    for (int k = started + 1; k < nthreads; ++k) point_worker(&jobs[k]);
+    for (int k = 1; k <= started; ++k) pthread_join(th[k], NULL);
+    int err = 0;
+    for (int k = 0; k < nthreads; ++k) if (jobs[k].err) err = jobs[k].err;
     return err;
 }
 
-void orc_margins(const orc_mesh *m, int64_t npts, const int32_t *tri, const double *q, double *out)
+/* Locate arbitrary query points (no foot, no clip): the lowest-index
+ * containing triangle and the flags of orc_locate.  Returns -1 if some point
+ * lies in no triangle (its tri is -1). */
+int orc_locate_points(const orc_mesh *m, int64_t npts, const double *q, int32_t *tri, uint8_t *flags)
 {
-    for (int64_t i = 0; i < npts; ++i)
-        out[i] = (tri[i] >= 0 && tri[i] < m->nt) ? orc_tri_margin(m, tri[i], q[2 * i], q[2 * i + 1]) : -1e300;
+    return orc_locate_points2(m, npts, q, NULL, tri, flags, 1);
+}
+
+int orc_locate_points2(const orc_mesh *m, int64_t npts, const double *q, const double *ql, int32_t *tri,
+                       uint8_t *flags, int nthreads)
+{
+    point_job J;
+    memset(&J, 0, sizeof(J));
+    J.m = m;
+    J.q = q;
+    J.ql = ql;
+    J.tri = tri;
+    J.flags = flags;
+    return run_points(&J, npts, nthreads);
+}
+
+/* Exact signs of each point against the three edges of a given triangle
+ * (the edge opposite vertex k first, as tri_signs): the point lies in the
+ * closed triangle iff all three are >= 0.  -2 marks an index that is not a
+ * triangle of the mesh. */
+void orc_tri_signs2(const orc_mesh *m, int64_t npts, const int32_t *tri, const double *q, const double *ql,
+                    int8_t *signs, int nthreads)
+{
+    point_job J;
+    memset(&J, 0, sizeof(J));
+    J.m = m;
+    J.q = q;
+    J.ql = ql;
+    J.tri_in = tri;
+    J.signs = signs;
+    run_points(&J, npts, nthreads);
 }
 
 void orc_feet(int kind, const double *p, double dt, int64_t n, int64_t npts, const double *xy,

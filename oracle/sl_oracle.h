@@ -33,6 +33,8 @@ typedef struct orc_mesh orc_mesh;
 void orc_field(int kind, const double *p, double x, double y, double t, double *fx, double *fy);
 int orc_foot(int kind, const double *p, double dt, double t, double x, double y, double *X, double *Y);
 int orc_orient_sign(double ax, double ay, double bx, double by, double cx, double cy);
+/* orient(a, b, q) for q = (qxh + qxl, qyh + qyl), the sum taken exactly */
+int orc_orient_sign2(double ax, double ay, double bx, double by, double qxh, double qyh, double qxl, double qyl);
 void orc_set_force_exact(int on);
 long orc_exact_calls(void);
 
@@ -41,7 +43,8 @@ void orc_mesh_destroy(orc_mesh *m);
 int orc_mesh_bins(const orc_mesh *m);
 int orc_locate(const orc_mesh *m, double X, double Y, int32_t *tri, int *flags);
 double orc_interp(const orc_mesh *m, int32_t j, double X, double Y, const double *V);
-double orc_tri_margin(const orc_mesh *m, int32_t j, double X, double Y);
+/* orc_locate for the point (X + Xl, Y + Yl), taken exactly */
+int orc_locate2(const orc_mesh *m, double X, double Y, double Xl, double Yl, int32_t *tri, int *flags);
 
 int orc_step_range(const orc_mesh *m, int kind, const double *p, double dt, int64_t n,
                    const double *vin, double *vout, double *feet, int32_t *tri, uint8_t *flags,
@@ -58,11 +61,13 @@ int orc_step(const orc_mesh *m, int kind, const double *p, double dt, int64_t n,
 int orc_run(const orc_mesh *m, int kind, const double *p, double dt, int64_t n0, int nsteps,
             double *v, double *scratch, int nthreads);
 int orc_locate_points(const orc_mesh *m, int64_t npts, const double *q, int32_t *tri, uint8_t *flags);
-void orc_margins(const orc_mesh *m, int64_t npts, const int32_t *tri, const double *q, double *out);
+/* threaded; ql (the low parts of the points) may be NULL */
+int orc_locate_points2(const orc_mesh *m, int64_t npts, const double *q, const double *ql, int32_t *tri,
+                       uint8_t *flags, int nthreads);
+void orc_tri_signs2(const orc_mesh *m, int64_t npts, const int32_t *tri, const double *q, const double *ql,
+                    int8_t *signs, int nthreads);
 void orc_feet(int kind, const double *p, double dt, int64_t n, int64_t npts, const double *xy,
               double *feet, uint8_t *clipped);
-void orc_feet_f32(int kind, const double *p, double dt, int64_t n, int64_t npts, const float *xy, float *feet,
-                  uint8_t *clipped);
 
 #ifdef __cplusplus
 }

@@ -17,10 +17,10 @@ from ._build import LIB as _LIB_PATH
 __all__ = [
     "SL_OK", "SL_E_ARG", "SL_E_MESH", "SL_E_NOMEM", "SL_E_CUDA", "SL_E_WALK_LIMIT", "SL_E_STATE",
     "SL_FP64", "SL_FP32", "SL_CURVE_NONE", "SL_CURVE_HILBERT", "SL_CURVE_MORTON",
-    "SL_OPT_STATS", "SL_OPT_WALK_CAP", "SL_OPT_KERNEL", "SL_OPT_BLOCK", "SL_OPT_TILES_PER_SM", "SL_OPT_CONFIG",
-    "SL_OPT_CONFIG_FIRST", "SL_OPT_STRATEGY", "SL_OPT_OUTSIDE", "SL_OPT_SPLIT", "SL_OPT_ASYNC",
+    "SL_OPT_STATS", "SL_OPT_WALK_CAP", "SL_OPT_KERNEL", "SL_OPT_BLOCK", "SL_OPT_CONFIG",
+    "SL_OPT_CONFIG_FIRST", "SL_OPT_STRATEGY", "SL_OPT_OUTSIDE", "SL_OPT_SPLIT", "SL_OPT_ASYNC", "SL_OPT_PRECISE",
     "SL_NODE_CLIPPED", "SL_NODE_DEGENERATE", "SL_NODE_EXACT", "SL_NODE_FALLBACK", "SL_NODE_WALK_LIMIT",
-    "SL_NODE_RANGE", "SL_NODE_EXCLUDED", "SLError", "sl_problem", "problems", "pack_meshes",
+    "SL_NODE_RANGE", "SL_NODE_EXCLUDED", "SL_NODE_PRECISE", "SLError", "sl_problem", "problems", "pack_meshes",
     "sl_mesh_create", "sl_mesh_validate", "sl_mesh_reorder", "sl_step", "sl_run", "sl_run_host", "sl_mesh_get_t0",
     "sl_mesh_set_t0", "sl_mesh_reset_t0", "sl_mesh_status", "sl_mesh_stats", "sl_mesh_set_option", "sl_mesh_info",
     "sl_mesh_export", "sl_mesh_destroy", "sl_last_error", "library", "EXPORTED", "sl_step_noalloc",
@@ -30,11 +30,13 @@ __all__ = [
 SL_OK, SL_E_ARG, SL_E_MESH, SL_E_NOMEM, SL_E_CUDA, SL_E_WALK_LIMIT, SL_E_STATE = range(7)
 SL_FP64, SL_FP32 = 0, 1
 SL_CURVE_NONE, SL_CURVE_HILBERT, SL_CURVE_MORTON = 0, 1, 2
-SL_OPT_STATS, SL_OPT_WALK_CAP, SL_OPT_KERNEL, SL_OPT_BLOCK, SL_OPT_TILES_PER_SM, SL_OPT_CONFIG = range(6)
-SL_OPT_CONFIG_FIRST, SL_OPT_STRATEGY, SL_OPT_OUTSIDE, SL_OPT_SPLIT, SL_OPT_ASYNC = 7, 8, 9, 10, 11
+SL_OPT_STATS, SL_OPT_WALK_CAP, SL_OPT_KERNEL, SL_OPT_BLOCK = range(4)
+SL_OPT_CONFIG = 5
+SL_OPT_CONFIG_FIRST, SL_OPT_STRATEGY, SL_OPT_OUTSIDE, SL_OPT_SPLIT, SL_OPT_ASYNC, SL_OPT_PRECISE = 7, 8, 9, 10, 11, 12
 SL_NODE_CLIPPED, SL_NODE_DEGENERATE, SL_NODE_EXACT, SL_NODE_FALLBACK, SL_NODE_WALK_LIMIT, SL_NODE_RANGE = (
     1, 2, 4, 8, 16, 32)
 SL_NODE_EXCLUDED = 64
+SL_NODE_PRECISE = 128
 SL_NPARAMS = 48
 SL_NOALLOC_MAX_NODES = 1 << 20
 SL_NOALLOC_MAX_PROBLEMS = 256
@@ -63,7 +65,7 @@ class sl_problem(ctypes.Structure):
 
 class sl_debug(ctypes.Structure):
     _fields_ = [("feet", ctypes.c_void_p), ("tri", ctypes.c_void_p), ("moves", ctypes.c_void_p),
-                ("flags", ctypes.c_void_p)]
+                ("flags", ctypes.c_void_p), ("feet_lo", ctypes.c_void_p)]
 
 
 class sl_tune(ctypes.Structure):
@@ -243,12 +245,13 @@ def sl_mesh_export(h):
 
 
 def sl_step(h, probs, n, v_in, v_out, debug=None, stream=None):
-    """debug: None or a dict with any of 'feet', 'tri', 'moves', 'flags'
-    (device tensors of 2N float64, N int32, N int32, N uint8)."""
+    """debug: None or a dict with any of 'feet', 'tri', 'moves', 'flags',
+    'feet_lo' (device tensors of 2N float64, N int32, N int32, N uint8, 2N
+    float64); the foot the kernel located is feet + feet_lo exactly."""
     dbg = None
     if debug:
         dbg = sl_debug(_ptr(debug.get("feet")), _ptr(debug.get("tri")), _ptr(debug.get("moves")),
-                       _ptr(debug.get("flags")))
+                       _ptr(debug.get("flags")), _ptr(debug.get("feet_lo")))
     _check(library().sl_step(h, probs, int(n), _ptr(v_in), _ptr(v_out),
                              ctypes.byref(dbg) if dbg is not None else None, _stream(stream)))
 

@@ -28,6 +28,9 @@ static void split_df(double v, float2 &o)
     o.y = (float)(v - (double)h);
 }
 
+FastArgs make_fast_args(const sl_mesh *m, const FastProb *fp, const void *vin, void *vout, const sl_debug *dbg,
+                        const FastProb *fh = nullptr);
+
 // A coordinate in [0,1] as g + l: g = v rounded to the grid of 2^-24 (a float,
 // exactly), l = fl32(v - g), |l| <= 2^-25, |v - g - l| <= 2^-49.  Differences
 // of the g parts of two coordinates are exact in float (multiples of 2^-24
@@ -238,10 +241,16 @@ static StepArgs make_args(const sl_mesh *m, const ProbStep *probs_dev, const voi
     return a;
 }
 
+void fast_args_for(const sl_mesh *m, const FastProb *fp, const void *vin, void *vout, const sl_debug *dbg,
+                   const FastProb *fh, FastArgs &out)
+{
+    out = make_fast_args(m, fp, vin, vout, dbg, fh);
+}
+
 // fp: the step's constants on the device; fh: the same on the host (or
 // NULL), copied into the kernel parameters for a single problem.
-static FastArgs make_fast_args(const sl_mesh *m, const FastProb *fp, const void *vin, void *vout, const sl_debug *dbg,
-                               const FastProb *fh = nullptr)
+FastArgs make_fast_args(const sl_mesh *m, const FastProb *fp, const void *vin, void *vout, const sl_debug *dbg,
+                        const FastProb *fh)
 {
     FastArgs a;
     std::memset(&a, 0, sizeof(a));
@@ -277,6 +286,7 @@ static FastArgs make_fast_args(const sl_mesh *m, const FastProb *fp, const void 
     a.grid_M = m->opt_strategy == 2 ? m->grid_M : 0;
     a.grid_t0v = (const int4 *)m->d.grid_t0v;
     a.count = m->N;     // every node; the level launches of strategy (c) narrow it
+    a.steep_g2 = m->precision == SL_FP64 ? (float)((double)m->opt_precise * (double)m->opt_precise) : 0.0f;
     return a;
 }
 
@@ -333,18 +343,25 @@ sl_status fast_constants_one(const sl_problem &q, int64_t n, int32_t p, FastProb
     return SL_OK;
 }
 
+std::vector<double> field_table_key(int32_t n_problems, const sl_problem *probs, bool &need1, bool &need2)
+{
+    need1 = need2 = false;
+    std::vector<double> key((size_t)n_problems * kTableKeyStride);
+    for (int32_t p = 0; p < n_problems; ++p) {
+        const int kind = probs[p].kind;
+        need1 |= kind == SL_FIELD_SWIRL || kind == SL_FIELD_PAPER || kind == SL_FIELD_FOURIER8;
+        need2 |= kind == SL_FIELD_PAPER || kind == SL_FIELD_FOURIER8;
+        key[kTableKeyStride * p] = kind;
+        for (int k = 0; k < SL_NPARAMS; ++k) key[kTableKeyStride * p + 1 + k] = probs[p].p[k];
+    }
+    return key;
+}
+
 // Node tables of the trigonometric fields, rebuilt when the fields change.
 static sl_status ensure_tables(sl_mesh *m, const sl_problem *probs, cudaStream_t s)
 {
     bool need1 = false, need2 = false;
-    std::vector<double> key((size_t)m->n_problems * 49);
-    for (int32_t p = 0; p < m->n_problems; ++p) {
-        const int kind = probs[p].kind;
-        need1 |= kind == SL_FIELD_SWIRL || kind == SL_FIELD_PAPER || kind == SL_FIELD_FOURIER8;
-        need2 |= kind == SL_FIELD_PAPER || kind == SL_FIELD_FOURIER8;
-        key[49 * p] = kind;
-        for (int k = 0; k < SL_NPARAMS; ++k) key[49 * p + 1 + k] = probs[p].p[k];
-    }
+    const std::vector<double> key = field_table_key(m->n_problems, probs, need1, need2);
     if (!need1) return SL_OK;
     if (key == m->table_key && m->d.g1 && (!need2 || m->d.g2)) return SL_OK;
     if (!m->d.g1) SL_CUDA(cudaMalloc(&m->d.g1, sizeof(float4) * m->N));
@@ -606,7 +623,7 @@ extern "C" sl_status sl_step(sl_mesh *m, const sl_problem *probs, int64_t n, con
     std::vector<ProbStep> host(m->n_problems);
     st = fill_step(m, probs, n, host.data());
     if (st != SL_OK) return st;
-    const bool debug = dbg && (dbg->feet || dbg->tri || dbg->moves || dbg->flags);
+    const bool debug = dbg && (dbg->feet || dbg->tri || dbg->moves || dbg->flags || dbg->feet_lo);
     m->graph.valid = false;   // the per-step buffers are overwritten
     if (!use_fast(m)) {
         st = ensure_probs(m, sizeof(ProbStep) * m->n_problems);

@@ -444,10 +444,6 @@ extern "C" sl_status sl_mesh_set_option(sl_mesh *m, int32_t option, int64_t valu
         if (value != 0 && (value < 32 || value > 1024 || value % 32)) return sl::fail(SL_E_ARG, "block size must be 0 or a multiple of 32 in [32, 1024]");
         m->opt_block = (int32_t)value;
         break;
-    case SL_OPT_TILES_PER_SM:
-        if (value < 0 || value > 64) return sl::fail(SL_E_ARG, "tiles per SM out of range");
-        m->opt_tiles_per_sm = (int32_t)value;
-        break;
     case SL_OPT_CONFIG:
         if (value < 0 || value > 5) return sl::fail(SL_E_ARG, "launch configuration must be 0..5");
         m->opt_config = (int32_t)value;
@@ -486,6 +482,10 @@ extern "C" sl_status sl_mesh_set_option(sl_mesh *m, int32_t option, int64_t valu
     case SL_OPT_OUTSIDE:
         if (value != 0 && value != 1) return sl::fail(SL_E_ARG, "outside mode must be 0 (clip) or 1 (exclude)");
         m->opt_outside = (int32_t)value;
+        break;
+    case SL_OPT_PRECISE:
+        if (value < 0 || value > (1 << 30)) return sl::fail(SL_E_ARG, "precise gradient bound out of range");
+        m->opt_precise = (int32_t)value;
         break;
     case SL_OPT_ASYNC:
         if (value != 0 && value != 1) return sl::fail(SL_E_ARG, "async must be 0 or 1");

@@ -13,7 +13,8 @@
 // The scratch: kNoAllocMaxNodes (hi, lo) float pairs (8 MiB) for the step's
 // output values and kNoAllocMaxProblems per-problem constant records
 // (16 KiB), held by every GPU that loads this library until the process
-// exits.  All calls on a device share it and every call overwrites what it
+// exits.  The constants reach their records through kernel parameters, not
+// through a copy from host memory.  All calls on a device share it and every call overwrites what it
 // uses (nothing has to start at zero), so calls that overlap on the GPU --
 // two streams, or two meshes stepped concurrently -- race on it and must be
 // serialised by the caller.
@@ -74,20 +75,25 @@ sl_status scratch_for(int dev, DeviceScratch &out)
 bool tables_ready(const sl_mesh *m, const sl_problem *probs)
 {
     bool need1 = false, need2 = false;
-    for (int32_t p = 0; p < m->n_problems; ++p) {
-        const int kind = probs[p].kind;
-        need1 |= kind == SL_FIELD_SWIRL || kind == SL_FIELD_PAPER || kind == SL_FIELD_FOURIER8;
-        need2 |= kind == SL_FIELD_PAPER || kind == SL_FIELD_FOURIER8;
-    }
+    const std::vector<double> key = field_table_key(m->n_problems, probs, need1, need2);
     if (!need1) return true;
     if (!m->d.g1 || (need2 && !m->d.g2)) return false;
-    if (m->table_key.size() != (size_t)m->n_problems * 49) return false;
-    for (int32_t p = 0; p < m->n_problems; ++p) {
-        if (m->table_key[49 * (size_t)p] != (double)probs[p].kind) return false;
-        for (int k = 0; k < SL_NPARAMS; ++k)
-            if (m->table_key[49 * (size_t)p + 1 + k] != probs[p].p[k]) return false;
-    }
-    return true;
+    return key == m->table_key;
+}
+
+// The step's per-problem constants travel to the static array in the
+// parameters of a small kernel, kConstChunk problems per launch (4 KiB of
+// parameters), so no host buffer has to outlive the call.
+constexpr int kConstChunk = 63;
+struct ConstChunk {
+    int32_t base, count;
+    FastProb p[kConstChunk];
+};
+
+__global__ void k_noalloc_constants(const ConstChunk c)
+{
+    const int t = threadIdx.x;
+    if (t < c.count) g_noalloc_probs[c.base + t] = c.p[t];
 }
 
 }  // namespace
@@ -126,42 +132,22 @@ extern "C" sl_status sl_step_noalloc(sl_mesh *m, const sl_problem *probs, int64_
         if (st != SL_OK) return st;
     }
     cudaStream_t s = (cudaStream_t)stream;
-    // pageable source: the copy is staged before the call returns
-    e = cudaMemcpyAsync(sc.probs, host, sizeof(FastProb) * m->n_problems, cudaMemcpyHostToDevice, s);
-    if (e != cudaSuccess) return fail(SL_E_CUDA, std::string("sl_step_noalloc: constants copy: ") + cudaGetErrorString(e));
+    for (int32_t b = 0; b < m->n_problems; b += kConstChunk) {
+        ConstChunk c;
+        c.base = b;
+        c.count = m->n_problems - b < kConstChunk ? m->n_problems - b : kConstChunk;
+        std::memcpy(c.p, host + b, sizeof(FastProb) * (size_t)c.count);
+        k_noalloc_constants<<<1, kConstChunk, 0, s>>>(c);
+    }
 
     // V^n (double) -> (hi, lo) pairs in the caller's output buffer; the step
-    // writes V^{n+1} pairs to the static scratch; then back to double.
+    // writes V^{n+1} pairs to the static scratch; then back to double.  The
+    // fused kernel in the launch configuration sl_step would take for this
+    // step (SL_OPT_KERNEL = 1 and SL_OPT_SPLIT do not apply here).
     launch_to_df(v_in, (float2 *)v_out, m->N, s);
     FastArgs a;
-    std::memset(&a, 0, sizeof(a));
-    a.xyq = (const float4 *)m->d.xyq;
-    a.xyh = (const float2 *)m->d.xyh;
-    a.xyd = (const double2 *)m->d.xy;
-    for (int k = 0; k < 3; ++k) {
-        a.tv[k] = m->d.tv[k];
-        a.tn[k] = m->d.tn[k];
-    }
-    a.he = (const float4 *)m->d.he;
-    a.t0 = m->d.t0;
-    a.t0v = (int4 *)m->d.t0v;
-    a.vin = v_out;
-    a.vout = sc.values;
-    a.g1 = (const float4 *)m->d.g1;
-    a.g2 = (const float4 *)m->d.g2;
-    a.probs = sc.probs;
-    a.node_off = m->d.node_off;
-    a.nprob = m->n_problems;
-    a.walk_cap = m->opt_walk_cap > 0 ? m->opt_walk_cap : default_walk_cap(m);
-    a.N = m->N;
-    a.status = m->d.status;
-    a.stats = m->d.stats;
-    a.keep_t0 = m->opt_strategy == 1 || m->opt_strategy == 2;   // (a), direct: T^0 kept
-    a.exclude = m->opt_outside == 1;
-    a.grid_M = m->opt_strategy == 2 ? m->grid_M : 0;
-    a.grid_t0v = (const int4 *)m->d.grid_t0v;
-    a.count = m->N;
-    launch_fast_df(a, m->opt_stats != 0, false, m->opt_config, s);
+    fast_args_for(m, sc.probs, v_out, sc.values, nullptr, host, a);
+    launch_fast_df(a, m->opt_stats != 0, false, m->t0_initial ? m->opt_config_first : m->opt_config, s);
     launch_from_df(sc.values, v_out, m->N, s);
     e = cudaGetLastError();
     if (e != cudaSuccess) return fail(SL_E_CUDA, std::string("sl_step_noalloc: launch: ") + cudaGetErrorString(e));

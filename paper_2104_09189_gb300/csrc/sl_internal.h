@@ -87,7 +87,6 @@ struct sl_mesh {
     int32_t opt_walk_cap = 0;         // 0 = default
     int32_t opt_kernel = 0;
     int32_t opt_block = 0;
-    int32_t opt_tiles_per_sm = 0;
     int32_t opt_config = 5;           // launch configuration of the fast kernels (later steps)
     int32_t opt_config_first = 0;     // ... for a step whose walks start at the initial triangles
     int32_t opt_strategy = 0;         // 0 = strategy (b), 1 = strategy (a) (T^0 never overwritten),
@@ -98,6 +97,7 @@ struct sl_mesh {
     int32_t opt_outside = 0;          // 0 = clip feet that leave the square, 1 = exclude the node
     int32_t opt_split = 0;            // 1 = split steps (settle pass + finish pass), FP64 meshes
     int32_t opt_async = 0;            // 1 = sl_run without stats returns unsynchronised
+    int32_t opt_precise = 32;         // gradient bound of the FP64 value path (0 = off)
     bool t0_initial = true;           // T^0 holds the initial start triangles
     int32_t sms = 0;                  // multiprocessors of the device
     bool stepped = false;
@@ -111,6 +111,14 @@ struct sl_mesh {
 
 namespace sl {
 struct FastProb;
+struct FastArgs;
+
+// Node tables of the trigonometric fields: which tables the problems need
+// (need1: g1 for SWIRL, PAPER, FOURIER8; need2: g2 for PAPER, FOURIER8) and
+// the key the tables are built for, kTableKeyStride doubles per problem
+// (kind, p[0..SL_NPARAMS-1]).
+constexpr size_t kTableKeyStride = 1 + SL_NPARAMS;
+std::vector<double> field_table_key(int32_t n_problems, const sl_problem *probs, bool &need1, bool &need2);
 // host side (mesh_host.cpp)
 sl_status build_and_validate(sl_mesh *m, const int32_t *nbr_in);
 sl_status reorder_host(sl_mesh *m, int32_t curve, int32_t *node_perm, int32_t *tri_perm);
@@ -118,6 +126,12 @@ sl_status reorder_host(sl_mesh *m, int32_t curve, int32_t *node_perm, int32_t *t
 sl_status upload(sl_mesh *m);
 // the fast kernels' constants of step n of one problem, validated as sl_step validates them
 sl_status fast_constants_one(const sl_problem &q, int64_t n, int32_t p, FastProb &f);
+// the arguments of a fast-kernel step of the whole mesh: the step's constants
+// on the device (fp) and on the host (fh, or NULL; a single problem's are
+// also passed in the kernel parameters), values vin -> vout, debug outputs
+// or NULL
+void fast_args_for(const sl_mesh *m, const FastProb *fp, const void *vin, void *vout, const sl_debug *dbg,
+                   const FastProb *fh, FastArgs &out);
 void free_device(sl_mesh *m);
 sl_status reset_t0_sync(sl_mesh *m);
 sl_status upload_grid_table(sl_mesh *m, const std::vector<int32_t> &slot_tri);

@@ -361,11 +361,70 @@ __device__ __forceinline__ float2 p1_value_of(float2 V1, float2 V2, float2 V3, d
     return make_float2(v.h, v.l);
 }
 
-__device__ __forceinline__ float2 p1_value(const FastArgs &a, int w0, int w1, int w2, df n1, df n2, df den)
+// V^n is steep in the triangle (SL_OPT_PRECISE): max_k (v_k - v_3)^2 >
+// G^2 den on the high parts, den twice the area, so that max |v_k - v_3| / sqrt(den)
+// -- about the P1 gradient -- exceeds G.  The double-float value is then off
+// by more than about 2^-46 G, and precise_value takes over.
+__device__ __forceinline__ bool steep(float2 V1, float2 V2, float2 V3, float den_h, float g2)
 {
-    const float2 *vin = (const float2 *)a.vin;
-    return p1_value_of(vin[w0], vin[w1], vin[w2], n1, n2, den);
+    const float d1 = __fsub_rn(V1.x, V3.x), d2 = __fsub_rn(V2.x, V3.x);
+    return fmaxf(__fmul_rn(d1, d1), __fmul_rn(d2, d2)) > __fmul_rn(g2, den_h);
 }
+
+__device__ __forceinline__ double wide(float2 p) { return __dadd_rn((double)p.x, (double)p.y); }
+
+// The P1 value of an unclipped node in FP64, on its located triangle (w0,
+// w1, w2): the Euler foot X = x_i - dt f(x_i, t_{n+1}) (Eq. 4) from the
+// node's double coordinates, with the step's constants and the node tables
+// widened from their float pairs (48 bits of constants whose product with
+// the node's velocity, the displacement, is far below 1: within about 2^-52
+// of the double foot); then the barycentric coordinates of Eq. 6 on the
+// triangle's double vertices and the interpolation of Remark 1, all in
+// double.  Returns the value as a (hi, lo) pair.  Rare (steep data only), so
+// kept out of line: its double registers do not weigh on the walk.
+__device__ __noinline__ float2 precise_value(const double2 *__restrict__ xyd, const float4 *__restrict__ g1,
+                                             const float4 *__restrict__ g2, const FastProb &P, int64_t i, int w0,
+                                             int w1, int w2, float2 V1, float2 V2, float2 V3)
+{
+    const double2 x = xyd[i];
+    double X = x.x, Y = x.y;
+    const double c0 = wide(P.c[0]), c1 = wide(P.c[1]), c2 = wide(P.c[2]);
+    switch (P.kind) {
+    case SL_FIELD_AFFINE: {
+        const double c3 = wide(P.c[3]), c4 = wide(P.c[4]), c5 = wide(P.c[5]);
+        X = x.x - ((c0 + c1 * x.x) + c2 * x.y);
+        Y = x.y - ((c3 + c4 * x.x) + c5 * x.y);
+        break;
+    }
+    case SL_FIELD_ROTATION:     // c0 = dt p0, (c1, c2) = centre (either split sums to it)
+        X = x.x + c0 * (x.y - c2);
+        Y = x.y - c0 * (x.x - c1);
+        break;
+    case SL_FIELD_SWIRL: {
+        const float4 g = g1[i];
+        X = x.x - c0 * wide(make_float2(g.x, g.z));
+        Y = x.y - c0 * wide(make_float2(g.y, g.w));
+        break;
+    }
+    case SL_FIELD_PAPER:
+    case SL_FIELD_FOURIER8: {
+        const float4 g = g1[i], q = g2[i];
+        X = x.x - (c0 * wide(make_float2(g.x, g.z)) + c1 * wide(make_float2(q.x, q.z)));
+        Y = x.y - (c0 * wide(make_float2(g.y, g.w)) + c1 * wide(make_float2(q.y, q.w)));
+        break;
+    }
+    default: break;
+    }
+    const double2 A = xyd[w0], B = xyd[w1], C = xyd[w2];
+    const double den = (B.y - C.y) * (A.x - C.x) + (C.x - B.x) * (A.y - C.y);
+    const double t1 = ((B.y - C.y) * (X - C.x) + (C.x - B.x) * (Y - C.y)) / den;
+    const double t2 = ((C.y - A.y) * (X - C.x) + (A.x - C.x) * (Y - C.y)) / den;
+    const double v3 = wide(V3);
+    const double v = v3 + t1 * (wide(V1) - v3) + t2 * (wide(V2) - v3);
+    const float h = __double2float_rn(v);
+    return make_float2(h, __double2float_rn(v - (double)h));
+}
+
 
 // A foot that comes out of the foot arithmetic as its own node's stored
 // coordinate pair, bit for bit, is that node (see step_node): a boundary
@@ -454,6 +513,42 @@ __device__ __forceinline__ void lean_hops(const FastArgs &a, float fx, float fy,
     }
 }
 
+// Debug output of a foot held as a float pair (h, l): feet receives the sum
+// rounded to double and feet_lo the exact rest (Knuth's TwoSum in double), so
+// that feet + feet_lo is, exactly, the point the kernel located.  One double
+// cannot always hold the pair: a remainder far below the grid part's last bit
+// puts more than 53 bits between them.
+__device__ __forceinline__ void write_foot(const FastArgs &a, int64_t i, df X, df Y)
+{
+    const double xh = X.h, xl = X.l, yh = Y.h, yl = Y.l;
+    const double sx = __dadd_rn(xh, xl), sy = __dadd_rn(yh, yl);
+    if (a.dbg.feet) {
+        a.dbg.feet[2 * i] = sx;
+        a.dbg.feet[2 * i + 1] = sy;
+    }
+    if (a.dbg.feet_lo) {
+        const double bx = __dsub_rn(sx, xh), by = __dsub_rn(sy, yh);
+        a.dbg.feet_lo[2 * i] = __dadd_rn(__dsub_rn(xh, __dsub_rn(sx, bx)), __dsub_rn(xl, bx));
+        a.dbg.feet_lo[2 * i + 1] = __dadd_rn(__dsub_rn(yh, __dsub_rn(sy, by)), __dsub_rn(yl, by));
+    }
+}
+
+// Debug output of a foot that is its own node (see step_node): the point
+// located is the node's double coordinate, not the float pair it was found
+// equal to.
+__device__ __forceinline__ void write_node_foot(const FastArgs &a, int64_t i)
+{
+    const double2 p = a.xyd[i];
+    if (a.dbg.feet) {
+        a.dbg.feet[2 * i] = p.x;
+        a.dbg.feet[2 * i + 1] = p.y;
+    }
+    if (a.dbg.feet_lo) {
+        a.dbg.feet_lo[2 * i] = 0.0;
+        a.dbg.feet_lo[2 * i + 1] = 0.0;
+    }
+}
+
 struct NodeCounters {
     uint32_t hops = 0, exact = 0, clipped = 0, fallback = 0, limit = 0, filter2 = 0, excluded = 0;
 };
@@ -496,10 +591,7 @@ __device__ __forceinline__ void step_node(const FastArgs &a, int64_t i, int pi, 
             a.t0v[i] = a.t0v[a.parent[i]];
         }
         if (kDebug) {
-            if (a.dbg.feet) {
-                a.dbg.feet[2 * i] = (double)X.h + (double)X.l;
-                a.dbg.feet[2 * i + 1] = (double)Y.h + (double)Y.l;
-            }
+            write_foot(a, i, X, Y);
             if (a.dbg.tri) a.dbg.tri[i] = -1;
             if (a.dbg.moves) a.dbg.moves[i] = 0;
             if (a.dbg.flags) a.dbg.flags[i] = (uint8_t)SL_NODE_EXCLUDED;
@@ -543,10 +635,7 @@ __device__ __forceinline__ void step_node(const FastArgs &a, int64_t i, int pi, 
             a.t0v[i] = tq;
         }
         if (kDebug) {
-            if (a.dbg.feet) {
-                a.dbg.feet[2 * i] = (double)X.h + (double)X.l;
-                a.dbg.feet[2 * i + 1] = (double)Y.h + (double)Y.l;
-            }
+            write_node_foot(a, i);
             if (a.dbg.tri) a.dbg.tri[i] = j0;
             if (a.dbg.moves) a.dbg.moves[i] = 0;
             if (a.dbg.flags) a.dbg.flags[i] = (uint8_t)(flags | SL_NODE_DEGENERATE);
@@ -688,8 +777,18 @@ __device__ __forceinline__ void step_node(const FastArgs &a, int64_t i, int pi, 
     }
     if (s1 == 0 || s2 == 0 || s3 == 0) flags |= SL_NODE_DEGENERATE;
 
-    // the P1 value (Remark 1) with the barycentric coordinates of Eq. 6
-    ((float2 *)a.vout)[i] = p1_value(a, w0, w1, w2, n1, n2, den);
+    // the P1 value (Remark 1) with the barycentric coordinates of Eq. 6, in
+    // FP64 where V^n is steep (SL_OPT_PRECISE)
+    {
+        const float2 *vin = (const float2 *)a.vin;
+        const float2 V1 = vin[w0], V2 = vin[w1], V3 = vin[w2];
+        if (a.steep_g2 > 0.0f && !(flags & SL_NODE_CLIPPED) && steep(V1, V2, V3, den.h, a.steep_g2)) {
+            ((float2 *)a.vout)[i] = precise_value(a.xyd, a.g1, a.g2, P, i, w0, w1, w2, V1, V2, V3);
+            flags |= SL_NODE_PRECISE;
+        } else {
+            ((float2 *)a.vout)[i] = p1_value_of(V1, V2, V3, n1, n2, den);
+        }
+    }
     if ((hops > 0 || (kExt && a.parent)) && !(kExt && a.keep_t0)) {
         a.t0[i] = j;
         a.t0v[i] = make_int4(3 * j, w0, w1, w2);
@@ -697,10 +796,7 @@ __device__ __forceinline__ void step_node(const FastArgs &a, int64_t i, int pi, 
     if (c.limit) atomicOr(a.status, 1u << SL_E_WALK_LIMIT);
     if (flags & SL_NODE_RANGE) atomicOr(a.status, 1u << SL_E_ARG);
     if (kDebug) {
-        if (a.dbg.feet) {
-            a.dbg.feet[2 * i] = (double)X.h + (double)X.l;
-            a.dbg.feet[2 * i + 1] = (double)Y.h + (double)Y.l;
-        }
+        write_foot(a, i, X, Y);
         if (a.dbg.tri) a.dbg.tri[i] = j;
         if (a.dbg.moves) a.dbg.moves[i] = (int32_t)hops;
         if (a.dbg.flags) a.dbg.flags[i] = (uint8_t)flags;
@@ -734,7 +830,9 @@ __device__ __forceinline__ bool settle_test(const Numerators &t)
 }
 
 // A node the settle test left undecided: 0 = to the finish pass, 1 = settled
-// in T^0 with the barycentric value, 2 = settled with the node's own value.
+// in T^0 with the barycentric value and a sign exactly zero (the foot on a
+// boundary edge), 2 = settled with the node's own value, 3 = settled in T^0,
+// every sign certified positive.
 //  * The foot is node i (as in step_node).  When T^0 has node i as a vertex,
 //    two of its signs are zero, so the test cannot have passed: settled with
 //    the node's value.  (A foot inside the square at its node, f = 0 there,
@@ -766,7 +864,7 @@ __device__ __forceinline__ int settle_decide(const FastArgs &a, int64_t i, int4 
     if (s1 == 2 && !(nb1 < 0 && (fside >> (-1 - nb1) & 1u))) return 0;
     if (s2 == 2 && !(nb2 < 0 && (fside >> (-1 - nb2) & 1u))) return 0;
     if (s3 == 2 && !(nb3 < 0 && (fside >> (-1 - nb3) & 1u))) return 0;
-    return 1;
+    return (s1 == 2 || s2 == 2 || s3 == 2) ? 1 : 3;
 }
 
 // Settle pass of a split step: the nodes whose foot is certainly in the
@@ -799,25 +897,21 @@ __device__ __forceinline__ bool settle_node(const FastArgs &a, int64_t i, int pi
             ((float2 *)a.vout)[i] = vin[i];
             c.clipped = clipped;
             if (kDebug) {
-                if (a.dbg.feet) {
-                    a.dbg.feet[2 * i] = (double)X.h + (double)X.l;
-                    a.dbg.feet[2 * i + 1] = (double)Y.h + (double)Y.l;
-                }
+                write_node_foot(a, i);
                 if (a.dbg.tri) a.dbg.tri[i] = tri_of(tq.x);
                 if (a.dbg.moves) a.dbg.moves[i] = 0;
                 if (a.dbg.flags) a.dbg.flags[i] = (uint8_t)((clipped ? SL_NODE_CLIPPED : 0u) | SL_NODE_DEGENERATE);
             }
             return true;
         }
-        degenerate = true;
+        degenerate = d == 1;
     }
+    // steep V^n: the finish pass evaluates the value in FP64 (step_node)
+    if (!clipped && a.steep_g2 > 0.0f && steep(V1, V2, V3, t.den.h, a.steep_g2)) return false;
     ((float2 *)a.vout)[i] = p1_value_of(V1, V2, V3, t.n1, t.n2, t.den);
     c.clipped = clipped;
     if (kDebug) {
-        if (a.dbg.feet) {
-            a.dbg.feet[2 * i] = (double)X.h + (double)X.l;
-            a.dbg.feet[2 * i + 1] = (double)Y.h + (double)Y.l;
-        }
+        write_foot(a, i, X, Y);
         if (a.dbg.tri) a.dbg.tri[i] = tri_of(tq.x);
         if (a.dbg.moves) a.dbg.moves[i] = 0;
         if (a.dbg.flags)
@@ -1113,7 +1207,7 @@ __global__ void k_field_tables(FieldTableArgs a)
     const double pi = 3.14159265358979323846;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < a.N; i += (int64_t)gridDim.x * blockDim.x) {
         const int pidx = a.nprob == 1 ? 0 : problem_of(a.node_off, a.nprob, i);
-        const double *q = a.params + 49 * (int64_t)pidx;
+        const double *q = a.params + (1 + SL_NPARAMS) * (int64_t)pidx;
         const int kind = (int)q[0];
         const double *p = q + 1;
         const double2 xy = a.xyd ? a.xyd[i] : make_double2((double)a.xyf[i].x, (double)a.xyf[i].y);

@@ -60,6 +60,8 @@ struct FastArgs {
     uint32_t *status;
     unsigned long long *stats;
     sl_debug dbg;
+    float steep_g2;               // G^2 of SL_OPT_PRECISE (double-float kernel; 0 = off): a value
+                                  // with (v_k - v_3)^2 > G^2 den is evaluated in FP64
     int32_t keep_t0;              // strategy (a) or direct location: T^0 is never overwritten
     int32_t exclude;              // nodes whose foot leaves the square are excluded (Sec. 4)
     int32_t grid_M;               // > 0: start at the direct location on the structured grid (Sec. 4)
@@ -98,7 +100,7 @@ struct FieldTableArgs {
     const int64_t *node_off;
     int32_t nprob;
     int64_t N;
-    const double *params;         // nprob x (kind, p[48]) as 49 doubles
+    const double *params;         // nprob x (kind, p[SL_NPARAMS]) as 1 + SL_NPARAMS doubles
     float4 *g1, *g2;
 };
 void launch_field_tables(const FieldTableArgs &a, cudaStream_t s);

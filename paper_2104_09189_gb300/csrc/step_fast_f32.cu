@@ -127,6 +127,10 @@ __global__ void __launch_bounds__(kBlock, kMinBlocks) k_step_fast_f32(FastArgs a
                     a.dbg.feet[2 * i] = (double)X;
                     a.dbg.feet[2 * i + 1] = (double)Y;
                 }
+                if (a.dbg.feet_lo) {
+                    a.dbg.feet_lo[2 * i] = 0.0;
+                    a.dbg.feet_lo[2 * i + 1] = 0.0;
+                }
                 if (a.dbg.tri) a.dbg.tri[i] = -1;
                 if (a.dbg.moves) a.dbg.moves[i] = 0;
                 if (a.dbg.flags) a.dbg.flags[i] = (uint8_t)SL_NODE_EXCLUDED;
@@ -331,6 +335,10 @@ __global__ void __launch_bounds__(kBlock, kMinBlocks) k_step_fast_f32(FastArgs a
                 if (a.dbg.feet) {
                     a.dbg.feet[2 * i] = (double)X;
                     a.dbg.feet[2 * i + 1] = (double)Y;
+                }
+                if (a.dbg.feet_lo) {
+                    a.dbg.feet_lo[2 * i] = 0.0;
+                    a.dbg.feet_lo[2 * i + 1] = 0.0;
                 }
                 if (a.dbg.tri) a.dbg.tri[i] = j;
                 if (a.dbg.moves) a.dbg.moves[i] = (int32_t)hops;

@@ -109,6 +109,10 @@ __device__ __forceinline__ void plain_walk_value(const StepArgs &a, int64_t i, i
             a.dbg.feet[2 * i] = X;
             a.dbg.feet[2 * i + 1] = Y;
         }
+        if (a.dbg.feet_lo) {
+            a.dbg.feet_lo[2 * i] = 0.0;
+            a.dbg.feet_lo[2 * i + 1] = 0.0;
+        }
         if (a.dbg.tri) a.dbg.tri[i] = j;
         if (a.dbg.moves) a.dbg.moves[i] = (int32_t)hops;
         if (a.dbg.flags) a.dbg.flags[i] = (uint8_t)flags;
@@ -151,6 +155,10 @@ __global__ void __launch_bounds__(256) k_step_plain_f64(StepArgs a)
                     if (a.dbg.feet) {
                         a.dbg.feet[2 * i] = qx;
                         a.dbg.feet[2 * i + 1] = qy;
+                    }
+                    if (a.dbg.feet_lo) {
+                        a.dbg.feet_lo[2 * i] = 0.0;
+                        a.dbg.feet_lo[2 * i + 1] = 0.0;
                     }
                     if (a.dbg.tri) a.dbg.tri[i] = -1;
                     if (a.dbg.moves) a.dbg.moves[i] = 0;

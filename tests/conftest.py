@@ -25,3 +25,15 @@ def pytest_collection_modifyitems(config, items):
     for item in items:
         if "gpu" in item.keywords:
             item.add_marker(skip)
+
+
+def pytest_terminal_summary(terminalreporter):
+    """Figures the full-size parity tests recorded (errors against the
+    oracle, feet on an edge or a vertex), one line per test."""
+    mod = sys.modules.get("gpu_helpers")
+    rows = getattr(mod, "REPORT", None) if mod else None
+    if not rows:
+        return
+    terminalreporter.section("parity figures")
+    for name, fig in rows:
+        terminalreporter.write_line(f"{name}: " + ", ".join(f"{k}={v}" for k, v in fig.items()))

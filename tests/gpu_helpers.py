@@ -6,9 +6,20 @@ import oracle
 import paper_2104_09189_gb300 as sl
 
 REL_TOL_FP64 = 1e-12          # normwise relative, at every step
-FOOT_DELTA = 1e-12            # feet may differ by rounding of the field's
-                              # trig functions (CUDA vs libm): triangles of
-                              # feet closer than this to an edge line may differ
+FOOT_TOL_FP64 = 1e-12         # the GPU's foot against the oracle's: both are
+                              # Eq. 4 in (about) double precision; they differ
+                              # by rounding and by the trig functions of CUDA
+                              # and libm, never by more than this
+ON_EDGE = oracle.FLAG_DEGENERATE | oracle.FLAG_MULTI
+NODE_DEGENERATE = 2           # SL_NODE_DEGENERATE
+
+REPORT = []                   # (test, figures) lines printed at the end of the run
+
+
+def report(name, **figures):
+    """Record figures of a parity test (error, feet on an edge or vertex) for
+    the summary printed at the end of the pytest run."""
+    REPORT.append((name, figures))
 
 
 class DeviceRun:
@@ -57,6 +68,7 @@ class DeviceRun:
         N = self.mesh.n_nodes
         vout = t.empty_like(v_dev)
         dbg = {"feet": t.zeros(2 * N, dtype=t.float64, device=self.dev),
+               "feet_lo": t.full((2 * N,), 7.0, dtype=t.float64, device=self.dev),
                "tri": t.full((N,), -7, dtype=t.int32, device=self.dev),
                "moves": t.zeros(N, dtype=t.int32, device=self.dev),
                "flags": t.zeros(N, dtype=t.uint8, device=self.dev)}
@@ -65,6 +77,8 @@ class DeviceRun:
         res = {}
         feet = np.empty((N, 2))
         feet[self.node_perm] = dbg["feet"].cpu().numpy().reshape(N, 2)
+        feet_lo = np.empty((N, 2))
+        feet_lo[self.node_perm] = dbg["feet_lo"].cpu().numpy().reshape(N, 2)
         tri = np.empty(N, dtype=np.int64)
         d = dbg["tri"].cpu().numpy()
         tri[self.node_perm] = np.where(d < 0, -1, self.tri_perm[np.maximum(d, 0)])   # -1: excluded
@@ -72,25 +86,53 @@ class DeviceRun:
         moves[self.node_perm] = dbg["moves"].cpu().numpy()
         flags = np.empty(N, dtype=np.uint8)
         flags[self.node_perm] = dbg["flags"].cpu().numpy()
-        res.update(feet=feet, tri=tri, moves=moves, flags=flags, v=self.from_dev(vout))
+        res.update(feet=feet, feet_lo=feet_lo, tri=tri, moves=moves, flags=flags, v=self.from_dev(vout))
         return vout, res
 
 
-def compare_step(om, gpu, orc_v, orc_tri, orc_feet, rel_tol=REL_TOL_FP64, delta=FOOT_DELTA):
-    """Value parity (normwise relative) and triangle parity: exact for feet
-    farther than `delta` from every edge line of the oracle's triangle;
-    closer feet (on or next to an edge or a vertex) are counted and the GPU's
-    triangle must contain the oracle's foot up to `delta`.
-    Returns (max relative error, number of near-degenerate feet)."""
+def exact_triangle_parity(om, tri, feet, feet_lo=None, gpu_flags=None, keep=None):
+    """Triangle parity on the GPU's own feet, with no tolerance.
+
+    The oracle locates exactly the point each GPU thread located (feet +
+    feet_lo, summed exactly).  A foot strictly inside one triangle (neither
+    DEGENERATE nor MULTI) must be in the GPU's triangle: the same index.  A
+    foot on an edge or a vertex, where several triangles are correct
+    (reading c4), must be contained in the GPU's triangle: its three exact
+    orientation signs >= 0.  With gpu_flags, the GPU's SL_NODE_DEGENERATE bit
+    must be set exactly where a sign of its triangle is zero.  keep selects
+    the nodes to check (excluded nodes have no triangle).
+    Returns the number of feet on an edge or a vertex."""
+    idx = np.arange(len(tri)) if keep is None else np.nonzero(keep)[0]
+    q = feet[idx]
+    ql = None if feet_lo is None else feet_lo[idx]
+    otri, oflags = om.locate(q, ql)
+    on_edge = (oflags & ON_EDGE) != 0
+    gt = np.asarray(tri)[idx]
+    bad = np.nonzero(~on_edge & (gt != otri))[0]
+    assert bad.size == 0, (f"{bad.size} feet strictly inside a triangle located elsewhere, e.g. nodes "
+                           f"{idx[bad[:5]]}: GPU {gt[bad[:5]]} oracle {otri[bad[:5]]}")
+    sg = om.signs(gt.astype(np.int32), q, ql)
+    outside = np.nonzero((sg < 0).any(axis=1))[0]
+    assert outside.size == 0, f"GPU triangle does not contain the foot of nodes {idx[outside[:5]]}"
+    if gpu_flags is not None:
+        zero = (sg == 0).any(axis=1)
+        gdeg = (np.asarray(gpu_flags)[idx] & NODE_DEGENERATE) != 0
+        wrong = np.nonzero(zero != gdeg)[0]
+        assert wrong.size == 0, f"SL_NODE_DEGENERATE differs from the exact signs at nodes {idx[wrong[:5]]}"
+    return int(on_edge.sum())
+
+
+def compare_step(om, gpu, orc_v, orc_feet=None, rel_tol=REL_TOL_FP64, foot_tol=FOOT_TOL_FP64, keep=None):
+    """One step of the GPU against the oracle: the values normwise (relative
+    to max |V|), the feet to rounding, and the located triangles exactly
+    (exact_triangle_parity on the GPU's feet).
+    Returns (max relative value error, number of feet on an edge or vertex)."""
     scale = max(np.abs(orc_v).max(), 1e-300)
     err = np.abs(gpu["v"] - orc_v).max() / scale
     assert err <= rel_tol, f"value error {err:.3e} > {rel_tol:.1e}"
-    margin = om.margins(orc_tri.astype(np.int32), orc_feet)
-    safe = margin > delta
-    bad = np.nonzero(safe & (gpu["tri"] != orc_tri))[0]
-    assert bad.size == 0, f"{bad.size} non-degenerate feet located in a different triangle, e.g. node {bad[:5]}"
-    near = np.nonzero(~safe)[0]
-    if near.size:
-        m2 = om.margins(gpu["tri"][near].astype(np.int32), orc_feet[near])
-        assert np.all(m2 >= -delta), f"GPU triangle does not contain the foot for nodes {near[m2 < -delta][:5]}"
-    return err, int(near.size)
+    sel = slice(None) if keep is None else keep
+    if orc_feet is not None:
+        d = np.abs(gpu["feet"][sel] - orc_feet[sel]).max()
+        assert d <= foot_tol, f"foot differs from the oracle's by {d:.3e}"
+    on_edge = exact_triangle_parity(om, gpu["tri"], gpu["feet"], gpu.get("feet_lo"), gpu.get("flags"), keep)
+    return err, on_edge

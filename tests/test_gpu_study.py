@@ -8,7 +8,7 @@ import pytest
 import oracle
 import paper_2104_09189_gb300 as sl
 import sl_inputs as si
-from gpu_helpers import FOOT_DELTA, REL_TOL_FP64, DeviceRun
+from gpu_helpers import REL_TOL_FP64, DeviceRun, exact_triangle_parity
 
 pytestmark = pytest.mark.gpu
 
@@ -53,8 +53,7 @@ def test_exclusion_matches_the_oracle(kernel):
         keep = ~out
         err = np.abs(res["v"][keep] - ov[keep]).max() / np.abs(ov).max()
         assert err <= REL_TOL_FP64
-        safe = keep & (om.margins(np.where(keep, otri, 0).astype(np.int32), oft) > FOOT_DELTA)
-        assert np.array_equal(res["tri"][safe], otri[safe])
+        exact_triangle_parity(om, res["tri"], res["feet"], res["feet_lo"], res["flags"], keep=keep)
         vo = ov
     st = sl.sl_mesh_stats(g.h)
     assert st["excluded"] == n_out
@@ -190,23 +189,24 @@ def test_direct_location_on_the_courant_grid(kernel, prec, curve, shuffle):
             assert np.array_equal(out, (res["flags"] & sl.SL_NODE_EXCLUDED) != 0)
             keep = ~out
             assert np.abs(res["v"][keep] - ov[keep]).max() <= REL_TOL_FP64 * np.abs(ov).max()
-            safe = keep & (om.margins(np.where(keep, otri, 0).astype(np.int32), oft) > FOOT_DELTA)
-            assert np.array_equal(res["tri"][safe], otri[safe])
+            exact_triangle_parity(om, res["tri"], res["feet"], res["feet_lo"], res["flags"], keep=keep)
             vo = ov
         else:
-            # FP32: the oracle's own float feet (the FP32 path's operation
-            # order), located exactly on the float-rounded mesh; a node is
-            # excluded when its float foot leaves the square
+            # FP32: a node is excluded when its own float foot (reported
+            # unclipped) leaves the square, which agrees with the double
+            # Euler foot wherever that is farther than float rounding from
+            # the boundary; the kept feet are located exactly on the
+            # float-rounded mesh
             xy32 = m.xy.astype(np.float32)
             om32 = oracle.OracleMesh(xy32.astype(np.float64), m.tri)
-            f32, outside = oracle.feet_f32(f.kind, f.packed(), dt, n, xy32)
-            out = outside != 0
-            assert np.array_equal(out, (res["flags"] & sl.SL_NODE_EXCLUDED) != 0)
-            keep = ~out
-            ft = f32.astype(np.float64)[keep]
-            tri_o, _ = om32.locate(ft)
-            safe = om32.margins(tri_o.astype(np.int32), ft) > FOOT_DELTA
-            assert np.array_equal(res["tri"][keep][safe], tri_o[safe])
+            out = (res["flags"] & sl.SL_NODE_EXCLUDED) != 0
+            ft = res["feet"]
+            assert np.array_equal(out, ~((ft >= 0.0) & (ft <= 1.0)).all(axis=1))
+            _, _, ofl, oft = om32.step(f.kind, f.packed(), dt, n, vo, exclude=True)
+            margin = np.minimum(np.abs(oft), np.abs(oft - 1.0)).min(axis=1)
+            sure = margin > 8 * 2.0 ** -24
+            assert np.array_equal(out[sure], ((ofl & oracle.FLAG_EXCLUDED) != 0)[sure])
+            exact_triangle_parity(om32, res["tri"], ft, None, res["flags"], keep=~out)
             om32.close()
         hops.append(res["moves"][(res["flags"] & sl.SL_NODE_EXCLUDED) == 0].mean())
     assert max(hops) < 0.01
@@ -248,8 +248,7 @@ def test_strategy_c_matches_the_oracle_and_walks_little(kernel, prec):
         if prec == sl.SL_FP64:
             ov, otri, ofl, oft = om.step(f.kind, f.packed(), dt, n, vo)
             assert np.abs(res["v"] - ov).max() <= REL_TOL_FP64 * np.abs(ov).max()
-            safe = om.margins(otri.astype(np.int32), oft) > FOOT_DELTA
-            assert np.array_equal(res["tri"][safe], otri[safe])
+            exact_triangle_parity(om, res["tri"], res["feet"], res["feet_lo"], res["flags"])
             vo = ov
         # T^0_i is the triangle located for node i (Algorithm 1, strategy (c))
         sl.sl_mesh_get_t0(g.h, t0)

@@ -111,3 +111,83 @@ def test_bin_count_rule():
     mesh = si.grid_mesh(10, 0.25, 3)
     om = oracle.OracleMesh(mesh.xy, mesh.tri)
     assert om.bins == math.ceil(math.sqrt(mesh.n_tri / 2))
+
+
+def _brute_pair(mesh, qh, ql):
+    """Lowest containing triangle of qh + ql, its degeneracy and the number of
+    containers, in rationals."""
+    from exact import orient_pair
+    best, count, degen = -1, 0, False
+    for j in range(mesh.n_tri):
+        p1, p2, p3 = (mesh.xy[v] for v in mesh.tri[j])
+        s = (orient_pair(p2, p3, qh, ql), orient_pair(p3, p1, qh, ql), orient_pair(p1, p2, qh, ql))
+        if min(s) >= 0:
+            if count == 0:
+                best, degen = j, (0 in s)
+            count += 1
+    return best, count, degen
+
+
+@pytest.mark.parametrize("M,jitter,seed", [(3, 0.25, 2), (5, 0.0, 0), (4, 0.2, 13)])
+def test_locate_pair_points_matches_brute_force(M, jitter, seed):
+    """Location of points given as exact sums of two doubles per coordinate
+    (the double-float kernel's feet): brute force over every triangle in
+    rationals, including points that lie exactly on an edge only through
+    their low parts, and points a remainder-ulp off an edge."""
+    mesh = shuffled(si.grid_mesh(M, jitter=jitter, seed=seed), seed + 7)
+    om = oracle.OracleMesh(mesh.xy, mesh.tri)
+    rnd = random.Random(seed)
+    qh, ql = [], []
+    for _ in range(150):
+        qh.append((rnd.random(), rnd.random()))
+        ql.append(tuple(rnd.uniform(-1, 1) * 2.0 ** rnd.randint(-80, -55) for _ in range(2)))
+    for t in mesh.tri[: min(mesh.n_tri, 30)]:
+        for k in range(3):
+            a, b = (F(float(c)) for c in mesh.xy[t[k]]), (F(float(c)) for c in mesh.xy[t[(k + 1) % 3]])
+            a, b = tuple(a), tuple(b)
+            s = F(rnd.randint(1, 2**40 - 1), 2**40)
+            q = (a[0] + s * (b[0] - a[0]), a[1] + s * (b[1] - a[1]))
+            hx, hy = float(q[0]), float(q[1])
+            lx, ly = float(q[0] - F(hx)), float(q[1] - F(hy))
+            if F(hx) + F(lx) != q[0] or F(hy) + F(ly) != q[1]:
+                continue
+            qh.append((hx, hy))
+            ql.append((lx, ly))                                   # exactly on the edge
+            qh.append((hx, hy))
+            ql.append((math.nextafter(lx, math.inf) if lx else 2.0**-1074, ly))   # just off it
+    # a point nudged off a boundary edge leaves the square: keep covered points
+    brute = [_brute_pair(mesh, h, l) for h, l in zip(qh, ql)]
+    keep = [i for i, b in enumerate(brute) if b[0] >= 0]
+    assert len(keep) >= len(brute) - 30
+    qh, ql = np.array(qh)[keep], np.array(ql)[keep]
+    brute = [brute[i] for i in keep]
+    tri, flags = om.locate(qh, ql)
+    on_edge = 0
+    for i in range(qh.shape[0]):
+        best, count, degen = brute[i]
+        assert tri[i] == best, (i, qh[i], ql[i], tri[i], best)
+        assert bool(flags[i] & oracle.FLAG_DEGENERATE) == degen
+        assert bool(flags[i] & oracle.FLAG_MULTI) == (count > 1)
+        on_edge += degen
+    assert on_edge >= 20
+    # the exact signs of the located triangle: all >= 0, a zero iff degenerate
+    sg = om.signs(tri, qh, ql)
+    assert np.all(sg >= 0)
+    assert np.array_equal((sg == 0).any(axis=1), (flags & oracle.FLAG_DEGENERATE) != 0)
+    # zero remainders: the plain location
+    t0, f0 = om.locate(qh)
+    t1, f1 = om.locate(qh, np.zeros_like(qh))
+    assert np.array_equal(t0, t1) and np.array_equal(f0, f1)
+
+
+def test_signs_match_rationals_and_flag_non_triangles():
+    mesh = si.grid_mesh(4, 0.25, 21)
+    om = oracle.OracleMesh(mesh.xy, mesh.tri)
+    rnd = np.random.default_rng(4)
+    q = rnd.random((200, 2))
+    tri = rnd.integers(0, mesh.n_tri, 200).astype(np.int32)
+    tri[:3] = (-1, mesh.n_tri, -5)
+    sg = om.signs(tri, q)
+    assert np.all(sg[:3] == -2)
+    for i in range(3, 200):
+        assert tuple(sg[i]) == contains(mesh.xy, mesh.tri[tri[i]], q[i])

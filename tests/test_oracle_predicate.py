@@ -13,6 +13,8 @@ import numpy as np
 import pytest
 
 import oracle
+from fractions import Fraction as F
+
 from exact import orient as exact_orient
 
 
@@ -87,3 +89,73 @@ def test_orient_antisymmetry_and_cyclic():
         s = oracle.orient_sign(a, b, c)
         assert oracle.orient_sign(b, c, a) == s
         assert oracle.orient_sign(b, a, c) == -s
+
+
+def _exact_orient_pair(a, b, qh, ql):
+    """orient(a, b, qh + ql) in rationals."""
+    ax, ay, bx, by = (F(float(v)) for v in (a[0], a[1], b[0], b[1]))
+    qx, qy = F(float(qh[0])) + F(float(ql[0])), F(float(qh[1])) + F(float(ql[1]))
+    d = (bx - ax) * (qy - ay) - (by - ay) * (qx - ax)
+    return (d > 0) - (d < 0)
+
+
+def _split(v):
+    """A rational v as (hi, lo) doubles with hi + lo == v exactly."""
+    hi = float(v)
+    lo = float(v - F(hi))
+    assert F(hi) + F(lo) == v, "test construction: remainder not representable"
+    return hi, lo
+
+
+def _pair_cases(seed=5):
+    rnd = random.Random(seed)
+    out = []
+    # random points with a remainder below half an ulp of the high part
+    for _ in range(300):
+        a, b = (rnd.random(), rnd.random()), (rnd.random(), rnd.random())
+        qh = (rnd.random(), rnd.random())
+        ql = tuple(rnd.uniform(-1, 1) * 2.0 ** rnd.randint(-80, -54) for _ in range(2))
+        out.append((a, b, qh, ql))
+    # points exactly on the line a-b whose high part is not: a + s (b - a)
+    # with s carrying 70 bits, so the coordinates need more than one double;
+    # then the same point nudged by one ulp of its remainder either way
+    for _ in range(300):
+        a = (F(rnd.randint(0, 2**20), 2**20), F(rnd.randint(0, 2**20), 2**20))
+        b = (F(rnd.randint(0, 2**20), 2**20), F(rnd.randint(0, 2**20), 2**20))
+        s = F(rnd.randint(1, 2**70 - 1), 2**70)
+        q = (a[0] + s * (b[0] - a[0]), a[1] + s * (b[1] - a[1]))
+        (xh, xl), (yh, yl) = _split(q[0]), _split(q[1])
+        af, bf = (float(a[0]), float(a[1])), (float(b[0]), float(b[1]))
+        out.append((af, bf, (xh, yh), (xl, yl)))
+        for d in (-1.0, 1.0):
+            out.append((af, bf, (xh, yh), (math.nextafter(xl, d * math.inf) if xl else d * 2.0**-1074, yl)))
+            out.append((af, bf, (xh, yh), (xl, math.nextafter(yl, d * math.inf) if yl else d * 2.0**-1074)))
+    # a remainder that is subnormal, and one that cancels the high part's offset
+    out.append(((0.0, 0.0), (1.0, 1.0), (0.5, 0.5), (5e-324, 0.0)))
+    out.append(((0.0, 0.0), (1.0, 1.0), (0.5, 0.5), (0.0, -5e-324)))
+    out.append(((0.0, 0.0), (1.0, 0.0), (0.3, 2.0**-60), (0.0, -2.0**-60)))
+    return out
+
+
+@pytest.mark.parametrize("force_exact", [False, True])
+def test_orient_sign_of_pair_points_matches_rationals(force_exact):
+    """The sign for a point given as an exact sum of two doubles per
+    coordinate (a double-float foot), against rationals, with and without
+    the double filter; zero exactly when the sum lies on the line."""
+    bad = []
+    zeros = 0
+    for a, b, qh, ql in _pair_cases():
+        got = oracle.orient_sign2(a, b, qh, ql, force_exact=force_exact)
+        want = _exact_orient_pair(a, b, qh, ql)
+        zeros += want == 0
+        if got != want:
+            bad.append((a, b, qh, ql, got, want))
+    assert not bad, bad[:5]
+    assert zeros >= 300
+
+
+def test_orient_sign_of_pair_points_with_zero_remainder_is_the_plain_sign():
+    rnd = np.random.default_rng(9)
+    for _ in range(300):
+        a, b, c = rnd.random(2), rnd.random(2), rnd.random(2)
+        assert oracle.orient_sign2(a, b, c, (0.0, 0.0)) == oracle.orient_sign(a, b, c)

@@ -206,25 +206,6 @@ def test_swirl_converges_under_refinement():
     assert errs[2] < 0.6 * errs[0]
 
 
-@pytest.mark.parametrize("fld,dt", [(si.swirl_field(), 0.05), (si.rotation_field(), 0.02), (si.paper_field(), 0.03),
-                                     (si.fourier8_field(5), 0.02)])
-def test_fp32_feet_agree_with_double_feet(fld, dt):
-    """The FP32 path's feet (orc_feet_f32) are the double feet of the same
-    float coordinates up to float rounding: a few float ulps of the unit
-    square, and exactly on the boundary when clipped."""
-    m = si.grid_mesh(40, 0.25, 6)
-    xy32 = m.xy.astype(np.float32)
-    p = fld.packed()
-    for n in (0, 3, 7):
-        f32, c32 = oracle.feet_f32(fld.kind, p, dt, n, xy32)
-        f64, c64 = oracle.feet(fld.kind, p, dt, n, xy32.astype(np.float64))
-        inside = (c32 == 0) & (c64 == 0)
-        assert np.abs(f32[inside].astype(np.float64) - f64[inside]).max() <= 8 * 2.0 ** -24
-        for i in np.nonzero(c32)[0]:
-            X, Y = f32[i]
-            assert X in (0.0, 1.0) or Y in (0.0, 1.0)
-
-
 def test_exclusion_keeps_the_value_of_nodes_whose_foot_leaves():
     """Sec. 4 excludes the nodes whose Euler foot leaves the domain.  A
     translation by (+0.25, 0) (f = (-0.25, 0), dt = 1) sends exactly the

@@ -89,3 +89,57 @@ def test_noalloc_requires_node_tables_built_first():
         assert e.value.status == sl.SL_E_STATE
     finally:
         sl.sl_mesh_destroy(h)
+
+
+def test_noalloc_matches_sl_step_on_a_batch_on_two_calls_in_a_row():
+    """Six problems of uneven sizes with rotation and swirl fields: the
+    per-problem constants in the static array and the per-block problem
+    lookup, against sl_step."""
+    import torch
+    fields = [si.rotation_field(), si.swirl_field(), si.rotation_field(3.0, 0.4, 0.6), si.swirl_field(),
+              si.rotation_field(), si.swirl_field()]
+    probs_in = []
+    for k, (M, f) in enumerate(zip((7, 40, 13, 64, 3, 25), fields)):
+        mesh = si.grid_mesh(M, 0.25, 50 + k)
+        probs_in.append((mesh, f, 0.6 / M, si.gaussian(mesh.xy, 0.45, 0.55, 0.15)))
+    no, to, xy, tri = sl.pack_meshes([(m.xy, m.tri) for m, _, _, _ in probs_in])
+    pr = sl.problems([(f.kind, dt, f.packed()) for _, f, dt, _ in probs_in])
+    v0 = torch.tensor(np.concatenate([v for _, _, _, v in probs_in]), dtype=torch.float64, device="cuda")
+    ref = sl.sl_mesh_create(no, to, xy, tri, precision=sl.SL_FP64, seed=3)
+    new = sl.sl_mesh_create(no, to, xy, tri, precision=sl.SL_FP64, seed=3)
+    try:
+        scratch = torch.empty_like(v0)
+        sl.sl_step(new, pr, 0, v0, scratch)        # builds the swirl's node tables
+        sl.sl_mesh_reset_t0(new)
+        a_ref, b_ref = torch.empty_like(v0), torch.empty_like(v0)
+        a_new, b_new = torch.empty_like(v0), torch.empty_like(v0)
+        sl.sl_step(ref, pr, 0, v0, a_ref)
+        sl.sl_step(ref, pr, 1, a_ref, b_ref)
+        sl.sl_step_noalloc(new, pr, 0, v0, a_new)
+        sl.sl_step_noalloc(new, pr, 1, a_new, b_new)
+        sl.sl_mesh_status(new)
+        torch.cuda.synchronize()
+        for got, want in ((a_new, a_ref), (b_new, b_ref)):
+            for k in range(len(probs_in)):
+                g, w = got[no[k]:no[k + 1]].cpu().numpy(), want[no[k]:no[k + 1]].cpu().numpy()
+                assert np.abs(g - w).max() <= REL_TOL * np.abs(w).max(), k
+    finally:
+        sl.sl_mesh_destroy(ref)
+        sl.sl_mesh_destroy(new)
+
+
+def test_noalloc_refuses_more_problems_than_its_limit():
+    import torch
+    n = sl.SL_NOALLOC_MAX_PROBLEMS + 1
+    mesh = si.grid_mesh(1, 0.0, 1)
+    no, to, xy, tri = sl.pack_meshes([(mesh.xy, mesh.tri)] * n)
+    pr = sl.problems([(si.FIELD_ROTATION, 0.01, si.rotation_field().packed())] * n)
+    h = sl.sl_mesh_create(no, to, xy, tri, precision=sl.SL_FP64, seed=1)
+    try:
+        v = torch.zeros(int(no[-1]), dtype=torch.float64, device="cuda")
+        w = torch.empty_like(v)
+        with pytest.raises(sl.SLError) as e:
+            sl.sl_step_noalloc(h, pr, 0, v, w)
+        assert e.value.status == sl.SL_E_ARG and str(sl.SL_NOALLOC_MAX_PROBLEMS) in str(e.value)
+    finally:
+        sl.sl_mesh_destroy(h)
