@@ -180,7 +180,7 @@ def build_workload(args):
     return Workload(prob.name, [prob], prob.precision, prob.n_steps, desc)
 
 
-TRAFFIC_SOURCES = ("step_fast.cu", "step_fast.cuh", "df.cuh", "predicates.cuh", "step_common.cuh", "step_kernels.cuh")
+TRAFFIC_SOURCES = ("step_fast.cu", "step_fast_impl.cuh", "step_fast_c01.cu", "step_fast_c23.cu", "step_fast_c45.cu", "step_fast.cuh", "df.cuh", "predicates.cuh", "step_common.cuh", "step_kernels.cuh")
 
 
 def committed_traffic(workload_key, split=0):

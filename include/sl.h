@@ -163,7 +163,7 @@ typedef enum {
                                 stats is NULL, and the device status is read by the next
                                 sl_mesh_status (or a synchronising sl_run).  Lets a caller queue
                                 many runs back to back. */
-    SL_OPT_PRECISE = 12      /* FP64 meshes, double-float kernel: gradient bound G >= 0 (value
+    SL_OPT_PRECISE = 12,     /* FP64 meshes, double-float kernel: gradient bound G >= 0 (value
                                 units per unit length; default 32; 0 = never).  The double-float
                                 foot and barycentric coordinates carry about 2^-48 of rounding (a
                                 foot moved by a few 2^-49), so a step's value is off by about
@@ -173,6 +173,15 @@ typedef enum {
                                 and the P1 value are evaluated again in FP64 from the double
                                 coordinates, as the plain kernel does; the located triangle is
                                 the same.  Scale G with the magnitude of V. */
+    SL_OPT_RECORDS = 13      /* half-edge walk records of the double-float kernel: 0 = 16-byte
+                                records (default); 1 = 8-byte records where the mesh allows them
+                                (every vertex across an edge within 2^17 grid units of 2^-24 of
+                                the vertex it replaces, i.e. triangles narrower than about 2^-7,
+                                and at most 44.7 M triangles), else 16-byte ones.  An 8-byte
+                                record is one 64-bit gather per hop, which takes fewer L1
+                                wavefronts for a warp's 32 scattered lanes, but more instructions
+                                to unpack; sl_autotune measures both.  Results are identical.
+                                Setting it rebuilds the records (synchronises). */
 } sl_option;
 
 /*
@@ -321,6 +330,9 @@ typedef struct {
     float first_ms[SL_TUNE_MAX_CONFIGS];  /* one step from the initial start triangles */
     float rest_ms[SL_TUNE_MAX_CONFIGS];   /* mean of the later steps */
     float split_ms[SL_TUNE_MAX_CONFIGS];  /* [0]: mean of the later steps, split (FP64 meshes) */
+    int32_t records;                      /* chosen SL_OPT_RECORDS */
+    float compact_first_ms;               /* the chosen configurations with 8-byte records: first */
+    float compact_rest_ms;                /* ... and later steps (split if chosen); -1: not eligible */
 } sl_tune;
 
 /*
@@ -330,7 +342,10 @@ typedef struct {
  * timed with CUDA events on `stream`; the fastest configuration of each
  * phase becomes SL_OPT_CONFIG_FIRST and SL_OPT_CONFIG.  On FP64 meshes the
  * later steps are also timed split (SL_OPT_SPLIT = 1, whose passes have a
- * launch shape of their own), and the faster form is kept.  v (device, N values,
+ * launch shape of their own), and the faster form is kept; then, where the
+ * mesh allows 8-byte walk records, the chosen configurations are timed with
+ * them, and they are kept (SL_OPT_RECORDS = 1) if a 50-step run (the first
+ * step and 49 later ones) is faster.  v (device, N values,
  * V^0) and v_scratch (device, N values) are used as in sl_run; v, T^0 and
  * the statistics counters are restored before returning (the call
  * synchronises and allocates temporary device buffers).  No counterpart in
@@ -401,6 +416,12 @@ sl_status sl_mesh_stats(sl_mesh *m, sl_stats *out, int32_t reset, void *stream);
  * Host only, except SL_OPT_STRATEGY, which resets T^0 and synchronises.
  */
 sl_status sl_mesh_set_option(sl_mesh *m, int32_t option, int64_t value);
+
+/* sl_mesh_get_option -- the current value of an sl_option (value: host),
+ * except SL_OPT_RECORDS, for which it gives the size in bytes of the
+ * half-edge walk records the mesh uses (8 or 16).  SL_E_ARG for an unknown
+ * option.  No counterpart in the paper. */
+sl_status sl_mesh_get_option(const sl_mesh *m, int32_t option, int64_t *value);
 
 /* sl_mesh_info -- the sizes of the handle (host outputs, each may be NULL):
  * nodes and triangles over all problems, problems, precision.  No

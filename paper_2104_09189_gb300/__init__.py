@@ -18,13 +18,13 @@ __all__ = [
     "SL_OK", "SL_E_ARG", "SL_E_MESH", "SL_E_NOMEM", "SL_E_CUDA", "SL_E_WALK_LIMIT", "SL_E_STATE",
     "SL_FP64", "SL_FP32", "SL_CURVE_NONE", "SL_CURVE_HILBERT", "SL_CURVE_MORTON",
     "SL_OPT_STATS", "SL_OPT_WALK_CAP", "SL_OPT_KERNEL", "SL_OPT_BLOCK", "SL_OPT_CONFIG",
-    "SL_OPT_CONFIG_FIRST", "SL_OPT_STRATEGY", "SL_OPT_OUTSIDE", "SL_OPT_SPLIT", "SL_OPT_ASYNC", "SL_OPT_PRECISE",
+    "SL_OPT_CONFIG_FIRST", "SL_OPT_STRATEGY", "SL_OPT_OUTSIDE", "SL_OPT_SPLIT", "SL_OPT_ASYNC", "SL_OPT_PRECISE", "SL_OPT_RECORDS",
     "SL_NODE_CLIPPED", "SL_NODE_DEGENERATE", "SL_NODE_EXACT", "SL_NODE_FALLBACK", "SL_NODE_WALK_LIMIT",
     "SL_NODE_RANGE", "SL_NODE_EXCLUDED", "SL_NODE_PRECISE", "SLError", "sl_problem", "problems", "pack_meshes",
     "sl_mesh_create", "sl_mesh_validate", "sl_mesh_reorder", "sl_step", "sl_run", "sl_run_host", "sl_mesh_get_t0",
     "sl_mesh_set_t0", "sl_mesh_reset_t0", "sl_mesh_status", "sl_mesh_stats", "sl_mesh_set_option", "sl_mesh_info",
     "sl_mesh_export", "sl_mesh_destroy", "sl_last_error", "library", "EXPORTED", "sl_step_noalloc",
-    "SL_NOALLOC_MAX_NODES", "SL_NOALLOC_MAX_PROBLEMS", "sl_autotune", "sl_probe_gather",
+    "SL_NOALLOC_MAX_NODES", "SL_NOALLOC_MAX_PROBLEMS", "sl_autotune", "sl_probe_gather", "sl_mesh_get_option",
 ]
 
 SL_OK, SL_E_ARG, SL_E_MESH, SL_E_NOMEM, SL_E_CUDA, SL_E_WALK_LIMIT, SL_E_STATE = range(7)
@@ -33,6 +33,7 @@ SL_CURVE_NONE, SL_CURVE_HILBERT, SL_CURVE_MORTON = 0, 1, 2
 SL_OPT_STATS, SL_OPT_WALK_CAP, SL_OPT_KERNEL, SL_OPT_BLOCK = range(4)
 SL_OPT_CONFIG = 5
 SL_OPT_CONFIG_FIRST, SL_OPT_STRATEGY, SL_OPT_OUTSIDE, SL_OPT_SPLIT, SL_OPT_ASYNC, SL_OPT_PRECISE = 7, 8, 9, 10, 11, 12
+SL_OPT_RECORDS = 13
 SL_NODE_CLIPPED, SL_NODE_DEGENERATE, SL_NODE_EXACT, SL_NODE_FALLBACK, SL_NODE_WALK_LIMIT, SL_NODE_RANGE = (
     1, 2, 4, 8, 16, 32)
 SL_NODE_EXCLUDED = 64
@@ -48,7 +49,7 @@ _STATUS_NAMES = {0: "SL_OK", 1: "SL_E_ARG", 2: "SL_E_MESH", 3: "SL_E_NOMEM", 4: 
 EXPORTED = ("sl_mesh_create", "sl_mesh_validate", "sl_mesh_reorder", "sl_step", "sl_run", "sl_run_host", "sl_mesh_get_t0",
             "sl_mesh_set_t0", "sl_mesh_reset_t0", "sl_mesh_status", "sl_mesh_stats", "sl_mesh_set_option", "sl_mesh_info",
             "sl_mesh_export", "sl_mesh_destroy", "sl_last_error", "sl_step_noalloc", "sl_autotune",
-            "sl_probe_gather")
+            "sl_probe_gather", "sl_mesh_get_option")
 
 
 class SLError(RuntimeError):
@@ -71,7 +72,8 @@ class sl_debug(ctypes.Structure):
 class sl_tune(ctypes.Structure):
     _fields_ = [("config_first", ctypes.c_int32), ("config_rest", ctypes.c_int32), ("n_configs", ctypes.c_int32),
                 ("split", ctypes.c_int32), ("first_ms", ctypes.c_float * 8), ("rest_ms", ctypes.c_float * 8),
-                ("split_ms", ctypes.c_float * 8)]
+                ("split_ms", ctypes.c_float * 8), ("records", ctypes.c_int32), ("compact_first_ms", ctypes.c_float),
+                ("compact_rest_ms", ctypes.c_float)]
 
 
 class sl_stats(ctypes.Structure):
@@ -108,6 +110,7 @@ def library():
         "sl_mesh_reset_t0": [P, P],
         "sl_mesh_stats": [P, P, I32, P],
         "sl_mesh_set_option": [P, I32, I64],
+        "sl_mesh_get_option": [P, I32, P],
         "sl_mesh_info": [P, P, P, P, P],
         "sl_mesh_export": [P, P, P, P],
         "sl_step_noalloc": [P, P, I64, P, P, P],
@@ -299,6 +302,13 @@ def sl_mesh_set_option(h, option, value):
     _check(library().sl_mesh_set_option(h, int(option), int(value)))
 
 
+def sl_mesh_get_option(h, option):
+    """The option's value (SL_OPT_RECORDS: the walk records' size in bytes)."""
+    v = ctypes.c_int64()
+    _check(library().sl_mesh_get_option(h, int(option), ctypes.byref(v)))
+    return v.value
+
+
 def sl_mesh_destroy(h):
     if h:
         library().sl_mesh_destroy(h)
@@ -330,4 +340,6 @@ def sl_autotune(h, probs, probe_steps, v, v_scratch, stream=None):
     return {"config_first": t.config_first, "config_rest": t.config_rest, "split": t.split,
             "first_ms": [round(float(x), 4) for x in list(t.first_ms)[:n]],
             "rest_ms": [round(float(x), 4) for x in list(t.rest_ms)[:n]],
-            "split_ms": [round(float(x), 4) for x in list(t.split_ms)[:n] if x >= 0]}
+            "split_ms": [round(float(x), 4) for x in list(t.split_ms)[:n] if x >= 0],
+            "records": t.records, "compact_first_ms": round(float(t.compact_first_ms), 4),
+            "compact_rest_ms": round(float(t.compact_rest_ms), 4)}

@@ -62,7 +62,7 @@ def build(force=False, verbose=False):
         return LIB
     os.makedirs(BUILD, exist_ok=True)
     srcs = _sources()
-    with cf.ThreadPoolExecutor(max_workers=min(8, len(srcs))) as ex:
+    with cf.ThreadPoolExecutor(max_workers=min(16, len(srcs))) as ex:
         results = list(ex.map(lambda s: _compile(s, verbose), srcs))
     if verbose:
         for _, err in results:

@@ -65,7 +65,7 @@ void free_device(sl_mesh *m)
 {
     DeviceMesh &d = m->d;
     void *ptrs[] = {d.xy, d.tv[0], d.tv[1], d.tv[2], d.tn[0], d.tn[1], d.tn[2], d.t0, d.t0_init, d.t0v, d.node_off,
-                    d.status, d.stats, d.probs, d.fprobs, d.xyq, d.xyh, d.g1, d.g2, d.tparams, d.dfa, d.dfb, d.he, d.grid_t0v, d.tree_order, d.tree_parent, d.queue, d.queue_count,
+                    d.status, d.stats, d.probs, d.fprobs, d.xyq, d.xyh, d.g1, d.g2, d.tparams, d.dfa, d.dfb, d.he, d.he8, d.grid_t0v, d.tree_order, d.tree_parent, d.queue, d.queue_count,
                     m->host_v, m->host_v2};
     for (void *p : ptrs)
         if (p) cudaFree(p);
@@ -130,14 +130,48 @@ static sl_status upload_arrays(sl_mesh *m)
         SL_CUDA(cudaMemcpy(d.tn[k], col.data(), sizeof(int32_t) * Nt, cudaMemcpyHostToDevice));
     }
     // half-edge walk records of the fast kernels
-    launch_build_he(d.tv, d.tn, m->precision == SL_FP64 ? (const float2 *)d.xyh : (const float2 *)d.xy, Nt,
-                    (float4 *)d.he, 0);
+    sl_status st = build_walk_records(m);
+    if (st != SL_OK) return st;
     SL_CUDA(cudaMemcpy(d.t0, m->t0.data(), sizeof(int32_t) * N, cudaMemcpyHostToDevice));
     SL_CUDA(cudaMemcpy(d.t0_init, m->t0_init.data(), sizeof(int32_t) * N, cudaMemcpyHostToDevice));
     SL_CUDA(cudaMemcpy(d.node_off, m->node_off.data(), sizeof(int64_t) * (m->n_problems + 1), cudaMemcpyHostToDevice));
     launch_fill_t0v(d.t0, d.tv[0], d.tv[1], d.tv[2], (int4 *)d.t0v, N, 0);
     SL_CUDA(cudaGetLastError());
     SL_CUDA(cudaDeviceSynchronize());
+    return SL_OK;
+}
+
+// Compact 8-byte records for FP64 meshes whose triangles are narrow enough
+// (k_build_he8 reports an overflow otherwise), else 16-byte records; only
+// one form is kept on the device.
+sl_status build_walk_records(sl_mesh *m)
+{
+    DeviceMesh &d = m->d;
+    const int64_t Nt = m->Nt;
+    if (m->precision == SL_FP64 && m->opt_records == 1) {
+        if (!d.he8) SL_CUDA(cudaMalloc(&d.he8, sizeof(uint2) * 3 * (Nt > 0 ? Nt : 1)));
+        uint32_t *overflow = d.status + 1;   // a reserved status word, zero again afterwards
+        SL_CUDA(cudaMemset(overflow, 0, sizeof(uint32_t)));
+        launch_build_he8(d.tv, d.tn, (const float2 *)d.xyh, Nt, (uint2 *)d.he8, overflow, 0);
+        SL_CUDA(cudaGetLastError());
+        uint32_t h = 0;
+        SL_CUDA(cudaMemcpy(&h, overflow, sizeof(h), cudaMemcpyDeviceToHost));
+        SL_CUDA(cudaMemset(overflow, 0, sizeof(uint32_t)));
+        if (!h) {
+            if (d.he) cudaFree(d.he);
+            d.he = nullptr;
+            m->graph.valid = false;
+            return SL_OK;
+        }
+    }
+    if (d.he8) cudaFree(d.he8);
+    d.he8 = nullptr;
+    if (!d.he) SL_CUDA(cudaMalloc(&d.he, sizeof(float4) * 3 * (Nt > 0 ? Nt : 1)));
+    launch_build_he(d.tv, d.tn, m->precision == SL_FP64 ? (const float2 *)d.xyh : (const float2 *)d.xy, Nt,
+                    (float4 *)d.he, 0);
+    SL_CUDA(cudaGetLastError());
+    SL_CUDA(cudaDeviceSynchronize());
+    m->graph.valid = false;
     return SL_OK;
 }
 
@@ -154,7 +188,6 @@ sl_status upload(sl_mesh *m)
         SL_CUDA(cudaMalloc(&d.tv[k], sizeof(int32_t) * Nt));
         SL_CUDA(cudaMalloc(&d.tn[k], sizeof(int32_t) * Nt));
     }
-    SL_CUDA(cudaMalloc(&d.he, sizeof(float4) * 3 * Nt));
     SL_CUDA(cudaMalloc(&d.t0, sizeof(int32_t) * N));
     if (m->precision == SL_FP64) SL_CUDA(cudaMalloc(&d.xyh, sizeof(float2) * N));
     SL_CUDA(cudaMalloc(&d.t0_init, sizeof(int32_t) * N));
@@ -263,6 +296,7 @@ FastArgs make_fast_args(const sl_mesh *m, const FastProb *fp, const void *vin, v
         a.tn[k] = m->d.tn[k];
     }
     a.he = (const float4 *)m->d.he;
+    a.he8 = (const uint2 *)m->d.he8;
     a.t0 = m->d.t0;
     a.t0v = (int4 *)m->d.t0v;
     a.vin = vin;
@@ -895,10 +929,11 @@ extern "C" sl_status sl_autotune(sl_mesh *m, const sl_problem *probs, int32_t pr
     const size_t vbytes = (m->precision == SL_FP64 ? sizeof(double) : sizeof(float)) * m->N;
     void *v_save = nullptr, *t_save = nullptr, *s_save = nullptr;
     cudaEvent_t e0 = nullptr, e1 = nullptr, e2 = nullptr;
-    const int32_t cfg0 = m->opt_config, cfgf0 = m->opt_config_first, split0 = m->opt_split;
+    const int32_t cfg0 = m->opt_config, cfgf0 = m->opt_config_first, split0 = m->opt_split, rec0 = m->opt_records;
     const bool init0 = m->t0_initial;
     std::memset(out, 0, sizeof(*out));
     for (int k = 0; k < SL_TUNE_MAX_CONFIGS; ++k) out->first_ms[k] = out->rest_ms[k] = out->split_ms[k] = -1.0f;
+    out->compact_first_ms = out->compact_rest_ms = -1.0f;
     auto cleanup = [&]() {
         if (v_save) cudaFree(v_save);
         if (t_save) cudaFree(t_save);
@@ -980,6 +1015,47 @@ extern "C" sl_status sl_autotune(sl_mesh *m, const sl_problem *probs, int32_t pr
             }
             m->opt_split = 0;
         }
+        out->records = m->opt_records;
+        if (m->precision == SL_FP64) {
+            // the other walk-record form at the chosen configurations, scored
+            // by a 50-step run (first step + 49 later ones)
+            const float first_now = out->first_ms[out->config_first];
+            const float rest_now = out->split ? out->split_ms[0] : out->rest_ms[out->config_rest];
+            const int32_t other = m->opt_records ? 0 : 1;
+            m->opt_records = other;
+            sl_status r = build_walk_records(m);
+            if (r != SL_OK) return r;
+            if (other == 0 || m->d.he8) {
+                m->opt_config_first = out->config_first;
+                m->opt_config = out->config_rest;
+                m->opt_split = out->split;
+                SL_CUDA(cudaMemcpyAsync(v, v_save, vbytes, cudaMemcpyDeviceToDevice, s));
+                r = sl_mesh_reset_t0(m, s);
+                if (r != SL_OK) return r;
+                SL_CUDA(cudaEventRecord(e0, s));
+                r = run_steps(m, probs, 0, 1, v, v_scratch, 0, s);
+                if (r != SL_OK) return r;
+                m->t0_initial = false;
+                SL_CUDA(cudaEventRecord(e1, s));
+                r = run_steps(m, probs, 1, probe_steps, v, v_scratch, 0, s);
+                if (r != SL_OK) return r;
+                SL_CUDA(cudaEventRecord(e2, s));
+                SL_CUDA(cudaEventSynchronize(e2));
+                float f = 0.f, g = 0.f;
+                SL_CUDA(cudaEventElapsedTime(&f, e0, e1));
+                SL_CUDA(cudaEventElapsedTime(&g, e1, e2));
+                g /= (float)probe_steps;
+                out->compact_first_ms = other ? f : first_now;
+                out->compact_rest_ms = other ? g : rest_now;
+                if (f + 49.0f * g < first_now + 49.0f * rest_now) out->records = other;
+                m->opt_split = 0;
+            }
+            if (m->opt_records != out->records) {
+                m->opt_records = out->records;
+                r = build_walk_records(m);
+                if (r != SL_OK) return r;
+            }
+        }
         // restore values, T^0 and counters; keep the chosen configurations
         SL_CUDA(cudaMemcpyAsync(v, v_save, vbytes, cudaMemcpyDeviceToDevice, s));
         SL_CUDA(cudaMemcpyAsync(m->d.t0, t_save, sizeof(int32_t) * m->N, cudaMemcpyDeviceToDevice, s));
@@ -1001,6 +1077,10 @@ extern "C" sl_status sl_autotune(sl_mesh *m, const sl_problem *probs, int32_t pr
         m->opt_config_first = cfgf0;
         m->opt_split = split0;
         m->t0_initial = init0;
+        if (m->opt_records != rec0) {
+            m->opt_records = rec0;
+            build_walk_records(m);
+        }
         if (m->graph.exec) cudaGraphExecDestroy((cudaGraphExec_t)m->graph.exec);
         m->graph = GraphCache();
     }

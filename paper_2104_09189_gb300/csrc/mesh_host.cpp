@@ -427,6 +427,27 @@ static sl_status courant_slots(const sl_mesh *m, int32_t &M, std::vector<int32_t
     return SL_OK;
 }
 
+extern "C" sl_status sl_mesh_get_option(const sl_mesh *m, int32_t option, int64_t *value)
+{
+    if (!m || !value) return sl::fail(SL_E_ARG, "sl_mesh_get_option: NULL argument");
+    switch (option) {
+    case SL_OPT_STATS: *value = m->opt_stats; break;
+    case SL_OPT_WALK_CAP: *value = m->opt_walk_cap; break;
+    case SL_OPT_KERNEL: *value = m->opt_kernel; break;
+    case SL_OPT_BLOCK: *value = m->opt_block; break;
+    case SL_OPT_CONFIG: *value = m->opt_config; break;
+    case SL_OPT_CONFIG_FIRST: *value = m->opt_config_first; break;
+    case SL_OPT_STRATEGY: *value = m->opt_strategy; break;
+    case SL_OPT_OUTSIDE: *value = m->opt_outside; break;
+    case SL_OPT_SPLIT: *value = m->opt_split; break;
+    case SL_OPT_ASYNC: *value = m->opt_async; break;
+    case SL_OPT_PRECISE: *value = m->opt_precise; break;
+    case SL_OPT_RECORDS: *value = m->d.he8 ? 8 : 16; break;
+    default: return sl::fail(SL_E_ARG, "unknown option");
+    }
+    return SL_OK;
+}
+
 extern "C" sl_status sl_mesh_set_option(sl_mesh *m, int32_t option, int64_t value)
 {
     if (!m) return sl::fail(SL_E_ARG, "sl_mesh_set_option: mesh is NULL");
@@ -483,6 +504,13 @@ extern "C" sl_status sl_mesh_set_option(sl_mesh *m, int32_t option, int64_t valu
         if (value != 0 && value != 1) return sl::fail(SL_E_ARG, "outside mode must be 0 (clip) or 1 (exclude)");
         m->opt_outside = (int32_t)value;
         break;
+    case SL_OPT_RECORDS: {
+        if (value != 0 && value != 1) return sl::fail(SL_E_ARG, "records must be 0 (16 bytes) or 1 (compact where they fit)");
+        m->opt_records = (int32_t)value;
+        const sl_status st = sl::build_walk_records(m);
+        if (st != SL_OK) return st;
+        break;
+    }
     case SL_OPT_PRECISE:
         if (value < 0 || value > (1 << 30)) return sl::fail(SL_E_ARG, "precise gradient bound out of range");
         m->opt_precise = (int32_t)value;

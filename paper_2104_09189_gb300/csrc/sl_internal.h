@@ -51,7 +51,8 @@ struct DeviceMesh {
     void *g1 = nullptr, *g2 = nullptr;   // field node tables, float4 (hi, lo) per node
     double *tparams = nullptr;        // field parameters the tables were built from (device)
     void *dfa = nullptr, *dfb = nullptr;   // value scratch of sl_step for the fast FP64 kernel
-    void *he = nullptr;               // float4 half-edge walk records of the fast kernels (3 Nt)
+    void *he = nullptr;               // float4 half-edge walk records of the fast kernels (3 Nt), or NULL
+    void *he8 = nullptr;              // uint2 compact records (FP64 meshes that fit, 3 Nt), or NULL
 };
 
 struct GraphCache {
@@ -98,6 +99,7 @@ struct sl_mesh {
     int32_t opt_split = 0;            // 1 = split steps (settle pass + finish pass), FP64 meshes
     int32_t opt_async = 0;            // 1 = sl_run without stats returns unsynchronised
     int32_t opt_precise = 32;         // gradient bound of the FP64 value path (0 = off)
+    int32_t opt_records = 0;          // 0 = 16-byte walk records, 1 = compact records where they fit
     bool t0_initial = true;           // T^0 holds the initial start triangles
     int32_t sms = 0;                  // multiprocessors of the device
     bool stepped = false;
@@ -124,6 +126,8 @@ sl_status build_and_validate(sl_mesh *m, const int32_t *nbr_in);
 sl_status reorder_host(sl_mesh *m, int32_t curve, int32_t *node_perm, int32_t *tri_perm);
 // device side (api_device.cu)
 sl_status upload(sl_mesh *m);
+// (re)build the half-edge walk records in the form opt_records and the mesh allow
+sl_status build_walk_records(sl_mesh *m);
 // the fast kernels' constants of step n of one problem, validated as sl_step validates them
 sl_status fast_constants_one(const sl_problem &q, int64_t n, int32_t p, FastProb &f);
 // the arguments of a fast-kernel step of the whole mesh: the step's constants

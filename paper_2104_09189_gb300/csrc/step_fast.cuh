@@ -43,7 +43,8 @@ struct FastArgs {
     const float2 *xyh;            // FP64 meshes: high parts (xh, yh) for the FP32 hop tests
     const int32_t *tv[3];
     const int32_t *tn[3];         // -1 - side on the boundary (0: x=0, 1: x=1, 2: y=0, 3: y=1)
-    const float4 *he;             // half-edge walk records, 3 per triangle (k_build_he)
+    const float4 *he;             // half-edge walk records, 3 per triangle (k_build_he), or NULL
+    const uint2 *he8;             // FP64 meshes whose records fit in 8 bytes (k_build_he8), or NULL
     int32_t *t0;
     int4 *t0v;                    // per node: (3 T^0, T[0][T^0], T[1][T^0], T[2][T^0]), kept in
                                   // step with t0
@@ -80,6 +81,14 @@ struct FastArgs {
 
 // config: launch configuration 0..kFastConfigs-1 (see step_fast.cu)
 void launch_fast_df(const FastArgs &a, bool stats, bool debug, int config, cudaStream_t s);
+// one launch configuration each (step_fast_c*.cu)
+void launch_fast_df_c0(const FastArgs &a, bool stats, bool debug, cudaStream_t s);
+void launch_fast_df_c1(const FastArgs &a, bool stats, bool debug, cudaStream_t s);
+void launch_fast_df_c2(const FastArgs &a, bool stats, bool debug, cudaStream_t s);
+void launch_fast_df_c3(const FastArgs &a, bool stats, bool debug, cudaStream_t s);
+void launch_fast_df_c4(const FastArgs &a, bool stats, bool debug, cudaStream_t s);
+void launch_fast_df_c5(const FastArgs &a, bool stats, bool debug, cudaStream_t s);
+void launch_fast_df_ext(const FastArgs &a, bool stats, bool debug, cudaStream_t s);
 // a split step: lean settle pass + finish pass over its queue
 void launch_split_df(const FastArgs &a, bool stats, bool debug, int sms, bool reset, cudaStream_t s);
 constexpr int kFastConfigs = 6;
@@ -116,6 +125,23 @@ void launch_field_tables(const FieldTableArgs &a, cudaStream_t s);
 // of t, the triangle the walk is in.
 void launch_build_he(const int32_t *const tv[3], const int32_t *const tn[3], const float2 *xyc, int64_t nt,
                      float4 *he, cudaStream_t s);
+
+// Compact 8-byte half-edge records of FP64 meshes, he8[3 t + k] for the edge
+// of triangle t opposite its vertex W = T[k][t].  Interior edge, u, k', Q
+// and e0' = 3 u + (k'+1) mod 3 as above; (dx, dy) = Q - W in units of 2^-24
+// (the hop coordinates are on that grid, so the difference is an exact
+// integer), stored biased, b = d + 2^17 in [2, 2^18 - 2]:
+//   word 0 = bx | (by & 0x3FFF) << 18,
+//   word 1 = by >> 14 | f << 4 | e0' << 5,
+// f = 1 when e0' is slot 2 of u (the other exit is then e0' - 2, else
+// e0' + 1).  The float with bits 0x3F000000 | b is 0.5 + b 2^-24, so Q = W +
+// that - (0.5 + 2^-7), all exact.  Boundary edge: zero offset and e0' = 3 t
+// + (k+1) mod 3, an exit of t itself (a walk can never cross it: the foot
+// lies in the square).  Sets *overflow to 1 when some |dx| or |dy| exceeds
+// 2^17 - 2 (a triangle wider than about 2^-7) or e0' reaches 2^27 (more than
+// 44.7 M triangles): the mesh then keeps 16-byte records.
+void launch_build_he8(const int32_t *const tv[3], const int32_t *const tn[3], const float2 *xyh, int64_t nt,
+                      uint2 *he8, uint32_t *overflow, cudaStream_t s);
 
 // t0v[i] = (3 t0[i], its three vertex ids in slot order)
 void launch_fill_t0v(const int32_t *t0, const int32_t *tv0, const int32_t *tv1, const int32_t *tv2, int4 *t0v,

@@ -580,3 +580,34 @@ def test_steep_data_takes_the_fp64_value_path(split):
     assert all(n == 0 for _, n, _ in outs[0])
     # the FP64 path is what keeps the steep nodes within the tolerance
     assert max(e for e, _, _ in outs[32]) < max(e for e, _, _ in outs[0])
+
+
+@pytest.mark.parametrize("split", [0, 1])
+def test_compact_walk_records_give_identical_results(split):
+    """The 8-byte half-edge records of fine meshes (SL_OPT_RECORDS) make the
+    same hops as the 16-byte ones: values, located triangles, hop counts
+    and flags bitwise equal over steps from the initial start triangles and
+    later ones, on a mesh fine enough for them (the C2 construction at 512^2);
+    a coarse mesh keeps 16-byte records."""
+    prob = si.config("C2", M=512)
+    runs = []
+    for records in (0, 1):
+        g = DeviceRun(prob.mesh, prob.field, prob.dt, curve=sl.SL_CURVE_HILBERT)
+        sl.sl_mesh_set_option(g.h, sl.SL_OPT_SPLIT, split)
+        sl.sl_mesh_set_option(g.h, sl.SL_OPT_RECORDS, records)
+        assert sl.sl_mesh_get_option(g.h, sl.SL_OPT_RECORDS) == (16 if records == 0 else 8)
+        v = g.to_dev(prob.v0)
+        out = []
+        for n in range(3):
+            v, res = g.step(n, v)
+            out.append(res)
+        runs.append(out)
+        g.close()
+    for a, b in zip(*runs):
+        for key in ("v", "tri", "moves", "flags", "feet", "feet_lo"):
+            assert np.array_equal(a[key], b[key]), key
+    assert runs[0][0]["moves"].mean() > 5          # the first step walks
+    coarse = DeviceRun(si.grid_mesh(100, 0.25, 3), prob.field, prob.dt)
+    sl.sl_mesh_set_option(coarse.h, sl.SL_OPT_RECORDS, 1)      # too coarse: 16-byte records stay
+    assert sl.sl_mesh_get_option(coarse.h, sl.SL_OPT_RECORDS) == 16
+    coarse.close()
