@@ -320,7 +320,10 @@ FastArgs make_fast_args(const sl_mesh *m, const FastProb *fp, const void *vin, v
     a.grid_M = m->opt_strategy == 2 ? m->grid_M : 0;
     a.grid_t0v = (const int4 *)m->d.grid_t0v;
     a.count = m->N;     // every node; the level launches of strategy (c) narrow it
-    a.steep_g2 = m->precision == SL_FP64 ? (float)((double)m->opt_precise * (double)m->opt_precise) : 0.0f;
+    // G^2; +inf when the FP64 value path is off (no gradient exceeds it)
+    a.steep_g2 = m->precision == SL_FP64 && m->opt_precise > 0
+                     ? (float)((double)m->opt_precise * (double)m->opt_precise)
+                     : __builtin_inff();
     return a;
 }
 
@@ -458,15 +461,21 @@ static sl_status ensure_queue(sl_mesh *m)
     return SL_OK;
 }
 
+static bool split_step(const sl_mesh *m, bool initial)
+{
+    return m->precision == SL_FP64 && m->opt_split && !initial && m->opt_strategy == 0 && !m->opt_outside;
+}
+
 // initial: the step starts from the initial start triangles (never split).
 // split_seq: the number of split steps already enqueued in this sequence of
 // steps (NULL: a sequence of one).  Split steps use the two queue counters
-// in turn; the first one of a sequence zeroes its counter, and each finish
-// pass zeroes the counter of the next, so the steps between need no memset.
+// in turn; the first one of a sequence zeroes its counter, and each settle
+// pass zeroes the counter of the next step, so the steps between need no
+// memset.
 static sl_status launch_fast(sl_mesh *m, const FastArgs &a, bool debug, int config, bool initial, cudaStream_t s,
                              int32_t *split_seq = nullptr)
 {
-    if (m->precision == SL_FP64 && m->opt_split && !initial && m->opt_strategy == 0 && !m->opt_outside) {
+    if (split_step(m, initial)) {
         if (!m->d.queue) return fail(SL_E_STATE, "split step without its queue scratch");
         const int32_t q = split_seq ? *split_seq : 0;
         FastArgs x = a;

@@ -18,7 +18,7 @@ static void launch_finish(const FastArgs &a, bool stats, bool debug, unsigned gr
 }
 
 template <int kBlock, int kMinBlocks>
-static void launch_split_cfg(const FastArgs &a, bool stats, bool debug, int sms, bool reset, cudaStream_t s)
+static void launch_settle_cfg(const FastArgs &a, bool stats, bool debug, bool reset, cudaStream_t s)
 {
     const unsigned grid = (unsigned)((a.N + kBlock - 1) / kBlock);
     if (grid == 0) return;
@@ -51,19 +51,30 @@ static void launch_split_cfg(const FastArgs &a, bool stats, bool debug, int sms,
         default: k_settle_df<false, false, kBlock, kMinBlocks, SL_FIELD_ZERO><<<grid, kBlock, 0, s>>>(a); break;
         }
     }
+}
+
+// The settle pass needs 32 registers, so it runs at 128 x 14 (56 resident
+// warps per SM): faster than at 48 or 64.  The caller provides a.queue (N
+// entries) and a.queue_count (zeroed here when reset, else by the previous
+// step's settle pass through its queue_next).
+void launch_settle_df(const FastArgs &a, bool stats, bool debug, bool reset, cudaStream_t s)
+{
+    launch_settle_cfg<128, 14>(a, stats, debug, reset, s);
+}
+
+// The finish pass: a persistent grid of 8 blocks of 128 per SM over the queue.
+void launch_finish_df(const FastArgs &a, bool stats, bool debug, int sms, cudaStream_t s)
+{
     const unsigned g2 = (unsigned)(sms > 0 ? sms : 152) * 8u;
     if (a.he8) launch_finish<true>(a, stats, debug, g2, s);
     else launch_finish<false>(a, stats, debug, g2, s);
 }
 
-// A split step (settle pass + finish pass over the queue).  The settle pass
-// needs 32 registers, so it runs at 128 x 14 (56 resident warps per SM):
-// faster than at 48 or 64.  The caller provides a.queue (N entries) and
-// a.queue_count (zeroed here when reset, else by the previous finish pass
-// through its queue_next).
+// A split step (settle pass + finish pass over the queue).
 void launch_split_df(const FastArgs &a, bool stats, bool debug, int sms, bool reset, cudaStream_t s)
 {
-    launch_split_cfg<128, 14>(a, stats, debug, sms, reset, s);
+    launch_settle_df(a, stats, debug, reset, s);
+    launch_finish_df(a, stats, debug, sms, s);
 }
 
 // Launch configurations (threads per block x resident blocks per SM the

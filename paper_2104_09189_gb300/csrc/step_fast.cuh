@@ -61,7 +61,7 @@ struct FastArgs {
     uint32_t *status;
     unsigned long long *stats;
     sl_debug dbg;
-    float steep_g2;               // G^2 of SL_OPT_PRECISE (double-float kernel; 0 = off): a value
+    float steep_g2;               // G^2 of SL_OPT_PRECISE (double-float kernel; +inf = off): a value
                                   // with (v_k - v_3)^2 > G^2 den is evaluated in FP64
     int32_t keep_t0;              // strategy (a) or direct location: T^0 is never overwritten
     int32_t exclude;              // nodes whose foot leaves the square are excluded (Sec. 4)
@@ -76,7 +76,7 @@ struct FastArgs {
     // split steps: the nodes the settle pass leaves to the finish pass
     int32_t *queue;
     uint32_t *queue_count;
-    uint32_t *queue_next;         // split steps: the next step's counter, zeroed by the finish pass (or NULL)
+    uint32_t *queue_next;         // split steps: the next step's counter, zeroed by the settle pass (or NULL)
 };
 
 // config: launch configuration 0..kFastConfigs-1 (see step_fast.cu)
@@ -91,6 +91,9 @@ void launch_fast_df_c5(const FastArgs &a, bool stats, bool debug, cudaStream_t s
 void launch_fast_df_ext(const FastArgs &a, bool stats, bool debug, cudaStream_t s);
 // a split step: lean settle pass + finish pass over its queue
 void launch_split_df(const FastArgs &a, bool stats, bool debug, int sms, bool reset, cudaStream_t s);
+// its two passes on their own (reset: zero the queue counter first)
+void launch_settle_df(const FastArgs &a, bool stats, bool debug, bool reset, cudaStream_t s);
+void launch_finish_df(const FastArgs &a, bool stats, bool debug, int sms, cudaStream_t s);
 constexpr int kFastConfigs = 6;
 void launch_fast_f32(const FastArgs &a, bool stats, bool debug, int config, cudaStream_t s);
 

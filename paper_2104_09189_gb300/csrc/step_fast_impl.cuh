@@ -868,7 +868,7 @@ __device__ __forceinline__ void step_node(const FastArgs &a, int64_t i, int pi, 
     {
         const float2 *vin = (const float2 *)a.vin;
         const float2 V1 = vin[w0], V2 = vin[w1], V3 = vin[w2];
-        if (a.steep_g2 > 0.0f && !(flags & SL_NODE_CLIPPED) && steep(V1, V2, V3, den.h, a.steep_g2)) {
+        if (!(flags & SL_NODE_CLIPPED) && steep(V1, V2, V3, den.h, a.steep_g2)) {
             ((float2 *)a.vout)[i] = precise_value(a.xyd, a.g1, a.g2, P, i, w0, w1, w2, V1, V2, V3);
             flags |= SL_NODE_PRECISE;
         } else {
@@ -992,9 +992,10 @@ __device__ __forceinline__ bool settle_node(const FastArgs &a, int64_t i, int pi
         }
         degenerate = d == 1;
     }
+    const float2 val = p1_value_of(V1, V2, V3, t.n1, t.n2, t.den);
     // steep V^n: the finish pass evaluates the value in FP64 (step_node)
-    if (!clipped && a.steep_g2 > 0.0f && steep(V1, V2, V3, t.den.h, a.steep_g2)) return false;
-    ((float2 *)a.vout)[i] = p1_value_of(V1, V2, V3, t.n1, t.n2, t.den);
+    if (!clipped && steep(V1, V2, V3, t.den.h, a.steep_g2)) return false;
+    ((float2 *)a.vout)[i] = val;
     c.clipped = clipped;
     if (kDebug) {
         write_foot(a, i, X, Y);
@@ -1015,6 +1016,9 @@ __global__ void __launch_bounds__(kBlock, kMinBlocks) k_settle_df(FastArgs a)
     const bool active = i < a.N;
     NodeCounters c;
     const int pi = kKind < 0 ? block_problem(a.node_off, a.nprob, a.N, i) : 0;
+    // the next step's counter (its previous user, the finish pass of the
+    // step before, has completed)
+    if (a.queue_next && blockIdx.x == 0 && threadIdx.x == 0) *a.queue_next = 0;
     const bool queued = active && !settle_node<kDebug, kKind>(a, i, pi, c);
     // warp-aggregated append to the queue of the finish pass
     const unsigned mask = __ballot_sync(0xffffffffu, queued);
@@ -1034,7 +1038,6 @@ template <bool kStats, bool kDebug, bool kCompact>
 __global__ void __launch_bounds__(128, 8) k_finish_df(FastArgs a)
 {
     const uint32_t count = *a.queue_count;
-    if (a.queue_next && blockIdx.x == 0 && threadIdx.x == 0) *a.queue_next = 0;
     NodeCounters tot;
     uint32_t done = 0, hmax = 0;
     for (uint32_t q = blockIdx.x * blockDim.x + threadIdx.x; q < count; q += gridDim.x * blockDim.x) {

@@ -611,3 +611,31 @@ def test_compact_walk_records_give_identical_results(split):
     sl.sl_mesh_set_option(coarse.h, sl.SL_OPT_RECORDS, 1)      # too coarse: 16-byte records stay
     assert sl.sl_mesh_get_option(coarse.h, sl.SL_OPT_RECORDS) == 16
     coarse.close()
+
+
+def test_split_graph_replays_are_identical():
+    """A recorded run of split steps whose finish passes sit in conditional
+    graph nodes (taken only when a settle pass queued nodes), replayed three
+    times from the same V^0 and start triangles: the same values, T^0 and
+    statistics every time, equal to eager steps."""
+    prob = si.config("C2", M=160)
+    g = DeviceRun(prob.mesh, prob.field, prob.dt, curve=sl.SL_CURVE_HILBERT)
+    sl.sl_mesh_set_option(g.h, sl.SL_OPT_SPLIT, 1)
+    sl.sl_mesh_set_option(g.h, sl.SL_OPT_STATS, 1)
+    v0 = g.to_dev(prob.v0)
+    w = g.torch.empty_like(v0)
+    results = []
+    for use_graph in (True, True, True, False):
+        sl.sl_mesh_reset_t0(g.h)
+        sl.sl_mesh_stats(g.h, reset=True)
+        v = v0.clone()
+        sl.sl_run(g.h, g.probs, 0, 5, v, w, use_graph=use_graph)
+        t0 = g.torch.empty(prob.mesh.n_nodes, dtype=g.torch.int32, device=g.dev)
+        sl.sl_mesh_get_t0(g.h, t0)
+        results.append((v.cpu().numpy(), t0.cpu().numpy(), sl.sl_mesh_stats(g.h)))
+    g.close()
+    assert results[0][2]["walk_moves"] > 0
+    for v, t0, st in results[1:]:
+        assert np.array_equal(v, results[0][0])
+        assert np.array_equal(t0, results[0][1])
+        assert st == results[0][2]
