@@ -64,6 +64,11 @@ def parse():
                          "structured Courant grid at alpha = 5, N = 1e6..8e6")
     ap.add_argument("--study-cells", type=int, default=386,
                     help="cells per side of the study mesh (386: 1.5e5 nodes, the paper's size)")
+    ap.add_argument("--no-secondary", action="store_true",
+                    help="skip the secondary workloads (C4 FP32, C5 FP64 and FP32) of the default line")
+    ap.add_argument("--secondary-runs", type=int, default=5, help="timed runs of each secondary workload")
+    ap.add_argument("--records", type=int, choices=[0, 1], default=None,
+                    help="SL_OPT_RECORDS for the double-float kernel (default: chosen by sl_autotune)")
     return ap.parse_args()
 
 
@@ -244,10 +249,147 @@ def cpu_sample(wl, seconds, steps=2):
         budget -= dt + n_s * steps / rate
         if budget <= 0:
             break
+    # one thread on a smaller sample of the first problem (a few seconds)
+    prob = wl.probs[0]
+    om = oracle.OracleMesh(prob.mesh.xy, prob.mesh.tri)
+    n1 = int(min(prob.mesh.n_nodes, max(1000, rate / threads * 3.0)))
+    lo1 = (prob.mesh.n_nodes - n1) // 2
+    t0 = time.perf_counter()
+    om.step(prob.field.kind, prob.field.packed(), prob.dt, 0, prob.v0, lo=lo1, hi=lo1 + n1, nthreads=1, want_feet=False)
+    one = n1 / (time.perf_counter() - t0)
+    om.close()
     return {"value": done_nodes / elapsed, "unit": "node-updates/s", "cores": threads, "kind": "oracle",
             "sample": f"{steps} steps (n=0..{steps - 1}) of " + "; ".join(parts[:4]) +
                       (f" and {len(parts) - 4} more problems" if len(parts) > 4 else "") +
-                      f"; bin grid build excluded; {threads} threads"}
+                      f"; bin grid build excluded; {threads} threads",
+            "value_1_thread": one,
+            "sample_1_thread": f"step n=0 of {prob.name} nodes [{lo1}, {lo1 + n1}), 1 thread"}
+
+
+def oracle_reference(probs, n_steps):
+    """V^{n_steps} of the FP64 oracle for every problem (original numbering),
+    its threads over the machine's host cores."""
+    import oracle
+    out = []
+    for p in probs:
+        om = oracle.OracleMesh(p.mesh.xy, p.mesh.tri)
+        out.append(om.run(p.field.kind, p.field.packed(), p.dt, 0, n_steps, p.v0))
+        om.close()
+    return out
+
+
+def error_vs_oracle(probs, got, want):
+    """Errors of a GPU result against the FP64 oracle: max and L2 (RMS) of
+    the absolute error, and the normwise relative error max|dV| / max|V^0|
+    of the worst problem (P1 is a convex combination, so max|V^0| bounds
+    every value of a run)."""
+    off = np.cumsum([0] + [p.mesh.n_nodes for p in probs])
+    err = np.abs(got - np.concatenate(want))
+    rel = max(float(err[off[k]:off[k + 1]].max() / max(np.abs(p.v0).max(), 1e-300)) for k, p in enumerate(probs))
+    return {"max_abs": float(err.max()), "l2_rms": float(np.sqrt((err ** 2).mean())), "max_rel_to_max_v0": rel,
+            "reference": "CPU oracle (FP64), same problems and steps"}
+
+
+class _Args:
+    """The subset of the command-line arguments build_workload reads."""
+
+    def __init__(self, config, precision, curve="hilbert"):
+        self.config, self.precision, self.cells, self.curve = config, precision, None, curve
+
+
+def secondary_workload(sl, torch, config, precision, runs, warmup, oracle_cache):
+    """One of the benchmark spec's systems patterns measured on its own workload
+    (C4: FP32 filtered precision on the 16.8M-node mesh; C5: the 256-problem
+    batch, FP64 and FP32): the same timed path as the headline (autotuned,
+    one CUDA graph per run, runs queued back to back, CUDA events), the
+    result's error against the FP64 oracle, the exact-stage (fallback) test
+    count and the speed-up over the plain FP64 GPU kernel on the same
+    problems."""
+    wl = build_workload(_Args(config, precision))
+    S, N = wl.n_steps, wl.nodes
+    prec = sl.SL_FP64 if precision == "fp64" else sl.SL_FP32
+    no, to, xy, tri = sl.pack_meshes([(p.mesh.xy, p.mesh.tri) for p in wl.probs])
+    probs = sl.problems([(p.field.kind, p.dt, p.field.packed()) for p in wl.probs])
+    v0_all = np.concatenate([p.v0 for p in wl.probs])
+
+    def handle(pr):
+        h = sl.sl_mesh_create(no, to, xy, tri, precision=pr, seed=wl.probs[0].seed)
+        lp, _ = sl.sl_mesh_reorder(h, sl.SL_CURVE_HILBERT)
+        perm = lp.astype(np.int64) + np.repeat(no[:-1], np.diff(no))
+        return h, perm
+
+    h, perm = handle(prec)
+    vt = torch.float64 if prec == sl.SL_FP64 else torch.float32
+    v0 = torch.tensor(v0_all[perm], dtype=vt, device="cuda")
+    v, w = v0.clone(), torch.empty_like(v0)
+    tune = sl.sl_autotune(h, probs, 3, v, w)
+    sl.sl_mesh_set_option(h, sl.SL_OPT_STATS, 1)
+    sl.sl_mesh_stats(h, reset=True)
+    sl.sl_mesh_reset_t0(h)
+    v.copy_(v0)
+    sl.sl_run(h, probs, 0, S, v, w, use_graph=True)
+    stats = sl.sl_mesh_stats(h, reset=True)
+    got = np.empty(N)
+    got[perm] = v.double().cpu().numpy()
+    sl.sl_mesh_set_option(h, sl.SL_OPT_STATS, 0)
+    for _ in range(warmup):
+        sl.sl_mesh_reset_t0(h)
+        sl.sl_run(h, probs, 0, S, v, w, use_graph=True)
+    stream = torch.cuda.current_stream()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    sl.sl_mesh_set_option(h, sl.SL_OPT_ASYNC, 1)
+    e0.record(stream)
+    for _ in range(runs):
+        sl.sl_mesh_reset_t0(h)
+        sl.sl_run(h, probs, 0, S, v, w, use_graph=True, stats=False)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    sl.sl_mesh_set_option(h, sl.SL_OPT_ASYNC, 0)
+    sl.sl_mesh_status(h)
+    ms = e0.elapsed_time(e1) / runs
+    sl.sl_mesh_destroy(h)
+    # the plain FP64 kernel on the same problems (FP64 mesh), one run
+    hp, pp = handle(sl.SL_FP64)
+    sl.sl_mesh_set_option(hp, sl.SL_OPT_KERNEL, 1)
+    a64 = torch.tensor(v0_all[pp], dtype=torch.float64, device="cuda")
+    b64 = torch.empty_like(a64)
+    sl.sl_run(hp, probs, 0, S, a64, b64, use_graph=True)
+    sl.sl_mesh_reset_t0(hp)
+    a64.copy_(torch.tensor(v0_all[pp], dtype=torch.float64, device="cuda"))
+    torch.cuda.synchronize()
+    e0.record(stream)
+    sl.sl_run(hp, probs, 0, S, a64, b64, use_graph=True)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    plain_ms = e0.elapsed_time(e1)
+    sl.sl_mesh_destroy(hp)
+    del v, w, v0, a64, b64
+    torch.cuda.empty_cache()
+    key = config
+    if key not in oracle_cache:
+        t0 = time.perf_counter()
+        oracle_cache[key] = (oracle_reference(wl.probs, S), time.perf_counter() - t0)
+    want, oracle_s = oracle_cache[key]
+    err = error_vs_oracle(wl.probs, got, want)
+    bpn = BYTES_PER_NODE[precision]
+    peaks, peak_src = measured_peaks()
+    value = N * S / (ms / 1e3)
+    achieved = bpn * N * S / (ms / 1e3) / 1e9
+    return {
+        "workload": wl.description, "nodes": N, "steps_per_run": S, "precision": precision,
+        "value": value, "unit": "node-updates/s", "ms_per_run": ms, "runs": runs,
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peaks.get("hbm_gbs", 6800.0), "unit": "GB/s",
+                     "frac": achieved / peaks.get("hbm_gbs", 6800.0), "algorithmic_bytes_per_node": bpn,
+                     "peak_source": peak_src},
+        "error_vs_fp64_oracle": err,
+        "walk": {"mean_hops_per_node_update": stats["walk_moves"] / max(1, stats["node_updates"]),
+                 "exact_tests": stats["exact_tests"], "filter2_tests": stats["filter2_tests"],
+                 "fallback_tests": stats["exact_tests"] + stats["filter2_tests"], "clipped": stats["clipped"]},
+        "plain_fp64": {"value": N * S / (plain_ms / 1e3), "ms_per_run": plain_ms},
+        "speedup_vs_plain_fp64": plain_ms / ms,
+        "autotune": tune, "oracle_seconds": oracle_s,
+    }
 
 
 def run_reference(args):
@@ -474,6 +616,8 @@ def main():
         tune = sl.sl_autotune(h, probs, 3, v, w)
     if args.split is not None:
         sl.sl_mesh_set_option(h, sl.SL_OPT_SPLIT, args.split)
+    if args.records is not None and prec == sl.SL_FP64:
+        sl.sl_mesh_set_option(h, sl.SL_OPT_RECORDS, args.records)
     split = (args.split if args.split is not None else (tune or {}).get("split", 0)) if prec == sl.SL_FP64 else 0
     setup_s = time.perf_counter() - t_setup
 
@@ -548,38 +692,15 @@ def main():
         gather = {"probe_ms": probe_ms, "later_step_ms": rest_ms, "frac_of_gather_bound": probe_ms / rest_ms,
                   "kernel": "k_gather_probe (node pair and start state, three vertex pairs, three values, one write)"}
 
+    # FP32 workloads: the error of the result against the FP64 oracle
     fp32_check = None
-    if wl.precision == "fp32" and not args.no_plain:
-        # the same workload on the FP64 mesh: the fast FP64 path (within 1e-12
-        # of the oracle) gives the error of the FP32 result; the plain FP64
-        # kernel gives the speed-up baseline
-        v32 = np.empty(N)
+    if wl.precision == "fp32" and not args.no_cpu and rank == 0 and args.cells is None:
         sl.sl_mesh_reset_t0(h)
         vv = v0.clone()
-        sl.sl_run(h, probs, 0, S, vv, w, use_graph=False)
-        v32[perm] = vv.double().cpu().numpy()
-        h64 = sl.sl_mesh_create(no, to, xy, tri, precision=sl.SL_FP64, seed=wl.probs[0].seed)
-        lp64, _ = sl.sl_mesh_reorder(h64, curve)
-        perm64 = lp64.astype(np.int64) + np.repeat(no[:-1], np.diff(no))
-        a64 = torch.tensor(v0_all[perm64], dtype=torch.float64, device="cuda")
-        b64 = torch.empty_like(a64)
-        sl.sl_run(h64, probs, 0, S, a64, b64, use_graph=True)
-        v64 = np.empty(N)
-        v64[perm64] = a64.cpu().numpy()
-        err = np.abs(v32 - v64)
-        sl.sl_mesh_set_option(h64, sl.SL_OPT_KERNEL, 1)
-        a64.copy_(torch.tensor(v0_all[perm64], dtype=torch.float64, device="cuda"))
-
-        def plain_run():
-            sl.sl_mesh_reset_t0(h64)
-            sl.sl_run(h64, probs, 0, S, a64, b64, use_graph=True)
-
-        plain_run()
-        tp = timed(lambda: [plain_run() for _ in range(2)]) / 1e3
-        sl.sl_mesh_destroy(h64)
-        fp32_check = {"max_err_vs_fp64": float(err.max()), "l2_err_vs_fp64": float(np.sqrt((err ** 2).mean())),
-                      "reference": "fast FP64 GPU path on the FP64 mesh (itself within 1e-12 of the CPU oracle)",
-                      "plain_fp64_node_updates_per_s": N * S * 2 / tp}
+        sl.sl_run(h, probs, 0, S, vv, w, use_graph=True)
+        got = np.empty(N)
+        got[perm] = vv.double().cpu().numpy()
+        fp32_check = error_vs_oracle(wl.probs, got, oracle_reference(wl.probs, S))
 
     plain = None
     if wl.precision == "fp64" and not args.no_plain and args.kernel != 1:
@@ -596,6 +717,15 @@ def main():
     bpn = BYTES_PER_NODE[wl.precision]
     peaks, peak_src = measured_peaks()
     achieved_gbs = bpn * N / launch_s / 1e9
+    hbm = peaks.get("hbm_gbs", 6800.0)
+
+    def phase(ms):
+        a = bpn * N / (ms / 1e3) / 1e9
+        return {"ms": ms, "achieved": a, "frac": a / hbm}
+
+    phase_roofline = {"first_step": phase(first_ms), "later_steps": phase(rest_ms),
+                      "note": "eager launches after the timed region; the first step walks from the initial "
+                              "incident triangles, the later ones from the previous foot triangles"}
 
     # end to end through the C ABI with host buffers (pinned)
     e2e = None
@@ -621,6 +751,17 @@ def main():
         cpu = cpu_sample(wl, args.cpu_seconds)
 
     sl.sl_mesh_destroy(h)
+    del v, w, v0
+    torch.cuda.empty_cache()
+
+    # the precision and batching patterns on their own workloads
+    secondary = None
+    if (rank == 0 and world == 1 and not args.no_secondary and args.config == "C3" and args.cells is None
+            and args.kernel != 1):
+        cache = {}
+        secondary = [secondary_workload(sl, torch, c, p, args.secondary_runs, 2, cache)
+                     for c, p in (("C4", "fp32"), ("C5", "fp64"), ("C5", "fp32"))]
+
     if rank != 0:
         if dist:
             dist.destroy_process_group()
@@ -633,6 +774,9 @@ def main():
         "steps": args.steps,
         "warmup": args.warmup,
         "ms_per_step": 1e3 * elapsed / args.steps,
+        "step_definition": f"one benchmark step = one run of the whole path: {S} SL steps of the workload "
+                           "(sl_run, one CUDA graph) from the initial start triangles",
+        "ms_per_sl_step": 1e3 * elapsed / (args.steps * S),
         "higher_is_better": True,
         "scaling": "weak",
         "vs_baseline": None,
@@ -650,7 +794,8 @@ def main():
                                 ("k_step_fast_df" + (" (later steps split: k_settle_df + k_finish_df)" if split else "")
                                  if prec == sl.SL_FP64 else "k_step_fast_f32"))
                                + " (one step over all nodes; duration = timed region / steps)",
-                     "launch_ms": launch_s * 1e3},
+                     "launch_ms": launch_s * 1e3,
+                     "phases": phase_roofline},
         "cpu_baseline": cpu,
         "e2e": e2e,
         "gpu_launches": args.steps * (launches_per_run(S, prec == sl.SL_FP64 and args.kernel != 1)
@@ -658,16 +803,17 @@ def main():
         "clocks": clocks,
         "walk": {"first_run_mean_hops_per_node_update": stats["walk_moves"] / max(1, stats["node_updates"]),
                  "max_hops": stats["max_moves"], "exact_tests": stats["exact_tests"],
-                 "clipped": stats["clipped"], "fallbacks": stats["fallbacks"]},
+                 "filter2_tests": stats["filter2_tests"], "clipped": stats["clipped"],
+                 "fallbacks": stats["fallbacks"]},
         "setup_s": setup_s,
         "phases": phases,
         "per_run_ms": {"min": min(per_run), "median": statistics.median(per_run), "max": max(per_run)},
         "gather_probe": gather,
         "autotune": tune,
         "plain_fp64": plain,
-        "speedup_vs_plain_fp64": ((value / world) / plain["value"] if plain else
-                                  ((value / world) / fp32_check["plain_fp64_node_updates_per_s"] if fp32_check else None)),
-        "fp32_check": fp32_check,
+        "speedup_vs_plain_fp64": (value / world) / plain["value"] if plain else None,
+        "fp32_error_vs_fp64_oracle": fp32_check,
+        "secondary": secondary,
     }
     print(json.dumps(line), flush=True)
     if dist:

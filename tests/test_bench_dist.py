@@ -9,6 +9,7 @@ import socket
 import subprocess
 import sys
 
+import numpy as np
 import pytest
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
@@ -84,3 +85,22 @@ def test_reference_arm_runs_on_rank_zero_only():
                        cwd=ROOT)
     assert p.returncode == 0, p.stderr
     assert p.stdout.strip() == ""
+
+
+def test_error_vs_oracle_scales_by_each_problems_initial_max():
+    """bench.error_vs_oracle: absolute max and RMS over all nodes; the
+    relative figure divides each problem's error by its own max |V^0|."""
+    import bench
+
+    class P:
+        def __init__(self, n, scale):
+            self.mesh = type("M", (), {"n_nodes": n})()
+            self.v0 = np.full(n, scale)
+
+    probs = [P(3, 2.0), P(2, 0.5)]
+    want = [np.zeros(3), np.zeros(2)]
+    got = np.array([0.0, 1e-3, 0.0, 0.0, 2e-3])
+    e = bench.error_vs_oracle(probs, got, want)
+    assert e["max_abs"] == 2e-3
+    assert abs(e["l2_rms"] - np.sqrt((1e-6 + 4e-6) / 5)) < 1e-15
+    assert abs(e["max_rel_to_max_v0"] - 4e-3) < 1e-15
