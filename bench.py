@@ -48,7 +48,9 @@ def parse():
                     help="precision of the batch workload C5 (default fp64)")
     ap.add_argument("--cells", type=int, default=None, help="override cells per side (smaller test runs)")
     ap.add_argument("--kernel", type=int, default=0, help="SL_OPT_KERNEL (0 auto, 1 plain FP64, 2 tiled)")
-    ap.add_argument("--curve", default="hilbert", choices=["none", "hilbert", "morton"])
+    ap.add_argument("--curve", default="auto", choices=["auto", "none", "hilbert", "morton"],
+                    help="node / triangle numbering: auto = chosen by sl_autotune_layout (as given, Hilbert, "
+                         "Morton), else that curve")
     ap.add_argument("--config-id", type=int, default=None, help="SL_OPT_CONFIG launch configuration (0..5); "
                     "default: chosen by sl_autotune")
     ap.add_argument("--no-e2e", action="store_true")
@@ -169,6 +171,7 @@ class Workload:
 
 
 def build_workload(args):
+    """The workload of a configuration (curve=auto until the layout is tuned)."""
     if args.config == "C5":
         prec = args.precision or "fp64"
         probs = si.batch_config(256, precision=prec)
@@ -293,7 +296,7 @@ def error_vs_oracle(probs, got, want):
 class _Args:
     """The subset of the command-line arguments build_workload reads."""
 
-    def __init__(self, config, precision, curve="hilbert"):
+    def __init__(self, config, precision, curve="auto"):
         self.config, self.precision, self.cells, self.curve = config, precision, None, curve
 
 
@@ -318,11 +321,13 @@ def secondary_workload(sl, torch, config, precision, runs, warmup, oracle_cache)
         perm = lp.astype(np.int64) + np.repeat(no[:-1], np.diff(no))
         return h, perm
 
-    h, perm = handle(prec)
+    h = sl.sl_mesh_create(no, to, xy, tri, precision=prec, seed=wl.probs[0].seed)
     vt = torch.float64 if prec == sl.SL_FP64 else torch.float32
-    v0 = torch.tensor(v0_all[perm], dtype=vt, device="cuda")
-    v, w = v0.clone(), torch.empty_like(v0)
-    tune = sl.sl_autotune(h, probs, 3, v, w)
+    v, w = torch.tensor(v0_all, dtype=vt, device="cuda"), torch.empty(N, dtype=vt, device="cuda")
+    lp, _, tune = sl.sl_autotune_layout(h, probs, 3, v, w)
+    wl.description = wl.description.replace("curve=auto", f"curve={tune['curve']} (autotuned)")
+    perm = lp.astype(np.int64) + np.repeat(no[:-1], np.diff(no))
+    v0 = v.clone()
     sl.sl_mesh_set_option(h, sl.SL_OPT_STATS, 1)
     sl.sl_mesh_stats(h, reset=True)
     sl.sl_mesh_reset_t0(h)
@@ -596,9 +601,7 @@ def main():
     t_setup = time.perf_counter()
     no, to, xy, tri = sl.pack_meshes([(p.mesh.xy, p.mesh.tri) for p in wl.probs])
     h = sl.sl_mesh_create(no, to, xy, tri, precision=prec, seed=wl.probs[0].seed)
-    curve = {"none": sl.SL_CURVE_NONE, "hilbert": sl.SL_CURVE_HILBERT, "morton": sl.SL_CURVE_MORTON}[args.curve]
-    lperm, _ = sl.sl_mesh_reorder(h, curve)
-    perm = lperm.astype(np.int64) + np.repeat(no[:-1], np.diff(no))     # global new -> old
+    tuning = args.config_id is None and args.kernel != 1
     if args.kernel:
         sl.sl_mesh_set_option(h, sl.SL_OPT_KERNEL, args.kernel)
     if args.config_id is not None:
@@ -607,12 +610,23 @@ def main():
     probs = sl.problems([(p.field.kind, p.dt, p.field.packed()) for p in wl.probs])
     vt = torch.float64 if prec == sl.SL_FP64 else torch.float32
     v0_all = np.concatenate([p.v0 for p in wl.probs])
+    tune = None
+    if args.curve == "auto" and tuning:
+        # numbering, then launch configurations, by measurement
+        v = torch.tensor(v0_all, dtype=vt, device="cuda")
+        w = torch.empty_like(v)
+        lperm, _, tune = sl.sl_autotune_layout(h, probs, 3, v, w)
+        wl.description = wl.description.replace("curve=auto", f"curve={tune['curve']} (autotuned)")
+    else:
+        curve = {"none": sl.SL_CURVE_NONE, "hilbert": sl.SL_CURVE_HILBERT, "morton": sl.SL_CURVE_MORTON}[
+            "hilbert" if args.curve == "auto" else args.curve]
+        lperm, _ = sl.sl_mesh_reorder(h, curve)
+    perm = lperm.astype(np.int64) + np.repeat(no[:-1], np.diff(no))     # global new -> old
     v0 = torch.tensor(v0_all[perm], dtype=vt, device="cuda")
     v = v0.clone()
     w = torch.empty_like(v)
     stream = torch.cuda.current_stream()
-    tune = None
-    if args.config_id is None and args.kernel != 1:
+    if tuning and tune is None:
         tune = sl.sl_autotune(h, probs, 3, v, w)
     if args.split is not None:
         sl.sl_mesh_set_option(h, sl.SL_OPT_SPLIT, args.split)

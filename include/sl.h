@@ -333,6 +333,10 @@ typedef struct {
     int32_t records;                      /* chosen SL_OPT_RECORDS */
     float compact_first_ms;               /* the chosen configurations with 8-byte records: first */
     float compact_rest_ms;                /* ... and later steps (split if chosen); -1: not eligible */
+    int32_t curve;                        /* sl_autotune_layout: chosen numbering (SL_CURVE_NONE = as
+                                             given at the call), else -1 */
+    float curve_ms[3];                    /* sl_autotune_layout: first step + probe_steps later steps
+                                             per sl_curve value (-1: not tried) */
 } sl_tune;
 
 /*
@@ -353,6 +357,26 @@ typedef struct {
  */
 sl_status sl_autotune(sl_mesh *m, const sl_problem *probs, int32_t probe_steps, void *v, void *v_scratch,
                       sl_tune *out, void *stream);
+
+/*
+ * sl_autotune_layout -- choose the numbering of nodes and triangles by
+ * measurement, then tune as sl_autotune.  For each layout in `curves` (bit c
+ * set = try sl_curve c; SL_CURVE_NONE = the numbering at the call), the mesh
+ * is renumbered (per problem, as sl_mesh_reorder) and one step from the
+ * initial start triangles plus `probe_steps` later steps are timed in the
+ * current launch configuration; the fastest layout is kept.  Nodes that are
+ * neighbours in space are neighbours in memory along a space-filling curve
+ * (Hilbert or Morton), which decides how many sectors a warp's gathers
+ * touch.  v (device, N values of V^0 in the numbering at the call) is
+ * permuted in place to the kept numbering; node_perm / tri_perm (host, N /
+ * Nt int32, or NULL) receive new -> old indices relative to the numbering
+ * at the call, local to each problem.  T^0 follows the renumbering.  out
+ * receives sl_autotune's results and the curve fields.  Synchronises;
+ * allocates temporary device buffers.  No counterpart in the paper (its
+ * meshes keep the Triangle library's numbering).
+ */
+sl_status sl_autotune_layout(sl_mesh *m, const sl_problem *probs, int32_t probe_steps, int32_t curves, void *v,
+                             void *v_scratch, int32_t *node_perm, int32_t *tri_perm, sl_tune *out, void *stream);
 
 /*
  * sl_probe_gather -- the memory-system ceiling of a later step (FP64

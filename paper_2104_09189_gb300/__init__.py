@@ -25,6 +25,7 @@ __all__ = [
     "sl_mesh_set_t0", "sl_mesh_reset_t0", "sl_mesh_status", "sl_mesh_stats", "sl_mesh_set_option", "sl_mesh_info",
     "sl_mesh_export", "sl_mesh_destroy", "sl_last_error", "library", "EXPORTED", "sl_step_noalloc",
     "SL_NOALLOC_MAX_NODES", "SL_NOALLOC_MAX_PROBLEMS", "sl_autotune", "sl_probe_gather", "sl_mesh_get_option",
+    "sl_autotune_layout",
 ]
 
 SL_OK, SL_E_ARG, SL_E_MESH, SL_E_NOMEM, SL_E_CUDA, SL_E_WALK_LIMIT, SL_E_STATE = range(7)
@@ -49,7 +50,7 @@ _STATUS_NAMES = {0: "SL_OK", 1: "SL_E_ARG", 2: "SL_E_MESH", 3: "SL_E_NOMEM", 4: 
 EXPORTED = ("sl_mesh_create", "sl_mesh_validate", "sl_mesh_reorder", "sl_step", "sl_run", "sl_run_host", "sl_mesh_get_t0",
             "sl_mesh_set_t0", "sl_mesh_reset_t0", "sl_mesh_status", "sl_mesh_stats", "sl_mesh_set_option", "sl_mesh_info",
             "sl_mesh_export", "sl_mesh_destroy", "sl_last_error", "sl_step_noalloc", "sl_autotune",
-            "sl_probe_gather", "sl_mesh_get_option")
+            "sl_probe_gather", "sl_mesh_get_option", "sl_autotune_layout")
 
 
 class SLError(RuntimeError):
@@ -73,7 +74,7 @@ class sl_tune(ctypes.Structure):
     _fields_ = [("config_first", ctypes.c_int32), ("config_rest", ctypes.c_int32), ("n_configs", ctypes.c_int32),
                 ("split", ctypes.c_int32), ("first_ms", ctypes.c_float * 8), ("rest_ms", ctypes.c_float * 8),
                 ("split_ms", ctypes.c_float * 8), ("records", ctypes.c_int32), ("compact_first_ms", ctypes.c_float),
-                ("compact_rest_ms", ctypes.c_float)]
+                ("compact_rest_ms", ctypes.c_float), ("curve", ctypes.c_int32), ("curve_ms", ctypes.c_float * 3)]
 
 
 class sl_stats(ctypes.Structure):
@@ -115,6 +116,7 @@ def library():
         "sl_mesh_export": [P, P, P, P],
         "sl_step_noalloc": [P, P, I64, P, P, P],
         "sl_autotune": [P, P, I32, P, P, P, P],
+        "sl_autotune_layout": [P, P, I32, I32, P, P, P, P, P, P],
         "sl_probe_gather": [P, P, P, I32, P, P],
     }
     for name, args in sig.items():
@@ -330,16 +332,40 @@ def sl_probe_gather(h, v, v_scratch, reps=10, stream=None):
     return float(ms.value)
 
 
+def _tune_dict(t):
+    n = t.n_configs
+    d = {"config_first": t.config_first, "config_rest": t.config_rest, "split": t.split,
+         "first_ms": [round(float(x), 4) for x in list(t.first_ms)[:n]],
+         "rest_ms": [round(float(x), 4) for x in list(t.rest_ms)[:n]],
+         "split_ms": [round(float(x), 4) for x in list(t.split_ms)[:n] if x >= 0],
+         "records": t.records, "compact_first_ms": round(float(t.compact_first_ms), 4),
+         "compact_rest_ms": round(float(t.compact_rest_ms), 4)}
+    if t.curve >= 0:
+        d["curve"] = {0: "as given", 1: "hilbert", 2: "morton"}[t.curve]
+        d["curve_ms"] = {name: round(float(x), 4) for name, x in zip(("as given", "hilbert", "morton"), t.curve_ms)
+                         if x >= 0}
+    return d
+
+
 def sl_autotune(h, probs, probe_steps, v, v_scratch, stream=None):
     """Time every launch configuration of the fast kernels on this mesh and
     set the fastest (see sl.h); returns the measurements."""
     t = sl_tune()
     _check(library().sl_autotune(h, probs, int(probe_steps), _ptr(v), _ptr(v_scratch), ctypes.byref(t),
                                  _stream(stream)))
-    n = t.n_configs
-    return {"config_first": t.config_first, "config_rest": t.config_rest, "split": t.split,
-            "first_ms": [round(float(x), 4) for x in list(t.first_ms)[:n]],
-            "rest_ms": [round(float(x), 4) for x in list(t.rest_ms)[:n]],
-            "split_ms": [round(float(x), 4) for x in list(t.split_ms)[:n] if x >= 0],
-            "records": t.records, "compact_first_ms": round(float(t.compact_first_ms), 4),
-            "compact_rest_ms": round(float(t.compact_rest_ms), 4)}
+    return _tune_dict(t)
+
+
+def sl_autotune_layout(h, probs, probe_steps, v, v_scratch, curves=0b111, stream=None):
+    """Choose the numbering (curves: bit c = try sl_curve c, SL_CURVE_NONE =
+    as given) and then the launch configurations by measurement; v (device
+    V^0) is permuted in place.  Returns (node_perm, tri_perm, measurements),
+    the permutations new -> old relative to the numbering at the call, local
+    to each problem."""
+    info = sl_mesh_info(h)
+    node_perm = np.empty(info["n_nodes"], dtype=np.int32)
+    tri_perm = np.empty(info["n_tri"], dtype=np.int32)
+    t = sl_tune()
+    _check(library().sl_autotune_layout(h, probs, int(probe_steps), int(curves), _ptr(v), _ptr(v_scratch),
+                                        _ptr(node_perm), _ptr(tri_perm), ctypes.byref(t), _stream(stream)))
+    return node_perm, tri_perm, _tune_dict(t)

@@ -893,6 +893,127 @@ extern "C" void sl_mesh_destroy(sl_mesh *m)
     delete m;
 }
 
+// After a renumbering: the recorded graph is stale, and the start tables of
+// strategies 2 and 3 follow the triangle numbering.
+static sl_status renumbered(sl_mesh *m)
+{
+    if (m->graph.exec) cudaGraphExecDestroy((cudaGraphExec_t)m->graph.exec);
+    m->graph = GraphCache();
+    sl_status st = upload_arrays(m);
+    if (st == SL_OK && (m->opt_strategy == 2 || m->opt_strategy == 3))
+        st = sl_mesh_set_option(m, SL_OPT_STRATEGY, m->opt_strategy);
+    return st;
+}
+
+extern "C" sl_status sl_autotune_layout(sl_mesh *m, const sl_problem *probs, int32_t probe_steps, int32_t curves,
+                                        void *v, void *v_scratch, int32_t *node_perm, int32_t *tri_perm, sl_tune *out,
+                                        void *stream)
+{
+    if (!m || !probs || !v || !v_scratch || !out) return fail(SL_E_ARG, "sl_autotune_layout: NULL argument");
+    if (probe_steps < 1 || probe_steps > 1000) return fail(SL_E_ARG, "sl_autotune_layout: probe_steps must be in [1, 1000]");
+    if (curves < 1 || curves > 7) return fail(SL_E_ARG, "sl_autotune_layout: curves must be a non-empty set of sl_curve bits");
+    if (!use_fast(m)) return fail(SL_E_STATE, "sl_autotune_layout: the plain kernel has no launch configurations");
+    sl_status st = check_device(m);
+    if (st != SL_OK) return st;
+    cudaStream_t s = (cudaStream_t)stream;
+    const int64_t N = m->N, Nt = m->Nt;
+    const size_t esz = m->precision == SL_FP64 ? sizeof(double) : sizeof(float);
+    SL_CUDA(cudaStreamSynchronize(s));
+    std::vector<uint8_t> v0(esz * N), vl(esz * N);
+    SL_CUDA(cudaMemcpy(v0.data(), v, esz * N, cudaMemcpyDeviceToHost));
+    if (m->stepped) SL_CUDA(cudaMemcpy(m->t0.data(), m->d.t0, sizeof(int32_t) * N, cudaMemcpyDeviceToHost));
+    // composite new -> old permutations (local) from the numbering at the call
+    std::vector<int32_t> cn(N), ct(Nt), pn(N), pt(Nt);
+    for (int32_t p = 0; p < m->n_problems; ++p) {
+        for (int64_t i = m->node_off[p]; i < m->node_off[p + 1]; ++i) cn[i] = (int32_t)(i - m->node_off[p]);
+        for (int64_t j = m->tri_off[p]; j < m->tri_off[p + 1]; ++j) ct[j] = (int32_t)(j - m->tri_off[p]);
+    }
+    auto compose = [&]() {   // cn <- cn o pn (pn: new -> old relative to the current numbering)
+        for (int32_t p = 0; p < m->n_problems; ++p) {
+            const int64_t n0 = m->node_off[p], t0 = m->tri_off[p];
+            std::vector<int32_t> a(cn.begin() + n0, cn.begin() + m->node_off[p + 1]);
+            for (int64_t i = n0; i < m->node_off[p + 1]; ++i) cn[i] = a[pn[i]];
+            std::vector<int32_t> b(ct.begin() + t0, ct.begin() + m->tri_off[p + 1]);
+            for (int64_t j = t0; j < m->tri_off[p + 1]; ++j) ct[j] = b[pt[j]];
+        }
+    };
+    auto load_v = [&]() -> sl_status {   // V^0 in the current numbering
+        for (int32_t p = 0; p < m->n_problems; ++p)
+            for (int64_t i = m->node_off[p]; i < m->node_off[p + 1]; ++i)
+                std::memcpy(&vl[esz * i], &v0[esz * (m->node_off[p] + cn[i])], esz);
+        SL_CUDA(cudaMemcpy(v, vl.data(), esz * N, cudaMemcpyHostToDevice));
+        return SL_OK;
+    };
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    SL_CUDA(cudaEventCreate(&e0));
+    SL_CUDA(cudaEventCreate(&e1));
+    auto time_layout = [&](float &ms) -> sl_status {
+        sl_status r = load_v();
+        if (r == SL_OK) r = sl_mesh_reset_t0(m, s);
+        if (r != SL_OK) return r;
+        SL_CUDA(cudaEventRecord(e0, s));
+        r = run_steps(m, probs, 0, 1, v, v_scratch, 0, s);
+        if (r != SL_OK) return r;
+        m->t0_initial = false;
+        r = run_steps(m, probs, 1, probe_steps, v, v_scratch, 0, s);
+        if (r != SL_OK) return r;
+        SL_CUDA(cudaEventRecord(e1, s));
+        SL_CUDA(cudaEventSynchronize(e1));
+        SL_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+        return SL_OK;
+    };
+    float times[3] = {-1.0f, -1.0f, -1.0f};
+    int32_t best = -1, current = SL_CURVE_NONE;
+    st = SL_OK;
+    bool warmed = false;
+    for (int32_t c = SL_CURVE_NONE; c <= SL_CURVE_MORTON && st == SL_OK; ++c) {
+        if (!(curves >> c & 1)) continue;
+        if (c != SL_CURVE_NONE) {
+            st = reorder_host(m, c, pn.data(), pt.data());
+            if (st == SL_OK) st = renumbered(m);
+            if (st != SL_OK) break;
+            compose();
+            current = c;
+        }
+        if (!warmed) {   // lazy module loading and first-touch costs, untimed
+            float ms = 0.f;
+            st = time_layout(ms);
+            warmed = true;
+            if (st != SL_OK) break;
+        }
+        st = time_layout(times[c]);
+        if (st == SL_OK && (best < 0 || times[c] < times[best])) best = c;
+    }
+    if (st == SL_OK && best >= 0 && best != current) {
+        if (best == SL_CURVE_NONE) {
+            // back to the numbering at the call: the inverse of the composite
+            for (int32_t p = 0; p < m->n_problems; ++p) {
+                for (int64_t i = m->node_off[p]; i < m->node_off[p + 1]; ++i)
+                    pn[m->node_off[p] + cn[i]] = (int32_t)(i - m->node_off[p]);
+                for (int64_t j = m->tri_off[p]; j < m->tri_off[p + 1]; ++j)
+                    pt[m->tri_off[p] + ct[j]] = (int32_t)(j - m->tri_off[p]);
+            }
+            st = permute_host(m, pn.data(), pt.data());
+        } else {
+            st = reorder_host(m, best, pn.data(), pt.data());
+        }
+        if (st == SL_OK) st = renumbered(m);
+        if (st == SL_OK) compose();
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (st == SL_OK) st = load_v();
+    if (st == SL_OK) st = sl_mesh_reset_t0(m, s);
+    if (st == SL_OK) SL_CUDA(cudaStreamSynchronize(s));
+    if (node_perm) std::copy(cn.begin(), cn.end(), node_perm);
+    if (tri_perm) std::copy(ct.begin(), ct.end(), tri_perm);
+    if (st != SL_OK) return st;
+    st = sl_autotune(m, probs, probe_steps, v, v_scratch, out, stream);
+    out->curve = best;
+    for (int k = 0; k < 3; ++k) out->curve_ms[k] = times[k];
+    return st;
+}
+
 extern "C" sl_status sl_probe_gather(sl_mesh *m, const void *v, void *v_scratch, int32_t reps, float *ms_out,
                                      void *stream)
 {
@@ -943,6 +1064,8 @@ extern "C" sl_status sl_autotune(sl_mesh *m, const sl_problem *probs, int32_t pr
     std::memset(out, 0, sizeof(*out));
     for (int k = 0; k < SL_TUNE_MAX_CONFIGS; ++k) out->first_ms[k] = out->rest_ms[k] = out->split_ms[k] = -1.0f;
     out->compact_first_ms = out->compact_rest_ms = -1.0f;
+    out->curve = -1;
+    out->curve_ms[0] = out->curve_ms[1] = out->curve_ms[2] = -1.0f;
     auto cleanup = [&]() {
         if (v_save) cudaFree(v_save);
         if (t_save) cudaFree(t_save);

@@ -205,26 +205,66 @@ static uint64_t morton_key(uint32_t x, uint32_t y)
     return d;
 }
 
-sl_status reorder_host(sl_mesh *m, int32_t curve, int32_t *node_perm, int32_t *tri_perm)
+// Renumber every problem by explicit permutations, new -> old and local to
+// the problem (node_perm: N entries, tri_perm: Nt entries): coordinates,
+// triangles, neighbours and both T^0 lists follow.
+sl_status permute_host(sl_mesh *m, const int32_t *node_perm, const int32_t *tri_perm)
 {
-    if (curve == SL_CURVE_NONE) {
-        if (node_perm)
-            for (int32_t p = 0; p < m->n_problems; ++p)
-                for (int64_t i = m->node_off[p]; i < m->node_off[p + 1]; ++i) node_perm[i] = (int32_t)(i - m->node_off[p]);
-        if (tri_perm)
-            for (int32_t p = 0; p < m->n_problems; ++p)
-                for (int64_t j = m->tri_off[p]; j < m->tri_off[p + 1]; ++j) tri_perm[j] = (int32_t)(j - m->tri_off[p]);
-        return SL_OK;
-    }
-    auto key = [curve](double x, double y) {
-        uint32_t qx = quantize(x), qy = quantize(y);
-        return curve == SL_CURVE_HILBERT ? hilbert_key(qx, qy) : morton_key(qx, qy);
-    };
     std::vector<double> xy2(m->xy.size());
     std::vector<int32_t> tri2(m->tri.size()), nbr2(m->nbr.size()), t02(m->t0.size()), t0i2(m->t0.size());
     for (int32_t p = 0; p < m->n_problems; ++p) {
         const int64_t n0 = m->node_off[p], n = m->node_off[p + 1] - n0;
         const int64_t j0 = m->tri_off[p], nt = m->tri_off[p + 1] - j0;
+        const double *xy = m->xy.data() + 2 * n0;
+        const int32_t *tri = m->tri.data() + 3 * j0;
+        std::vector<int32_t> inv_n(n, -1), inv_t(nt, -1);
+        for (int64_t a = 0; a < n; ++a) {
+            const int32_t old = node_perm[n0 + a];
+            if (old < 0 || old >= n || inv_n[old] >= 0) return fail(SL_E_ARG, "not a permutation of a problem's nodes");
+            inv_n[old] = (int32_t)a;
+        }
+        for (int64_t a = 0; a < nt; ++a) {
+            const int32_t old = tri_perm[j0 + a];
+            if (old < 0 || old >= nt || inv_t[old] >= 0) return fail(SL_E_ARG, "not a permutation of a problem's triangles");
+            inv_t[old] = (int32_t)a;
+        }
+        for (int64_t a = 0; a < n; ++a) {
+            const int64_t old = node_perm[n0 + a];
+            xy2[2 * (n0 + a)] = xy[2 * old];
+            xy2[2 * (n0 + a) + 1] = xy[2 * old + 1];
+            t02[n0 + a] = (int32_t)j0 + inv_t[m->t0[n0 + old] - (int32_t)j0];
+            t0i2[n0 + a] = (int32_t)j0 + inv_t[m->t0_init[n0 + old] - (int32_t)j0];
+        }
+        for (int64_t a = 0; a < nt; ++a) {
+            const int64_t old = tri_perm[j0 + a];
+            for (int k = 0; k < 3; ++k) {
+                tri2[3 * (j0 + a) + k] = inv_n[tri[3 * old + k]];
+                const int32_t nb = m->nbr[3 * (j0 + old) + k];
+                nbr2[3 * (j0 + a) + k] = nb < 0 ? -1 : inv_t[nb];
+            }
+        }
+    }
+    m->xy.swap(xy2);
+    m->tri.swap(tri2);
+    m->nbr.swap(nbr2);
+    m->t0.swap(t02);
+    m->t0_init.swap(t0i2);
+    return SL_OK;
+}
+
+sl_status reorder_host(sl_mesh *m, int32_t curve, int32_t *node_perm, int32_t *tri_perm)
+{
+    std::vector<int32_t> np(m->N), tp(m->Nt);
+    for (int32_t p = 0; p < m->n_problems; ++p) {
+        const int64_t n0 = m->node_off[p], n = m->node_off[p + 1] - n0;
+        const int64_t j0 = m->tri_off[p], nt = m->tri_off[p + 1] - j0;
+        for (int64_t i = 0; i < n; ++i) np[n0 + i] = (int32_t)i;
+        for (int64_t j = 0; j < nt; ++j) tp[j0 + j] = (int32_t)j;
+        if (curve == SL_CURVE_NONE) continue;
+        auto key = [curve](double x, double y) {
+            uint32_t qx = quantize(x), qy = quantize(y);
+            return curve == SL_CURVE_HILBERT ? hilbert_key(qx, qy) : morton_key(qx, qy);
+        };
         const double *xy = m->xy.data() + 2 * n0;
         const int32_t *tri = m->tri.data() + 3 * j0;
         std::vector<std::pair<uint64_t, int32_t>> nk(n), tk(nt);
@@ -241,33 +281,13 @@ sl_status reorder_host(sl_mesh *m, int32_t curve, int32_t *node_perm, int32_t *t
         });
         std::sort(nk.begin(), nk.end());
         std::sort(tk.begin(), tk.end());
-        std::vector<int32_t> inv_n(n), inv_t(nt);
-        for (int64_t a = 0; a < n; ++a) inv_n[nk[a].second] = (int32_t)a;
-        for (int64_t a = 0; a < nt; ++a) inv_t[tk[a].second] = (int32_t)a;
-        for (int64_t a = 0; a < n; ++a) {
-            int64_t old = nk[a].second;
-            xy2[2 * (n0 + a)] = xy[2 * old];
-            xy2[2 * (n0 + a) + 1] = xy[2 * old + 1];
-            t02[n0 + a] = (int32_t)j0 + inv_t[m->t0[n0 + old] - (int32_t)j0];
-            t0i2[n0 + a] = (int32_t)j0 + inv_t[m->t0_init[n0 + old] - (int32_t)j0];
-            if (node_perm) node_perm[n0 + a] = (int32_t)old;
-        }
-        for (int64_t a = 0; a < nt; ++a) {
-            int64_t old = tk[a].second;
-            for (int k = 0; k < 3; ++k) {
-                tri2[3 * (j0 + a) + k] = inv_n[tri[3 * old + k]];
-                int32_t nb = m->nbr[3 * (j0 + old) + k];
-                nbr2[3 * (j0 + a) + k] = nb < 0 ? -1 : inv_t[nb];
-            }
-            if (tri_perm) tri_perm[j0 + a] = (int32_t)old;
-        }
+        for (int64_t a = 0; a < n; ++a) np[n0 + a] = nk[a].second;
+        for (int64_t a = 0; a < nt; ++a) tp[j0 + a] = tk[a].second;
     }
-    m->xy.swap(xy2);
-    m->tri.swap(tri2);
-    m->nbr.swap(nbr2);
-    m->t0.swap(t02);
-    m->t0_init.swap(t0i2);
-    return SL_OK;
+    if (node_perm) std::copy(np.begin(), np.end(), node_perm);
+    if (tri_perm) std::copy(tp.begin(), tp.end(), tri_perm);
+    if (curve == SL_CURVE_NONE) return SL_OK;
+    return permute_host(m, np.data(), tp.data());
 }
 
 }  // namespace sl

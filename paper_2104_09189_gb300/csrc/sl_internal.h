@@ -124,6 +124,8 @@ std::vector<double> field_table_key(int32_t n_problems, const sl_problem *probs,
 // host side (mesh_host.cpp)
 sl_status build_and_validate(sl_mesh *m, const int32_t *nbr_in);
 sl_status reorder_host(sl_mesh *m, int32_t curve, int32_t *node_perm, int32_t *tri_perm);
+// renumber by explicit new -> old permutations, local to each problem
+sl_status permute_host(sl_mesh *m, const int32_t *node_perm, const int32_t *tri_perm);
 // device side (api_device.cu)
 sl_status upload(sl_mesh *m);
 // (re)build the half-edge walk records in the form opt_records and the mesh allow

@@ -639,3 +639,35 @@ def test_split_graph_replays_are_identical():
         assert np.array_equal(v, results[0][0])
         assert np.array_equal(t0, results[0][1])
         assert st == results[0][2]
+
+
+def test_layout_autotuner_renumbers_consistently():
+    """sl_autotune_layout on a shuffled mesh: it times the numbering as
+    given, Hilbert and Morton, keeps the fastest, permutes V^0 in place and
+    returns the permutation; a run afterwards, mapped back through it, is
+    bitwise a run on an untuned copy of the mesh in its own numbering."""
+    import torch
+    from sl_inputs.meshes import shuffled
+    prob = si.config("C2", M=160)
+    mesh = shuffled(prob.mesh, 17)
+    v0 = si.gaussian(mesh.xy, 0.5, 0.75, 0.05)
+    no, to, xy, tri = sl.pack_meshes([(mesh.xy, mesh.tri)])
+    pr = sl.problems([(prob.field.kind, prob.dt, prob.field.packed())])
+    h = sl.sl_mesh_create(no, to, xy, tri, seed=4)
+    v = torch.tensor(v0, dtype=torch.float64, device="cuda")
+    w = torch.empty_like(v)
+    node_perm, tri_perm, tune = sl.sl_autotune_layout(h, pr, 2, v, w)
+    assert tune["curve"] in ("as given", "hilbert", "morton")
+    assert set(tune["curve_ms"]) == {"as given", "hilbert", "morton"}
+    assert np.array_equal(v.cpu().numpy(), v0[node_perm])
+    assert np.array_equal(np.sort(node_perm), np.arange(mesh.n_nodes))
+    sl.sl_run(h, pr, 0, 4, v, w)
+    got = np.empty(mesh.n_nodes)
+    got[node_perm] = v.cpu().numpy()
+    sl.sl_mesh_destroy(h)
+    h2 = sl.sl_mesh_create(no, to, xy, tri, seed=4)
+    v2 = torch.tensor(v0, dtype=torch.float64, device="cuda")
+    sl.sl_run(h2, pr, 0, 4, v2, torch.empty_like(v2))
+    want = v2.cpu().numpy()
+    sl.sl_mesh_destroy(h2)
+    assert np.array_equal(got, want)
