@@ -173,7 +173,7 @@ typedef enum {
                                 and the P1 value are evaluated again in FP64 from the double
                                 coordinates, as the plain kernel does; the located triangle is
                                 the same.  Scale G with the magnitude of V. */
-    SL_OPT_RECORDS = 13      /* half-edge walk records of the double-float kernel: 0 = 16-byte
+    SL_OPT_RECORDS = 13,     /* half-edge walk records of the double-float kernel: 0 = 16-byte
                                 records (default); 1 = 8-byte records where the mesh allows them
                                 (every vertex across an edge within 2^17 grid units of 2^-24 of
                                 the vertex it replaces, i.e. triangles narrower than about 2^-7,
@@ -182,6 +182,12 @@ typedef enum {
                                 wavefronts for a warp's 32 scattered lanes, but more instructions
                                 to unpack; sl_autotune measures both.  Results are identical.
                                 Setting it rebuilds the records (synchronises). */
+    SL_OPT_L2_WINDOW = 14    /* 0 = off (default); 1 = in runs recorded as a CUDA graph, the
+                                kernels mark the half-edge walk records as persisting in L2 (an
+                                access-policy window of at most the device's window size, hit ratio
+                                scaled to its persisting capacity, which this sets as the
+                                context's persisting L2 limit; restored, and the persisting lines
+                                reset, when the option goes back to 0 or the mesh is destroyed) */
 } sl_option;
 
 /*

@@ -100,6 +100,9 @@ struct sl_mesh {
     int32_t opt_async = 0;            // 1 = sl_run without stats returns unsynchronised
     int32_t opt_precise = 32;         // gradient bound of the FP64 value path (0 = off)
     int32_t opt_records = 0;          // 0 = 16-byte walk records, 1 = compact records where they fit
+    int32_t opt_l2 = 0;               // 1 = persisting L2 window on the walk records in recorded graphs
+    bool l2_limit_set = false;        // the context's persisting L2 limit was raised (l2_limit_prev saved)
+    size_t l2_limit_prev = 0;
     bool t0_initial = true;           // T^0 holds the initial start triangles
     int32_t sms = 0;                  // multiprocessors of the device
     bool stepped = false;
@@ -130,6 +133,8 @@ sl_status permute_host(sl_mesh *m, const int32_t *node_perm, const int32_t *tri_
 sl_status upload(sl_mesh *m);
 // (re)build the half-edge walk records in the form opt_records and the mesh allow
 sl_status build_walk_records(sl_mesh *m);
+// give back the persisting L2 lines and the context's previous limit
+void release_l2_window(sl_mesh *m);
 // the fast kernels' constants of step n of one problem, validated as sl_step validates them
 sl_status fast_constants_one(const sl_problem &q, int64_t n, int32_t p, FastProb &f);
 // the arguments of a fast-kernel step of the whole mesh: the step's constants
