@@ -128,6 +128,7 @@ static sl_status upload_arrays(sl_mesh *m)
 {
     DeviceMesh &d = m->d;
     const int64_t N = m->N, Nt = m->Nt;
+    m->table_key.clear();   // the field node tables follow the numbering: rebuilt at the next step
     if (m->precision == SL_FP64) {
         SL_CUDA(cudaMemcpy(d.xy, m->xy.data(), sizeof(double) * 2 * N, cudaMemcpyHostToDevice));
         // (grid, remainder) float pairs of the coordinates for the double-float
@@ -143,7 +144,6 @@ static sl_status upload_arrays(sl_mesh *m)
         std::vector<float2> hx(N);
         for (int64_t i = 0; i < N; ++i) hx[i] = make_float2(q[i].x, q[i].y);
         SL_CUDA(cudaMemcpy(d.xyh, hx.data(), sizeof(float2) * N, cudaMemcpyHostToDevice));
-        m->table_key.clear();   // node tables follow the numbering
     } else {
         std::vector<float> f(2 * N);
         for (int64_t q = 0; q < 2 * N; ++q) f[q] = (float)m->xy[q];
@@ -346,8 +346,13 @@ FastArgs make_fast_args(const sl_mesh *m, const FastProb *fp, const void *vin, v
     a.t0v = (int4 *)m->d.t0v;
     a.vin = vin;
     a.vout = vout;
-    a.g1 = (const float4 *)m->d.g1;
-    a.g2 = (const float4 *)m->d.g2;
+    if (m->precision == SL_FP64) {
+        a.g1 = (const float4 *)m->d.g1;
+        a.g2 = (const float4 *)m->d.g2;
+    } else {
+        a.g1f = (const float2 *)m->d.g1;
+        a.g2f = (const float2 *)m->d.g2;
+    }
     a.probs = fp;
     if (fh && m->n_problems == 1) {
         a.prob0 = fh[0];
@@ -446,8 +451,10 @@ static sl_status ensure_tables(sl_mesh *m, const sl_problem *probs, cudaStream_t
     const std::vector<double> key = field_table_key(m->n_problems, probs, need1, need2);
     if (!need1) return SL_OK;
     if (key == m->table_key && m->d.g1 && (!need2 || m->d.g2)) return SL_OK;
-    if (!m->d.g1) SL_CUDA(cudaMalloc(&m->d.g1, sizeof(float4) * m->N));
-    if (need2 && !m->d.g2) SL_CUDA(cudaMalloc(&m->d.g2, sizeof(float4) * m->N));
+    // FP64 meshes keep (hi, lo) pairs, FP32 meshes the values rounded to float
+    const size_t tsz = m->precision == SL_FP64 ? sizeof(float4) : sizeof(float2);
+    if (!m->d.g1) SL_CUDA(cudaMalloc(&m->d.g1, tsz * m->N));
+    if (need2 && !m->d.g2) SL_CUDA(cudaMalloc(&m->d.g2, tsz * m->N));
     if (!m->d.tparams) SL_CUDA(cudaMalloc(&m->d.tparams, sizeof(double) * key.size()));
     SL_CUDA(cudaStreamSynchronize(s));
     SL_CUDA(cudaMemcpy(m->d.tparams, key.data(), sizeof(double) * key.size(), cudaMemcpyHostToDevice));
@@ -458,8 +465,15 @@ static sl_status ensure_tables(sl_mesh *m, const sl_problem *probs, cudaStream_t
     ta.nprob = m->n_problems;
     ta.N = m->N;
     ta.params = m->d.tparams;
-    ta.g1 = (float4 *)m->d.g1;
-    ta.g2 = (float4 *)m->d.g2;
+    ta.g1 = ta.g2 = nullptr;
+    ta.g1f = ta.g2f = nullptr;
+    if (m->precision == SL_FP64) {
+        ta.g1 = (float4 *)m->d.g1;
+        ta.g2 = (float4 *)m->d.g2;
+    } else {
+        ta.g1f = (float2 *)m->d.g1;
+        ta.g2f = (float2 *)m->d.g2;
+    }
     launch_field_tables(ta, s);
     SL_CUDA(cudaGetLastError());
     SL_CUDA(cudaStreamSynchronize(s));

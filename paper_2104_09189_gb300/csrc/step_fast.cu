@@ -268,6 +268,8 @@ __global__ void k_field_tables(FieldTableArgs a)
         }
         if (a.g1) a.g1[i] = pack_df2(g1x, g1y);
         if (a.g2) a.g2[i] = pack_df2(g2x, g2y);
+        if (a.g1f) a.g1f[i] = make_float2(__double2float_rn(g1x), __double2float_rn(g1y));
+        if (a.g2f) a.g2f[i] = make_float2(__double2float_rn(g2x), __double2float_rn(g2y));
     }
 }
 

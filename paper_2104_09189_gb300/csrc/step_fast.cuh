@@ -50,7 +50,8 @@ struct FastArgs {
                                   // step with t0
     const void *vin;              // FP64: float2 (hi, lo) values; FP32: float values
     void *vout;
-    const float4 *g1, *g2;        // field tables (hi, lo) per node, or NULL
+    const float4 *g1, *g2;        // field tables (hi, lo) per node (FP64 meshes), or NULL
+    const float2 *g1f, *g2f;      // field tables rounded to float (FP32 meshes), or NULL
     const FastProb *probs;
     FastProb prob0;               // single: a copy of probs[0] (kernel parameter space)
     int32_t single;               // one problem, prob0 valid
@@ -113,7 +114,8 @@ struct FieldTableArgs {
     int32_t nprob;
     int64_t N;
     const double *params;         // nprob x (kind, p[SL_NPARAMS]) as 1 + SL_NPARAMS doubles
-    float4 *g1, *g2;
+    float4 *g1, *g2;              // FP64 meshes: (hi, lo) pairs
+    float2 *g1f, *g2f;            // FP32 meshes: the values rounded to float
 };
 void launch_field_tables(const FieldTableArgs &a, cudaStream_t s);
 

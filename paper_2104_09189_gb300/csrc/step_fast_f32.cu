@@ -51,14 +51,14 @@ __device__ __forceinline__ void foot_f32(const FastProb &P, const FastArgs &a, i
         Y = __fsub_rn(y, __fmul_rn(c0, __fsub_rn(x, c1)));
         break;
     case SL_FIELD_SWIRL: {
-        const float4 g = a.g1[i];
+        const float2 g = a.g1f[i];
         X = __fsub_rn(x, __fmul_rn(c0, g.x));
         Y = __fsub_rn(y, __fmul_rn(c0, g.y));
         break;
     }
     case SL_FIELD_PAPER:
     case SL_FIELD_FOURIER8: {
-        const float4 g = a.g1[i], q = a.g2[i];
+        const float2 g = a.g1f[i], q = a.g2f[i];
         X = __fsub_rn(x, __fadd_rn(__fmul_rn(c0, g.x), __fmul_rn(c1, q.x)));
         Y = __fsub_rn(y, __fadd_rn(__fmul_rn(c0, g.y), __fmul_rn(c1, q.y)));
         break;
@@ -157,27 +157,32 @@ __global__ void __launch_bounds__(kBlock, kMinBlocks) k_step_fast_f32(FastArgs a
                 e1 = 3 * j0 + (s0 == 2 ? 0 : s0 + 1);
                 e2 = 3 * j0 + (s0 == 0 ? 2 : s0 - 1);
             }
-            float2 A = a.xyf[tq.y], B = a.xyf[tq.z], C = a.xyf[tq.w];
+            // the vertices relative to the foot, a_k = W_k - X, rounded once
+            float a0x, a0y, a1x, a1y, a2x, a2y;
+            {
+                const float2 A = a.xyf[tq.y], B = a.xyf[tq.z], C = a.xyf[tq.w];
+                a0x = __fsub_rn(A.x, X);
+                a0y = __fsub_rn(A.y, Y);
+                a1x = __fsub_rn(B.x, X);
+                a1y = __fsub_rn(B.y, Y);
+                a2x = __fsub_rn(C.x, X);
+                a2y = __fsub_rn(C.y, Y);
+            }
             bool moved = false;
             const uint32_t cap = (uint32_t)a.walk_cap;
             bool found = false;
             int s1 = 0, s2 = 0, s3 = 0;
-            float o1 = 0.0f, o2 = 0.0f, dn = 1.0f;
+            float o1 = 0.0f, o2 = 0.0f, o3 = 0.0f;
             for (;;) {
-                const float ax = __fsub_rn(A.x, C.x), ay = __fsub_rn(A.y, C.y);
-                const float bx = __fsub_rn(B.x, C.x), by = __fsub_rn(B.y, C.y);
-                const float xx = __fsub_rn(X, C.x), xy = __fsub_rn(Y, C.y);
-                float eb1, eb2, ed;
-                o1 = cross_f32(xx, xy, bx, by, eb1);    // orient(W1, W2, X): theta of W0 * den
-                o2 = cross_f32(ax, ay, xx, xy, eb2);    // orient(W2, W0, X): theta of W1 * den
-                dn = cross_f32(ax, ay, bx, by, ed);     // orient(W0, W1, W2) > 0
-                float o3 = 1.0f;
+                float eb1, eb2;
+                o1 = cross_f32(a1x, a1y, a2x, a2y, eb1);    // orient(W1, W2, X): theta of W0 * den
+                o2 = cross_f32(a2x, a2y, a0x, a0y, eb2);    // orient(W2, W0, X): theta of W1 * den
                 s1 = o1 > eb1 ? 1 : (o1 < -eb1 ? -1 : 2);
                 s2 = o2 > eb2 ? 1 : (o2 < -eb2 ? -1 : 2);
                 s3 = 1;
                 if (!moved) {
-                    o3 = __fsub_rn(__fsub_rn(dn, o1), o2);
-                    const float eb3 = ed + eb1 + eb2 + 0x1p-23f * (fabsf(dn) + fabsf(o1) + fabsf(o2));
+                    float eb3;
+                    o3 = cross_f32(a0x, a0y, a1x, a1y, eb3);    // orient(W0, W1, X): theta of W2 * den
                     s3 = o3 > eb3 ? 1 : (o3 < -eb3 ? -1 : 2);
                 }
                 if (s1 == 2 || s2 == 2 || s3 == 2) {
@@ -199,15 +204,20 @@ __global__ void __launch_bounds__(kBlock, kMinBlocks) k_step_fast_f32(FastArgs a
                 if (s1 == 2 || s2 == 2 || s3 == 2) {
                     // the foot on a vertex (e.g. a node whose field vanishes): the
                     // two edges through that vertex have orientation exactly 0
-                    const bool onA = X == A.x && Y == A.y, onB = X == B.x && Y == B.y, onC = X == C.x && Y == C.y;
+                    // (a difference of two floats is zero only when they are equal)
+                    const bool onA = a0x == 0.0f && a0y == 0.0f, onB = a1x == 0.0f && a1y == 0.0f;
+                    const bool onC = a2x == 0.0f && a2y == 0.0f;
                     if (s1 == 2 && (onB || onC)) s1 = 0;
                     if (s2 == 2 && (onC || onA)) s2 = 0;
                     if (s3 == 2 && (onA || onB)) s3 = 0;
                 }
                 if (s1 == 2 || s2 == 2 || s3 == 2) {
-                    // double predicate on the floats promoted exactly (the
-                    // barrier keeps the conversions of the loop-invariant foot
-                    // inside this rare branch)
+                    // double predicate on the float coordinates promoted exactly:
+                    // the vertices reloaded by slot (W0 is slot e0 - 3 j, W1 slot
+                    // e1 - 3 j) in this rare branch; the barrier keeps the
+                    // conversions of the loop-invariant foot inside it
+                    const int32_t jj = tri_of_f32(e0), sa = e0 - 3 * jj, sb = e1 - 3 * jj, sc = 3 - sa - sb;
+                    const float2 A = a.xyf[a.tv[sa][jj]], B = a.xyf[a.tv[sb][jj]], C = a.xyf[a.tv[sc][jj]];
                     float xb = X, yb = Y;
                     asm volatile("" : "+f"(xb), "+f"(yb));
                     const double Xd = xb, Yd = yb;
@@ -259,35 +269,46 @@ __global__ void __launch_bounds__(kBlock, kMinBlocks) k_step_fast_f32(FastArgs a
                 const float4 R = __ldg(&a.he[k == 0 ? e0 : (k == 1 ? e1 : e2)]);
                 if (isnan(R.x)) break;    // a boundary edge: not for a foot inside a valid mesh
                 // the next triangle: (W2, W1, Q), (W0, W2, Q) or (W1, W0, Q)
-                if (k == 0) A = C;
-                else if (k == 1) B = C;
-                else {
-                    const float2 t = A;
-                    A = B;
-                    B = t;
+                if (k == 0) {
+                    a0x = a2x;
+                    a0y = a2y;
+                } else if (k == 1) {
+                    a1x = a2x;
+                    a1y = a2y;
+                } else {
+                    const float tx = a0x, ty = a0y;
+                    a0x = a1x;
+                    a0y = a1y;
+                    a1x = tx;
+                    a1y = ty;
                 }
-                C = make_float2(R.x, R.y);
+                a2x = __fsub_rn(R.x, X);
+                a2y = __fsub_rn(R.y, Y);
                 e0 = __float_as_int(R.z);
                 e1 = __float_as_int(R.w);
                 moved = true;
                 ++hops;
                 // lean hops: the two exits of the entered triangle, taken while
-                // one is certainly negative (the same stage-A bound); the full
-                // test above decides where no edge is certainly negative
+                // one is certainly negative (the same stage-A bound, on the
+                // vertices relative to the foot); the full test above decides
+                // where no edge is certainly negative
                 while (hops < cap) {
-                    const float ax = __fsub_rn(A.x, C.x), ay = __fsub_rn(A.y, C.y);
-                    const float bx = __fsub_rn(B.x, C.x), by = __fsub_rn(B.y, C.y);
-                    const float xx = __fsub_rn(X, C.x), xy = __fsub_rn(Y, C.y);
                     float eb1, eb2;
-                    const float q1 = cross_f32(xx, xy, bx, by, eb1);
-                    const float q2 = cross_f32(ax, ay, xx, xy, eb2);
+                    const float q1 = cross_f32(a1x, a1y, a2x, a2y, eb1);
+                    const float q2 = cross_f32(a2x, a2y, a0x, a0y, eb2);
                     const bool c1 = q1 < -eb1, c2 = q2 < -eb2 && !(c1 && q1 <= q2);
                     if (!(c1 || c2)) break;
                     const float4 Q = __ldg(&a.he[c2 ? e1 : e0]);
                     if (isnan(Q.x)) break;    // a boundary edge: not for a foot inside a valid mesh
-                    if (c2) B = C;
-                    else A = C;
-                    C = make_float2(Q.x, Q.y);
+                    if (c2) {
+                        a1x = a2x;
+                        a1y = a2y;
+                    } else {
+                        a0x = a2x;
+                        a0y = a2y;
+                    }
+                    a2x = __fsub_rn(Q.x, X);
+                    a2y = __fsub_rn(Q.y, Y);
                     e0 = __float_as_int(Q.z);
                     e1 = __float_as_int(Q.w);
                     ++hops;
@@ -300,7 +321,9 @@ __global__ void __launch_bounds__(kBlock, kMinBlocks) k_step_fast_f32(FastArgs a
             if (s1 == 0 || s2 == 0 || s3 == 0) flags |= SL_NODE_DEGENERATE;
 
             // the located triangle in slot order: its vertex ids and the
-            // numerators of Eq. 6 relative to its vertex 2
+            // numerators of Eq. 6, orient(V1, V2, X), orient(V2, V0, X) and
+            // orient(V0, V1, X), on the vertices relative to the foot (their
+            // sum is twice the triangle's area)
             int w0 = tq.y, w1 = tq.z, w2 = tq.w;
             const int32_t j = tri_of_f32(e0);
             if (moved) {
@@ -309,16 +332,15 @@ __global__ void __launch_bounds__(kBlock, kMinBlocks) k_step_fast_f32(FastArgs a
                 w2 = a.tv[2][j];
                 // (W0, W1, W2) = slots (s, s+1, s+2)
                 const int32_t s = e0 - 3 * j;
-                const float2 V0 = s == 0 ? A : (s == 1 ? C : B), V1 = s == 0 ? B : (s == 1 ? A : C);
-                const float2 V2 = s == 0 ? C : (s == 1 ? B : A);
-                const float ax = __fsub_rn(V0.x, V2.x), ay = __fsub_rn(V0.y, V2.y);
-                const float bx = __fsub_rn(V1.x, V2.x), by = __fsub_rn(V1.y, V2.y);
-                const float xx = __fsub_rn(X, V2.x), xy = __fsub_rn(Y, V2.y);
+                const float v0x = s == 0 ? a0x : (s == 1 ? a2x : a1x), v0y = s == 0 ? a0y : (s == 1 ? a2y : a1y);
+                const float v1x = s == 0 ? a1x : (s == 1 ? a0x : a2x), v1y = s == 0 ? a1y : (s == 1 ? a0y : a2y);
+                const float v2x = s == 0 ? a2x : (s == 1 ? a1x : a0x), v2y = s == 0 ? a2y : (s == 1 ? a1y : a0y);
                 float eb;
-                o1 = cross_f32(xx, xy, bx, by, eb);
-                o2 = cross_f32(ax, ay, xx, xy, eb);
-                dn = cross_f32(ax, ay, bx, by, eb);
+                o1 = cross_f32(v1x, v1y, v2x, v2y, eb);
+                o2 = cross_f32(v2x, v2y, v0x, v0y, eb);
+                o3 = cross_f32(v0x, v0y, v1x, v1y, eb);
             }
+            const float dn = __fadd_rn(__fadd_rn(o1, o2), o3);
             // theta of W0, W1 (Eq. 6) and the P1 value (Remark 1) in float
             const float r = __frcp_rn(dn);
             const float th1 = __fmul_rn(o1, r), th2 = __fmul_rn(o2, r);

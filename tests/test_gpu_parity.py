@@ -641,32 +641,36 @@ def test_split_graph_replays_are_identical():
         assert st == results[0][2]
 
 
-def test_layout_autotuner_renumbers_consistently():
-    """sl_autotune_layout on a shuffled mesh: it times the numbering as
-    given, Hilbert and Morton, keeps the fastest, permutes V^0 in place and
-    returns the permutation; a run afterwards, mapped back through it, is
-    bitwise a run on an untuned copy of the mesh in its own numbering."""
+@pytest.mark.parametrize("precision", [sl.SL_FP64, sl.SL_FP32], ids=["fp64", "fp32"])
+def test_layout_autotuner_renumbers_consistently(precision):
+    """sl_autotune_layout on a shuffled mesh with the swirl field (whose node
+    tables are built by the timed steps and must follow every renumbering):
+    it times the numbering as given, Hilbert and Morton, keeps the fastest,
+    permutes V^0 in place and returns the permutation; a run afterwards,
+    mapped back through it, is bitwise a run on an untuned copy of the mesh
+    in its own numbering."""
     import torch
     from sl_inputs.meshes import shuffled
     prob = si.config("C2", M=160)
     mesh = shuffled(prob.mesh, 17)
     v0 = si.gaussian(mesh.xy, 0.5, 0.75, 0.05)
+    dt = torch.float64 if precision == sl.SL_FP64 else torch.float32
     no, to, xy, tri = sl.pack_meshes([(mesh.xy, mesh.tri)])
     pr = sl.problems([(prob.field.kind, prob.dt, prob.field.packed())])
-    h = sl.sl_mesh_create(no, to, xy, tri, seed=4)
-    v = torch.tensor(v0, dtype=torch.float64, device="cuda")
+    h = sl.sl_mesh_create(no, to, xy, tri, precision=precision, seed=4)
+    v = torch.tensor(v0, dtype=dt, device="cuda")
     w = torch.empty_like(v)
     node_perm, tri_perm, tune = sl.sl_autotune_layout(h, pr, 2, v, w)
     assert tune["curve"] in ("as given", "hilbert", "morton")
     assert set(tune["curve_ms"]) == {"as given", "hilbert", "morton"}
-    assert np.array_equal(v.cpu().numpy(), v0[node_perm])
+    assert np.array_equal(v.cpu().numpy(), v0.astype(v.cpu().numpy().dtype)[node_perm])
     assert np.array_equal(np.sort(node_perm), np.arange(mesh.n_nodes))
     sl.sl_run(h, pr, 0, 4, v, w)
     got = np.empty(mesh.n_nodes)
     got[node_perm] = v.cpu().numpy()
     sl.sl_mesh_destroy(h)
-    h2 = sl.sl_mesh_create(no, to, xy, tri, seed=4)
-    v2 = torch.tensor(v0, dtype=torch.float64, device="cuda")
+    h2 = sl.sl_mesh_create(no, to, xy, tri, precision=precision, seed=4)
+    v2 = torch.tensor(v0, dtype=dt, device="cuda")
     sl.sl_run(h2, pr, 0, 4, v2, torch.empty_like(v2))
     want = v2.cpu().numpy()
     sl.sl_mesh_destroy(h2)
