@@ -71,6 +71,8 @@ def parse():
     ap.add_argument("--secondary-runs", type=int, default=5, help="timed runs of each secondary workload")
     ap.add_argument("--l2-window", type=int, choices=[0, 1], default=0,
                     help="SL_OPT_L2_WINDOW: walk records persisting in L2 during graph runs")
+    ap.add_argument("--pdl", type=int, choices=[0, 1], default=1,
+                    help="SL_OPT_PDL: step kernels launched with programmatic stream serialization")
     ap.add_argument("--records", type=int, choices=[0, 1], default=None,
                     help="SL_OPT_RECORDS for the double-float kernel (default: chosen by sl_autotune)")
     return ap.parse_args()
@@ -636,6 +638,8 @@ def main():
         sl.sl_mesh_set_option(h, sl.SL_OPT_RECORDS, args.records)
     if args.l2_window:
         sl.sl_mesh_set_option(h, sl.SL_OPT_L2_WINDOW, 1)
+    if not args.pdl:
+        sl.sl_mesh_set_option(h, sl.SL_OPT_PDL, 0)
     split = (args.split if args.split is not None else (tune or {}).get("split", 0)) if prec == sl.SL_FP64 else 0
     setup_s = time.perf_counter() - t_setup
 

@@ -175,19 +175,25 @@ typedef enum {
                                 the same.  Scale G with the magnitude of V. */
     SL_OPT_RECORDS = 13,     /* half-edge walk records of the double-float kernel: 0 = 16-byte
                                 records (default); 1 = 8-byte records where the mesh allows them
-                                (every vertex across an edge within 2^17 grid units of 2^-24 of
-                                the vertex it replaces, i.e. triangles narrower than about 2^-7,
+                                (every edge shorter than 2^17 grid units of 2^-24, about 2^-7,
                                 and at most 44.7 M triangles), else 16-byte ones.  An 8-byte
                                 record is one 64-bit gather per hop, which takes fewer L1
                                 wavefronts for a warp's 32 scattered lanes, but more instructions
                                 to unpack; sl_autotune measures both.  Results are identical.
                                 Setting it rebuilds the records (synchronises). */
-    SL_OPT_L2_WINDOW = 14    /* 0 = off (default); 1 = in runs recorded as a CUDA graph, the
+    SL_OPT_L2_WINDOW = 14,   /* 0 = off (default); 1 = in runs recorded as a CUDA graph, the
                                 kernels mark the half-edge walk records as persisting in L2 (an
                                 access-policy window of at most the device's window size, hit ratio
                                 scaled to its persisting capacity, which this sets as the
                                 context's persisting L2 limit; restored, and the persisting lines
                                 reset, when the option goes back to 0 or the mesh is destroyed) */
+    SL_OPT_PDL = 15          /* 1 = (default) in a sequence of steps (sl_run, sl_run_host), every
+                                step kernel that follows a step kernel of the same sequence is
+                                launched with programmatic stream serialization: its blocks may
+                                start while the kernel before it finishes, compute their feet
+                                (which need only the node coordinates and the field), and wait
+                                for that kernel before they read T^0 or V^n.  0 = plain launches.
+                                Results are identical.  No counterpart in the paper. */
 } sl_option;
 
 /*

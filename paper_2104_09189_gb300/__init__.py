@@ -18,7 +18,7 @@ __all__ = [
     "SL_OK", "SL_E_ARG", "SL_E_MESH", "SL_E_NOMEM", "SL_E_CUDA", "SL_E_WALK_LIMIT", "SL_E_STATE",
     "SL_FP64", "SL_FP32", "SL_CURVE_NONE", "SL_CURVE_HILBERT", "SL_CURVE_MORTON",
     "SL_OPT_STATS", "SL_OPT_WALK_CAP", "SL_OPT_KERNEL", "SL_OPT_BLOCK", "SL_OPT_CONFIG",
-    "SL_OPT_CONFIG_FIRST", "SL_OPT_STRATEGY", "SL_OPT_OUTSIDE", "SL_OPT_SPLIT", "SL_OPT_ASYNC", "SL_OPT_PRECISE", "SL_OPT_RECORDS", "SL_OPT_L2_WINDOW",
+    "SL_OPT_CONFIG_FIRST", "SL_OPT_STRATEGY", "SL_OPT_OUTSIDE", "SL_OPT_SPLIT", "SL_OPT_ASYNC", "SL_OPT_PRECISE", "SL_OPT_RECORDS", "SL_OPT_L2_WINDOW", "SL_OPT_PDL",
     "SL_NODE_CLIPPED", "SL_NODE_DEGENERATE", "SL_NODE_EXACT", "SL_NODE_FALLBACK", "SL_NODE_WALK_LIMIT",
     "SL_NODE_RANGE", "SL_NODE_EXCLUDED", "SL_NODE_PRECISE", "SLError", "sl_problem", "problems", "pack_meshes",
     "sl_mesh_create", "sl_mesh_validate", "sl_mesh_reorder", "sl_step", "sl_run", "sl_run_host", "sl_mesh_get_t0",
@@ -36,6 +36,7 @@ SL_OPT_CONFIG = 5
 SL_OPT_CONFIG_FIRST, SL_OPT_STRATEGY, SL_OPT_OUTSIDE, SL_OPT_SPLIT, SL_OPT_ASYNC, SL_OPT_PRECISE = 7, 8, 9, 10, 11, 12
 SL_OPT_RECORDS = 13
 SL_OPT_L2_WINDOW = 14
+SL_OPT_PDL = 15
 SL_NODE_CLIPPED, SL_NODE_DEGENERATE, SL_NODE_EXACT, SL_NODE_FALLBACK, SL_NODE_WALK_LIMIT, SL_NODE_RANGE = (
     1, 2, 4, 8, 16, 32)
 SL_NODE_EXCLUDED = 64

@@ -530,10 +530,14 @@ static bool split_step(const sl_mesh *m, bool initial)
 // steps (NULL: a sequence of one).  Split steps use the two queue counters
 // in turn; the first one of a sequence zeroes its counter, and each settle
 // pass zeroes the counter of the next step, so the steps between need no
-// memset.
+// memset.  after_step: the last launch on the stream is a step kernel of
+// the same sequence, so with SL_OPT_PDL this step's kernels are launched
+// with programmatic serialization (launch_step_kernel); the experiment
+// options keep plain launches.
 static sl_status launch_fast(sl_mesh *m, const FastArgs &a, bool debug, int config, bool initial, cudaStream_t s,
-                             int32_t *split_seq = nullptr)
+                             int32_t *split_seq = nullptr, bool after_step = false)
 {
+    const bool pdl = m->opt_pdl && !(a.exclude || a.order || a.grid_M > 0 || a.keep_t0);
     if (split_step(m, initial)) {
         if (!m->d.queue) return fail(SL_E_STATE, "split step without its queue scratch");
         const int32_t q = split_seq ? *split_seq : 0;
@@ -541,10 +545,16 @@ static sl_status launch_fast(sl_mesh *m, const FastArgs &a, bool debug, int conf
         x.queue = m->d.queue;
         x.queue_count = m->d.queue_count + (q & 1);
         x.queue_next = split_seq ? m->d.queue_count + ((q + 1) & 1) : nullptr;
-        launch_split_df(x, m->opt_stats != 0, debug, m->sms, q == 0, s);
+        // the first split step of a sequence zeroes its counter with a memset
+        x.pdl = pdl && after_step && q > 0;
+        launch_settle_df(x, m->opt_stats != 0, debug, q == 0, s);
+        x.pdl = pdl;     // the finish pass follows its settle pass
+        launch_finish_df(x, m->opt_stats != 0, debug, m->sms, s);
         if (split_seq) ++*split_seq;
     } else {
-        for_levels(m, a, [&](const FastArgs &x) {
+        FastArgs y = a;
+        y.pdl = pdl && after_step;
+        for_levels(m, y, [&](const FastArgs &x) {
             if (m->precision == SL_FP64) launch_fast_df(x, m->opt_stats != 0, debug, config, s);
             else launch_fast_f32(x, m->opt_stats != 0, debug, config, s);
         });
@@ -639,7 +649,7 @@ static sl_status run_steps(sl_mesh *m, const sl_problem *probs, int64_t n0, int3
             for (int32_t k = 0; k < n_steps; ++k) {
                 FastArgs args = make_fast_args(m, (const FastProb *)((char *)m->d.fprobs + fper * k), a, b, nullptr,
                                                fh.data() + (size_t)k * m->n_problems);
-                sl_status st = launch_fast(m, args, false, config_of(k), k == 0 && first_initial, q, &split_seq);
+                sl_status st = launch_fast(m, args, false, config_of(k), k == 0 && first_initial, q, &split_seq, k > 0);
                 if (st != SL_OK) return st;
                 void *t = a;
                 a = b;
@@ -656,7 +666,7 @@ static sl_status run_steps(sl_mesh *m, const sl_problem *probs, int64_t n0, int3
             if (fast) {
                 FastArgs args = make_fast_args(m, (const FastProb *)((char *)m->d.fprobs + fper * k), a, b, nullptr,
                                                fh.data() + (size_t)k * m->n_problems);
-                st = launch_fast(m, args, false, config_of(k), k == 0 && first_initial, q, &split_seq);
+                st = launch_fast(m, args, false, config_of(k), k == 0 && first_initial, q, &split_seq, k > 0);
             } else {
                 StepArgs args = make_args(m, (const ProbStep *)((char *)m->d.probs + per * k), a, b, nullptr);
                 st = launch_step(m, args, false, q);

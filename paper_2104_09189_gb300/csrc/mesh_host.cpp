@@ -464,6 +464,7 @@ extern "C" sl_status sl_mesh_get_option(const sl_mesh *m, int32_t option, int64_
     case SL_OPT_PRECISE: *value = m->opt_precise; break;
     case SL_OPT_RECORDS: *value = m->d.he8 ? 8 : 16; break;
     case SL_OPT_L2_WINDOW: *value = m->opt_l2; break;
+    case SL_OPT_PDL: *value = m->opt_pdl; break;
     default: return sl::fail(SL_E_ARG, "unknown option");
     }
     return SL_OK;
@@ -536,6 +537,10 @@ extern "C" sl_status sl_mesh_set_option(sl_mesh *m, int32_t option, int64_t valu
         if (value != 0 && value != 1) return sl::fail(SL_E_ARG, "L2 window must be 0 or 1");
         m->opt_l2 = (int32_t)value;
         if (!value) sl::release_l2_window(m);
+        break;
+    case SL_OPT_PDL:
+        if (value != 0 && value != 1) return sl::fail(SL_E_ARG, "pdl must be 0 or 1");
+        m->opt_pdl = (int32_t)value;
         break;
     case SL_OPT_PRECISE:
         if (value < 0 || value > (1 << 30)) return sl::fail(SL_E_ARG, "precise gradient bound out of range");

@@ -101,6 +101,7 @@ struct sl_mesh {
     int32_t opt_precise = 32;         // gradient bound of the FP64 value path (0 = off)
     int32_t opt_records = 0;          // 0 = 16-byte walk records, 1 = compact records where they fit
     int32_t opt_l2 = 0;               // 1 = persisting L2 window on the walk records in recorded graphs
+    int32_t opt_pdl = 1;              // 1 = step kernels after the first of a sequence: programmatic serialization
     bool l2_limit_set = false;        // the context's persisting L2 limit was raised (l2_limit_prev saved)
     size_t l2_limit_prev = 0;
     bool t0_initial = true;           // T^0 holds the initial start triangles

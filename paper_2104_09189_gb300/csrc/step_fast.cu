@@ -9,11 +9,11 @@ template <bool kCompact>
 static void launch_finish(const FastArgs &a, bool stats, bool debug, unsigned grid, cudaStream_t s)
 {
     if (stats) {
-        if (debug) k_finish_df<true, true, kCompact><<<grid, 128, 0, s>>>(a);
-        else k_finish_df<true, false, kCompact><<<grid, 128, 0, s>>>(a);
+        if (debug) launch_step_kernel(k_finish_df<true, true, kCompact>, grid, 128, s, a);
+        else launch_step_kernel(k_finish_df<true, false, kCompact>, grid, 128, s, a);
     } else {
-        if (debug) k_finish_df<false, true, kCompact><<<grid, 128, 0, s>>>(a);
-        else k_finish_df<false, false, kCompact><<<grid, 128, 0, s>>>(a);
+        if (debug) launch_step_kernel(k_finish_df<false, true, kCompact>, grid, 128, s, a);
+        else launch_step_kernel(k_finish_df<false, false, kCompact>, grid, 128, s, a);
     }
 }
 
@@ -24,31 +24,31 @@ static void launch_settle_cfg(const FastArgs &a, bool stats, bool debug, bool re
     if (grid == 0) return;
     if (reset) cudaMemsetAsync(a.queue_count, 0, sizeof(uint32_t), s);
     if (stats) {
-        if (debug) k_settle_df<true, true, kBlock, kMinBlocks, -1><<<grid, kBlock, 0, s>>>(a);
-        else k_settle_df<true, false, kBlock, kMinBlocks, -1><<<grid, kBlock, 0, s>>>(a);
+        if (debug) launch_step_kernel(k_settle_df<true, true, kBlock, kMinBlocks, -1>, grid, kBlock, s, a);
+        else launch_step_kernel(k_settle_df<true, false, kBlock, kMinBlocks, -1>, grid, kBlock, s, a);
     } else if (debug) {
-        k_settle_df<false, true, kBlock, kMinBlocks, -1><<<grid, kBlock, 0, s>>>(a);
+        launch_step_kernel(k_settle_df<false, true, kBlock, kMinBlocks, -1>, grid, kBlock, s, a);
     } else if (!a.single) {
-        k_settle_df<false, false, kBlock, kMinBlocks, -1><<<grid, kBlock, 0, s>>>(a);
+        launch_step_kernel(k_settle_df<false, false, kBlock, kMinBlocks, -1>, grid, kBlock, s, a);
     } else {
         // the timed path of a single mesh: the field kind compiled in
         switch (a.prob0.kind) {
         case SL_FIELD_AFFINE:
-            k_settle_df<false, false, kBlock, kMinBlocks, SL_FIELD_AFFINE><<<grid, kBlock, 0, s>>>(a);
+            launch_step_kernel(k_settle_df<false, false, kBlock, kMinBlocks, SL_FIELD_AFFINE>, grid, kBlock, s, a);
             break;
         case SL_FIELD_ROTATION:
-            k_settle_df<false, false, kBlock, kMinBlocks, SL_FIELD_ROTATION><<<grid, kBlock, 0, s>>>(a);
+            launch_step_kernel(k_settle_df<false, false, kBlock, kMinBlocks, SL_FIELD_ROTATION>, grid, kBlock, s, a);
             break;
         case SL_FIELD_SWIRL:
-            k_settle_df<false, false, kBlock, kMinBlocks, SL_FIELD_SWIRL><<<grid, kBlock, 0, s>>>(a);
+            launch_step_kernel(k_settle_df<false, false, kBlock, kMinBlocks, SL_FIELD_SWIRL>, grid, kBlock, s, a);
             break;
         case SL_FIELD_PAPER:
-            k_settle_df<false, false, kBlock, kMinBlocks, SL_FIELD_PAPER><<<grid, kBlock, 0, s>>>(a);
+            launch_step_kernel(k_settle_df<false, false, kBlock, kMinBlocks, SL_FIELD_PAPER>, grid, kBlock, s, a);
             break;
         case SL_FIELD_FOURIER8:
-            k_settle_df<false, false, kBlock, kMinBlocks, SL_FIELD_FOURIER8><<<grid, kBlock, 0, s>>>(a);
+            launch_step_kernel(k_settle_df<false, false, kBlock, kMinBlocks, SL_FIELD_FOURIER8>, grid, kBlock, s, a);
             break;
-        default: k_settle_df<false, false, kBlock, kMinBlocks, SL_FIELD_ZERO><<<grid, kBlock, 0, s>>>(a); break;
+        default: launch_step_kernel(k_settle_df<false, false, kBlock, kMinBlocks, SL_FIELD_ZERO>, grid, kBlock, s, a); break;
         }
     }
 }
@@ -70,12 +70,6 @@ void launch_finish_df(const FastArgs &a, bool stats, bool debug, int sms, cudaSt
     else launch_finish<false>(a, stats, debug, g2, s);
 }
 
-// A split step (settle pass + finish pass over the queue).
-void launch_split_df(const FastArgs &a, bool stats, bool debug, int sms, bool reset, cudaStream_t s)
-{
-    launch_settle_df(a, stats, debug, reset, s);
-    launch_finish_df(a, stats, debug, sms, s);
-}
 
 // Launch configurations (threads per block x resident blocks per SM the
 // register budget is sized for): 0 = 256 x 4 (64 registers), 1 = 256 x 3,
@@ -361,7 +355,9 @@ __global__ void k_build_he8(HalfEdge8Args a)
             int kp = 0;
             if (a.tn[1][u] == t) kp = 1;
             else if (a.tn[2][u] == t) kp = 2;
-            const float2 q = a.xyh[a.tv[kp][u]], w = a.xyh[a.tv[k][t]];
+            // Q and the entered triangle's first vertex W0 = T[k'+1][u] (an
+            // edge of u)
+            const float2 q = a.xyh[a.tv[kp][u]], w = a.xyh[a.tv[kp == 2 ? 0 : kp + 1][u]];
             // grid values: the differences and their scaling by 2^24 are exact
             const float fx = __fmul_rn(__fsub_rn(q.x, w.x), 16777216.0f);
             const float fy = __fmul_rn(__fsub_rn(q.y, w.y), 16777216.0f);

@@ -78,7 +78,46 @@ struct FastArgs {
     int32_t *queue;
     uint32_t *queue_count;
     uint32_t *queue_next;         // split steps: the next step's counter, zeroed by the settle pass (or NULL)
+    // host side only: launch with programmatic stream serialization (the
+    // kernel before it on the stream is a step kernel of the same sequence of
+    // steps; see launch_step_kernel)
+    int32_t pdl;
 };
+
+// Programmatic dependent launch.  A step kernel launched with programmatic
+// stream serialization may be scheduled while the kernel before it on the
+// stream is still running: its launch and the start of its blocks overlap
+// that kernel's last wave.  Every step kernel signals its dependents as its
+// blocks start (pdl_launch_dependents) and then waits (pdl_wait) until the
+// kernel before it has completed and its writes are visible, before anything
+// else.  (Waiting later, after the foot, which needs no data a step writes,
+// stopped the compiler from issuing the start-state load ahead of the foot
+// arithmetic and cost more than it hid.)  For a kernel launched without the
+// attribute both are no-ops.
+#ifdef __CUDACC__
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void pdl_launch_dependents() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+
+template <typename Kernel>
+inline void launch_step_kernel(Kernel k, unsigned grid, unsigned block, cudaStream_t s, const FastArgs &a)
+{
+    if (!a.pdl) {
+        k<<<grid, block, 0, s>>>(a);
+        return;
+    }
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(grid);
+    cfg.blockDim = dim3(block);
+    cfg.dynamicSmemBytes = 0;
+    cfg.stream = s;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    cudaLaunchKernelEx(&cfg, k, a);
+}
+#endif
 
 // config: launch configuration 0..kFastConfigs-1 (see step_fast.cu)
 void launch_fast_df(const FastArgs &a, bool stats, bool debug, int config, cudaStream_t s);
@@ -90,9 +129,8 @@ void launch_fast_df_c3(const FastArgs &a, bool stats, bool debug, cudaStream_t s
 void launch_fast_df_c4(const FastArgs &a, bool stats, bool debug, cudaStream_t s);
 void launch_fast_df_c5(const FastArgs &a, bool stats, bool debug, cudaStream_t s);
 void launch_fast_df_ext(const FastArgs &a, bool stats, bool debug, cudaStream_t s);
-// a split step: lean settle pass + finish pass over its queue
-void launch_split_df(const FastArgs &a, bool stats, bool debug, int sms, bool reset, cudaStream_t s);
-// its two passes on their own (reset: zero the queue counter first)
+// the two passes of a split step: lean settle pass, then the finish pass over
+// its queue (reset: zero the queue counter first)
 void launch_settle_df(const FastArgs &a, bool stats, bool debug, bool reset, cudaStream_t s);
 void launch_finish_df(const FastArgs &a, bool stats, bool debug, int sms, cudaStream_t s);
 constexpr int kFastConfigs = 6;
@@ -132,18 +170,19 @@ void launch_build_he(const int32_t *const tv[3], const int32_t *const tn[3], con
                      float4 *he, cudaStream_t s);
 
 // Compact 8-byte half-edge records of FP64 meshes, he8[3 t + k] for the edge
-// of triangle t opposite its vertex W = T[k][t].  Interior edge, u, k', Q
-// and e0' = 3 u + (k'+1) mod 3 as above; (dx, dy) = Q - W in units of 2^-24
-// (the hop coordinates are on that grid, so the difference is an exact
+// of triangle t opposite its vertex T[k][t].  Interior edge, u, k', Q and
+// e0' = 3 u + (k'+1) mod 3 as above; (dx, dy) = Q - W0 with W0 = T[k'+1][u],
+// the entered triangle's first vertex (Q - W0 is an edge of u), in units of
+// 2^-24 (the hop coordinates are on that grid, so the difference is an exact
 // integer), stored biased, b = d + 2^17 in [2, 2^18 - 2]:
 //   word 0 = bx | (by & 0x3FFF) << 18,
 //   word 1 = by >> 14 | f << 4 | e0' << 5,
 // f = 1 when e0' is slot 2 of u (the other exit is then e0' - 2, else
-// e0' + 1).  The float with bits 0x3F000000 | b is 0.5 + b 2^-24, so Q = W +
-// that - (0.5 + 2^-7), all exact.  Boundary edge: zero offset and e0' = 3 t
+// e0' + 1).  The float with bits 0x3F000000 | b is 0.5 + b 2^-24, so Q = W0
+// + that - (0.5 + 2^-7), all exact.  Boundary edge: zero offset and e0' = 3 t
 // + (k+1) mod 3, an exit of t itself (a walk can never cross it: the foot
 // lies in the square).  Sets *overflow to 1 when some |dx| or |dy| exceeds
-// 2^17 - 2 (a triangle wider than about 2^-7) or e0' reaches 2^27 (more than
+// 2^17 - 2 (an edge longer than about 2^-7) or e0' reaches 2^27 (more than
 // 44.7 M triangles): the mesh then keeps 16-byte records.
 void launch_build_he8(const int32_t *const tv[3], const int32_t *const tn[3], const float2 *xyh, int64_t nt,
                       uint2 *he8, uint32_t *overflow, cudaStream_t s);

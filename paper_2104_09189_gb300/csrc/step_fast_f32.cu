@@ -104,6 +104,8 @@ __global__ void __launch_bounds__(kBlock, kMinBlocks) k_step_fast_f32(FastArgs a
     // a spanning-tree level mixes problems within a block: search per node
     const int pi = kExt && a.order ? (active && a.nprob > 1 ? problem_of(a.node_off, a.nprob, i) : 0)
                                    : block_problem(a.node_off, a.nprob, a.N, i);
+    pdl_launch_dependents();
+    pdl_wait();
     if (active) {
         const FastProb &P = a.probs[pi];
         const float2 xf = a.xyf[i];
@@ -378,11 +380,11 @@ static void launch_f32_cfg(const FastArgs &a, bool stats, bool debug, cudaStream
     const unsigned grid = (unsigned)((a.count + kBlock - 1) / kBlock);
     if (grid == 0) return;
     if (stats) {
-        if (debug) k_step_fast_f32<true, true, kBlock, kMinBlocks, kExt><<<grid, kBlock, 0, s>>>(a);
-        else k_step_fast_f32<true, false, kBlock, kMinBlocks, kExt><<<grid, kBlock, 0, s>>>(a);
+        if (debug) launch_step_kernel(k_step_fast_f32<true, true, kBlock, kMinBlocks, kExt>, grid, kBlock, s, a);
+        else launch_step_kernel(k_step_fast_f32<true, false, kBlock, kMinBlocks, kExt>, grid, kBlock, s, a);
     } else {
-        if (debug) k_step_fast_f32<false, true, kBlock, kMinBlocks, kExt><<<grid, kBlock, 0, s>>>(a);
-        else k_step_fast_f32<false, false, kBlock, kMinBlocks, kExt><<<grid, kBlock, 0, s>>>(a);
+        if (debug) launch_step_kernel(k_step_fast_f32<false, true, kBlock, kMinBlocks, kExt>, grid, kBlock, s, a);
+        else launch_step_kernel(k_step_fast_f32<false, false, kBlock, kMinBlocks, kExt>, grid, kBlock, s, a);
     }
 }
 

@@ -493,7 +493,9 @@ __device__ __forceinline__ bool foot_pair(const FastArgs &a, int64_t i, const Fa
 // stays below hop_bound(S), S = the sum of the six |a|.  The more negative
 // exit is taken (the first on a tie), as in the certified walk.  A boundary
 // record carries NaN coordinates: the next test fails and the loop ends, its
-// first code naming an edge of the triangle the walk is still in.
+// first code naming an edge of the triangle the walk is still in.  (S summed
+// at every hop measured faster than a walk radius fixed for a run of hops,
+// both as the only bound and as a fast accept ahead of S.)
 __device__ __forceinline__ void lean_hops(const FastArgs &a, float fx, float fy, float p0x, float p0y, float p1x,
                                           float p1y, float p2x, float p2y, int32_t &e0, int32_t &e1, uint32_t &hops,
                                           uint32_t cap)
@@ -522,8 +524,9 @@ __device__ __forceinline__ int32_t tri_of(int32_t h) { return (int32_t)__umulhi(
 
 // Fields of a compact record (k_build_he8).  he8_offx / he8_offy: 0.5 + b
 // 2^-24 for the biased delta b, by its bits; subtracting kHe8Bias (0.5 +
-// 2^-7) leaves d 2^-24 exactly.  he8_e0: the exit code opposite W0 of the
-// entered triangle; he8_d1: the step from it to the exit opposite W1.
+// 2^-7) leaves d 2^-24 exactly, d = Q - W0 of the entered triangle.  he8_e0:
+// the exit code opposite W0 of the entered triangle; he8_d1: the step from
+// it to the exit opposite W1.
 constexpr float kHe8Bias = 0.5078125f;
 __device__ __forceinline__ float he8_offx(uint2 R) { return __uint_as_float((R.x & 0x3FFFFu) | 0x3F000000u); }
 __device__ __forceinline__ float he8_offy(uint2 R)
@@ -534,14 +537,14 @@ __device__ __forceinline__ int32_t he8_e0(uint2 R) { return (int32_t)(R.y >> 5);
 __device__ __forceinline__ int32_t he8_d1(uint2 R) { return 1 - 3 * (int32_t)((R.y >> 4) & 1u); }
 
 // The same FP32 hops on 8-byte half-edge records (k_build_he8), for meshes
-// fine enough that a triangle's new vertex is within 2^17 grid units (of
-// 2^-24) of the vertex it replaces.  State as in lean_hops, with the
-// vertices already relative to the foot, a_k = W_k - X, and the exits e0 and
-// e0 + d1.  Crossing the exit opposite W_c loads that half-edge's record and
-// the entered triangle's new vertex is W_c + d: wc = W_c - X - kHe8Bias is
-// formed while the load is in flight (exact: a multiple of 2^-24 below 1),
-// and a2 = he8_off + wc is exact too.  A hop is taken only across an edge
-// the foot lies certainly beyond, never a boundary edge for a foot in the
+// fine enough that every edge is within 2^17 grid units (of 2^-24).  State as
+// in lean_hops, with the vertices already relative to the foot, a_k = W_k -
+// X, and the exits e0 and e0 + d1.  Crossing the exit opposite W_c loads
+// that half-edge's record; the entered triangle's W0 is the vertex the
+// current state keeps in slot 0 after the crossing (W0 when c = 1, W2 when c
+// = 0), and its new vertex is that W0 + d: a2 = a0 + (he8_off - kHe8Bias),
+// exact (multiples of 2^-24 below 1).  A hop is taken only across an edge the
+// foot lies certainly beyond, never a boundary edge for a foot in the
 // square; a boundary record would decode to the current triangle anyway.
 __device__ __forceinline__ void lean_hops8(const uint2 *__restrict__ he8, float a0x, float a0y, float a1x, float a1y,
                                            float a2x, float a2y, int32_t &e0, int32_t &d1, uint32_t &hops,
@@ -553,19 +556,19 @@ __device__ __forceinline__ void lean_hops8(const uint2 *__restrict__ he8, float 
         const float S = fabsf(a0x) + fabsf(a0y) + fabsf(a1x) + fabsf(a1y) + fabsf(a2x) + fabsf(a2y);
         if (!(fminf(o1, o2) < -hop_bound(S))) break;
         const bool c2 = o2 < o1;
-        const uint2 R = __ldg(&he8[c2 ? e0 + d1 : e0]);
-        const float wcx = __fsub_rn(c2 ? a1x : a0x, kHe8Bias), wcy = __fsub_rn(c2 ? a1y : a0y, kHe8Bias);
+        const uint2 Q = __ldg(&he8[c2 ? e0 + d1 : e0]);
         if (c2) { a1x = a2x; a1y = a2y; }
         else { a0x = a2x; a0y = a2y; }
-        a2x = __fadd_rn(he8_offx(R), wcx);
-        a2y = __fadd_rn(he8_offy(R), wcy);
-        e0 = he8_e0(R);
-        d1 = he8_d1(R);
+        a2x = __fadd_rn(__fsub_rn(he8_offx(Q), kHe8Bias), a0x);
+        a2y = __fadd_rn(__fsub_rn(he8_offy(Q), kHe8Bias), a0y);
+        e0 = he8_e0(Q);
+        d1 = he8_d1(Q);
         ++hops;
     }
 }
 
-// The new vertex of a compact record, W + d, with W a hop coordinate.
+// The new vertex of a compact record, W0 + d, with W0 (the entered
+// triangle's first vertex) a hop coordinate.
 __device__ __forceinline__ float2 he8_vertex(uint2 R, float wx, float wy)
 {
     return make_float2(__fadd_rn(__fsub_rn(he8_offx(R), kHe8Bias), wx),
@@ -733,10 +736,10 @@ __device__ __forceinline__ void step_node(const FastArgs &a, int64_t i, int pi, 
             const uint2 R = __ldg(&a.he8[tq.x + k]);
             if (tri_of(he8_e0(R)) != tri_of(tq.x)) {     // not a boundary edge
                 // the next triangle: (W2, W1, Q), (W0, W2, Q) or (W1, W0, Q),
-                // Q = the left vertex (A, B or C) + the record's offset
+                // Q = its first vertex + the record's offset
                 const float p0x = k == 1 ? A.x : (k == 0 ? C.x : B.x), p0y = k == 1 ? A.y : (k == 0 ? C.y : B.y);
                 const float p1x = k == 0 ? B.x : (k == 1 ? C.x : A.x), p1y = k == 0 ? B.y : (k == 1 ? C.y : A.y);
-                const float2 Q = he8_vertex(R, k == 0 ? A.x : (k == 1 ? B.x : C.x), k == 0 ? A.y : (k == 1 ? B.y : C.y));
+                const float2 Q = he8_vertex(R, p0x, p0y);
                 e0 = he8_e0(R);
                 e1 = he8_d1(R);     // compact records: e1 holds the step to the second exit
                 ids = false;
@@ -832,8 +835,7 @@ __device__ __forceinline__ void step_node(const FastArgs &a, int64_t i, int pi, 
             const uint2 R = __ldg(&a.he8[3 * j + k]);
             if (tri_of(he8_e0(R)) == j) break;    // a boundary edge: not for a foot inside a valid mesh
             const float2 P0 = a.xyh[k == 1 ? w0 : (k == 0 ? w2 : w1)], P1 = a.xyh[k == 0 ? w1 : (k == 1 ? w2 : w0)];
-            const float2 W = a.xyh[k == 0 ? w0 : (k == 1 ? w1 : w2)];
-            const float2 Q = he8_vertex(R, W.x, W.y);
+            const float2 Q = he8_vertex(R, P0.x, P0.y);
             e0 = he8_e0(R);
             e1 = he8_d1(R);
             ids = false;
@@ -897,6 +899,8 @@ __global__ void __launch_bounds__(kBlock, kMinBlocks) k_step_fast_df(FastArgs a)
 {
     const int64_t i = kExt ? node_of_thread(a) : (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     const bool active = kExt ? i >= 0 : i < a.N;
+    pdl_launch_dependents();
+    pdl_wait();
     NodeCounters c;
     // a spanning-tree level mixes problems within a block: search per node
     const int pi = kExt && a.order ? (active && a.nprob > 1 ? problem_of(a.node_off, a.nprob, i) : 0)
@@ -923,15 +927,16 @@ __device__ __forceinline__ bool settle_test(const Numerators &t)
 //    two of its signs are zero, so the test cannot have passed: settled with
 //    the node's value.  (A foot inside the square at its node, f = 0 there,
 //    is left to the finish pass, which takes the same decision.)
-//  * A foot clipped onto a side of the square lies on the boundary edge of
-//    its triangle on that side: that sign is exactly zero (the side codes of
-//    step_node).  Any other sign that is not certainly positive leaves the
-//    node to the finish pass.
+//  * Otherwise the signs are taken as step_node's certified test takes them
+//    at T^0: the per-numerator bounds, the double-float third numerator, and
+//    a zero sign for a foot on a side of the square (clipped onto it, or
+//    there by itself) across the boundary edge of its triangle on that side
+//    (the side codes).  A negative sign, or one those stages leave undecided
+//    (the exact stage), leaves the node to the finish pass.
 __device__ __forceinline__ int settle_decide(const FastArgs &a, int64_t i, int4 tq, df X, df Y, bool clipped,
                                              bool at_node, const Numerators &t)
 {
     if (at_node) return (tq.y == (int32_t)i || tq.z == (int32_t)i || tq.w == (int32_t)i) ? 2 : 0;
-    if (!clipped) return 0;
     // the signs exactly as step_node's certified test takes them
     const Certified u = certify_bounds(t);
     const int s1 = u.n1.h > u.ea ? 1 : (u.n1.h < -u.ea ? -1 : 2);
@@ -993,7 +998,10 @@ __device__ __forceinline__ bool settle_node(const FastArgs &a, int64_t i, int pi
         degenerate = d == 1;
     }
     const float2 val = p1_value_of(V1, V2, V3, t.n1, t.n2, t.den);
-    // steep V^n: the finish pass evaluates the value in FP64 (step_node)
+    // steep V^n: the finish pass evaluates the value in FP64 (step_node).
+    // (Calling that out-of-line path from here put a stack frame and the call
+    // convention on this pass, which then ran slower in recorded runs than
+    // the finish pass's occasional node costs.)
     if (!clipped && steep(V1, V2, V3, t.den.h, a.steep_g2)) return false;
     ((float2 *)a.vout)[i] = val;
     c.clipped = clipped;
@@ -1014,6 +1022,8 @@ __global__ void __launch_bounds__(kBlock, kMinBlocks) k_settle_df(FastArgs a)
 {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     const bool active = i < a.N;
+    pdl_launch_dependents();
+    pdl_wait();
     NodeCounters c;
     const int pi = kKind < 0 ? block_problem(a.node_off, a.nprob, a.N, i) : 0;
     // the next step's counter (its previous user, the finish pass of the
@@ -1037,6 +1047,8 @@ __global__ void __launch_bounds__(kBlock, kMinBlocks) k_settle_df(FastArgs a)
 template <bool kStats, bool kDebug, bool kCompact>
 __global__ void __launch_bounds__(128, 8) k_finish_df(FastArgs a)
 {
+    pdl_launch_dependents();
+    pdl_wait();
     const uint32_t count = *a.queue_count;
     NodeCounters tot;
     uint32_t done = 0, hmax = 0;
@@ -1077,11 +1089,11 @@ template <int kBlock, int kMinBlocks, bool kExt, bool kCompact>
 inline void launch_fast_df_form(const FastArgs &a, bool stats, bool debug, unsigned grid, cudaStream_t s)
 {
     if (stats) {
-        if (debug) k_step_fast_df<true, true, kBlock, kMinBlocks, kExt, kCompact><<<grid, kBlock, 0, s>>>(a);
-        else k_step_fast_df<true, false, kBlock, kMinBlocks, kExt, kCompact><<<grid, kBlock, 0, s>>>(a);
+        if (debug) launch_step_kernel(k_step_fast_df<true, true, kBlock, kMinBlocks, kExt, kCompact>, grid, kBlock, s, a);
+        else launch_step_kernel(k_step_fast_df<true, false, kBlock, kMinBlocks, kExt, kCompact>, grid, kBlock, s, a);
     } else {
-        if (debug) k_step_fast_df<false, true, kBlock, kMinBlocks, kExt, kCompact><<<grid, kBlock, 0, s>>>(a);
-        else k_step_fast_df<false, false, kBlock, kMinBlocks, kExt, kCompact><<<grid, kBlock, 0, s>>>(a);
+        if (debug) launch_step_kernel(k_step_fast_df<false, true, kBlock, kMinBlocks, kExt, kCompact>, grid, kBlock, s, a);
+        else launch_step_kernel(k_step_fast_df<false, false, kBlock, kMinBlocks, kExt, kCompact>, grid, kBlock, s, a);
     }
 }
 

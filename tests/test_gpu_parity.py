@@ -544,21 +544,21 @@ def test_split_steps_match_the_oracle_with_debug_outputs():
     g.close()
 
 
-@pytest.mark.parametrize("split", [0, 1])
-def test_steep_data_takes_the_fp64_value_path(split):
+def test_steep_data_takes_the_fp64_value_path():
     """A narrow Gaussian (sigma = 0.01, |grad V| up to 61) in the Fourier
     stream-function field: where V^n is steeper than SL_OPT_PRECISE's bound
     the value is evaluated in FP64 (flag SL_NODE_PRECISE) and every step
     stays within 1e-12 of one oracle step on the same V^n; with the bound at
-    0 no node takes that path.  The split form agrees bitwise with the
-    fused one."""
+    0 no node takes that path.  In the split form the settle pass leaves the
+    steep nodes to the finish pass: values and flags agree bitwise with the
+    fused form."""
     mesh = si.grid_mesh(400, 0.25, 41)
     fld = si.fourier8_field(11)
     dt = 0.01
     v0 = si.gaussian(mesh.xy, 0.5, 0.5, 0.01)
     om = oracle.OracleMesh(mesh.xy, mesh.tri)
     outs = {}
-    for bound in (32, 0):
+    for split, bound in ((0, 32), (1, 32), (0, 0)):
         g = DeviceRun(mesh, fld, dt, curve=sl.SL_CURVE_HILBERT)
         sl.sl_mesh_set_option(g.h, sl.SL_OPT_SPLIT, split)
         sl.sl_mesh_set_option(g.h, sl.SL_OPT_PRECISE, bound)
@@ -570,16 +570,20 @@ def test_steep_data_takes_the_fp64_value_path(split):
             one, _, _, _ = om.step(fld.kind, fld.packed(), dt, n, vin, want_feet=False)
             err = np.abs(res["v"] - one).max() / np.abs(v0).max()
             precise = (res["flags"] & sl.SL_NODE_PRECISE) != 0
-            steps.append((err, int(precise.sum()), res["v"]))
+            steps.append((err, int(precise.sum()), res["v"], res["flags"]))
             exact_triangle_parity(om, res["tri"], res["feet"], res["feet_lo"], res["flags"])
-        outs[bound] = steps
+        outs[(split, bound)] = steps
         g.close()
-    for err, n_precise, _ in outs[32]:
-        assert err <= 1e-12
-        assert n_precise > 100
-    assert all(n == 0 for _, n, _ in outs[0])
+    for key in ((0, 32), (1, 32)):
+        for err, n_precise, _, _ in outs[key]:
+            assert err <= 1e-12
+            assert n_precise > 100
+    assert all(n == 0 for _, n, _, _ in outs[(0, 0)])
     # the FP64 path is what keeps the steep nodes within the tolerance
-    assert max(e for e, _, _ in outs[32]) < max(e for e, _, _ in outs[0])
+    assert max(e for e, _, _, _ in outs[(0, 32)]) < max(e for e, _, _, _ in outs[(0, 0)])
+    for (_, _, va, fa), (_, _, vb, fb) in zip(outs[(0, 32)], outs[(1, 32)]):
+        assert np.array_equal(va, vb)
+        assert np.array_equal(fa, fb)
 
 
 @pytest.mark.parametrize("split", [0, 1])
@@ -614,10 +618,10 @@ def test_compact_walk_records_give_identical_results(split):
 
 
 def test_split_graph_replays_are_identical():
-    """A recorded run of split steps whose finish passes sit in conditional
-    graph nodes (taken only when a settle pass queued nodes), replayed three
-    times from the same V^0 and start triangles: the same values, T^0 and
-    statistics every time, equal to eager steps."""
+    """A recorded run of split steps (settle pass, then the finish pass over
+    the nodes it queued), replayed three times from the same V^0 and start
+    triangles: the same values, T^0 and statistics every time, equal to eager
+    steps."""
     prob = si.config("C2", M=160)
     g = DeviceRun(prob.mesh, prob.field, prob.dt, curve=sl.SL_CURVE_HILBERT)
     sl.sl_mesh_set_option(g.h, sl.SL_OPT_SPLIT, 1)
@@ -639,6 +643,41 @@ def test_split_graph_replays_are_identical():
         assert np.array_equal(v, results[0][0])
         assert np.array_equal(t0, results[0][1])
         assert st == results[0][2]
+
+
+@pytest.mark.parametrize("form", ["split", "fused", "fp32"])
+def test_programmatic_launches_give_identical_results(form):
+    """SL_OPT_PDL: the step kernels of a run launched with programmatic stream
+    serialization (each computes its feet while the kernel before it
+    finishes, then waits for it) give bitwise the values, T^0 and statistics
+    of plain launches, recorded as a graph and eager, in the split form (the
+    finish pass has queued nodes to walk here), the fused form and FP32."""
+    prob = si.config("C2", M=160)
+    precision = sl.SL_FP32 if form == "fp32" else sl.SL_FP64
+    g = DeviceRun(prob.mesh, prob.field, prob.dt, precision=precision, curve=sl.SL_CURVE_HILBERT)
+    if form == "split":
+        sl.sl_mesh_set_option(g.h, sl.SL_OPT_SPLIT, 1)
+    v0 = g.to_dev(prob.v0)
+    w = g.torch.empty_like(v0)
+    results = []
+    for pdl, stats, use_graph in ((0, 1, True), (1, 1, True), (1, 1, False), (0, 0, True), (1, 0, True)):
+        sl.sl_mesh_set_option(g.h, sl.SL_OPT_PDL, pdl)
+        sl.sl_mesh_set_option(g.h, sl.SL_OPT_STATS, stats)
+        assert sl.sl_mesh_get_option(g.h, sl.SL_OPT_PDL) == pdl
+        sl.sl_mesh_reset_t0(g.h)
+        sl.sl_mesh_stats(g.h, reset=True)
+        v = v0.clone()
+        sl.sl_run(g.h, g.probs, 0, 6, v, w, use_graph=use_graph)
+        t0 = g.torch.empty(prob.mesh.n_nodes, dtype=g.torch.int32, device=g.dev)
+        sl.sl_mesh_get_t0(g.h, t0)
+        results.append((v.cpu().numpy(), t0.cpu().numpy(), sl.sl_mesh_stats(g.h) if stats else None))
+    g.close()
+    assert results[0][2]["walk_moves"] > 0
+    for k, (v, t0, st) in enumerate(results[1:], 1):
+        assert np.array_equal(v, results[0][0]), k
+        assert np.array_equal(t0, results[0][1]), k
+        if st is not None:
+            assert st == results[0][2], k
 
 
 @pytest.mark.parametrize("precision", [sl.SL_FP64, sl.SL_FP32], ids=["fp64", "fp32"])
