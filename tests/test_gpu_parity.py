@@ -249,19 +249,33 @@ def test_graph_eager_reorder_and_resume_are_bitwise_identical(kernel):
     g2.close()
 
 
-def test_run_host_matches_device_run():
+@pytest.mark.parametrize("precision", [sl.SL_FP64, sl.SL_FP32], ids=["fp64", "fp32"])
+@pytest.mark.parametrize("steps", [5, 6])
+def test_run_host_matches_device_run(precision, steps):
+    """sl_run_host on pageable and on page-locked host memory, recorded and
+    eager: bitwise the device run, for an odd and an even number of steps,
+    and again on the same handle."""
+    import torch
     prob = si.config("C1")
-    g = DeviceRun(prob.mesh, prob.field, prob.dt)
+    dt = np.float64 if precision == sl.SL_FP64 else np.float32
+    g = DeviceRun(prob.mesh, prob.field, prob.dt, precision=precision)
     v = g.to_dev(prob.v0)
     w = g.torch.empty_like(v)
-    sl.sl_run(g.h, g.probs, 0, 5, v, w)
+    sl.sl_run(g.h, g.probs, 0, steps, v, w)
     dev_result = g.from_dev(v)
     g.close()
-    g = DeviceRun(prob.mesh, prob.field, prob.dt)
-    host = prob.v0.copy()
-    sl.sl_run_host(g.h, g.probs, 0, 5, host)
-    assert np.array_equal(host, dev_result)
-    g.close()
+    for pinned in (False, True):
+        for use_graph in (True, False):
+            g = DeviceRun(prob.mesh, prob.field, prob.dt, precision=precision)
+            for _ in range(2):
+                sl.sl_mesh_reset_t0(g.h)
+                if pinned:
+                    host = torch.tensor(prob.v0.astype(dt)).pin_memory().numpy()
+                else:
+                    host = prob.v0.astype(dt).copy()
+                sl.sl_run_host(g.h, g.probs, 0, steps, host, use_graph=use_graph)
+                assert np.array_equal(host.astype(np.float64), dev_result), (pinned, use_graph)
+            g.close()
 
 
 @pytest.mark.parametrize("kernel", [1, 2], ids=["plain", "fast"])
