@@ -305,8 +305,8 @@ class _Args:
 
 
 def secondary_workload(sl, torch, config, precision, runs, warmup, oracle_cache):
-    """One of the benchmark spec's systems patterns measured on its own workload
-    (C4: FP32 filtered precision on the 16.8M-node mesh; C5: the 256-problem
+    """A further workload measured beside the headline one (C4: the FP32
+    filtered-precision path on the 16.8M-node mesh; C5: the 256-problem
     batch, FP64 and FP32): the same timed path as the headline (autotuned,
     one CUDA graph per run, runs queued back to back, CUDA events), the
     result's error against the FP64 oracle, the exact-stage (fallback) test
