@@ -98,17 +98,17 @@ __device__ __forceinline__ bool clip_df(df x, df y, df &X, df &Y)
     return true;
 }
 
-// Euler foot X = x - dt f(x, t_{n+1}) (Eq. 4) in double-float, with the
-// field's time factors folded into the per-step constants.
+// Displacement d = -dt f(x, t_{n+1}) of the Euler foot X = x + d (Eq. 4) in
+// double-float, with the field's time factors folded into the per-step
+// constants.
 template <int kKind>
-__device__ __forceinline__ void foot_df_k(const FastProb &P, const FastArgs &a, int64_t i, df x, df y, df &X, df &Y)
+__device__ __forceinline__ void disp_df_k(const FastProb &P, const FastArgs &a, int64_t i, df x, df y, df &DX,
+                                          df &DY)
 {
     switch (kKind) {
     case SL_FIELD_AFFINE: {
-        df fx = df_add(df_add(dfp(P.c[0]), df_mul(dfp(P.c[1]), x)), df_mul(dfp(P.c[2]), y));
-        df fy = df_add(df_add(dfp(P.c[3]), df_mul(dfp(P.c[4]), x)), df_mul(dfp(P.c[5]), y));
-        X = df_sub(x, fx);
-        Y = df_sub(y, fy);
+        DX = df_neg(df_add(df_add(dfp(P.c[0]), df_mul(dfp(P.c[1]), x)), df_mul(dfp(P.c[2]), y)));
+        DY = df_neg(df_add(df_add(dfp(P.c[3]), df_mul(dfp(P.c[4]), x)), df_mul(dfp(P.c[5]), y)));
         break;
     }
     case SL_FIELD_ROTATION:
@@ -117,46 +117,63 @@ __device__ __forceinline__ void foot_df_k(const FastProb &P, const FastArgs &a, 
             // subtract exactly, the remainders with one rounding (2^-49)
             const df dy = df_make(__fsub_rn(y.h, P.c[2].x), __fsub_rn(y.l, P.c[2].y));
             const df dx = df_make(__fsub_rn(x.h, P.c[1].x), __fsub_rn(x.l, P.c[1].y));
-            X = df_add(x, df_mul(dfp(P.c[0]), dy));
-            Y = df_sub(y, df_mul(dfp(P.c[0]), dx));
+            DX = df_mul(dfp(P.c[0]), dy);
+            DY = df_neg(df_mul(dfp(P.c[0]), dx));
         } else {
-            X = df_add(x, df_mul(dfp(P.c[0]), df_sub(y, dfp(P.c[2]))));
-            Y = df_sub(y, df_mul(dfp(P.c[0]), df_sub(x, dfp(P.c[1]))));
+            DX = df_mul(dfp(P.c[0]), df_sub(y, dfp(P.c[2])));
+            DY = df_neg(df_mul(dfp(P.c[0]), df_sub(x, dfp(P.c[1]))));
         }
         break;
     case SL_FIELD_SWIRL: {
         const float4 g = a.g1[i];
         const df k = dfp(P.c[0]);
-        X = df_sub(x, df_mul(k, df_make(g.x, g.z)));
-        Y = df_sub(y, df_mul(k, df_make(g.y, g.w)));
+        DX = df_neg(df_mul(k, df_make(g.x, g.z)));
+        DY = df_neg(df_mul(k, df_make(g.y, g.w)));
         break;
     }
     case SL_FIELD_PAPER:
     case SL_FIELD_FOURIER8: {
         const float4 g = a.g1[i], q = a.g2[i];
         const df k0 = dfp(P.c[0]), k1 = dfp(P.c[1]);
-        X = df_sub(x, df_add(df_mul(k0, df_make(g.x, g.z)), df_mul(k1, df_make(q.x, q.z))));
-        Y = df_sub(y, df_add(df_mul(k0, df_make(g.y, g.w)), df_mul(k1, df_make(q.y, q.w))));
+        DX = df_neg(df_add(df_mul(k0, df_make(g.x, g.z)), df_mul(k1, df_make(q.x, q.z))));
+        DY = df_neg(df_add(df_mul(k0, df_make(g.y, g.w)), df_mul(k1, df_make(q.y, q.w))));
         break;
     }
     default:
-        X = x;
-        Y = y;
+        DX = df_make(0.0f, 0.0f);
+        DY = df_make(0.0f, 0.0f);
         break;
     }
 }
 
 // The same for a kind known only at run time.
-__device__ __forceinline__ void foot_df(const FastProb &P, const FastArgs &a, int64_t i, df x, df y, df &X, df &Y)
+__device__ __forceinline__ void disp_df(const FastProb &P, const FastArgs &a, int64_t i, df x, df y, df &DX, df &DY)
 {
     switch (P.kind) {
-    case SL_FIELD_AFFINE: foot_df_k<SL_FIELD_AFFINE>(P, a, i, x, y, X, Y); break;
-    case SL_FIELD_ROTATION: foot_df_k<SL_FIELD_ROTATION>(P, a, i, x, y, X, Y); break;
-    case SL_FIELD_SWIRL: foot_df_k<SL_FIELD_SWIRL>(P, a, i, x, y, X, Y); break;
-    case SL_FIELD_PAPER: foot_df_k<SL_FIELD_PAPER>(P, a, i, x, y, X, Y); break;
-    case SL_FIELD_FOURIER8: foot_df_k<SL_FIELD_FOURIER8>(P, a, i, x, y, X, Y); break;
-    default: foot_df_k<SL_FIELD_ZERO>(P, a, i, x, y, X, Y); break;
+    case SL_FIELD_AFFINE: disp_df_k<SL_FIELD_AFFINE>(P, a, i, x, y, DX, DY); break;
+    case SL_FIELD_ROTATION: disp_df_k<SL_FIELD_ROTATION>(P, a, i, x, y, DX, DY); break;
+    case SL_FIELD_SWIRL: disp_df_k<SL_FIELD_SWIRL>(P, a, i, x, y, DX, DY); break;
+    case SL_FIELD_PAPER: disp_df_k<SL_FIELD_PAPER>(P, a, i, x, y, DX, DY); break;
+    case SL_FIELD_FOURIER8: disp_df_k<SL_FIELD_FOURIER8>(P, a, i, x, y, DX, DY); break;
+    default: disp_df_k<SL_FIELD_ZERO>(P, a, i, x, y, DX, DY); break;
     }
+}
+
+// A foot coordinate x + d straight in the (grid, remainder) form of the
+// certified test, for a node coordinate x = (grid, remainder) and a
+// displacement d = (h, l): dg = d.h rounded to the grid of 2^-24, g = x.g +
+// dg (grid values below 1: exact), r = (x.r + (d.h - dg)) + d.l, where d.h -
+// dg is exact (a multiple of ulp(d.h) below 2^-25).  |r| <= 2^-24 and a few
+// ulps of d, within the margins of hop_bound and cert_bound_g, and the pair
+// is within about 2^-48 of x + d.  Returns false unless g lies at least
+// 2^-23 inside (0, 1), so that x + d does: the caller then takes the
+// double-float sum, the boundary rounding and the clip.
+__device__ __forceinline__ bool foot_grid(df x, df d, df &X)
+{
+    const float dg = __fmul_rn(rintf(__fmul_rn(d.h, 16777216.0f)), 0x1p-24f);
+    const float g = __fadd_rn(x.h, dg);
+    X = df_make(g, __fadd_rn(__fadd_rn(x.l, __fsub_rn(d.h, dg)), d.l));
+    return g >= 0x1p-23f && g <= 1.0f - 0x1p-23f;
 }
 
 // Error bound of the FP32 hop test.  Node coordinates are stored as a grid
@@ -455,19 +472,26 @@ __device__ __forceinline__ void foot_to_grid(df &X, df &Y)
     Y = df_make(g, r);
 }
 
-// The foot of node i for this step: Euler (Eq. 4) in double-float, decided
-// against the boundary in double rounding, clipped, and returned in the
-// (grid, remainder) form of the certified test.  Returns true when clipped.
-// at_node: a foot on or beyond a side that is the node itself (an outward
-// boundary node); a foot inside the square is not reported here.
+// The foot of node i for this step: Euler (Eq. 4) in double-float, in the
+// (grid, remainder) form of the certified test.  A foot well inside the
+// square comes straight in that form (foot_grid); any other is summed in
+// double-float, decided against the boundary in double rounding, clipped and
+// then split.  Returns true when clipped.  at_node: a foot on or beyond a side
+// that is the node itself (an outward boundary node); a foot inside the
+// square is not reported here.
 template <int kKind>
 __device__ __forceinline__ bool foot_pair(const FastArgs &a, int64_t i, const FastProb &P, df &X, df &Y,
                                           bool &at_node)
 {
     const float4 xq = a.xyq[i];
     const df x = df_make(xq.x, xq.z), y = df_make(xq.y, xq.w);
-    if (kKind < 0) foot_df(P, a, i, x, y, X, Y);
-    else foot_df_k<kKind < 0 ? 0 : kKind>(P, a, i, x, y, X, Y);
+    df DX, DY;
+    if (kKind < 0) disp_df(P, a, i, x, y, DX, DY);
+    else disp_df_k<kKind < 0 ? 0 : kKind>(P, a, i, x, y, DX, DY);
+    at_node = false;
+    if (foot_grid(x, DX, X) & foot_grid(y, DY, Y)) return false;
+    X = df_add(x, DX);
+    Y = df_add(y, DY);
     const bool inside = df_inside(X, Y);
     bool clipped = false;
     if (!inside) {
@@ -635,39 +659,48 @@ __device__ __forceinline__ void step_node(const FastArgs &a, int64_t i, int pi, 
     const FastProb &P = a.probs[pi];
     const float4 xq = a.xyq[i];
     const df x = df_make(xq.x, xq.z), y = df_make(xq.y, xq.w);
+    df DX, DY;
+    disp_df(P, a, i, x, y, DX, DY);
     df X, Y;
-    foot_df(P, a, i, x, y, X, Y);
-    round_boundary(X);
-    round_boundary(Y);
     uint32_t flags = 0;
-    if (kExt && a.exclude && (df_neg_strict(X) || df_gt1(X) || df_neg_strict(Y) || df_gt1(Y))) {
-        // the paper's experiments exclude nodes whose foot leaves the domain
-        // (Sec. 4): V unchanged, no walk, T^0 unchanged
-        ((float2 *)a.vout)[i] = ((const float2 *)a.vin)[i];
-        c.excluded = 1;
-        if (a.parent) {
-            // strategy (c): the children start where this node would have
-            a.t0[i] = a.t0[a.parent[i]];
-            a.t0v[i] = a.t0v[a.parent[i]];
+    bool at_node;
+    // From here on the foot is in its (grid, remainder) form, Xg + Xr
+    // exactly, the form the certified test needs (the exact stage takes any
+    // float pair).  A foot well inside the square comes straight in that form
+    // (foot_grid, as in the settle pass; a node whose field vanishes keeps its
+    // own pair there); any other is summed in double-float, decided against
+    // the boundary, excluded or clipped, and then split (0 and 1 are grid
+    // points, so the split does not move a foot off a side).
+    if (foot_grid(x, DX, X) & foot_grid(y, DY, Y)) {
+        at_node = foot_is_node(x, y, X, Y);
+    } else {
+        X = df_add(x, DX);
+        Y = df_add(y, DY);
+        round_boundary(X);
+        round_boundary(Y);
+        if (kExt && a.exclude && (df_neg_strict(X) || df_gt1(X) || df_neg_strict(Y) || df_gt1(Y))) {
+            // the paper's experiments exclude nodes whose foot leaves the
+            // domain (Sec. 4): V unchanged, no walk, T^0 unchanged
+            ((float2 *)a.vout)[i] = ((const float2 *)a.vin)[i];
+            c.excluded = 1;
+            if (a.parent) {
+                // strategy (c): the children start where this node would have
+                a.t0[i] = a.t0[a.parent[i]];
+                a.t0v[i] = a.t0v[a.parent[i]];
+            }
+            if (kDebug) {
+                write_foot(a, i, X, Y);
+                if (a.dbg.tri) a.dbg.tri[i] = -1;
+                if (a.dbg.moves) a.dbg.moves[i] = 0;
+                if (a.dbg.flags) a.dbg.flags[i] = (uint8_t)SL_NODE_EXCLUDED;
+            }
+            return;
         }
-        if (kDebug) {
-            write_foot(a, i, X, Y);
-            if (a.dbg.tri) a.dbg.tri[i] = -1;
-            if (a.dbg.moves) a.dbg.moves[i] = 0;
-            if (a.dbg.flags) a.dbg.flags[i] = (uint8_t)SL_NODE_EXCLUDED;
+        if (clip_df(x, y, X, Y)) {
+            flags |= SL_NODE_CLIPPED;
+            c.clipped = 1;
         }
-        return;
-    }
-    if (clip_df(x, y, X, Y)) {
-        flags |= SL_NODE_CLIPPED;
-        c.clipped = 1;
-    }
-    const bool at_node = foot_is_node(x, y, X, Y);
-    // From here on the foot is its (grid, remainder) form, Xg + Xr exactly:
-    // within 2^-49 of the double-float foot, and the form the certified test
-    // needs (the exact stage takes any float pair).  The boundary decisions
-    // above are not affected: 0 and 1 are grid points.
-    {
+        at_node = foot_is_node(x, y, X, Y);
         float g, r;
         to_grid(X, g, r);
         X = df_make(g, r);
