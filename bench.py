@@ -75,6 +75,9 @@ def parse():
                     help="SL_OPT_PDL: step kernels launched with programmatic stream serialization")
     ap.add_argument("--records", type=int, choices=[0, 1], default=None,
                     help="SL_OPT_RECORDS for the double-float kernel (default: chosen by sl_autotune)")
+    ap.add_argument("--precise", type=int, default=None,
+                    help="SL_OPT_PRECISE: gradient bound G of the FP64 value path (default: the library's, 32; "
+                         "0 = never)")
     return ap.parse_args()
 
 
@@ -611,6 +614,8 @@ def main():
     if args.config_id is not None:
         sl.sl_mesh_set_option(h, sl.SL_OPT_CONFIG, args.config_id)
         sl.sl_mesh_set_option(h, sl.SL_OPT_CONFIG_FIRST, args.config_id)
+    if args.precise is not None and prec == sl.SL_FP64:
+        sl.sl_mesh_set_option(h, sl.SL_OPT_PRECISE, args.precise)
     probs = sl.problems([(p.field.kind, p.dt, p.field.packed()) for p in wl.probs])
     vt = torch.float64 if prec == sl.SL_FP64 else torch.float32
     v0_all = np.concatenate([p.v0 for p in wl.probs])

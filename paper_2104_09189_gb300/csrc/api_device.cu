@@ -122,6 +122,26 @@ void free_device(sl_mesh *m)
     m->capture_stream = nullptr;
 }
 
+// The longest edge of the mesh as |dx| + |dy| in the hop coordinates h of
+// the double-float kernel (floats: the differences and sums are exact in
+// double), rounded up to a float: the bound of the runs of lean hops
+// (lean_walk).
+static float hop_edge_bound(const sl_mesh *m, const std::vector<float2> &h)
+{
+    double L = 0.0;
+    for (int32_t p = 0; p < m->n_problems; ++p) {
+        const int64_t n0 = m->node_off[p];
+        for (int64_t j = m->tri_off[p]; j < m->tri_off[p + 1]; ++j)
+            for (int k = 0; k < 3; ++k) {
+                const float2 a = h[n0 + m->tri[3 * j + k]], b = h[n0 + m->tri[3 * j + (k + 1) % 3]];
+                const double d = std::fabs((double)a.x - (double)b.x) + std::fabs((double)a.y - (double)b.y);
+                if (d > L) L = d;
+            }
+    }
+    const float f = (float)L;
+    return (double)f >= L ? f : std::nextafter(f, __builtin_inff());
+}
+
 // Copy the host arrays (current numbering) to the device, converting local
 // indices to global ones.
 static sl_status upload_arrays(sl_mesh *m)
@@ -144,6 +164,7 @@ static sl_status upload_arrays(sl_mesh *m)
         std::vector<float2> hx(N);
         for (int64_t i = 0; i < N; ++i) hx[i] = make_float2(q[i].x, q[i].y);
         SL_CUDA(cudaMemcpy(d.xyh, hx.data(), sizeof(float2) * N, cudaMemcpyHostToDevice));
+        m->hop_L = hop_edge_bound(m, hx);
     } else {
         std::vector<float> f(2 * N);
         for (int64_t q = 0; q < 2 * N; ++q) f[q] = (float)m->xy[q];
@@ -370,6 +391,7 @@ FastArgs make_fast_args(const sl_mesh *m, const FastProb *fp, const void *vin, v
     a.grid_M = m->opt_strategy == 2 ? m->grid_M : 0;
     a.grid_t0v = (const int4 *)m->d.grid_t0v;
     a.count = m->N;     // every node; the level launches of strategy (c) narrow it
+    a.hop_L = m->hop_L;
     // G^2; +inf when the FP64 value path is off (no gradient exceeds it)
     a.steep_g2 = m->precision == SL_FP64 && m->opt_precise > 0
                      ? (float)((double)m->opt_precise * (double)m->opt_precise)

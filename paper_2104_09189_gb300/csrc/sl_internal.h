@@ -105,6 +105,8 @@ struct sl_mesh {
     bool l2_limit_set = false;        // the context's persisting L2 limit was raised (l2_limit_prev saved)
     size_t l2_limit_prev = 0;
     bool t0_initial = true;           // T^0 holds the initial start triangles
+    float hop_L = __builtin_inff();   // FP64 meshes: a bound of every edge's |dx| + |dy| in the hop
+                                      // coordinates (upload_arrays)
     int32_t sms = 0;                  // multiprocessors of the device
     bool stepped = false;
     std::vector<double> table_key;    // field parameters of the current node tables

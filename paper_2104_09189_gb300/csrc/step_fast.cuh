@@ -62,6 +62,8 @@ struct FastArgs {
     uint32_t *status;
     unsigned long long *stats;
     sl_debug dbg;
+    float hop_L;                  // FP64 meshes: an upper bound of every edge's |dx| + |dy| in the hop
+                                  // coordinates (the runs of lean hops; +inf: a bound per hop)
     float steep_g2;               // G^2 of SL_OPT_PRECISE (double-float kernel; +inf = off): a value
                                   // with (v_k - v_3)^2 > G^2 den is evaluated in FP64
     int32_t keep_t0;              // strategy (a) or direct location: T^0 is never overwritten

@@ -517,30 +517,95 @@ __device__ __forceinline__ bool foot_pair(const FastArgs &a, int64_t i, const Fa
 // stays below hop_bound(S), S = the sum of the six |a|.  The more negative
 // exit is taken (the first on a tie), as in the certified walk.  A boundary
 // record carries NaN coordinates: the next test fails and the loop ends, its
-// first code naming an edge of the triangle the walk is still in.  (S summed
-// at every hop measured faster than a walk radius fixed for a run of hops,
-// both as the only bound and as a fast accept ahead of S.)
-__device__ __forceinline__ void lean_hops(const FastArgs &a, float fx, float fy, float p0x, float p0y, float p1x,
-                                          float p1y, float p2x, float p2y, int32_t &e0, int32_t &e1, uint32_t &hops,
-                                          uint32_t cap)
+// first code naming an edge of the triangle the walk is still in.
+//
+// A walk that is still going after kLeanPlain hops continues in runs that
+// share one bound.  Where the test with the triangle's own bound passes, the
+// next kLeanRun hops are tested against hop_bound(3 (M + kLeanRun L)), M the
+// largest |a_k|_1 of that triangle and L (FastArgs::hop_L) the longest edge
+// of the mesh in the same norm: each hop's new vertex shares an edge with a
+// vertex of the triangle before, so after j hops every |a_k|_1 is at most M
+// + j L and S at most three times that.  A test that fails against the run's
+// bound is taken again with the triangle's own, so the hops, where the loop
+// stops and every result are those of a test with S at every hop, at about a
+// third fewer instructions per hop.  Short walks, most of a steady step's,
+// keep the bound per hop and skip the setting up of runs.
+constexpr uint32_t kLeanPlain = 4;
+constexpr uint32_t kLeanRun = 16;
+
+__device__ __forceinline__ float lean_run_bound(float m0, float m1, float m2, float L)
 {
-    float a0x = __fsub_rn(p0x, fx), a0y = __fsub_rn(p0y, fy), a1x = __fsub_rn(p1x, fx), a1y = __fsub_rn(p1y, fy);
-    float a2x = __fsub_rn(p2x, fx), a2y = __fsub_rn(p2y, fy);
-    while (hops < cap) {
-        const float o1 = __fmaf_rn(a1x, a2y, -__fmul_rn(a1y, a2x));    // ~ theta of W0 * den
-        const float o2 = __fmaf_rn(a2x, a0y, -__fmul_rn(a2y, a0x));    // ~ theta of W1 * den
+    return hop_bound(__fmul_ru(3.0f, __fmaf_ru((float)kLeanRun, L, fmaxf(fmaxf(m0, m1), m2))));
+}
+
+// The lean walk on either record form: Rec::hop(c2) crosses the exit opposite
+// W1 (c2) or W0 and returns the new vertex relative to the foot, given the
+// kept slot-0 vertex.
+template <typename Rec>
+__device__ __forceinline__ void lean_walk(Rec &rec, float a0x, float a0y, float a1x, float a1y, float a2x, float a2y,
+                                          uint32_t &hops, uint32_t cap, float L)
+{
+    float o1, o2;
+    // the first hops, each on its own bound
+    for (uint32_t n = 0;; ++n) {
+        if (hops >= cap) return;
+        o1 = __fmaf_rn(a1x, a2y, -__fmul_rn(a1y, a2x));    // ~ theta of W0 * den
+        o2 = __fmaf_rn(a2x, a0y, -__fmul_rn(a2y, a0x));    // ~ theta of W1 * den
         const float S = fabsf(a0x) + fabsf(a0y) + fabsf(a1x) + fabsf(a1y) + fabsf(a2x) + fabsf(a2y);
-        if (!(fminf(o1, o2) < -hop_bound(S))) break;
+        if (!(fminf(o1, o2) < -hop_bound(S))) return;
+        if (n == kLeanPlain) break;
         const bool c2 = o2 < o1;
-        const float4 Q = __ldg(&a.he[c2 ? e1 : e0]);
         if (c2) { a1x = a2x; a1y = a2y; }
         else { a0x = a2x; a0y = a2y; }
+        rec.hop(c2, a0x, a0y, a2x, a2y);
+        ++hops;
+    }
+    // runs: the test at the current triangle has passed
+    for (;;) {
+        const float hb = lean_run_bound(fabsf(a0x) + fabsf(a0y), fabsf(a1x) + fabsf(a1y), fabsf(a2x) + fabsf(a2y), L);
+        const uint32_t lim = min(cap, hops + kLeanRun);
+        for (;;) {
+            const bool c2 = o2 < o1;
+            if (c2) { a1x = a2x; a1y = a2y; }
+            else { a0x = a2x; a0y = a2y; }
+            rec.hop(c2, a0x, a0y, a2x, a2y);
+            if (++hops >= lim) break;
+            o1 = __fmaf_rn(a1x, a2y, -__fmul_rn(a1y, a2x));
+            o2 = __fmaf_rn(a2x, a0y, -__fmul_rn(a2y, a0x));
+            if (!(fminf(o1, o2) < -hb)) break;
+        }
+        if (hops >= cap) return;
+        o1 = __fmaf_rn(a1x, a2y, -__fmul_rn(a1y, a2x));
+        o2 = __fmaf_rn(a2x, a0y, -__fmul_rn(a2y, a0x));
+        const float S = fabsf(a0x) + fabsf(a0y) + fabsf(a1x) + fabsf(a1y) + fabsf(a2x) + fabsf(a2y);
+        if (!(fminf(o1, o2) < -hop_bound(S))) return;
+    }
+}
+
+// 16-byte records: the new vertex's hop coordinates and both exit codes.
+struct Rec16 {
+    const float4 *he;
+    float fx, fy;
+    int32_t e0, e1;
+    __device__ __forceinline__ void hop(bool c2, float, float, float &a2x, float &a2y)
+    {
+        const float4 Q = __ldg(&he[c2 ? e1 : e0]);
         a2x = __fsub_rn(Q.x, fx);
         a2y = __fsub_rn(Q.y, fy);
         e0 = __float_as_int(Q.z);
         e1 = __float_as_int(Q.w);
-        ++hops;
     }
+};
+
+__device__ __forceinline__ void lean_hops(const FastArgs &a, float fx, float fy, float p0x, float p0y, float p1x,
+                                          float p1y, float p2x, float p2y, int32_t &e0, int32_t &e1, uint32_t &hops,
+                                          uint32_t cap)
+{
+    Rec16 r{a.he, fx, fy, e0, e1};
+    lean_walk(r, __fsub_rn(p0x, fx), __fsub_rn(p0y, fy), __fsub_rn(p1x, fx), __fsub_rn(p1y, fy), __fsub_rn(p2x, fx),
+              __fsub_rn(p2y, fy), hops, cap, a.hop_L);
+    e0 = r.e0;
+    e1 = r.e1;
 }
 
 // Triangle of a half-edge code h = 3 t + k (h >= 0).
@@ -570,25 +635,29 @@ __device__ __forceinline__ int32_t he8_d1(uint2 R) { return 1 - 3 * (int32_t)((R
 // exact (multiples of 2^-24 below 1).  A hop is taken only across an edge the
 // foot lies certainly beyond, never a boundary edge for a foot in the
 // square; a boundary record would decode to the current triangle anyway.
-__device__ __forceinline__ void lean_hops8(const uint2 *__restrict__ he8, float a0x, float a0y, float a1x, float a1y,
-                                           float a2x, float a2y, int32_t &e0, int32_t &d1, uint32_t &hops,
-                                           uint32_t cap)
-{
-    while (hops < cap) {
-        const float o1 = __fmaf_rn(a1x, a2y, -__fmul_rn(a1y, a2x));    // ~ theta of W0 * den
-        const float o2 = __fmaf_rn(a2x, a0y, -__fmul_rn(a2y, a0x));    // ~ theta of W1 * den
-        const float S = fabsf(a0x) + fabsf(a0y) + fabsf(a1x) + fabsf(a1y) + fabsf(a2x) + fabsf(a2y);
-        if (!(fminf(o1, o2) < -hop_bound(S))) break;
-        const bool c2 = o2 < o1;
+// 8-byte records: the new vertex as an offset from the entered triangle's
+// W0, the slot-0 vertex the state keeps after the crossing.
+struct Rec8 {
+    const uint2 *he8;
+    int32_t e0, d1;
+    __device__ __forceinline__ void hop(bool c2, float a0x, float a0y, float &a2x, float &a2y)
+    {
         const uint2 Q = __ldg(&he8[c2 ? e0 + d1 : e0]);
-        if (c2) { a1x = a2x; a1y = a2y; }
-        else { a0x = a2x; a0y = a2y; }
         a2x = __fadd_rn(__fsub_rn(he8_offx(Q), kHe8Bias), a0x);
         a2y = __fadd_rn(__fsub_rn(he8_offy(Q), kHe8Bias), a0y);
         e0 = he8_e0(Q);
         d1 = he8_d1(Q);
-        ++hops;
     }
+};
+
+__device__ __forceinline__ void lean_hops8(const uint2 *__restrict__ he8, float a0x, float a0y, float a1x, float a1y,
+                                           float a2x, float a2y, int32_t &e0, int32_t &d1, uint32_t &hops,
+                                           uint32_t cap, float L)
+{
+    Rec8 r{he8, e0, d1};
+    lean_walk(r, a0x, a0y, a1x, a1y, a2x, a2y, hops, cap, L);
+    e0 = r.e0;
+    d1 = r.d1;
 }
 
 // The new vertex of a compact record, W0 + d, with W0 (the entered
@@ -778,7 +847,7 @@ __device__ __forceinline__ void step_node(const FastArgs &a, int64_t i, int pi, 
                 ids = false;
                 ++hops;
                 lean_hops8(a.he8, __fsub_rn(p0x, X.h), __fsub_rn(p0y, Y.h), __fsub_rn(p1x, X.h), __fsub_rn(p1y, Y.h),
-                           __fsub_rn(Q.x, X.h), __fsub_rn(Q.y, Y.h), e0, e1, hops, cap);
+                           __fsub_rn(Q.x, X.h), __fsub_rn(Q.y, Y.h), e0, e1, hops, cap, a.hop_L);
             }
         } else if (k >= 0) {
             const float4 R = __ldg(&a.he[tq.x + k]);
@@ -874,7 +943,7 @@ __device__ __forceinline__ void step_node(const FastArgs &a, int64_t i, int pi, 
             ids = false;
             ++hops;
             lean_hops8(a.he8, __fsub_rn(P0.x, X.h), __fsub_rn(P0.y, Y.h), __fsub_rn(P1.x, X.h), __fsub_rn(P1.y, Y.h),
-                       __fsub_rn(Q.x, X.h), __fsub_rn(Q.y, Y.h), e0, e1, hops, cap);
+                       __fsub_rn(Q.x, X.h), __fsub_rn(Q.y, Y.h), e0, e1, hops, cap, a.hop_L);
             continue;
         }
         const float4 R = __ldg(&a.he[3 * j + k]);
