@@ -1,6 +1,7 @@
 // api_device.cu -- entry points of sl.h that touch the device: upload,
 // sl_step, sl_run (CUDA graph of the time loop), sl_run_host, T^0 import /
 // export, deferred status, counters, renumbering and destruction.
+#include <algorithm>
 #include <cmath>
 #include <cstring>
 #include <string>
@@ -109,7 +110,7 @@ void free_device(sl_mesh *m)
 {
     release_l2_window(m);
     DeviceMesh &d = m->d;
-    void *ptrs[] = {d.xy, d.tv[0], d.tv[1], d.tv[2], d.tn[0], d.tn[1], d.tn[2], d.t0, d.t0_init, d.t0v, d.node_off,
+    void *ptrs[] = {d.xy, d.tv[0], d.tv[1], d.tv[2], d.tn[0], d.tn[1], d.tn[2], d.t0, d.t0_init, d.t0v, d.node_off, d.chunk_prob,
                     d.status, d.stats, d.probs, d.fprobs, d.xyq, d.xyh, d.g1, d.g2, d.tparams, d.dfa, d.dfb, d.he, d.he8, d.grid_t0v, d.tree_order, d.tree_parent, d.queue, d.queue_count,
                     m->host_v, m->host_v2};
     for (void *p : ptrs)
@@ -201,6 +202,21 @@ static sl_status upload_arrays(sl_mesh *m)
     SL_CUDA(cudaMemcpy(d.t0, m->t0.data(), sizeof(int32_t) * N, cudaMemcpyHostToDevice));
     SL_CUDA(cudaMemcpy(d.t0_init, m->t0_init.data(), sizeof(int32_t) * N, cudaMemcpyHostToDevice));
     SL_CUDA(cudaMemcpy(d.node_off, m->node_off.data(), sizeof(int64_t) * (m->n_problems + 1), cudaMemcpyHostToDevice));
+    if (m->n_problems > 1) {
+        // the problems of each chunk of 128 nodes (chunk_problem), one sweep
+        const int64_t nc = (N + 127) >> 7;
+        std::vector<int2> cp(nc);
+        int32_t p = 0;
+        for (int64_t c = 0; c < nc; ++c) {
+            const int64_t first = c << 7, last = std::min(N, first + 128) - 1;
+            while (m->node_off[p + 1] <= first) ++p;
+            int32_t q = p;
+            while (m->node_off[q + 1] <= last) ++q;
+            cp[c] = make_int2(p, q);
+        }
+        if (!d.chunk_prob) SL_CUDA(cudaMalloc(&d.chunk_prob, sizeof(int2) * nc));
+        SL_CUDA(cudaMemcpy(d.chunk_prob, cp.data(), sizeof(int2) * nc, cudaMemcpyHostToDevice));
+    }
     launch_fill_t0v(d.t0, d.tv[0], d.tv[1], d.tv[2], (int4 *)d.t0v, N, 0);
     SL_CUDA(cudaGetLastError());
     SL_CUDA(cudaDeviceSynchronize());
@@ -380,6 +396,7 @@ FastArgs make_fast_args(const sl_mesh *m, const FastProb *fp, const void *vin, v
         a.single = 1;
     }
     a.node_off = m->d.node_off;
+    a.chunk_prob = (const int2 *)m->d.chunk_prob;
     a.nprob = m->n_problems;
     a.walk_cap = m->opt_walk_cap > 0 ? m->opt_walk_cap : default_walk_cap(m);
     a.N = m->N;

@@ -40,6 +40,8 @@ struct DeviceMesh {
     int32_t *tree_order = nullptr;    // strategy (c): nodes by spanning-tree level (N)
     int32_t *tree_parent = nullptr;   // strategy (c): parent of every node (N; the root its own)
     int64_t *node_off = nullptr;      // n_problems + 1
+    void *chunk_prob = nullptr;       // int2 per 128 nodes: problems of the first and last node (more
+                                      // than one problem)
     uint32_t *status = nullptr;       // [0] = OR of (1 << sl_status); others reserved
     unsigned long long *stats = nullptr;   // 8 counters (sl_stats order)
     void *probs = nullptr;            // per-problem step data (device)

@@ -140,24 +140,17 @@ __device__ __forceinline__ int problem_of(const int64_t *node_off, int nprob, in
     return lo;
 }
 
-// Problem of node i for a block of consecutive nodes: thread 0 finds the
-// problems of the block's first and last nodes (problems are contiguous node
-// ranges), every thread then searches only between them.  All threads of
-// the block must call it (it synchronises).
-__device__ __forceinline__ int block_problem(const int64_t *node_off, int nprob, int64_t N, int64_t i)
+// Problem of node i < N from the per-chunk table (kChunkShift: chunks of 128
+// consecutive nodes; for each, the problems of its first and last node, see
+// chunk_problem_table), searching only in a chunk that spans problems.  A
+// warp's lanes read the same entry.
+constexpr int kChunkShift = 7;
+
+__device__ __forceinline__ int chunk_problem(const int2 *chunk_prob, const int64_t *node_off, int64_t i)
 {
-    if (nprob == 1) return 0;
-    __shared__ int s_range[2];
-    if (threadIdx.x == 0) {
-        const int64_t first = (int64_t)blockIdx.x * blockDim.x;
-        const int64_t last = first + blockDim.x - 1 < N ? first + blockDim.x - 1 : N - 1;
-        s_range[0] = problem_of(node_off, nprob, first < N ? first : N - 1);
-        s_range[1] = problem_of(node_off, nprob, last);
-    }
-    __syncthreads();
-    const int p0 = s_range[0], p1 = s_range[1];
-    if (p0 == p1 || i >= N) return p0;
-    return p0 + problem_of(node_off + p0, p1 - p0 + 1, i);
+    const int2 c = __ldg(&chunk_prob[i >> kChunkShift]);
+    if (c.x == c.y) return c.x;
+    return c.x + problem_of(node_off + c.x, c.y - c.x + 1, i);
 }
 
 }  // namespace sl

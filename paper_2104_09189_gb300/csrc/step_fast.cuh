@@ -56,6 +56,8 @@ struct FastArgs {
     FastProb prob0;               // single: a copy of probs[0] (kernel parameter space)
     int32_t single;               // one problem, prob0 valid
     const int64_t *node_off;
+    const int2 *chunk_prob;       // more than one problem: per 128 nodes, the first and last node's
+                                  // problem (chunk_problem); else NULL
     int32_t nprob;
     int32_t walk_cap;
     int64_t N;

@@ -101,9 +101,10 @@ __global__ void __launch_bounds__(kBlock, kMinBlocks) k_step_fast_f32(FastArgs a
     const bool active = kExt ? i >= 0 : i < a.N;
     uint32_t hops = 0, exact_tests = 0, clipped_cnt = 0, fallback_cnt = 0, limit_cnt = 0, fp64_tests = 0;
     uint32_t excluded_cnt = 0;
-    // a spanning-tree level mixes problems within a block: search per node
-    const int pi = kExt && a.order ? (active && a.nprob > 1 ? problem_of(a.node_off, a.nprob, i) : 0)
-                                   : block_problem(a.node_off, a.nprob, a.N, i);
+    // the node's problem: the chunk table, or a search per node in a spanning-tree
+    // level (a level mixes problems)
+    const int pi = !active || a.nprob == 1 ? 0
+                   : (kExt && a.order ? problem_of(a.node_off, a.nprob, i) : chunk_problem(a.chunk_prob, a.node_off, i));
     pdl_launch_dependents();
     pdl_wait();
     if (active) {

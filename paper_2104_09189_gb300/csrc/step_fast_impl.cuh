@@ -1004,9 +1004,10 @@ __global__ void __launch_bounds__(kBlock, kMinBlocks) k_step_fast_df(FastArgs a)
     pdl_launch_dependents();
     pdl_wait();
     NodeCounters c;
-    // a spanning-tree level mixes problems within a block: search per node
-    const int pi = kExt && a.order ? (active && a.nprob > 1 ? problem_of(a.node_off, a.nprob, i) : 0)
-                                   : block_problem(a.node_off, a.nprob, a.N, i);
+    // the node's problem: the chunk table, or a search per node in a spanning-tree
+    // level (a level mixes problems)
+    const int pi = !active || a.nprob == 1 ? 0
+                   : (kExt && a.order ? problem_of(a.node_off, a.nprob, i) : chunk_problem(a.chunk_prob, a.node_off, i));
     if (active) step_node<kDebug, kExt, kCompact>(a, i, pi, c);
     if (kStats) warp_stats(a.stats, active, c.hops, c.exact, c.clipped, c.fallback, c.limit, c.filter2, c.excluded);
 }
@@ -1127,7 +1128,7 @@ __global__ void __launch_bounds__(kBlock, kMinBlocks) k_settle_df(FastArgs a)
     pdl_launch_dependents();
     pdl_wait();
     NodeCounters c;
-    const int pi = kKind < 0 ? block_problem(a.node_off, a.nprob, a.N, i) : 0;
+    const int pi = kKind < 0 && active && a.nprob > 1 ? chunk_problem(a.chunk_prob, a.node_off, i) : 0;
     // the next step's counter (its previous user, the finish pass of the
     // step before, has completed)
     if (a.queue_next && blockIdx.x == 0 && threadIdx.x == 0) *a.queue_next = 0;
@@ -1157,7 +1158,7 @@ __global__ void __launch_bounds__(128, 8) k_finish_df(FastArgs a)
     for (uint32_t q = blockIdx.x * blockDim.x + threadIdx.x; q < count; q += gridDim.x * blockDim.x) {
         NodeCounters c;
         const int64_t i = a.queue[q];
-        step_node<kDebug, false, kCompact>(a, i, a.nprob == 1 ? 0 : problem_of(a.node_off, a.nprob, i), c);
+        step_node<kDebug, false, kCompact>(a, i, a.nprob == 1 ? 0 : chunk_problem(a.chunk_prob, a.node_off, i), c);
         tot.hops += c.hops;
         hmax = c.hops > hmax ? c.hops : hmax;
         tot.exact += c.exact;
