@@ -32,7 +32,10 @@
  *
  * Floating point: compiled with -ffp-contract=off, so every operation is one
  * IEEE double operation in the order written.  Fields use the C library's
- * sin/cos/sqrt.
+ * sin/cos/sqrt; sin(k pi x) and cos(k pi x) reduce k x modulo 2 exactly
+ * first (sincos_pi), so that they vanish exactly where the definition makes
+ * them vanish: the swirl and stream-function fields are then exactly tangent
+ * to the sides of the square, as their definitions make them.
  *
  * Exact orientation: a double-precision evaluation with a forward error
  * bound, and, when the bound cannot certify the sign, an exact evaluation
@@ -52,6 +55,29 @@
 /* ------------------------------------------------------------------ */
 
 static const double PI = 3.14159265358979323846;
+
+
+/* sin(pi v) and cos(pi v) with the argument reduced exactly: r = v - 2
+ * round(v / 2) is exact (for v = 2n + r with n != 0, v and 2n are within a
+ * factor of two), so at integer and half-integer v the values are the exact
+ * 0 and +-1 of the definition; elsewhere the library's sin and cos of pi r. */
+static void sincos_pi(double v, double *s, double *c)
+{
+    const double r = v - 2.0 * nearbyint(0.5 * v);
+    if (r == 0.0) {
+        *s = 0.0;
+        *c = 1.0;
+    } else if (r == 1.0 || r == -1.0) {
+        *s = 0.0;
+        *c = -1.0;
+    } else if (r == 0.5 || r == -0.5) {
+        *s = r > 0.0 ? 1.0 : -1.0;
+        *c = 0.0;
+    } else {
+        *s = sin(PI * r);
+        *c = cos(PI * r);
+    }
+}
 
 void orc_field(int kind, const double *p, double x, double y, double t,
                double *fx, double *fy)
@@ -74,9 +100,13 @@ void orc_field(int kind, const double *p, double x, double y, double t,
     case ORC_FIELD_SWIRL: {
         /* cos(pi t / T) (sin^2(pi x) sin(2 pi y), -sin^2(pi y) sin(2 pi x)) */
         double c = cos(PI * t / p[0]);
-        double sx = sin(PI * x), sy = sin(PI * y);
-        *fx = c * (sx * sx) * sin(2.0 * PI * y);
-        *fy = -c * (sy * sy) * sin(2.0 * PI * x);
+        double sx, cx, sy, cy, s2x, s2y;
+        sincos_pi(x, &sx, &cx);
+        sincos_pi(y, &sy, &cy);
+        sincos_pi(2.0 * x, &s2x, &cx);
+        sincos_pi(2.0 * y, &s2y, &cy);
+        *fx = c * (sx * sx) * s2y;
+        *fy = -c * (sy * sy) * s2x;
         return;
     }
     case ORC_FIELD_FOURIER8: {
@@ -86,8 +116,11 @@ void orc_field(int kind, const double *p, double x, double y, double t,
         for (int m = 0; m < 8; ++m) {
             double k = p[4 * m], l = p[4 * m + 1], a = p[4 * m + 2], phi = p[4 * m + 3];
             double am = a * cos(2.0 * PI * t + phi);
-            gx += am * sin(k * PI * x) * (l * PI) * cos(l * PI * y);
-            gy -= am * (k * PI) * cos(k * PI * x) * sin(l * PI * y);
+            double skx, ckx, sly, cly;
+            sincos_pi(k * x, &skx, &ckx);
+            sincos_pi(l * y, &sly, &cly);
+            gx += am * skx * (l * PI) * cly;
+            gy -= am * (k * PI) * ckx * sly;
         }
         *fx = gx;
         *fy = gy;

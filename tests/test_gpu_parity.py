@@ -362,6 +362,51 @@ def test_batched_problems_match_single_runs(kernel):
         assert np.abs(seg - want).max() <= 1e-12 * np.abs(want).max()
 
 
+@pytest.mark.parametrize("form", ["fp64", "fp64_split", "fp32"])
+def test_many_tiny_problems_match_single_runs(form):
+    """A batch of 40 problems of 9 to 100 nodes, so that a block of nodes and
+    a chunk of the problem table span several problems: every problem's
+    values after 3 steps are those of the same problem run alone (its field
+    constants found through the table; a wrong problem would change them
+    entirely), and within the precision's tolerance of the oracle, both
+    relative to the problem's max |V^0|.  (Not bitwise: the initial start
+    triangle hashes the global node index, reading c5, so a foot on an edge
+    may end its walk in the other triangle, which rounds differently.)"""
+    import torch
+    prec = sl.SL_FP32 if form == "fp32" else sl.SL_FP64
+    probs = si.batch_config(40, seed=11, nmin=9, nmax=100, steps=3)
+    meshes = [(p.mesh.xy, p.mesh.tri) for p in probs]
+    no, to, xy, tri = sl.pack_meshes(meshes)
+    vt = torch.float32 if prec == sl.SL_FP32 else torch.float64
+
+    def run(meshes_, problems, v0):
+        n_, t_, x_, r_ = sl.pack_meshes(meshes_)
+        h = sl.sl_mesh_create(n_, t_, x_, r_, precision=prec)
+        if form == "fp64_split":
+            sl.sl_mesh_set_option(h, sl.SL_OPT_SPLIT, 1)
+        pr = sl.problems([(p.field.kind, p.dt, p.field.packed()) for p in problems])
+        v = torch.tensor(v0, dtype=vt, device="cuda:0")
+        w = torch.empty_like(v)
+        sl.sl_run(h, pr, 0, 3, v, w)
+        out = v.double().cpu().numpy()
+        sl.sl_mesh_destroy(h)
+        return out
+
+    got = run(meshes, probs, np.concatenate([p.v0 for p in probs]))
+    assert int(np.diff(no).max()) <= 100 and len(probs) == 40
+    # the batch tolerance scales with each problem's max |V^0| (a step of
+    # several domain widths decays some of these values a billionfold)
+    same, orc = (1e-13, 1e-12) if prec == sl.SL_FP64 else (1e-6, 1e-5)
+    for k, p in enumerate(probs):
+        scale = np.abs(p.v0).max()
+        alone = run([meshes[k]], [p], p.v0)
+        seg = got[no[k]:no[k + 1]]
+        assert np.abs(seg - alone).max() <= same * scale, k
+        om = oracle.OracleMesh(p.mesh.xy, p.mesh.tri)
+        want = om.run(p.field.kind, p.field.packed(), p.dt, 0, 3, p.v0)
+        assert np.abs(seg - want).max() <= orc * scale, k
+
+
 def test_bad_step_arguments():
     prob = si.config("C1", M=8)
     g = DeviceRun(prob.mesh, prob.field, prob.dt)
