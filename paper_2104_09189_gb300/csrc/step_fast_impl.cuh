@@ -528,7 +528,7 @@ __device__ __forceinline__ bool foot_pair(const FastArgs &a, int64_t i, const Fa
 // + j L and S at most three times that.  A test that fails against the run's
 // bound is taken again with the triangle's own, so the hops, where the loop
 // stops and every result are those of a test with S at every hop, at about a
-// third fewer instructions per hop.  Short walks, most of a steady step's,
+// quarter fewer instructions per hop.  Short walks, most of a steady step's,
 // keep the bound per hop and skip the setting up of runs.
 constexpr uint32_t kLeanPlain = 4;
 constexpr uint32_t kLeanRun = 16;
