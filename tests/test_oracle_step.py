@@ -71,6 +71,36 @@ def test_fourier_field_is_a_stream_function_gradient():
             assert oracle.field(si.FIELD_FOURIER8, p, s, side, 0.3)[1] == 0.0
 
 
+def test_trigonometric_fields_match_their_formulas():
+    """The swirl and stream-function fields against their formulas written
+    out in numpy (np.sin of the product with pi): within a few ulps of the
+    field's size at interior points, so the exact argument reduction of the
+    oracle's sine changes no value beyond rounding; exactly zero normal
+    component on all four sides."""
+    rnd = np.random.default_rng(7)
+    sw = si.swirl_field()
+    fo = si.fourier8_field(9)
+    p = fo.packed()
+    k, l, a, phi = p[0:32:4], p[1:32:4], p[2:32:4], p[3:32:4]
+    for x, y, t in rnd.random((200, 3)):
+        c = np.cos(np.pi * t / sw.packed()[0])
+        fx = c * np.sin(np.pi * x) ** 2 * np.sin(2 * np.pi * y)
+        fy = -c * np.sin(np.pi * y) ** 2 * np.sin(2 * np.pi * x)
+        gx, gy = oracle.field(sw.kind, sw.packed(), x, y, t)
+        assert abs(gx - fx) <= 1e-15 and abs(gy - fy) <= 1e-15
+        am = a * np.cos(2 * np.pi * t + phi)
+        fx = np.sum(am * np.sin(k * np.pi * x) * (l * np.pi) * np.cos(l * np.pi * y))
+        fy = -np.sum(am * (k * np.pi) * np.cos(k * np.pi * x) * np.sin(l * np.pi * y))
+        gx, gy = oracle.field(fo.kind, p, x, y, t)
+        scale = np.sum(np.abs(a) * (k + l) * np.pi)
+        assert abs(gx - fx) <= 1e-14 * scale and abs(gy - fy) <= 1e-14 * scale
+    for s in rnd.random(20):
+        for side in (0.0, 1.0):
+            for fld in (sw, fo):
+                assert oracle.field(fld.kind, fld.packed(), side, s, 0.3)[0] == 0.0
+                assert oracle.field(fld.kind, fld.packed(), s, side, 0.3)[1] == 0.0
+
+
 def _mesh(M=24, seed=4):
     m = si.grid_mesh(M, 0.25, seed)
     return m, oracle.OracleMesh(m.xy, m.tri)
